@@ -1,0 +1,489 @@
+// gic_analyze.cu -- A2: device-side analysis of a symmetric CSR pattern.
+//
+// From A's CSR (sorted columns, stored diagonal, symmetric pattern) build:
+//   * L = tril(A): a prefix of every row of A, so L entry p of row i is A
+//     entry rowptr[i] + (p - Lrowptr[i]);
+//   * U = L^T: by symmetry row j of U is the suffix of A's row j that starts
+//     at the diagonal; tperm maps every U entry (j,i) to L entry (i,j);
+//   * groups: maximal runs (cut every GMAX rows) of consecutive rows with
+//     identical column sets. Inside a group the diagonal block is dense and
+//     all rows share their columns outside it, so one warp solves a whole
+//     group (for hex elasticity a group is the 3 dofs of a node);
+//   * row levels of the lower-triangular dependency DAG.
+// Everything runs on the device; no host pass over the rows.
+#include <limits.h>
+#include <stdio.h>
+#include <stdlib.h>
+
+#include "gic_internal.cuh"
+
+namespace gic {
+
+// ---------------------------------------------------------------- scans
+// Exclusive prefix scan of int64 values (op = sum or max) in three passes.
+constexpr int SCAN_BLOCK = 1024;
+
+template <bool MAX>
+__device__ __forceinline__ long long scan_op(long long a, long long b) { return MAX ? (a > b ? a : b) : a + b; }
+
+template <bool MAX>
+__device__ long long block_inclusive_scan(long long v, long long *sh)
+{
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+        long long t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v = scan_op<MAX>(v, t);
+    }
+    if (lane == 31) sh[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        long long w = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : (MAX ? LLONG_MIN : 0);
+        for (int o = 1; o < 32; o <<= 1) {
+            long long t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w = scan_op<MAX>(w, t);
+        }
+        sh[lane] = w;
+    }
+    __syncthreads();
+    if (wid > 0) v = scan_op<MAX>(v, sh[wid - 1]);
+    __syncthreads();
+    return v;
+}
+
+// in: int32 values; inclusive scan written to out64; block totals to bsum.
+template <bool MAX>
+__global__ void k_scan_blocks(const int32_t *in, int64_t n, long long *out64, long long *bsum)
+{
+    __shared__ long long sh[32];
+    int64_t i = (int64_t)blockIdx.x * SCAN_BLOCK + threadIdx.x;
+    long long v = (i < n) ? (long long)in[i] : (MAX ? LLONG_MIN : 0);
+    long long s = block_inclusive_scan<MAX>(v, sh);
+    if (i < n) out64[i] = s;
+    if (threadIdx.x == SCAN_BLOCK - 1) bsum[blockIdx.x] = s;
+}
+
+// exclusive scan of the block totals in place (single block, any count)
+template <bool MAX>
+__global__ void k_scan_totals(long long *bsum, int64_t nb, long long *total)
+{
+    __shared__ long long sh[32];
+    long long carry = MAX ? LLONG_MIN : 0;
+    for (int64_t base = 0; base < nb; base += SCAN_BLOCK) {
+        int64_t i = base + threadIdx.x;
+        long long v = (i < nb) ? bsum[i] : (MAX ? LLONG_MIN : 0);
+        long long s = block_inclusive_scan<MAX>(v, sh);
+        long long excl = __shfl_up_sync(0xffffffffu, s, 1);
+        // exclusive value of element i within this chunk
+        __shared__ long long last;
+        if (threadIdx.x == SCAN_BLOCK - 1) last = s;
+        long long prev_lane = excl;
+        if ((threadIdx.x & 31) == 0) prev_lane = (threadIdx.x == 0) ? (MAX ? LLONG_MIN : 0) : sh[(threadIdx.x >> 5) - 1];
+        __syncthreads();
+        if (i < nb) bsum[i] = scan_op<MAX>(carry, prev_lane);
+        carry = scan_op<MAX>(carry, last);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+// out[i] = exclusive value at i (out has n+1 entries for sum scans)
+template <bool MAX>
+__global__ void k_scan_finish(const int32_t *in, int64_t n, const long long *incl, const long long *bsum,
+                              int32_t *out, int with_total, const long long *total)
+{
+    int64_t i = (int64_t)blockIdx.x * SCAN_BLOCK + threadIdx.x;
+    if (i < n) {
+        long long v = scan_op<MAX>(bsum[blockIdx.x], incl[i]);
+        if (MAX) {
+            out[i] = (int32_t)v; // inclusive max
+        } else {
+            out[i] = (int32_t)(v - in[i]); // exclusive sum
+        }
+    }
+    if (with_total && i == 0) out[n] = (int32_t)*total;
+}
+
+// Host wrapper. MAX = false: out[0..n] exclusive sums, *total (host) = sum.
+// MAX = true: out[0..n) inclusive running maxima.
+template <bool MAX>
+static int scan_i32(gic_handle *h, const int32_t *in, int64_t n, int32_t *out, long long *total_host)
+{
+    int64_t nb = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;
+    if (nb == 0) nb = 1;
+    long long *tmp = nullptr;
+    GIC_CUDA_TRY(cudaMalloc(&tmp, sizeof(long long) * (size_t)(n + nb + 1)));
+    long long *incl = tmp, *bsum = tmp + n, *total = tmp + n + nb;
+    k_scan_blocks<MAX><<<(unsigned)nb, SCAN_BLOCK, 0, h->stream>>>(in, n, incl, bsum);
+    k_scan_totals<MAX><<<1, SCAN_BLOCK, 0, h->stream>>>(bsum, nb, total);
+    k_scan_finish<MAX><<<(unsigned)nb, SCAN_BLOCK, 0, h->stream>>>(in, n, incl, bsum, out, MAX ? 0 : 1, total);
+    cudaError_t e = cudaGetLastError();
+    long long t = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&t, total, sizeof t, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e, "scan", __FILE__, __LINE__);
+        return GIC_ERR_CUDA;
+    }
+    if (total_host) *total_host = t;
+    return GIC_OK;
+}
+
+// ---------------------------------------------------------------- checks
+// Per row: bounds, strictly increasing columns, stored diagonal; Lcnt[i] =
+// number of entries with column <= i; same[i] = row i has the same columns
+// as row i-1.
+__global__ void k_validate(int64_t n, int64_t nnz, const int32_t *rowptr, const int32_t *col, int32_t *Lcnt,
+                           int32_t *same, unsigned *err)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t a = rowptr[i], b = rowptr[i + 1];
+        if (i == 0 && a != 0) atomicOr(err, 4u);
+        if (i == n - 1 && (int64_t)b != nnz) atomicOr(err, 4u);
+        if (b < a || a < 0 || (int64_t)b > nnz) {
+            atomicOr(err, 4u);
+            Lcnt[i] = 0;
+            same[i] = 0;
+            continue;
+        }
+        int cnt = 0, diag = 0, prev = -1;
+        for (int32_t p = a; p < b; ++p) {
+            int32_t c = col[p];
+            if (c <= prev || c < 0 || c >= n) atomicOr(err, 8u);
+            if (c <= i) cnt++;
+            if (c == i) diag = 1;
+            prev = c;
+        }
+        if (!diag) atomicOr(err, 16u);
+        Lcnt[i] = cnt;
+        int sm = 0;
+        if (i > 0) {
+            int32_t a0 = rowptr[i - 1], b0 = rowptr[i];
+            if (a0 >= 0 && b0 >= a0 && b0 - a0 == b - a) {
+                sm = 1;
+                for (int32_t k = 0; k < b - a; ++k)
+                    if (col[a0 + k] != col[a + k]) { sm = 0; break; }
+            }
+        }
+        same[i] = sm;
+    }
+}
+
+__device__ __forceinline__ int32_t find_col(const int32_t *col, int32_t lo, int32_t hi, int32_t key)
+{
+    // first position in [lo,hi) with col >= key
+    while (lo < hi) {
+        int32_t mid = lo + ((hi - lo) >> 1);
+        if (col[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Symmetry: every (i,j) has a stored (j,i).
+__global__ void k_symcheck(int64_t n, const int32_t *rowptr, const int32_t *col, unsigned *err)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+            int32_t j = col[p];
+            if (j < 0 || j >= n) continue;
+            int32_t q = find_col(col, rowptr[j], rowptr[j + 1], (int32_t)i);
+            if (q >= rowptr[j + 1] || col[q] != i) { atomicOr(err, 32u); return; }
+        }
+    }
+}
+
+__global__ void k_fill_L(int64_t n, const int32_t *rowptr, const int32_t *col, const int32_t *Lrowptr, int32_t *Lcol,
+                         int32_t *Ucnt)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t a = rowptr[i], lb = Lrowptr[i], lc = Lrowptr[i + 1] - lb;
+        for (int32_t k = 0; k < lc; ++k) Lcol[lb + k] = col[a + k];
+        Ucnt[i] = rowptr[i + 1] - a - lc + 1;
+    }
+}
+
+__global__ void k_fill_U(int64_t n, const int32_t *rowptr, const int32_t *col, const int32_t *Lrowptr,
+                         const int32_t *Urowptr, int32_t *Ucol, int32_t *tperm)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        int32_t ub = Urowptr[j], uc = Urowptr[j + 1] - ub;
+        int32_t d = rowptr[j] + (Lrowptr[j + 1] - Lrowptr[j]) - 1; // diagonal of row j in A
+        for (int32_t k = 0; k < uc; ++k) {
+            int32_t i = col[d + k]; // U entry (j, i), i >= j  <=>  L entry (i, j)
+            Ucol[ub + k] = i;
+            int32_t q = find_col(col, rowptr[i], rowptr[i + 1], (int32_t)j);
+            tperm[ub + k] = Lrowptr[i] + (q - rowptr[i]);
+        }
+    }
+}
+
+// key[i] = i where a new run of identical rows begins, else -1
+__global__ void k_run_keys(int64_t n, const int32_t *same, int32_t *key)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        key[i] = same[i] ? -1 : (int32_t)i;
+}
+
+// group starts: run start, or every GMAX rows inside a run
+__global__ void k_group_flags(int64_t n, const int32_t *runstart, int32_t *gflag)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        gflag[i] = ((i - runstart[i]) % GMAX) == 0;
+}
+
+__global__ void k_group_starts(int64_t n, const int32_t *gflag, const int32_t *gid, int32_t *grp, int32_t ngroups)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (gflag[i]) grp[gid[i]] = (int32_t)i;
+    if (blockIdx.x == 0 && threadIdx.x == 0) grp[ngroups] = (int32_t)n;
+}
+
+// Per-group maxima: external lower / upper counts and group size.
+__global__ void k_group_stats(int32_t ngroups, const int32_t *grp, const int32_t *Lrowptr, const int32_t *Urowptr,
+                              int32_t *stats)
+{
+    int mL = 0, mU = 0, mG = 0;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += (int64_t)gridDim.x * blockDim.x) {
+        int32_t s = grp[g], e = grp[g + 1] - 1;
+        int eL = Lrowptr[s + 1] - Lrowptr[s] - 1;
+        int eU = Urowptr[e + 1] - Urowptr[e] - 1;
+        mL = max(mL, eL);
+        mU = max(mU, eU);
+        mG = max(mG, e - s + 1);
+    }
+    atomicMax(&stats[0], mL);
+    atomicMax(&stats[1], mU);
+    atomicMax(&stats[2], mG);
+}
+
+// Row levels, one warp per group, sync-free: level[] starts at -1 and every
+// row's level is written once; a warp waits (bounded) for the levels of its
+// group's external lower columns. Groups are taken in round-robin order by a
+// co-resident grid, so the smallest unfinished group always progresses.
+__global__ void k_levels(int32_t ngroups, const int32_t *grp, const int32_t *Lrowptr, const int32_t *Lcol,
+                         int32_t *level, int32_t *maxlev, unsigned *err)
+{
+    int lane = threadIdx.x & 31;
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int mx_all = 0;
+    for (int64_t g = w; g < ngroups; g += nw) {
+        int32_t s = grp[g], e = grp[g + 1] - 1;
+        int32_t b0 = Lrowptr[s];
+        int32_t m = Lrowptr[s + 1] - b0 - 1;
+        int mx = -1;
+        for (int32_t k = lane; k < m; k += 32) {
+            int32_t j = Lcol[b0 + k];
+            int v = ld_acquire_i32(level + j);
+            long long it = 0;
+            while (v < 0 && it < SPIN_LIMIT) {
+                if (it > 32) __nanosleep(64);
+                v = ld_acquire_i32(level + j);
+                ++it;
+                if ((it & 1023) == 0 && *((volatile unsigned *)err) != 0u) break;
+            }
+            if (v < 0) { atomicOr(err, ERR_TIMEOUT); v = 0; }
+            mx = max(mx, v);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane <= e - s) st_release_i32(level + s + lane, mx + 1 + lane);
+        mx_all = max(mx_all, mx + 1 + (e - s));
+    }
+    if (lane == 0) atomicMax(maxlev, mx_all);
+}
+
+static const int T_ROWS = 256;
+
+static unsigned grid_rows(gic_handle *h, int64_t n)
+{
+    int64_t b = (n + T_ROWS - 1) / T_ROWS;
+    int64_t cap = (int64_t)h->num_sms * 16;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+}  // namespace gic
+
+namespace gic {
+
+int launch_persistent(gic_handle *h, const void *fn, int block, size_t smem, int64_t warps_needed, void **args)
+{
+    int per_sm = 0;
+    GIC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem));
+    if (per_sm < 1) return GIC_ERR_UNSUPPORTED;
+    int64_t grid = (int64_t)per_sm * h->num_sms;
+    int64_t need = (warps_needed * 32 + block - 1) / block;
+    if (need < 1) need = 1;
+    if (grid > need) grid = need;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    GIC_CUDA_TRY(cudaLaunchKernelExC(&cfg, fn, args));
+    return GIC_OK;
+}
+
+}  // namespace gic
+
+using namespace gic;
+
+static void free_pattern(Pattern &p)
+{
+    cudaFree(p.Lrowptr);
+    cudaFree(p.Lcol);
+    cudaFree(p.Urowptr);
+    cudaFree(p.Ucol);
+    cudaFree(p.tperm);
+    cudaFree(p.grp);
+    cudaFree(p.level);
+    p = Pattern();
+}
+
+static int analyze_impl(gic_handle *h, int64_t n, int64_t nnz, const int32_t *rowptr, const int32_t *col, Pattern &P)
+{
+    P.n = n;
+    P.nnzA = nnz;
+    P.rowptr = rowptr;
+    P.col = col;
+    P.device = h->device;
+    int32_t *tmp = nullptr; // Lcnt | same | Ucnt | key | runstart | gflag | gid | stats(4)
+    GIC_CUDA_TRY(cudaMalloc(&tmp, sizeof(int32_t) * (size_t)(7 * (n + 1) + 8)));
+    int32_t *Lcnt = tmp, *same = tmp + (n + 1), *Ucnt = tmp + 2 * (n + 1), *key = tmp + 3 * (n + 1);
+    int32_t *runstart = tmp + 4 * (n + 1), *gflag = tmp + 5 * (n + 1), *gid = tmp + 6 * (n + 1);
+    int32_t *stats = tmp + 7 * (n + 1);
+    int rc = GIC_OK;
+    long long tot = 0;
+    unsigned flags = 0;
+    unsigned gr = grid_rows(h, n);
+#define STEP(x) do { rc = (x); if (rc != GIC_OK) goto out; } while (0)
+#define CUDA_STEP(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { set_last_cuda_error(e_, #x, __FILE__, __LINE__); rc = GIC_ERR_CUDA; goto out; } } while (0)
+    CUDA_STEP(cudaMemsetAsync(h->dev_err, 0, sizeof(unsigned), h->stream));
+    CUDA_STEP(cudaMemsetAsync(stats, 0, sizeof(int32_t) * 8, h->stream));
+    k_validate<<<gr, T_ROWS, 0, h->stream>>>(n, nnz, rowptr, col, Lcnt, same, h->dev_err);
+    CUDA_STEP(cudaGetLastError());
+    STEP(read_and_clear_dev_err(h, &flags));
+    if (flags) { rc = GIC_ERR_INVALID_ARG; goto out; }
+    // only once every row is known to be in bounds
+    k_symcheck<<<gr, T_ROWS, 0, h->stream>>>(n, rowptr, col, h->dev_err);
+    CUDA_STEP(cudaGetLastError());
+    STEP(read_and_clear_dev_err(h, &flags));
+    if (flags) { rc = GIC_ERR_INVALID_ARG; goto out; }
+
+    CUDA_STEP(cudaMalloc(&P.Lrowptr, sizeof(int32_t) * (size_t)(n + 1)));
+    STEP(scan_i32<false>(h, Lcnt, n, P.Lrowptr, &tot));
+    P.nnzL = tot;
+    CUDA_STEP(cudaMalloc(&P.Lcol, sizeof(int32_t) * (size_t)(P.nnzL > 0 ? P.nnzL : 1)));
+    k_fill_L<<<gr, T_ROWS, 0, h->stream>>>(n, rowptr, col, P.Lrowptr, P.Lcol, Ucnt);
+    CUDA_STEP(cudaGetLastError());
+    CUDA_STEP(cudaMalloc(&P.Urowptr, sizeof(int32_t) * (size_t)(n + 1)));
+    STEP(scan_i32<false>(h, Ucnt, n, P.Urowptr, &tot));
+    if (tot != P.nnzL) { rc = GIC_ERR_INVALID_ARG; goto out; }
+    CUDA_STEP(cudaMalloc(&P.Ucol, sizeof(int32_t) * (size_t)(P.nnzL > 0 ? P.nnzL : 1)));
+    CUDA_STEP(cudaMalloc(&P.tperm, sizeof(int32_t) * (size_t)(P.nnzL > 0 ? P.nnzL : 1)));
+    k_fill_U<<<gr, T_ROWS, 0, h->stream>>>(n, rowptr, col, P.Lrowptr, P.Urowptr, P.Ucol, P.tperm);
+    CUDA_STEP(cudaGetLastError());
+
+    k_run_keys<<<gr, T_ROWS, 0, h->stream>>>(n, same, key);
+    STEP(scan_i32<true>(h, key, n, runstart, nullptr));
+    k_group_flags<<<gr, T_ROWS, 0, h->stream>>>(n, runstart, gflag);
+    STEP(scan_i32<false>(h, gflag, n, gid, &tot));
+    P.ngroups = (int32_t)tot;
+    CUDA_STEP(cudaMalloc(&P.grp, sizeof(int32_t) * (size_t)(P.ngroups + 1)));
+    k_group_starts<<<gr, T_ROWS, 0, h->stream>>>(n, gflag, gid, P.grp, P.ngroups);
+    k_group_stats<<<grid_rows(h, P.ngroups), T_ROWS, 0, h->stream>>>(P.ngroups, P.grp, P.Lrowptr, P.Urowptr, stats);
+    CUDA_STEP(cudaGetLastError());
+
+    CUDA_STEP(cudaMalloc(&P.level, sizeof(int32_t) * (size_t)n));
+    CUDA_STEP(cudaMemsetAsync(P.level, 0xff, sizeof(int32_t) * (size_t)n, h->stream));
+    {
+        int32_t ng = P.ngroups;
+        const int32_t *g_ = P.grp, *lr = P.Lrowptr, *lc = P.Lcol;
+        int32_t *lv = P.level, *ml = stats + 3;
+        unsigned *er = h->dev_err;
+        void *args[] = {&ng, &g_, &lr, &lc, &lv, &ml, &er};
+        STEP(launch_persistent(h, (const void *)k_levels, 256, 0, ng, args));
+    }
+    {
+        int32_t *hs = (int32_t *)h->host_pinned;
+        CUDA_STEP(cudaMemcpyAsync(hs, stats, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, h->stream));
+        CUDA_STEP(cudaStreamSynchronize(h->stream));
+        P.max_ext_lower = hs[0];
+        P.max_ext_upper = hs[1];
+        P.max_group = hs[2];
+        P.nlevels = n > 0 ? hs[3] + 1 : 0; // levels are 0-based
+    }
+    STEP(read_and_clear_dev_err(h, &flags));
+    if (flags & ERR_TIMEOUT) { rc = GIC_ERR_TIMEOUT; goto out; }
+out:
+#undef STEP
+#undef CUDA_STEP
+    cudaFree(tmp);
+    return rc;
+}
+
+extern "C" {
+
+int gic_analyze(gic_handle *h, int64_t n, int64_t nnz, const int32_t *rowptr, const int32_t *col, gic_pattern **P)
+{
+    GIC_TRY(check_handle(h));
+    if (!P || !rowptr || !col || n < 1 || nnz < n) return GIC_ERR_INVALID_ARG;
+    if (nnz >= (1ll << 31) || n >= (1ll << 31)) return GIC_ERR_TOO_LARGE;
+    *P = nullptr;
+    gic_pattern *out = new gic_pattern();
+    int rc = analyze_impl(h, n, nnz, rowptr, col, out->p);
+    if (rc != GIC_OK) {
+        free_pattern(out->p);
+        delete out;
+        return rc;
+    }
+    *P = out;
+    return GIC_OK;
+}
+
+int gic_pattern_destroy(gic_pattern *P)
+{
+    if (!P) return GIC_OK;
+    cudaSetDevice(P->p.device);
+    free_pattern(P->p);
+    delete P;
+    return GIC_OK;
+}
+
+int gic_pattern_info(const gic_pattern *P, int64_t *n, int64_t *nnzA, int64_t *nnzL, int32_t *nlevels,
+                     int32_t *ngroups)
+{
+    if (!P) return GIC_ERR_INVALID_ARG;
+    if (n) *n = P->p.n;
+    if (nnzA) *nnzA = P->p.nnzA;
+    if (nnzL) *nnzL = P->p.nnzL;
+    if (nlevels) *nlevels = P->p.nlevels;
+    if (ngroups) *ngroups = P->p.ngroups;
+    return GIC_OK;
+}
+
+int gic_pattern_export(gic_handle *h, const gic_pattern *P, int32_t *Lrowptr, int32_t *Lcol, int32_t *level,
+                       int32_t *group_start)
+{
+    GIC_TRY(check_handle(h));
+    if (!P) return GIC_ERR_INVALID_ARG;
+    const Pattern &p = P->p;
+    if (Lrowptr)
+        GIC_CUDA_TRY(cudaMemcpyAsync(Lrowptr, p.Lrowptr, sizeof(int32_t) * (size_t)(p.n + 1), cudaMemcpyDeviceToDevice, h->stream));
+    if (Lcol)
+        GIC_CUDA_TRY(cudaMemcpyAsync(Lcol, p.Lcol, sizeof(int32_t) * (size_t)p.nnzL, cudaMemcpyDeviceToDevice, h->stream));
+    if (level)
+        GIC_CUDA_TRY(cudaMemcpyAsync(level, p.level, sizeof(int32_t) * (size_t)p.n, cudaMemcpyDeviceToDevice, h->stream));
+    if (group_start)
+        GIC_CUDA_TRY(cudaMemcpyAsync(group_start, p.grp, sizeof(int32_t) * (size_t)(p.ngroups + 1), cudaMemcpyDeviceToDevice, h->stream));
+    return GIC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,263 @@
+// gic_ic0.cu -- A3: IC(0) on the device.
+//
+// IC(0) (Introduction; Baseline Methods; Supplementary 2) computes L on the
+// pattern of tril(A):
+//   L_ij = (a_ij - sum_{k<j} L_ik L_jk) / L_jj  (j < i),
+//   L_ii = sqrt(a_ii' - sum_{k<i} L_ik^2),  a_ii' = a_ii + alpha a_ii,
+// with k over the pattern. Row i depends on the rows of its strictly-lower
+// columns, the same DAG as the forward solve, so it uses the same
+// schedule: one warp per group of rows with identical patterns, groups dealt
+// round-robin to a co-resident grid, readiness = the row's diagonal entry
+// (stored last, with release semantics, over a sentinel).
+//
+// Per group (rows s..s+G-1, shared external columns J[0..m)):
+//   1. wait for the rows J[u], then gather M[u][v] = L_{J[u],J[v]} (v <= u)
+//      into shared memory;
+//   2. the external part of every group row solves the same lower-triangular
+//      system M l = a_J, so all G rows are swept together, column by column
+//      in ascending order (the order of the sum above);
+//   3. the in-group columns and the diagonal of each row follow in order.
+// A pivot <= 0 or non-finite records the smallest such row (atomicMin), and
+// the row publishes NaN so its dependants finish instead of waiting.
+#include <limits.h>
+#include <math.h>
+
+#include "gic_internal.cuh"
+
+namespace gic {
+
+constexpr int IC_WARPS = 4;
+
+struct IcWarpSmem {
+    double M[MAXDIM * MAXDIM];   // row-major, lower triangle of the external block
+    double invd[MAXDIM];         // 1 / M[v][v]
+    double lg[GMAX][MAXDIM];     // external part of each group row
+    double lin[GMAX][GMAX + 1];  // in-group part (and diagonal) of each group row
+    int32_t J[MAXDIM];
+    int32_t off[MAXDIM + 1];     // prefix of the gathered rows' lengths
+};
+
+__device__ __forceinline__ int find_in(const int32_t *J, int lo, int hi, int32_t key)
+{
+    // index of key in sorted J[lo,hi), or -1
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        int32_t v = J[mid];
+        if (v == key) return mid;
+        if (v < key) lo = mid + 1; else hi = mid;
+    }
+    return -1;
+}
+
+__global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t ngroups, const int32_t *__restrict__ grp,
+                                                       const int32_t *__restrict__ Arowptr,
+                                                       const double *__restrict__ valA,
+                                                       const int32_t *__restrict__ Lrowptr,
+                                                       const int32_t *__restrict__ Lcol, double *Lval,
+                                                       double alpha, unsigned long long *bad_row, unsigned *err)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    IcWarpSmem &S = reinterpret_cast<IcWarpSmem *>(smem_raw)[wib];
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+
+    for (int64_t g = w; g < ngroups; g += nw) {
+        const int32_t s = grp[g];
+        const int G = grp[g + 1] - s;
+        const int32_t b0 = Lrowptr[s];
+        const int m = Lrowptr[s + 1] - b0 - 1; // external columns (host checked m <= MAXDIM)
+
+        // 1. external columns, their readiness, their row lengths
+        for (int u = lane; u < m; u += 32) {
+            int32_t j = Lcol[b0 + u];
+            S.J[u] = j;
+            int32_t dpos = Lrowptr[j + 1] - 1;
+            double d = ld_acquire(Lval + dpos);
+            long long it = 0;
+            while (is_sentinel(d) && it < SPIN_LIMIT) {
+                if (it > 32) __nanosleep(it < 1024 ? 32 : 256);
+                d = ld_acquire(Lval + dpos);
+                ++it;
+                if ((it & 1023) == 0 && *((volatile unsigned *)err) != 0u) break;
+            }
+            if (is_sentinel(d)) atomicOr(err, ERR_TIMEOUT);
+            S.off[u + 1] = dpos + 1 - Lrowptr[j]; // length of row j (its diagonal included)
+        }
+        __syncwarp();
+        if (lane == 0) {
+            S.off[0] = 0;
+            for (int u = 0; u < m; ++u) S.off[u + 1] += S.off[u];
+        }
+        for (int idx = lane; idx < m * m; idx += 32) S.M[(idx / m) * MAXDIM + (idx % m)] = 0.0;
+        __syncwarp();
+        __threadfence(); // pairs with the producers' release of each diagonal
+
+        // gather M[u][v] = L_{J[u],J[v]} for the entries of row J[u] inside J
+        const int P = S.off[m];
+        int u = 0;
+        for (int idx = lane; idx < P; idx += 32) {
+            while (S.off[u + 1] <= idx) ++u;
+            int32_t j = S.J[u];
+            int32_t q = Lrowptr[j] + (idx - S.off[u]);
+            int32_t c = Lcol[q];
+            int v = find_in(S.J, 0, u + 1, c);
+            if (v >= 0) {
+                double val = Lval[q];
+                S.M[u * MAXDIM + v] = val;
+                if (v == u) S.invd[u] = 1.0 / val;
+            }
+        }
+        __syncwarp();
+
+        // 2. external parts of all group rows: forward sweep over v ascending.
+        // Lane owns columns u = lane and lane + 32 of every row.
+        double acc0[GMAX], acc1[GMAX];
+#pragma unroll
+        for (int t = 0; t < GMAX; ++t) {
+            acc0[t] = 0.0;
+            acc1[t] = 0.0;
+            if (t < G) {
+                int64_t ab = Arowptr[s + t];
+                if (lane < m) acc0[t] = valA[ab + lane];
+                if (lane + 32 < m) acc1[t] = valA[ab + lane + 32];
+            }
+        }
+        for (int v = 0; v < m; ++v) {
+            const int owner = v & 31;
+            const double iv = S.invd[v];
+            const double mu0 = (lane > v && lane < m) ? S.M[lane * MAXDIM + v] : 0.0;
+            const double mu1 = (lane + 32 > v && lane + 32 < m) ? S.M[(lane + 32) * MAXDIM + v] : 0.0;
+#pragma unroll
+            for (int t = 0; t < GMAX; ++t) {
+                if (t < G) {
+                    double mine = (v < 32) ? acc0[t] : acc1[t];
+                    double lv = __shfl_sync(0xffffffffu, mine * iv, owner);
+                    if (lane == owner) S.lg[t][v] = lv;
+                    acc0[t] = fma(-mu0, lv, acc0[t]);
+                    acc1[t] = fma(-mu1, lv, acc1[t]);
+                }
+            }
+        }
+        __syncwarp();
+
+        // 3. in-group columns and diagonals, row by row
+        for (int t = 0; t < G; ++t) {
+            const int32_t i = s + t;
+            const int64_t ab = Arowptr[i];
+            // in-group column s+q (q < t): (a_{i,s+q} - l_t . l_q - sum_{q'<q}) / L_{s+q,s+q}
+            for (int q = 0; q < t; ++q) {
+                double d = 0.0;
+                for (int v = lane; v < m; v += 32) d = fma(S.lg[t][v], S.lg[q][v], d);
+                d = warp_sum(d);
+                if (lane == 0) {
+                    double x = valA[ab + m + q] - d;
+                    for (int q2 = 0; q2 < q; ++q2) x = fma(-S.lin[t][q2], S.lin[q][q2], x);
+                    S.lin[t][q] = x / S.lin[q][q];
+                }
+                __syncwarp();
+            }
+            // diagonal
+            double d = 0.0;
+            for (int v = lane; v < m; v += 32) d = fma(S.lg[t][v], S.lg[t][v], d);
+            d = warp_sum(d);
+            double piv = 0.0;
+            if (lane == 0) {
+                const double a = valA[ab + m + t];
+                double x = __dadd_rn(a, __dmul_rn(alpha, a)) - d;
+                for (int q = 0; q < t; ++q) x = fma(-S.lin[t][q], S.lin[t][q], x);
+                if (!(x > 0.0) || !isfinite(x)) {
+                    atomicMin(bad_row, (unsigned long long)i);
+                    piv = qnan;
+                } else {
+                    piv = sqrt(x);
+                }
+                S.lin[t][t] = piv;
+            }
+            // publish row i: off-diagonals, then the diagonal with release
+            const int64_t lb = Lrowptr[i];
+            for (int v = lane; v < m; v += 32) Lval[lb + v] = S.lg[t][v];
+            __syncwarp();
+            if (lane < t) Lval[lb + m + lane] = S.lin[t][lane];
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) st_release(Lval + lb + m + t, piv);
+            __syncwarp();
+        }
+    }
+}
+
+__global__ void k_ic0_prepare(int64_t n, const int32_t *Lrowptr, double *Lval, unsigned long long *bad_row)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        Lval[Lrowptr[i + 1] - 1] = sentinel_d();
+    if (blockIdx.x == 0 && threadIdx.x == 0) *bad_row = ULLONG_MAX;
+}
+
+int launch_persistent(gic_handle *h, const void *fn, int block, size_t smem, int64_t warps_needed, void **args);
+
+static int ic0_once(gic_handle *h, const Pattern &P, const double *valA, double *valL, double alpha, int64_t *bad)
+{
+    if (P.max_ext_lower > MAXDIM || P.max_group > GMAX) return GIC_ERR_UNSUPPORTED;
+    unsigned long long *bad_dev = (unsigned long long *)((char *)h->dev_small + 60000);
+    int64_t blocks = (P.n + 255) / 256;
+    if (blocks > (int64_t)h->num_sms * 8) blocks = (int64_t)h->num_sms * 8;
+    k_ic0_prepare<<<(unsigned)blocks, 256, 0, h->stream>>>(P.n, P.Lrowptr, valL, bad_dev);
+    GIC_CUDA_TRY(cudaGetLastError());
+    size_t smem = sizeof(IcWarpSmem) * IC_WARPS;
+    static int attr_set[64] = {0};
+    if (!attr_set[h->device & 63]) {
+        GIC_CUDA_TRY(cudaFuncSetAttribute(k_ic0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set[h->device & 63] = 1;
+    }
+    int32_t ng = P.ngroups;
+    const int32_t *g = P.grp, *ar = P.rowptr, *lr = P.Lrowptr, *lc = P.Lcol;
+    unsigned *er = h->dev_err;
+    void *args[] = {&ng, &g, &ar, &valA, &lr, &lc, &valL, &alpha, &bad_dev, &er};
+    GIC_TRY(launch_persistent(h, (const void *)k_ic0, IC_WARPS * 32, smem, ng, args));
+    unsigned long long *hb = (unsigned long long *)((char *)h->host_pinned + 2048);
+    GIC_CUDA_TRY(cudaMemcpyAsync(hb, bad_dev, sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
+    unsigned flags = 0;
+    GIC_TRY(read_and_clear_dev_err(h, &flags)); // synchronises
+    if (flags & ERR_TIMEOUT) return GIC_ERR_TIMEOUT;
+    *bad = (*hb == ULLONG_MAX) ? -1 : (int64_t)*hb;
+    return (*bad >= 0) ? GIC_ERR_NOT_SPD : GIC_OK;
+}
+
+}  // namespace gic
+
+using namespace gic;
+
+extern "C" {
+
+int gic_ic0(gic_handle *h, const gic_pattern *P, const double *valA, double *valL, double alpha, int64_t *bad_row)
+{
+    GIC_TRY(check_handle(h));
+    if (!P || P->p.device != h->device || !valA || !valL || !(alpha >= 0.0)) return GIC_ERR_INVALID_ARG;
+    int64_t bad = -1;
+    int rc = ic0_once(h, P->p, valA, valL, alpha, &bad);
+    if (bad_row) *bad_row = bad;
+    return rc;
+}
+
+int gic_ic0_auto(gic_handle *h, const gic_pattern *P, const double *valA, double *valL, int max_tries,
+                 double *alpha_out, int64_t *bad_row)
+{
+    GIC_TRY(check_handle(h));
+    if (!P || P->p.device != h->device || !valA || !valL || max_tries < 0) return GIC_ERR_INVALID_ARG;
+    double alpha = 0.0;
+    int64_t bad = -1;
+    int rc = GIC_ERR_NOT_SPD;
+    for (int t = 0; t <= max_tries; ++t) {
+        rc = ic0_once(h, P->p, valA, valL, alpha, &bad);
+        if (rc != GIC_ERR_NOT_SPD) break;
+        alpha = (t == 0) ? 1e-3 : 2.0 * alpha;
+    }
+    if (alpha_out) *alpha_out = (rc == GIC_OK) ? alpha : alpha;
+    if (bad_row) *bad_row = bad;
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,143 @@
+// gic_internal.cuh -- shared device/host helpers of the CUDA library.
+// Nothing here is visible through the C-ABI; include/gicpcg.h is the boundary.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/gicpcg.h"
+
+namespace gic {
+
+// ---------------------------------------------------------------- errors
+#define GIC_CUDA_TRY(expr)                                   \
+    do {                                                     \
+        cudaError_t e_ = (expr);                             \
+        if (e_ != cudaSuccess) {                             \
+            gic::set_last_cuda_error(e_, #expr, __FILE__, __LINE__); \
+            return GIC_ERR_CUDA;                             \
+        }                                                    \
+    } while (0)
+
+#define GIC_TRY(expr)                  \
+    do {                               \
+        int s_ = (expr);               \
+        if (s_ != GIC_OK) return s_;   \
+    } while (0)
+
+void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+
+// Device error flags (bit set in handle->dev_err).
+enum : unsigned { ERR_TIMEOUT = 1u, ERR_BOUNDS = 2u };
+
+// Spin-wait limits: polls of one word before a waiting warp gives up, sets
+// ERR_TIMEOUT and writes NaN so that everything downstream drains. With the
+// back-off below this is about a second of waiting.
+constexpr long long SPIN_LIMIT = 1ll << 22;
+
+// A quiet-NaN bit pattern that arithmetic never produces (the GPU's
+// canonical NaN differs), used as "not written yet" in solve outputs.
+constexpr unsigned long long SENTINEL_BITS = 0x7ff4dead0000beefull;
+
+__device__ __forceinline__ double sentinel_d() { return __longlong_as_double((long long)SENTINEL_BITS); }
+__device__ __forceinline__ bool is_sentinel(double v)
+{
+    return (unsigned long long)__double_as_longlong(v) == SENTINEL_BITS;
+}
+
+__device__ __forceinline__ double ld_relaxed(const double *p)
+{
+    double v;
+    asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ double ld_acquire(const double *p)
+{
+    unsigned long long u;
+    asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(u) : "l"(p) : "memory");
+    return __longlong_as_double((long long)u);
+}
+__device__ __forceinline__ void st_relaxed(double *p, double v)
+{
+    asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ void st_release(double *p, double v)
+{
+    asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"((unsigned long long)__double_as_longlong(v))
+                 : "memory");
+}
+__device__ __forceinline__ int ld_acquire_i32(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_i32(int *p, int v)
+{
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Wait until *p is no longer the sentinel; bounded. On timeout sets the
+// error flag and returns NaN.
+__device__ __forceinline__ double wait_value(const double *p, unsigned *err)
+{
+    double v = ld_relaxed(p);
+    if (!is_sentinel(v)) return v;
+    for (long long it = 0; it < SPIN_LIMIT; ++it) {
+        if (it > 32) __nanosleep(it < 1024 ? 32 : 256);
+        v = ld_relaxed(p);
+        if (!is_sentinel(v)) return v;
+        if ((it & 1023) == 1023 && *((volatile unsigned *)err) != 0u) return __longlong_as_double(0x7ff8000000000000ll);
+    }
+    atomicOr(err, ERR_TIMEOUT);
+    return __longlong_as_double(0x7ff8000000000000ll);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------- pattern
+// Analysis of one symmetric CSR pattern (device arrays, library owned).
+struct Pattern {
+    int64_t n = 0, nnzA = 0, nnzL = 0;
+    int32_t ngroups = 0, nlevels = 0;
+    int32_t max_ext_lower = 0, max_ext_upper = 0, max_group = 0;
+    // A (borrowed, caller owned; must outlive the pattern)
+    const int32_t *rowptr = nullptr, *col = nullptr;
+    // L = tril(A) CSR; L entry p of row i is A entry rowptr[i] + (p - Lrowptr[i])
+    int32_t *Lrowptr = nullptr, *Lcol = nullptr;
+    // U = L^T CSR (the diagonal first in each row); tperm[q] = L position
+    int32_t *Urowptr = nullptr, *Ucol = nullptr, *tperm = nullptr;
+    // groups of consecutive rows with identical A patterns (<= GMAX rows)
+    int32_t *grp = nullptr;   // ngroups+1 start rows
+    int32_t *level = nullptr; // n row levels
+    int device = 0;
+};
+
+constexpr int GMAX = 8;    // rows per group
+constexpr int MAXDIM = 48; // max lower entries of a row handled by IC(0)
+
+}  // namespace gic
+
+struct gic_pattern {
+    gic::Pattern p;
+};
+
+struct gic_handle {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    unsigned *dev_err = nullptr;   // device error flags
+    void *dev_small = nullptr;     // 64 KiB of library scratch (scalars, Ke)
+    void *host_pinned = nullptr;   // 4 KiB pinned readback area
+};
+
+namespace gic {
+int check_handle(gic_handle *h);
+int read_and_clear_dev_err(gic_handle *h, unsigned *flags);
+}

@@ -1,0 +1,769 @@
+// gic_solve.cu -- A7: the PCG loop of Supplementary Algorithm 1 on the GPU.
+//
+// Kernels:
+//   k_lsolve / k_ltsolve  sync-free triangular solves (Supplementary 5,
+//       Eq.(11) read as plain forward/back substitution). One warp owns a
+//       group of consecutive rows with identical patterns; it gathers the
+//       group's off-block columns once, waits (bounded) on each needed
+//       solution entry, and finishes the dense diagonal block in registers.
+//       "Not yet computed" is a sentinel NaN stored in the solution vector,
+//       so the wait and the data are one 8-byte word. Groups are dealt
+//       round-robin to a co-resident (cooperative) grid in dependency order,
+//       so the first unfinished group can always run.
+//   k_spmv                CSR SpMV, one warp per row, with the dot product the
+//       PCG step needs fused in (p^T A p) or the initial residual b - A x0.
+//   k_update_p / k_update_xr   the vector updates of Algorithm 1, lines
+//       13-14 and 17-18, with r^T r fused into the second.
+// Every dot product is reduced deterministically: per-block (or per-warp)
+// partials in a fixed layout, summed in index order by the last block to
+// finish, which also computes alpha / beta and the stop test on the device.
+#include <math.h>
+#include <stdio.h>
+
+#include "gic_internal.cuh"
+
+namespace gic {
+
+struct Scalars {
+    double rz;    // r_k^T z_k
+    double pw;    // p^T A p
+    double alpha, beta;
+    double rr, bb; // ||r||^2, ||b||^2
+    double tol;
+    int iter, maxit, done, status;
+    unsigned counter; // last-block ticket
+    unsigned pad;
+};
+
+constexpr int SPMV_BLOCK = 256;
+constexpr int VEC_BLOCK = 256;
+constexpr int SOLVE_BLOCK = 256;
+constexpr int MAX_PARTIALS = 1 << 16;
+
+// ------------------------------------------------------------ helpers
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+    v = warp_sum(v);
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sh[k];
+    __syncthreads();
+    return s; // valid in thread 0
+}
+
+// Called by thread 0 of every block after writing partials[blockIdx.x]
+// (count = gridDim.x). Returns true in the one block that arrives last.
+__device__ __forceinline__ bool last_block(unsigned *counter, unsigned count)
+{
+    __threadfence();
+    unsigned t = atomicAdd(counter, 1u);
+    return t == count - 1;
+}
+
+// deterministic sum of partials[0..count) by one warp (lane-strided, then tree)
+__device__ __forceinline__ double warp_sum_partials(const double *partials, int count)
+{
+    int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int k = lane; k < count; k += 32) s += ((volatile const double *)partials)[k];
+    return warp_sum(s);
+}
+
+__global__ void k_fill_sentinel(int64_t n, double *a, double *b)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        a[i] = sentinel_d();
+        if (b) b[i] = sentinel_d();
+    }
+}
+
+// U values (transpose of L in U's CSR order) and reciprocal diagonal.
+template <typename TL>
+__global__ void k_transpose_vals(int64_t n, int64_t nnzL, const int32_t *tperm, const int32_t *Lrowptr, const TL *Lval,
+                                 TL *Uval, double *invd)
+{
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nnzL; q += stride) Uval[q] = Lval[tperm[q]];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        invd[i] = 1.0 / (double)Lval[Lrowptr[i + 1] - 1];
+}
+
+// ------------------------------------------------------------ SpTRSV
+// Forward: y_i = (r_i - sum_{j<i} L_ij y_j) / L_ii. y must hold the sentinel.
+template <typename TL>
+__global__ void __launch_bounds__(SOLVE_BLOCK) k_lsolve(int32_t ngroups, const int32_t *__restrict__ grp,
+                                                        const int32_t *__restrict__ Lrowptr,
+                                                        const int32_t *__restrict__ Lcol, const TL *__restrict__ Lval,
+                                                        const double *__restrict__ invd, const double *__restrict__ r,
+                                                        double *y, unsigned *err, const Scalars *sc)
+{
+    if (sc && sc->done) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t g = w; g < ngroups; g += nw) {
+        const int32_t s = grp[g];
+        const int G = grp[g + 1] - s;
+        const int32_t b0 = Lrowptr[s];
+        const int32_t m = Lrowptr[s + 1] - b0 - 1;
+        int32_t base[GMAX];
+        double acc[GMAX];
+#pragma unroll
+        for (int t = 0; t < GMAX; ++t) {
+            base[t] = (t < G) ? b0 + t * (m + 1) + (t * (t - 1)) / 2 : 0;
+            acc[t] = 0.0;
+        }
+        for (int32_t k = lane; k < m; k += 32) {
+            const int32_t j = Lcol[b0 + k];
+            const double yj = wait_value(y + j, err);
+#pragma unroll
+            for (int t = 0; t < GMAX; ++t)
+                if (t < G) acc[t] = fma((double)Lval[base[t] + k], yj, acc[t]);
+        }
+#pragma unroll
+        for (int t = 0; t < GMAX; ++t)
+            if (t < G) acc[t] = warp_sum(acc[t]);
+        if (lane == 0) {
+            double yl[GMAX];
+#pragma unroll
+            for (int t = 0; t < GMAX; ++t) {
+                if (t < G) {
+                    double v = r[s + t] - acc[t];
+#pragma unroll
+                    for (int u = 0; u < t; ++u) v = fma(-(double)Lval[base[t] + m + u], yl[u], v);
+                    yl[t] = v * invd[s + t];
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < GMAX; ++t)
+                if (t < G) st_relaxed(y + s + t, yl[t]);
+        }
+    }
+}
+
+// Backward: z_i = (y_i - sum_{j>i} L_ji z_j) / L_ii on U = L^T. z must hold
+// the sentinel. Groups are visited from the last one down. With PCG != 0
+// the kernel also resets y to the sentinel (for the next forward solve) and
+// forms r^T z, then beta = r_k^T z_k / r_{k-1}^T z_{k-1} (Algorithm 1 line 13).
+template <typename TL, bool PCG>
+__global__ void __launch_bounds__(SOLVE_BLOCK) k_ltsolve(int32_t ngroups, const int32_t *__restrict__ grp,
+                                                         const int32_t *__restrict__ Urowptr,
+                                                         const int32_t *__restrict__ Ucol, const TL *__restrict__ Uval,
+                                                         const double *__restrict__ invd, double *y, double *z,
+                                                         const double *__restrict__ r, double *partials,
+                                                         unsigned *err, Scalars *sc)
+{
+    if (sc && sc->done) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double dot = 0.0;
+    for (int64_t gg = w; gg < ngroups; gg += nw) {
+        const int64_t g = ngroups - 1 - gg;
+        const int32_t s = grp[g];
+        const int G = grp[g + 1] - s;
+        const int32_t e = s + G - 1;
+        const int32_t be = Urowptr[e];
+        const int32_t mu = Urowptr[e + 1] - be - 1;
+        int32_t base[GMAX], ext[GMAX];
+        double acc[GMAX];
+#pragma unroll
+        for (int t = 0; t < GMAX; ++t) {
+            // row s+t of U holds G-t in-group entries (diagonal first), then mu
+            base[t] = (t < G) ? Urowptr[s + t] : 0;
+            ext[t] = base[t] + (G - t);
+            acc[t] = 0.0;
+        }
+        for (int32_t k = lane; k < mu; k += 32) {
+            const int32_t j = Ucol[be + 1 + k];
+            const double zj = wait_value(z + j, err);
+#pragma unroll
+            for (int t = 0; t < GMAX; ++t)
+                if (t < G) acc[t] = fma((double)Uval[ext[t] + k], zj, acc[t]);
+        }
+#pragma unroll
+        for (int t = 0; t < GMAX; ++t)
+            if (t < G) acc[t] = warp_sum(acc[t]);
+        if (lane == 0) {
+            double zl[GMAX];
+#pragma unroll
+            for (int t = GMAX - 1; t >= 0; --t) {
+                if (t < G) {
+                    double v = y[s + t] - acc[t];
+#pragma unroll
+                    for (int u = t + 1; u < GMAX; ++u)
+                        if (u < G) v = fma(-(double)Uval[base[t] + (u - t)], zl[u], v);
+                    zl[t] = v * invd[s + t];
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < GMAX; ++t) {
+                if (t < G) {
+                    st_relaxed(z + s + t, zl[t]);
+                    if (PCG) {
+                        y[s + t] = sentinel_d();
+                        dot = fma(r[s + t], zl[t], dot);
+                    }
+                }
+            }
+        }
+    }
+    if (PCG) {
+        // per-warp partial, then the last warp of the grid reduces
+        if (lane == 0) partials[w] = dot;
+        __syncwarp();
+        unsigned last = 0;
+        if (lane == 0) {
+            __threadfence();
+            last = (atomicAdd(&sc->counter, 1u) == (unsigned)nw - 1u);
+        }
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (last) {
+            __threadfence();
+            double rz = warp_sum_partials(partials, (int)nw);
+            if (lane == 0) {
+                sc->counter = 0;
+                if (!(rz > 0.0) || !isfinite(rz)) {
+                    sc->status = GIC_ERR_BREAKDOWN;
+                    sc->done = 1;
+                } else {
+                    sc->beta = (sc->iter == 0) ? 0.0 : rz / sc->rz;
+                    sc->rz = rz;
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ SpMV
+// MODE 0: y = A x (optional x^T y into *out_dot)
+// MODE 1: y = A p, pw = p^T y, alpha = rz / pw          (Algorithm 1 lines 15-16)
+// MODE 2: r = b - A x, rr = r^T r, bb = b^T b, stop test (Algorithm 1 line 1)
+template <int MODE>
+__global__ void __launch_bounds__(SPMV_BLOCK) k_spmv(int64_t n, const int32_t *__restrict__ rowptr,
+                                                     const int32_t *__restrict__ col, const double *__restrict__ val,
+                                                     const double *__restrict__ x, double *__restrict__ y,
+                                                     const double *__restrict__ b, double *partials, double *out_dot,
+                                                     Scalars *sc)
+{
+    if (MODE != 0 && sc->done) return;
+    __shared__ double sh[SPMV_BLOCK / 32];
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double d1 = 0.0, d2 = 0.0;
+    for (int64_t i = w; i < n; i += nw) {
+        const int32_t a = rowptr[i], e = rowptr[i + 1];
+        double s = 0.0;
+        for (int32_t p = a + lane; p < e; p += 32) s = fma(val[p], __ldg(x + col[p]), s);
+        s = warp_sum(s);
+        if (lane == 0) {
+            if (MODE == 2) {
+                double bi = b[i];
+                double ri = bi - s;
+                y[i] = ri;
+                d1 = fma(ri, ri, d1);
+                d2 = fma(bi, bi, d2);
+            } else {
+                y[i] = s;
+                d1 = fma(x[i], s, d1);
+            }
+        }
+    }
+    if (MODE == 0 && !out_dot) return;
+    double s1 = block_sum(d1, sh);
+    double s2 = (MODE == 2) ? block_sum(d2, sh) : 0.0;
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = s1;
+        if (MODE == 2) partials[gridDim.x + blockIdx.x] = s2;
+    }
+    __shared__ bool is_last;
+    if (threadIdx.x == 0) is_last = last_block(&sc->counter, gridDim.x);
+    __syncthreads();
+    if (!is_last || threadIdx.x >= 32) return;
+    __threadfence();
+    double t1 = warp_sum_partials(partials, gridDim.x);
+    double t2 = (MODE == 2) ? warp_sum_partials(partials + gridDim.x, gridDim.x) : 0.0;
+    if (lane != 0) return;
+    sc->counter = 0;
+    if (MODE == 0) {
+        *out_dot = t1;
+    } else if (MODE == 1) {
+        sc->pw = t1;
+        if (!(t1 > 0.0) || !isfinite(t1)) {
+            sc->status = GIC_ERR_BREAKDOWN;
+            sc->done = 1;
+        } else {
+            sc->alpha = sc->rz / t1;
+        }
+    } else {
+        sc->rr = t1;
+        sc->bb = t2;
+        if (t2 == 0.0 || sqrt(t1) <= sc->tol * sqrt(t2)) {
+            sc->done = 1;
+            sc->status = GIC_OK;
+        }
+        if (!isfinite(t1)) {
+            sc->done = 1;
+            sc->status = GIC_ERR_BREAKDOWN;
+        }
+    }
+}
+
+// p = z + beta p (p = z on the first step); z back to the sentinel.
+// With IDENT the preconditioner is the identity: z is r itself, and r^T z is
+// formed here (the solves are skipped).
+template <bool IDENT>
+__global__ void __launch_bounds__(VEC_BLOCK) k_update_p(int64_t n, double *z, double *p, const double *r,
+                                                        double *partials, Scalars *sc)
+{
+    if (sc->done) return;
+    const int first = (sc->iter == 0);
+    const double beta = sc->beta;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (IDENT) {
+            const double zi = r[i];
+            p[i] = first ? zi : fma(beta, p[i], zi);
+        } else {
+            const double zi = z[i];
+            p[i] = first ? zi : fma(beta, p[i], zi);
+            z[i] = sentinel_d();
+        }
+    }
+}
+
+// r^T r for the identity preconditioner (r^T z with z = r): computes beta.
+__global__ void __launch_bounds__(VEC_BLOCK) k_ident_rz(int64_t n, const double *r, double *partials, Scalars *sc)
+{
+    if (sc->done) return;
+    __shared__ double sh[VEC_BLOCK / 32];
+    double d = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        d = fma(r[i], r[i], d);
+    double s = block_sum(d, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+    __shared__ bool is_last;
+    if (threadIdx.x == 0) is_last = last_block(&sc->counter, gridDim.x);
+    __syncthreads();
+    if (!is_last || threadIdx.x >= 32) return;
+    __threadfence();
+    double rz = warp_sum_partials(partials, gridDim.x);
+    if ((threadIdx.x & 31) != 0) return;
+    sc->counter = 0;
+    if (!(rz > 0.0) || !isfinite(rz)) {
+        sc->status = GIC_ERR_BREAKDOWN;
+        sc->done = 1;
+    } else {
+        sc->beta = (sc->iter == 0) ? 0.0 : rz / sc->rz;
+        sc->rz = rz;
+    }
+}
+
+// x += alpha p, r -= alpha w, rr = r^T r; iteration count and stop test.
+__global__ void __launch_bounds__(VEC_BLOCK) k_update_xr(int64_t n, double *x, double *r, const double *p,
+                                                         const double *w, double *partials, Scalars *sc)
+{
+    if (sc->done) return;
+    __shared__ double sh[VEC_BLOCK / 32];
+    const double alpha = sc->alpha;
+    double d = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        x[i] = fma(alpha, p[i], x[i]);
+        const double ri = fma(-alpha, w[i], r[i]);
+        r[i] = ri;
+        d = fma(ri, ri, d);
+    }
+    double s = block_sum(d, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+    __shared__ bool is_last;
+    if (threadIdx.x == 0) is_last = last_block(&sc->counter, gridDim.x);
+    __syncthreads();
+    if (!is_last || threadIdx.x >= 32) return;
+    __threadfence();
+    double rr = warp_sum_partials(partials, gridDim.x);
+    if ((threadIdx.x & 31) != 0) return;
+    sc->counter = 0;
+    sc->rr = rr;
+    sc->iter += 1;
+    if (sqrt(rr) <= sc->tol * sqrt(sc->bb)) {
+        sc->done = 1;
+        sc->status = GIC_OK;
+    } else if (!isfinite(rr)) {
+        sc->done = 1;
+        sc->status = GIC_ERR_BREAKDOWN;
+    } else if (sc->iter >= sc->maxit) {
+        sc->done = 1;
+        sc->status = GIC_ERR_NO_CONVERGENCE;
+    }
+}
+
+__global__ void k_init_scalars(Scalars *sc, double tol, int maxit)
+{
+    Scalars s = {};
+    s.tol = tol;
+    s.maxit = maxit;
+    s.status = GIC_OK;
+    *sc = s;
+}
+
+__global__ void k_convert_f64_f32(int64_t cnt, const double *src, float *dst)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
+}
+
+// ------------------------------------------------------------ host side
+int launch_persistent(gic_handle *h, const void *fn, int block, size_t smem, int64_t warps_needed, void **args);
+
+static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+struct SolveWs {
+    void *Uval;
+    double *invd, *r, *y, *z, *p, *w;
+    double *partials;
+    Scalars *sc;
+    size_t bytes;
+};
+
+static SolveWs carve(const Pattern &P, int l_dtype, void *ws)
+{
+    SolveWs o = {};
+    char *c = (char *)ws;
+    size_t off = 0;
+    size_t es = (l_dtype == GIC_F32) ? 4 : 8;
+    o.sc = (Scalars *)(c + off); off += align_up(sizeof(Scalars));
+    o.partials = (double *)(c + off); off += align_up(sizeof(double) * 2 * MAX_PARTIALS);
+    o.Uval = c + off; off += (l_dtype == GIC_IDENTITY) ? 0 : align_up(es * (size_t)P.nnzL);
+    o.invd = (double *)(c + off); off += (l_dtype == GIC_IDENTITY) ? 0 : align_up(8 * (size_t)P.n);
+    double **vecs[5] = {&o.r, &o.y, &o.z, &o.p, &o.w};
+    for (int k = 0; k < 5; ++k) { *vecs[k] = (double *)(c + off); off += align_up(8 * (size_t)P.n); }
+    o.bytes = off;
+    return o;
+}
+
+static unsigned vec_grid(gic_handle *h, int64_t n, int block)
+{
+    int64_t b = (n + block - 1) / block;
+    int64_t cap = (int64_t)h->num_sms * 4;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+static unsigned spmv_grid(gic_handle *h, int64_t n)
+{
+    int64_t warps = SPMV_BLOCK / 32;
+    int64_t b = (n + warps - 1) / warps;
+    int64_t cap = (int64_t)h->num_sms * 8;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+template <typename TL>
+static int launch_lsolve(gic_handle *h, const Pattern &P, const TL *Lval, const double *invd, const double *r,
+                         double *y, Scalars *sc)
+{
+    int32_t ng = P.ngroups;
+    const int32_t *g = P.grp, *lr = P.Lrowptr, *lc = P.Lcol;
+    unsigned *er = h->dev_err;
+    void *args[] = {&ng, &g, &lr, &lc, &Lval, &invd, &r, &y, &er, &sc};
+    return launch_persistent(h, (const void *)k_lsolve<TL>, SOLVE_BLOCK, 0, ng, args);
+}
+
+template <typename TL, bool PCG>
+static int launch_ltsolve(gic_handle *h, const Pattern &P, const TL *Uval, const double *invd, double *y, double *z,
+                          const double *r, double *partials, Scalars *sc)
+{
+    int32_t ng = P.ngroups;
+    const int32_t *g = P.grp, *ur = P.Urowptr, *uc = P.Ucol;
+    unsigned *er = h->dev_err;
+    void *args[] = {&ng, &g, &ur, &uc, &Uval, &invd, &y, &z, &r, &partials, &er, &sc};
+    int64_t need = ng;
+    if (PCG && need > MAX_PARTIALS) need = MAX_PARTIALS; // grid warps <= partial slots
+    return launch_persistent(h, (const void *)k_ltsolve<TL, PCG>, SOLVE_BLOCK, 0, need, args);
+}
+
+template <typename TL>
+static int setup_factor(gic_handle *h, const Pattern &P, const TL *Lval, TL *Uval, double *invd)
+{
+    int64_t cnt = P.nnzL > P.n ? P.nnzL : P.n;
+    k_transpose_vals<TL><<<vec_grid(h, cnt, 256), 256, 0, h->stream>>>(P.n, P.nnzL, P.tperm, P.Lrowptr, Lval, Uval, invd);
+    GIC_CUDA_TRY(cudaGetLastError());
+    return GIC_OK;
+}
+
+// Optional per-kernel-class timing of gic_pcg (CUDA events on the handle's
+// stream around every launch; the loop then synchronises every iteration).
+struct Prof {
+    int on = 0;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    double ms[GIC_PROF_CLASSES] = {0};
+    long long launches[GIC_PROF_CLASSES] = {0};
+};
+static Prof g_prof[64];
+
+static Prof &prof_of(gic_handle *h) { return g_prof[h->device & 63]; }
+
+#define PROF_BEGIN(cls)                                                                    \
+    if (pr.on) GIC_CUDA_TRY(cudaEventRecord(pr.ev[0], h->stream));
+#define PROF_END(cls)                                                                      \
+    if (pr.on) {                                                                           \
+        GIC_CUDA_TRY(cudaEventRecord(pr.ev[1], h->stream));                                \
+        GIC_CUDA_TRY(cudaEventSynchronize(pr.ev[1]));                                      \
+        float t_ = 0.f;                                                                    \
+        GIC_CUDA_TRY(cudaEventElapsedTime(&t_, pr.ev[0], pr.ev[1]));                       \
+        pr.ms[cls] += t_;                                                                  \
+        pr.launches[cls] += 1;                                                             \
+    }
+
+// One PCG iteration: lines 11-18 of Algorithm 1 and the stop test.
+template <typename TL>
+static int pcg_iteration(gic_handle *h, const Pattern &P, const double *valA, const TL *Lval, const SolveWs &W,
+                         double *x, int ident)
+{
+    const int64_t n = P.n;
+    Prof &pr = prof_of(h);
+    if (ident) {
+        PROF_BEGIN(GIC_PROF_VECTOR);
+        k_ident_rz<<<vec_grid(h, n, VEC_BLOCK), VEC_BLOCK, 0, h->stream>>>(n, W.r, W.partials, W.sc);
+        k_update_p<true><<<vec_grid(h, n, VEC_BLOCK), VEC_BLOCK, 0, h->stream>>>(n, W.z, W.p, W.r, W.partials, W.sc);
+        GIC_CUDA_TRY(cudaGetLastError());
+        PROF_END(GIC_PROF_VECTOR);
+    } else {
+        PROF_BEGIN(GIC_PROF_LSOLVE);
+        GIC_TRY(launch_lsolve<TL>(h, P, Lval, W.invd, W.r, W.y, W.sc));
+        PROF_END(GIC_PROF_LSOLVE);
+        PROF_BEGIN(GIC_PROF_LTSOLVE);
+        GIC_TRY((launch_ltsolve<TL, true>(h, P, (const TL *)W.Uval, W.invd, W.y, W.z, W.r, W.partials, W.sc)));
+        PROF_END(GIC_PROF_LTSOLVE);
+        PROF_BEGIN(GIC_PROF_VECTOR);
+        k_update_p<false><<<vec_grid(h, n, VEC_BLOCK), VEC_BLOCK, 0, h->stream>>>(n, W.z, W.p, W.r, W.partials, W.sc);
+        GIC_CUDA_TRY(cudaGetLastError());
+        PROF_END(GIC_PROF_VECTOR);
+    }
+    PROF_BEGIN(GIC_PROF_SPMV);
+    k_spmv<1><<<spmv_grid(h, n), SPMV_BLOCK, 0, h->stream>>>(n, P.rowptr, P.col, valA, W.p, W.w, nullptr, W.partials,
+                                                            nullptr, W.sc);
+    GIC_CUDA_TRY(cudaGetLastError());
+    PROF_END(GIC_PROF_SPMV);
+    PROF_BEGIN(GIC_PROF_VECTOR);
+    k_update_xr<<<vec_grid(h, n, VEC_BLOCK), VEC_BLOCK, 0, h->stream>>>(n, x, W.r, W.p, W.w, W.partials, W.sc);
+    GIC_CUDA_TRY(cudaGetLastError());
+    PROF_END(GIC_PROF_VECTOR);
+    return GIC_OK;
+}
+
+template <typename TL>
+static int pcg_run(gic_handle *h, const Pattern &P, const double *valA, const TL *Lval, int ident, const double *b,
+                   double *x, double rtol, int maxit, int32_t *iters, double *relres, const SolveWs &W)
+{
+    const int64_t n = P.n;
+    Prof &pr = prof_of(h);
+    k_init_scalars<<<1, 1, 0, h->stream>>>(W.sc, rtol, maxit);
+    if (!ident) {
+        GIC_TRY(setup_factor<TL>(h, P, Lval, (TL *)W.Uval, W.invd));
+        k_fill_sentinel<<<vec_grid(h, n, 256), 256, 0, h->stream>>>(n, W.y, W.z);
+    }
+    PROF_BEGIN(GIC_PROF_SPMV);
+    k_spmv<2><<<spmv_grid(h, n), SPMV_BLOCK, 0, h->stream>>>(n, P.rowptr, P.col, valA, x, W.r, b, W.partials, nullptr,
+                                                            W.sc);
+    GIC_CUDA_TRY(cudaGetLastError());
+    PROF_END(GIC_PROF_SPMV);
+    // Iterations are enqueued in batches; the host reads the device flag of
+    // the previous batch while the next one runs (finished kernels exit at
+    // once when done is set), so the GPU does not idle on the check.
+    const int BATCH = 4;
+    Scalars *hs = (Scalars *)h->host_pinned;
+    cudaEvent_t ev_done = nullptr;
+    GIC_CUDA_TRY(cudaEventCreateWithFlags(&ev_done, cudaEventDisableTiming));
+    int enq = 0, rc = GIC_OK;
+    bool pending = false;
+    while (true) {
+        int todo = BATCH;
+        if (enq + todo > maxit) todo = maxit - enq;
+        for (int k = 0; k < todo && rc == GIC_OK; ++k) rc = pcg_iteration<TL>(h, P, valA, Lval, W, x, ident);
+        if (rc != GIC_OK) break;
+        enq += todo;
+        if (pending) {
+            cudaError_t e = cudaEventSynchronize(ev_done);
+            if (e != cudaSuccess) { set_last_cuda_error(e, "pcg sync", __FILE__, __LINE__); rc = GIC_ERR_CUDA; break; }
+            if (hs->done || hs->iter >= maxit) break;
+        }
+        cudaError_t e = cudaMemcpyAsync(hs, W.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_done, h->stream);
+        if (e != cudaSuccess) { set_last_cuda_error(e, "pcg readback", __FILE__, __LINE__); rc = GIC_ERR_CUDA; break; }
+        pending = true;
+        if (enq >= maxit || todo == 0) {
+            e = cudaEventSynchronize(ev_done);
+            if (e != cudaSuccess) { set_last_cuda_error(e, "pcg sync", __FILE__, __LINE__); rc = GIC_ERR_CUDA; }
+            break;
+        }
+    }
+    cudaEventDestroy(ev_done);
+    if (rc != GIC_OK) return rc;
+    GIC_CUDA_TRY(cudaMemcpyAsync(hs, W.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream));
+    GIC_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    Scalars out = *hs;
+    unsigned flags = 0;
+    GIC_TRY(read_and_clear_dev_err(h, &flags));
+    if (iters) *iters = out.iter;
+    if (relres) *relres = (out.bb > 0.0) ? sqrt(out.rr) / sqrt(out.bb) : 0.0;
+    if (flags & ERR_TIMEOUT) return GIC_ERR_TIMEOUT;
+    if (!out.done) return GIC_ERR_NO_CONVERGENCE;
+    return out.status;
+}
+
+}  // namespace gic
+
+using namespace gic;
+
+static int check_pattern(gic_handle *h, const gic_pattern *P)
+{
+    GIC_TRY(check_handle(h));
+    if (!P || P->p.device != h->device) return GIC_ERR_INVALID_ARG;
+    return GIC_OK;
+}
+
+extern "C" {
+
+int gic_workspace_size(gic_handle *h, const gic_pattern *P, int op, int l_dtype, size_t *bytes)
+{
+    GIC_TRY(check_pattern(h, P));
+    if (!bytes || (l_dtype != GIC_F64 && l_dtype != GIC_F32 && l_dtype != GIC_IDENTITY)) return GIC_ERR_INVALID_ARG;
+    if (op != GIC_WS_SOLVE && op != GIC_WS_PCG) return GIC_ERR_INVALID_ARG;
+    *bytes = carve(P->p, l_dtype, nullptr).bytes;
+    return GIC_OK;
+}
+
+int gic_convert_f64_f32(gic_handle *h, int64_t count, const double *src, float *dst)
+{
+    GIC_TRY(check_handle(h));
+    if (count < 0 || (count > 0 && (!src || !dst))) return GIC_ERR_INVALID_ARG;
+    if (count == 0) return GIC_OK;
+    k_convert_f64_f32<<<vec_grid(h, count, 256), 256, 0, h->stream>>>(count, src, dst);
+    GIC_CUDA_TRY(cudaGetLastError());
+    return GIC_OK;
+}
+
+int gic_spmv(gic_handle *h, const gic_pattern *P, const double *valA, const double *x, double *y, double *xdoty)
+{
+    GIC_TRY(check_pattern(h, P));
+    if (!valA || !x || !y) return GIC_ERR_INVALID_ARG;
+    const Pattern &p = P->p;
+    // scalars + partials live in the handle's small scratch for this call
+    Scalars *sc = (Scalars *)h->dev_small;
+    double *partials = (double *)((char *)h->dev_small + 1024);
+    unsigned grid = spmv_grid(h, p.n);
+    if (xdoty && grid > (65536 - 1024) / 8) return GIC_ERR_UNSUPPORTED;
+    if (xdoty) GIC_CUDA_TRY(cudaMemsetAsync(sc, 0, sizeof(Scalars), h->stream));
+    k_spmv<0><<<grid, SPMV_BLOCK, 0, h->stream>>>(p.n, p.rowptr, p.col, valA, x, y, nullptr, partials, xdoty, sc);
+    GIC_CUDA_TRY(cudaGetLastError());
+    return GIC_OK;
+}
+
+int gic_lsolve(gic_handle *h, const gic_pattern *P, const void *valL, int l_dtype, const double *r, double *y,
+               void *ws, size_t ws_bytes)
+{
+    GIC_TRY(check_pattern(h, P));
+    if (!valL || !r || !y || !ws || (l_dtype != GIC_F64 && l_dtype != GIC_F32)) return GIC_ERR_INVALID_ARG;
+    const Pattern &p = P->p;
+    SolveWs W = carve(p, l_dtype, ws);
+    if (ws_bytes < W.bytes) return GIC_ERR_WORKSPACE;
+    k_fill_sentinel<<<vec_grid(h, p.n, 256), 256, 0, h->stream>>>(p.n, y, nullptr);
+    Prof &pr = prof_of(h);
+    if (l_dtype == GIC_F64) {
+        GIC_TRY(setup_factor<double>(h, p, (const double *)valL, (double *)W.Uval, W.invd));
+        PROF_BEGIN(GIC_PROF_LSOLVE);
+        GIC_TRY(launch_lsolve<double>(h, p, (const double *)valL, W.invd, r, y, nullptr));
+        PROF_END(GIC_PROF_LSOLVE);
+    } else {
+        GIC_TRY(setup_factor<float>(h, p, (const float *)valL, (float *)W.Uval, W.invd));
+        PROF_BEGIN(GIC_PROF_LSOLVE);
+        GIC_TRY(launch_lsolve<float>(h, p, (const float *)valL, W.invd, r, y, nullptr));
+        PROF_END(GIC_PROF_LSOLVE);
+    }
+    return GIC_OK;
+}
+
+int gic_ltsolve(gic_handle *h, const gic_pattern *P, const void *valL, int l_dtype, const double *y, double *z,
+                void *ws, size_t ws_bytes)
+{
+    GIC_TRY(check_pattern(h, P));
+    if (!valL || !y || !z || !ws || (l_dtype != GIC_F64 && l_dtype != GIC_F32)) return GIC_ERR_INVALID_ARG;
+    const Pattern &p = P->p;
+    SolveWs W = carve(p, l_dtype, ws);
+    if (ws_bytes < W.bytes) return GIC_ERR_WORKSPACE;
+    k_fill_sentinel<<<vec_grid(h, p.n, 256), 256, 0, h->stream>>>(p.n, z, nullptr);
+    Prof &pr = prof_of(h);
+    double *yy = const_cast<double *>(y); // not written when PCG = false
+    if (l_dtype == GIC_F64) {
+        GIC_TRY(setup_factor<double>(h, p, (const double *)valL, (double *)W.Uval, W.invd));
+        PROF_BEGIN(GIC_PROF_LTSOLVE);
+        GIC_TRY((launch_ltsolve<double, false>(h, p, (const double *)W.Uval, W.invd, yy, z, nullptr, nullptr, nullptr)));
+        PROF_END(GIC_PROF_LTSOLVE);
+    } else {
+        GIC_TRY(setup_factor<float>(h, p, (const float *)valL, (float *)W.Uval, W.invd));
+        PROF_BEGIN(GIC_PROF_LTSOLVE);
+        GIC_TRY((launch_ltsolve<float, false>(h, p, (const float *)W.Uval, W.invd, yy, z, nullptr, nullptr, nullptr)));
+        PROF_END(GIC_PROF_LTSOLVE);
+    }
+    return GIC_OK;
+}
+
+int gic_solve_error_flags(gic_handle *h, unsigned *flags)
+{
+    GIC_TRY(check_handle(h));
+    if (!flags) return GIC_ERR_INVALID_ARG;
+    return read_and_clear_dev_err(h, flags);
+}
+
+int gic_pcg(gic_handle *h, const gic_pattern *P, const double *valA, const void *valL, int l_dtype, const double *b,
+            double *x, double rtol, int maxit, int32_t *iters, double *relres, void *ws, size_t ws_bytes)
+{
+    GIC_TRY(check_pattern(h, P));
+    if (!valA || !b || !x || !ws || maxit < 0 || !(rtol >= 0.0)) return GIC_ERR_INVALID_ARG;
+    if (l_dtype != GIC_IDENTITY && !valL) return GIC_ERR_INVALID_ARG;
+    if (l_dtype != GIC_F64 && l_dtype != GIC_F32 && l_dtype != GIC_IDENTITY) return GIC_ERR_INVALID_ARG;
+    const Pattern &p = P->p;
+    SolveWs W = carve(p, l_dtype, ws);
+    if (ws_bytes < W.bytes) return GIC_ERR_WORKSPACE;
+    if (p.ngroups > 0 && (spmv_grid(h, p.n) > MAX_PARTIALS || vec_grid(h, p.n, VEC_BLOCK) > MAX_PARTIALS))
+        return GIC_ERR_UNSUPPORTED;
+    if (l_dtype == GIC_F32)
+        return pcg_run<float>(h, p, valA, (const float *)valL, 0, b, x, rtol, maxit, iters, relres, W);
+    return pcg_run<double>(h, p, valA, (const double *)valL, l_dtype == GIC_IDENTITY, b, x, rtol, maxit, iters,
+                           relres, W);
+}
+
+int gic_profile_enable(gic_handle *h, int on)
+{
+    GIC_TRY(check_handle(h));
+    Prof &pr = prof_of(h);
+    if (on && !pr.ev[0]) {
+        GIC_CUDA_TRY(cudaEventCreate(&pr.ev[0]));
+        GIC_CUDA_TRY(cudaEventCreate(&pr.ev[1]));
+    }
+    pr.on = on ? 1 : 0;
+    for (int k = 0; k < GIC_PROF_CLASSES; ++k) {
+        pr.ms[k] = 0.0;
+        pr.launches[k] = 0;
+    }
+    return GIC_OK;
+}
+
+int gic_profile_read(gic_handle *h, double *ms, int64_t *launches)
+{
+    GIC_TRY(check_handle(h));
+    Prof &pr = prof_of(h);
+    for (int k = 0; k < GIC_PROF_CLASSES; ++k) {
+        if (ms) ms[k] = pr.ms[k];
+        if (launches) launches[k] = pr.launches[k];
+    }
+    return GIC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,286 @@
+"""ctypes binding of libgicpcg.so (the C-ABI in include/gicpcg.h).
+
+Argument marshalling only: every function takes torch tensors (device memory
+owned by torch) or host scalars, passes raw pointers and sizes through the
+C-ABI, and turns a non-zero status into GicError. There is no fallback: if
+the CUDA library is missing or fails to load, every call raises.
+"""
+import ctypes as C
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgicpcg.so")
+
+GIC_OK = 0
+GIC_ERR_INVALID_ARG = -1
+GIC_ERR_NOT_SPD = -2
+GIC_ERR_NO_CONVERGENCE = -3
+GIC_ERR_TIMEOUT = -4
+GIC_ERR_CUDA = -5
+GIC_ERR_TOO_LARGE = -6
+GIC_ERR_UNSUPPORTED = -7
+GIC_ERR_BREAKDOWN = -8
+GIC_ERR_WORKSPACE = -9
+
+GIC_F64, GIC_F32, GIC_IDENTITY = 0, 1, 2
+GIC_WS_SOLVE, GIC_WS_PCG = 0, 1
+PROF_CLASSES = ("lsolve", "ltsolve", "spmv", "vector")
+
+_vp = C.c_void_p
+_i64 = C.c_int64
+_i32 = C.c_int32
+_int = C.c_int
+_dbl = C.c_double
+_sz = C.c_size_t
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "gic_create": (_int, [C.POINTER(_vp), _int, _vp]),
+    "gic_set_stream": (_int, [_vp, _vp]),
+    "gic_destroy": (_int, [_vp]),
+    "gic_status_string": (C.c_char_p, [_int]),
+    "gic_last_cuda_error": (C.c_char_p, []),
+    "gic_fem_hex_sizes": (_int, [_int, C.POINTER(_i64), C.POINTER(_i64)]),
+    "gic_fem_hex_assemble": (_int, [_vp, _int, _dbl, _int, _vp, _vp, _vp, _vp]),
+    "gic_analyze": (_int, [_vp, _i64, _i64, _vp, _vp, C.POINTER(_vp)]),
+    "gic_pattern_destroy": (_int, [_vp]),
+    "gic_pattern_info": (_int, [_vp, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64),
+                                C.POINTER(_i32), C.POINTER(_i32)]),
+    "gic_pattern_export": (_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "gic_ic0": (_int, [_vp, _vp, _vp, _vp, _dbl, C.POINTER(_i64)]),
+    "gic_ic0_auto": (_int, [_vp, _vp, _vp, _vp, _int, C.POINTER(_dbl), C.POINTER(_i64)]),
+    "gic_convert_f64_f32": (_int, [_vp, _i64, _vp, _vp]),
+    "gic_spmv": (_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "gic_lsolve": (_int, [_vp, _vp, _vp, _int, _vp, _vp, _vp, _sz]),
+    "gic_ltsolve": (_int, [_vp, _vp, _vp, _int, _vp, _vp, _vp, _sz]),
+    "gic_pcg": (_int, [_vp, _vp, _vp, _vp, _int, _vp, _vp, _dbl, _int, C.POINTER(_i32),
+                       C.POINTER(_dbl), _vp, _sz]),
+    "gic_workspace_size": (_int, [_vp, _vp, _int, _int, C.POINTER(_sz)]),
+    "gic_profile_enable": (_int, [_vp, _int]),
+    "gic_profile_read": (_int, [_vp, C.POINTER(_dbl), C.POINTER(_i64)]),
+    "gic_solve_error_flags": (_int, [_vp, C.POINTER(C.c_uint)]),
+}
+
+_lib = None
+
+
+class GicError(RuntimeError):
+    def __init__(self, fn, status):
+        self.status = status
+        text = lib().gic_status_string(status).decode()
+        extra = ""
+        if status == GIC_ERR_CUDA:
+            extra = ": " + lib().gic_last_cuda_error().decode()
+        super().__init__(f"{fn} failed with status {status} ({text}){extra}")
+
+
+def lib():
+    """Load libgicpcg.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library {LIB_PATH} is not built; run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _call(name, *args):
+    st = getattr(lib(), name)(*args)
+    if st != GIC_OK:
+        raise GicError(name, st)
+    return st
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "device tensors must be contiguous CUDA tensors"
+    return _vp(t.data_ptr())
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _vp(s.cuda_stream)
+
+
+class Handle:
+    """A library handle bound to a device and a torch stream."""
+
+    def __init__(self, device=0, stream=None):
+        self.device = device
+        h = _vp()
+        with torch.cuda.device(device):
+            _call("gic_create", C.byref(h), device, _stream_ptr(stream))
+        self.h = h
+
+    def set_stream(self, stream):
+        _call("gic_set_stream", self.h, _stream_ptr(stream))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().gic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Pattern:
+    """Analysis of a symmetric CSR pattern (library-owned device arrays).
+    Keeps references to rowptr/col, which the library borrows."""
+
+    def __init__(self, h: Handle, rowptr, col):
+        assert rowptr.dtype == torch.int32 and col.dtype == torch.int32
+        self.rowptr, self.col = rowptr, col
+        n = rowptr.numel() - 1
+        p = _vp()
+        _call("gic_analyze", h.h, n, col.numel(), _ptr(rowptr), _ptr(col), C.byref(p))
+        self.p = p
+        n_, nA, nL, nl, ng = _i64(), _i64(), _i64(), _i32(), _i32()
+        _call("gic_pattern_info", p, C.byref(n_), C.byref(nA), C.byref(nL), C.byref(nl), C.byref(ng))
+        self.n, self.nnzA, self.nnzL = n_.value, nA.value, nL.value
+        self.nlevels, self.ngroups = nl.value, ng.value
+
+    def export(self, h: Handle):
+        dev = self.rowptr.device
+        Lr = torch.empty(self.n + 1, dtype=torch.int32, device=dev)
+        Lc = torch.empty(self.nnzL, dtype=torch.int32, device=dev)
+        lev = torch.empty(self.n, dtype=torch.int32, device=dev)
+        grp = torch.empty(self.ngroups + 1, dtype=torch.int32, device=dev)
+        _call("gic_pattern_export", h.h, self.p, _ptr(Lr), _ptr(Lc), _ptr(lev), _ptr(grp))
+        return Lr, Lc, lev, grp
+
+    def close(self):
+        if getattr(self, "p", None):
+            lib().gic_pattern_destroy(self.p)
+            self.p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fem_hex_sizes(N):
+    n, nnz = _i64(), _i64()
+    _call("gic_fem_hex_sizes", N, C.byref(n), C.byref(nnz))
+    return n.value, nnz.value
+
+
+def fem_hex_assemble(h: Handle, N, E, nu=0.3, nb=1):
+    """E: float64 device tensor of nb*N^3 element moduli. Returns rowptr, col, val."""
+    n, nnz = fem_hex_sizes(N)
+    dev = E.device
+    rowptr = torch.empty(nb * n + 1, dtype=torch.int32, device=dev)
+    col = torch.empty(nb * nnz, dtype=torch.int32, device=dev)
+    val = torch.empty(nb * nnz, dtype=torch.float64, device=dev)
+    _call("gic_fem_hex_assemble", h.h, N, nu, nb, _ptr(E), _ptr(rowptr), _ptr(col), _ptr(val))
+    return rowptr, col, val
+
+
+def ic0(h: Handle, P: Pattern, valA, alpha=0.0, out=None):
+    """Returns (valL, bad_row); bad_row = -1 on success. Raises on other errors."""
+    valL = out if out is not None else torch.empty(P.nnzL, dtype=torch.float64, device=valA.device)
+    bad = _i64()
+    st = lib().gic_ic0(h.h, P.p, _ptr(valA), _ptr(valL), alpha, C.byref(bad))
+    if st not in (GIC_OK, GIC_ERR_NOT_SPD):
+        raise GicError("gic_ic0", st)
+    return valL, bad.value
+
+
+def ic0_auto(h: Handle, P: Pattern, valA, max_tries=20, out=None):
+    """Returns (valL, alpha, bad_row)."""
+    valL = out if out is not None else torch.empty(P.nnzL, dtype=torch.float64, device=valA.device)
+    a, bad = _dbl(), _i64()
+    st = lib().gic_ic0_auto(h.h, P.p, _ptr(valA), _ptr(valL), max_tries, C.byref(a), C.byref(bad))
+    if st not in (GIC_OK, GIC_ERR_NOT_SPD):
+        raise GicError("gic_ic0_auto", st)
+    return valL, a.value, (bad.value if st != GIC_OK else -1)
+
+
+def to_f32(h: Handle, src):
+    dst = torch.empty(src.numel(), dtype=torch.float32, device=src.device)
+    _call("gic_convert_f64_f32", h.h, src.numel(), _ptr(src), _ptr(dst))
+    return dst
+
+
+def spmv(h: Handle, P: Pattern, valA, x, y=None, with_dot=False):
+    y = y if y is not None else torch.empty_like(x)
+    d = torch.empty(1, dtype=torch.float64, device=x.device) if with_dot else None
+    _call("gic_spmv", h.h, P.p, _ptr(valA), _ptr(x), _ptr(y), _ptr(d))
+    return (y, d) if with_dot else y
+
+
+def workspace(h: Handle, P: Pattern, op, l_dtype):
+    b = _sz()
+    _call("gic_workspace_size", h.h, P.p, op, l_dtype, C.byref(b))
+    return torch.empty(max(b.value, 1), dtype=torch.uint8, device=P.rowptr.device)
+
+
+def _ldtype(valL):
+    if valL is None:
+        return GIC_IDENTITY
+    return {torch.float64: GIC_F64, torch.float32: GIC_F32}[valL.dtype]
+
+
+def lsolve(h: Handle, P: Pattern, valL, r, y=None, ws=None):
+    dt = _ldtype(valL)
+    ws = ws if ws is not None else workspace(h, P, GIC_WS_SOLVE, dt)
+    y = y if y is not None else torch.empty_like(r)
+    _call("gic_lsolve", h.h, P.p, _ptr(valL), dt, _ptr(r), _ptr(y), _ptr(ws), ws.numel())
+    return y
+
+
+def ltsolve(h: Handle, P: Pattern, valL, y, z=None, ws=None):
+    dt = _ldtype(valL)
+    ws = ws if ws is not None else workspace(h, P, GIC_WS_SOLVE, dt)
+    z = z if z is not None else torch.empty_like(y)
+    _call("gic_ltsolve", h.h, P.p, _ptr(valL), dt, _ptr(y), _ptr(z), _ptr(ws), ws.numel())
+    return z
+
+
+def pcg(h: Handle, P: Pattern, valA, valL, b, x=None, rtol=1e-8, maxit=10000, ws=None, check=True):
+    """Supplementary Algorithm 1. valL None = plain CG. Returns dict."""
+    dt = _ldtype(valL)
+    ws = ws if ws is not None else workspace(h, P, GIC_WS_PCG, dt)
+    x = x if x is not None else torch.zeros_like(b)
+    it, rr = _i32(), _dbl()
+    st = lib().gic_pcg(h.h, P.p, _ptr(valA), _ptr(valL), dt, _ptr(b), _ptr(x), rtol, maxit,
+                       C.byref(it), C.byref(rr), _ptr(ws), ws.numel())
+    if check and st not in (GIC_OK, GIC_ERR_NO_CONVERGENCE):
+        raise GicError("gic_pcg", st)
+    return dict(x=x, iters=it.value, relres=rr.value, status=st)
+
+
+def profile_enable(h: Handle, on=True):
+    _call("gic_profile_enable", h.h, 1 if on else 0)
+
+
+def profile_read(h: Handle):
+    ms = (_dbl * len(PROF_CLASSES))()
+    la = (_i64 * len(PROF_CLASSES))()
+    _call("gic_profile_read", h.h, ms, la)
+    return {k: dict(ms=ms[i], launches=la[i]) for i, k in enumerate(PROF_CLASSES)}
+
+
+def error_flags(h: Handle):
+    f = C.c_uint()
+    _call("gic_solve_error_flags", h.h, C.byref(f))
+    return f.value

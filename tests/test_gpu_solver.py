@@ -1,0 +1,360 @@
+"""GPU parity of the solver path (A1-A3, A7) against the CPU oracle, through
+the C-ABI. Integer work (patterns, levels, groups, breakdown rows) must match
+bit for bit; float64 results to round-off; PCG to the stated tolerances:
+same 1e-8 relative residual, ||x_gpu - x_oracle|| / ||x_oracle|| <= 1e-6,
+iteration counts within 2% (at least 1)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2412_07127_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_07127_gb300 import build, gicpcg
+    build.build()
+    return gicpcg
+
+
+@pytest.fixture(scope="module")
+def h(G):
+    return G.Handle(0)
+
+
+def _dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.to(DEV)
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _upload(A):
+    return _dev(A.rowptr), _dev(A.col), _dev(A.val)
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _iters_ok(gi, oi):
+    return abs(gi - oi) <= max(1, int(0.02 * oi))
+
+
+def _spd_pattern(n, density, seed, band=None):
+    rng = np.random.default_rng(seed)
+    M = (rng.random((n, n)) < density) * rng.standard_normal((n, n))
+    if band is not None:
+        i, j = np.indices((n, n))
+        M[np.abs(i - j) > band] = 0
+    S = M + M.T
+    return S + np.diag(np.abs(S).sum(1) + 1.0)
+
+
+# ---------------------------------------------------------------- A1
+@pytest.mark.parametrize("N", [1, 2, 5, 8])
+def test_assemble_matches_oracle(G, h, N):
+    E = I.material_field(N, N)
+    rp, c, v = G.fem_hex_assemble(h, N, _dev(E))
+    A = O.fem_hex_assemble(N, E)
+    assert np.array_equal(_np(rp), A.rowptr) and np.array_equal(_np(c), A.col)
+    assert _rel(_np(v), A.val) <= 1e-13
+
+
+def test_assemble_batched_block_diagonal(G, h):
+    N, nb = 3, 3
+    Es = [I.material_field(N, 100 + k) for k in range(nb)]
+    rp, c, v = G.fem_hex_assemble(h, N, _dev(np.concatenate(Es)), nb=nb)
+    n, nnz = G.fem_hex_sizes(N)
+    rp, c, v = _np(rp), _np(c), _np(v)
+    for k in range(nb):
+        A = O.fem_hex_assemble(N, Es[k])
+        assert np.array_equal(rp[k * n:(k + 1) * n + 1] - k * nnz, A.rowptr)
+        assert np.array_equal(c[k * nnz:(k + 1) * nnz] - k * n, A.col)
+        assert _rel(v[k * nnz:(k + 1) * nnz], A.val) <= 1e-13
+
+
+# ---------------------------------------------------------------- A2
+@pytest.mark.parametrize("N", [1, 2, 5, 8])
+def test_analysis_fem(G, h, N):
+    A = O.fem_hex_assemble(N, I.material_field(N, 1))
+    rp, c, v = _upload(A)
+    P = G.Pattern(h, rp, c)
+    Lr, Lc, lev, grp = (_np(t) for t in P.export(h))
+    T = O.lower(A, with_values=False)
+    olev, onl = O.levels(T)
+    assert np.array_equal(Lr, T.rowptr) and np.array_equal(Lc, T.col)
+    assert np.array_equal(lev, olev) and P.nlevels == onl == 21 * N - 9
+    assert P.ngroups == A.n // 3 and np.array_equal(grp, np.arange(0, A.n + 1, 3))
+
+
+@pytest.mark.parametrize("case", ["random", "banded", "tridiag", "diag"])
+def test_analysis_generic(G, h, case):
+    if case == "random":
+        D = _spd_pattern(300, 0.02, 1)
+    elif case == "banded":
+        D = _spd_pattern(400, 0.3, 2, band=6)
+    elif case == "tridiag":
+        D = 4 * np.eye(3000) - np.eye(3000, k=1) - np.eye(3000, k=-1)
+    else:
+        D = np.diag(np.arange(1.0, 501.0))
+    A = O.csr_from_dense(D)
+    rp, c, v = _upload(A)
+    P = G.Pattern(h, rp, c)
+    Lr, Lc, lev, grp = (_np(t) for t in P.export(h))
+    T = O.lower(A, with_values=False)
+    olev, onl = O.levels(T)
+    assert np.array_equal(Lr, T.rowptr) and np.array_equal(Lc, T.col)
+    assert np.array_equal(lev, olev) and P.nlevels == onl
+    # groups: runs of rows with identical column sets, cut every 8 rows
+    starts, run = [], 0
+    for i in range(A.n):
+        if i == 0 or not np.array_equal(A.col[A.rowptr[i - 1]:A.rowptr[i]], A.col[A.rowptr[i]:A.rowptr[i + 1]]):
+            run = i
+        if (i - run) % 8 == 0:
+            starts.append(i)
+    assert np.array_equal(grp, np.array(starts + [A.n]))
+
+
+def test_analysis_rejects_bad_patterns(G, h):
+    D = _spd_pattern(50, 0.1, 3)
+    A = O.csr_from_dense(D)
+    # asymmetric: drop one off-diagonal entry of row 0
+    row0 = [p for p in range(A.rowptr[0], A.rowptr[1]) if A.col[p] != 0]
+    drop = row0[0]
+    col = np.delete(A.col, drop)
+    rowptr = A.rowptr.copy()
+    rowptr[1:] -= 1
+    with pytest.raises(G.GicError) as e:
+        G.Pattern(h, _dev(rowptr), _dev(col))
+    assert e.value.status == G.GIC_ERR_INVALID_ARG
+    # unsorted columns in a row
+    col = A.col.copy()
+    a, b = A.rowptr[5], A.rowptr[6]
+    col[a:b] = col[a:b][::-1]
+    with pytest.raises(G.GicError) as e:
+        G.Pattern(h, _dev(A.rowptr), _dev(col))
+    assert e.value.status == G.GIC_ERR_INVALID_ARG
+    # missing diagonal
+    D2 = D.copy()
+    D2[7, 7] = 0.0
+    rp, cl = [0], []
+    for i in range(50):
+        cl += [j for j in range(50) if D2[i, j] != 0]
+        rp.append(len(cl))
+    with pytest.raises(G.GicError) as e:
+        G.Pattern(h, _dev(np.array(rp, np.int32)), _dev(np.array(cl, np.int32)))
+    assert e.value.status == G.GIC_ERR_INVALID_ARG
+
+
+# ---------------------------------------------------------------- A3
+@pytest.mark.parametrize("N", [1, 2, 8, 12])
+def test_ic0_matches_oracle(G, h, N):
+    A = O.fem_hex_assemble(N, I.material_field(N, 3))
+    rp, c, v = _upload(A)
+    P = G.Pattern(h, rp, c)
+    Lg, bad = G.ic0(h, P, v)
+    Lo, obad = O.ic0(A)
+    assert bad == obad == -1
+    assert _rel(_np(Lg), Lo.val) <= 1e-11
+
+
+@pytest.mark.parametrize("case", ["random", "banded", "tridiag", "diag"])
+def test_ic0_generic(G, h, case):
+    if case == "random":
+        D = _spd_pattern(300, 0.02, 1)
+    elif case == "banded":
+        D = _spd_pattern(400, 0.3, 2, band=6)
+    elif case == "tridiag":
+        D = 4 * np.eye(3000) - np.eye(3000, k=1) - np.eye(3000, k=-1)
+    else:
+        D = np.diag(np.arange(1.0, 501.0))
+    A = O.csr_from_dense(D)
+    rp, c, v = _upload(A)
+    P = G.Pattern(h, rp, c)
+    Lg, bad = G.ic0(h, P, v)
+    Lo, obad = O.ic0(A)
+    assert bad == obad == -1
+    assert _rel(_np(Lg), Lo.val) <= 1e-11
+
+
+def test_ic0_breakdown_row_and_shift(G, h):
+    """Seeds whose IC(0) breaks down in the oracle (lognormal sigma = 2.5):
+    same first failing row, same shift, same shifted factor."""
+    found = 0
+    for seed in range(40):
+        N = 4
+        E = I.material_field(N, seed, sigma=2.5)
+        A = O.fem_hex_assemble(N, E)
+        Lo, obad = O.ic0(A)
+        if obad < 0:
+            continue
+        found += 1
+        rp, c, v = _upload(A)
+        P = G.Pattern(h, rp, c)
+        _, bad = G.ic0(h, P, v)
+        assert bad == obad
+        Lg, alpha, bad2 = G.ic0_auto(h, P, v)
+        Lo2, oalpha, obad2 = O.ic0_auto(A)
+        assert alpha == oalpha and bad2 == obad2 == -1
+        assert _rel(_np(Lg), Lo2.val) <= 1e-11
+        if found == 3:
+            break
+    assert found >= 1
+
+
+# ---------------------------------------------------------------- A7 kernels
+def test_spmv_matches_oracle(G, h):
+    N = 8
+    A = O.fem_hex_assemble(N, I.material_field(N, 4))
+    rp, c, v = _upload(A)
+    P = G.Pattern(h, rp, c)
+    x = np.random.default_rng(0).standard_normal(A.n)
+    y, d = G.spmv(h, P, v, _dev(x), with_dot=True)
+    yo = O.spmv(A, x)
+    assert _rel(_np(y), yo) <= 1e-13
+    assert abs(_np(d)[0] - x @ yo) <= 1e-12 * abs(x @ yo)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("case", ["fem8", "random", "tridiag"])
+def test_triangular_solves_match_oracle(G, h, dtype, case):
+    if case == "fem8":
+        A = O.fem_hex_assemble(8, I.material_field(8, 5))
+    elif case == "random":
+        A = O.csr_from_dense(_spd_pattern(300, 0.02, 1))
+    else:
+        A = O.csr_from_dense(4 * np.eye(3000) - np.eye(3000, k=1) - np.eye(3000, k=-1))
+    Lo, _ = O.ic0(A)
+    # the factor the GPU sees, exactly, in float64 for the oracle
+    Lval = Lo.val.astype(np.float32).astype(np.float64) if dtype == torch.float32 else Lo.val
+    Lref = O.CSR(Lo.rowptr, Lo.col, Lval)
+    rp, c, v = _upload(A)
+    P = G.Pattern(h, rp, c)
+    Ld = _dev(Lval).to(dtype)
+    r = np.random.default_rng(2).uniform(-1, 1, A.n)
+    y = G.lsolve(h, P, Ld, _dev(r))
+    z = G.ltsolve(h, P, Ld, y)
+    yo = O.lsolve(Lref, r)
+    zo = O.ltsolve(Lref, yo)
+    assert _rel(_np(y), yo) <= 1e-11
+    assert _rel(_np(z), zo) <= 1e-11
+    assert G.error_flags(h) == 0
+
+
+# ---------------------------------------------------------------- A7 PCG
+@pytest.mark.parametrize("N", [2, 4, 8, 12])
+def test_pcg_matches_oracle(G, h, N):
+    E = I.material_field(N, 7)
+    A = O.fem_hex_assemble(N, E)
+    b = I.rhs(A.n, 7)
+    rp, c, v = _upload(A)
+    P = G.Pattern(h, rp, c)
+    Lg, bad = G.ic0(h, P, v)
+    res = G.pcg(h, P, v, Lg, _dev(b), rtol=1e-8)
+    Lo, _ = O.ic0(A)
+    ro = O.pcg(A, b, Lo, tol=1e-8)
+    assert res["status"] == 0 and ro["status"] == 0
+    assert _iters_ok(res["iters"], ro["iters"]), (res["iters"], ro["iters"])
+    assert res["relres"] <= 1e-8
+    x = _np(res["x"])
+    assert np.linalg.norm(x - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
+    true_rel = np.linalg.norm(b - O.spmv(A, x)) / np.linalg.norm(b)
+    assert true_rel <= 1e-7
+
+
+def test_plain_cg_matches_oracle(G, h):
+    N = 4
+    A = O.fem_hex_assemble(N, I.material_field(N, 8))
+    b = I.rhs(A.n, 8)
+    rp, c, v = _upload(A)
+    P = G.Pattern(h, rp, c)
+    res = G.pcg(h, P, v, None, _dev(b), rtol=1e-8)
+    ro = O.pcg(A, b, None, tol=1e-8)
+    assert _iters_ok(res["iters"], ro["iters"]), (res["iters"], ro["iters"])
+    x = _np(res["x"])
+    assert np.linalg.norm(x - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
+
+
+def test_pcg_f32_factor(G, h):
+    N = 8
+    A = O.fem_hex_assemble(N, I.material_field(N, 9))
+    b = I.rhs(A.n, 9)
+    Lo, _ = O.ic0(A)
+    L32 = O.CSR(Lo.rowptr, Lo.col, Lo.val.astype(np.float32).astype(np.float64))
+    rp, c, v = _upload(A)
+    P = G.Pattern(h, rp, c)
+    Lg, _ = G.ic0(h, P, v)
+    res = G.pcg(h, P, v, G.to_f32(h, Lg), _dev(b), rtol=1e-8)
+    ro = O.pcg(A, b, L32, tol=1e-8)
+    assert _iters_ok(res["iters"], ro["iters"]), (res["iters"], ro["iters"])
+    x = _np(res["x"])
+    assert np.linalg.norm(x - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
+
+
+def test_pcg_edge_cases(G, h):
+    N = 3
+    A = O.fem_hex_assemble(N, I.material_field(N, 1))
+    rp, c, v = _upload(A)
+    P = G.Pattern(h, rp, c)
+    Lg, _ = G.ic0(h, P, v)
+    # b = 0: no iteration, x = 0
+    res = G.pcg(h, P, v, Lg, torch.zeros(A.n, dtype=torch.float64, device=DEV))
+    assert res["iters"] == 0 and res["status"] == 0 and torch.all(res["x"] == 0)
+    # x0 already the solution
+    b = I.rhs(A.n, 1)
+    xs = np.linalg.solve(A.to_dense(), b)
+    res = G.pcg(h, P, v, Lg, _dev(b), x=_dev(xs), rtol=1e-8)
+    assert res["iters"] == 0
+    # iteration cap
+    res = G.pcg(h, P, v, Lg, _dev(b), rtol=1e-14, maxit=3)
+    assert res["status"] == G.GIC_ERR_NO_CONVERGENCE and res["iters"] == 3
+    Lo, _ = O.ic0(A)
+    ro = O.pcg(A, b, Lo, tol=1e-14, maxit=3)
+    assert np.linalg.norm(_np(res["x"]) - ro["x"]) <= 1e-9 * np.linalg.norm(ro["x"])
+
+
+def test_pcg_deterministic(G, h):
+    N = 8
+    A = O.fem_hex_assemble(N, I.material_field(N, 2))
+    b = _dev(I.rhs(A.n, 2))
+    rp, c, v = _upload(A)
+    P = G.Pattern(h, rp, c)
+    Lg, _ = G.ic0(h, P, v)
+    r1 = G.pcg(h, P, v, Lg, b)
+    r2 = G.pcg(h, P, v, Lg, b)
+    assert r1["iters"] == r2["iters"] and torch.equal(r1["x"], r2["x"])
+
+
+def test_full_size_40_cube(G, h):
+    """The 40^3-element system (201,720 dofs, 15.5M nonzeros) the benchmark
+    times: assembly, analysis, IC(0) and PCG against the oracle."""
+    N = 40
+    E = I.material_field(N, 0)
+    b = I.rhs(3 * N * (N + 1) ** 2, 0)
+    rp, c, v = G.fem_hex_assemble(h, N, _dev(E))
+    A = O.fem_hex_assemble(N, E)
+    assert np.array_equal(_np(rp), A.rowptr) and np.array_equal(_np(c), A.col)
+    assert _rel(_np(v), A.val) <= 1e-13
+    P = G.Pattern(h, rp, c)
+    assert P.nlevels == 21 * N - 9 and P.ngroups == A.n // 3
+    Lg, alpha, bad = G.ic0_auto(h, P, v)
+    Lo, oalpha, obad = O.ic0_auto(A)
+    assert alpha == oalpha and bad == obad == -1
+    assert _rel(_np(Lg), Lo.val) <= 1e-10
+    res = G.pcg(h, P, v, Lg, _dev(b), rtol=1e-8)
+    ro = O.pcg(A, b, Lo, tol=1e-8)
+    assert _iters_ok(res["iters"], ro["iters"]), (res["iters"], ro["iters"])
+    x = _np(res["x"])
+    assert np.linalg.norm(x - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
