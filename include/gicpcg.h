@@ -170,6 +170,105 @@ int gic_profile_read(gic_handle *h, double *ms, int64_t *launches);
  * bit 0: a bounded wait ran out). Synchronous. */
 int gic_solve_error_flags(gic_handle *h, unsigned *flags);
 
+/* ------------------------------------------------- A4-A6: the GNN correction
+ * A batch is a block-diagonal pattern of `ngraphs` graphs of equal size
+ * (n divisible by ngraphs; ngraphs = 1 for one matrix). Per-graph statistics
+ * (the scale s, GraphNorm) are computed per graph.
+ * Parameters (theta, float32, gic_gnn_param_count() = 3504 values):
+ *   GraphNorm gamma[9], beta[9], alpha[9]; then for block l = 0,1,2 the edge
+ *   MLP W1[32][20], b1[32], W2[32], b2[1], and for l = 0,1 the node MLP
+ *   W3[32][11], b3[32], W4[9][32], b4[9]. */
+int gic_gnn_param_count(void);
+/* Graph inputs (Model Architecture; Supplementary 4, Table 2): per graph
+ * s = population standard deviation of tril(A)'s stored values; edge feature
+ * e0 = a_ij / s on L's pattern (nnzL float32, device); node features x9
+ * (n x 9 float32, device): degree, max/min/mean/variance of the neighbours'
+ * degrees, dominance |a_ii| / sum_{j!=i} |a_ij|, decay |a_ii| / max_{j!=i}
+ * |a_ij|, sin(i) and cos(i) of the row index within its graph (0 where a
+ * denominator or the neighbour set is empty). Ahat (nullable, nnzA float32)
+ * receives A / s. scale_dev (device, ngraphs float64) receives s;
+ * scale_host (nullable, host) too, then the call synchronises. */
+int gic_features(gic_handle *h, const gic_pattern *P, int ngraphs, const double *valA, float *x9,
+                 float *e0, float *Ahat, double *scale_dev, double *scale_host);
+/* Workspace (bytes, host output) of gic_gnn_forward (training = 0) or of
+ * gic_gnn_forward_train + gic_gnn_backward (training = 1). */
+int gic_gnn_workspace_size(gic_handle *h, const gic_pattern *P, int ngraphs, int training,
+                           size_t *bytes);
+/* g = GNN(A) on L's pattern (Eq.(7)-(9); Model Architecture): GraphNorm of
+ * x9, then 3 blocks of edge MLP 20->32->1 (tanh) on [e_cur, e0, x_i, x_j],
+ * sum and mean of the new edge values over each node's incident edges (a
+ * self-loop once), node MLP 11->32->9 (tanh) on [x, sum, mean] (none in the
+ * last block). theta, x9, e0: device float32; g: device float32 (nnzL).
+ * FP32 arithmetic. */
+int gic_gnn_forward(gic_handle *h, const gic_pattern *P, int ngraphs, const float *theta,
+                    const float *x9, const float *e0, float *g, void *ws, size_t ws_bytes);
+/* Same forward, keeping every layer's activations in ws for gic_gnn_backward. */
+int gic_gnn_forward_train(gic_handle *h, const gic_pattern *P, int ngraphs, const float *theta,
+                          const float *x9, const float *e0, float *g, void *ws, size_t ws_bytes);
+/* dtheta (device float32, 3504) = d(loss)/d(theta) given dg = d(loss)/dg,
+ * after gic_gnn_forward_train with the same inputs and ws. Deterministic. */
+int gic_gnn_backward(gic_handle *h, const gic_pattern *P, int ngraphs, const float *theta,
+                     const float *x9, const float *e0, const float *dg, float *dtheta, void *ws,
+                     size_t ws_bytes);
+/* Eq.(2) with the exp-then-sqrt diagonal map, original units, float64:
+ * Lout_ij = LIC_ij + sqrt(s) g_ij (i > j), Lout_ii = LIC_ii exp(g_ii / 2).
+ * *diag_ok (host, nullable; the call then synchronises) = 1 if every
+ * diagonal is positive and finite (else the caller keeps LIC). */
+int gic_gnn_correct(gic_handle *h, const gic_pattern *P, int ngraphs, const double *LIC,
+                    const float *g, const double *scale_dev, double *Lout, int *diag_ok);
+/* LIChat = LIC / sqrt(s) per graph (float32): the factor in units scaled by s. */
+int gic_scale_factor(gic_handle *h, const gic_pattern *P, int ngraphs, const double *LIC,
+                     const double *scale_dev, float *LIChat);
+/* Correction in scaled units, float32: Lhat = LIChat + g, diagonal
+ * LIChat exp(g / 2); and its backward dg = dLhat (off-diagonal),
+ * dLhat * Lhat / 2 (diagonal). */
+int gic_gnn_correct_scaled(gic_handle *h, const gic_pattern *P, const float *LIChat, const float *g,
+                           float *Lhat);
+int gic_gnn_correct_backward(gic_handle *h, const gic_pattern *P, const float *Lhat,
+                             const float *dLhat, float *dg);
+
+/* ------------------------------------------------- A8-A10: training
+ * Probe (Hutchinson) loss of Eq.(4)-(5) with the index/value products of
+ * Algorithms 1-2, in scaled units: per graph
+ *   loss_g = (1/m) sum_k || Lhat (Lhat^T z_k) - Ahat z_k ||_2^2
+ * and loss[ngraphs] = their mean. Ahat: nnzA float32 (A / s); Lhat: nnzL
+ * float32; Z: m x n float32 probes (probe k at Z + k*n), 1 <= m <= 16;
+ * loss: device float32, ngraphs + 1 values. dLhat (nullable, nnzL float32)
+ * receives d loss[ngraphs] / d Lhat on the pattern:
+ *   (2 / (m ngraphs)) sum_k (v_k,i u_k,j + z_k,i w_k,j),
+ * u = Lhat^T z, v = Lhat u - Ahat z, w = Lhat^T v. */
+int gic_probe_workspace_size(gic_handle *h, const gic_pattern *P, int ngraphs, int m, size_t *bytes);
+int gic_probe_loss(gic_handle *h, const gic_pattern *P, int ngraphs, const float *Ahat,
+                   const float *Lhat, const float *Z, int m, float *loss, float *dLhat, void *ws,
+                   size_t ws_bytes);
+/* One Adam step (Training and Inference: Adam with warm-up; beta1 0.9,
+ * beta2 0.999, eps 1e-8, bias-corrected, t = 1-based step) on np float32
+ * values in place (theta, first and second moments m1, m2). */
+int gic_adam_step(gic_handle *h, int64_t np, float *theta, const float *grad, float *m1,
+                  float *m2, int t, double lr);
+
+/* Number of kernels this handle has launched so far (host output). */
+int gic_launch_count(gic_handle *h, int64_t *count);
+
+/* ------------------------------------------------- end to end
+ * The paper's black-box use of PCG (Supplementary 2): A and b in host memory
+ * in, x in host memory out. Copies A (CSR: rowptr n+1, col nnz int32; val
+ * nnz float64) and b (n float64) to the device, analyses the pattern,
+ * factors IC(0) with the shift restart, corrects L with the GNN when theta
+ * (host float32, gic_gnn_param_count() values) is non-NULL, runs PCG from
+ * x0 = 0 with the factor in l_dtype precision (GIC_F64 or GIC_F32) and copies
+ * x (n float64) back. Host buffers may be pageable or pinned. ws: device
+ * workspace of gic_solve_host_workspace_size() bytes. Host outputs: iters,
+ * relres, and (nullable) alpha = the IC(0) shift used and used_gnn = 1 if the
+ * corrected factor was kept (0 if it fell back to plain IC(0) because its
+ * diagonal was not positive and finite). Synchronous. */
+int gic_solve_host(gic_handle *h, int64_t n, int64_t nnz, const int32_t *rowptr, const int32_t *col,
+                   const double *val, const double *b, double *x, const float *theta, int l_dtype,
+                   double rtol, int maxit, int32_t *iters, double *relres, double *alpha,
+                   int *used_gnn, void *ws, size_t ws_bytes);
+int gic_solve_host_workspace_size(gic_handle *h, int64_t n, int64_t nnz, int with_gnn, int l_dtype,
+                                  size_t *bytes);
+
 /* Workspace sizes (host output, bytes) of the calls that take one. */
 #define GIC_WS_SOLVE 0 /* gic_lsolve / gic_ltsolve */
 #define GIC_WS_PCG 1   /* gic_pcg */

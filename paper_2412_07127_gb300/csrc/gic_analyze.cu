@@ -113,8 +113,11 @@ static int scan_i32(gic_handle *h, const int32_t *in, int64_t n, int32_t *out, l
     long long *tmp = nullptr;
     GIC_CUDA_TRY(cudaMalloc(&tmp, sizeof(long long) * (size_t)(n + nb + 1)));
     long long *incl = tmp, *bsum = tmp + n, *total = tmp + n + nb;
+    ++h->launches;
     k_scan_blocks<MAX><<<(unsigned)nb, SCAN_BLOCK, 0, h->stream>>>(in, n, incl, bsum);
+    ++h->launches;
     k_scan_totals<MAX><<<1, SCAN_BLOCK, 0, h->stream>>>(bsum, nb, total);
+    ++h->launches;
     k_scan_finish<MAX><<<(unsigned)nb, SCAN_BLOCK, 0, h->stream>>>(in, n, incl, bsum, out, MAX ? 0 : 1, total);
     cudaError_t e = cudaGetLastError();
     long long t = 0;
@@ -200,6 +203,12 @@ __global__ void k_fill_L(int64_t n, const int32_t *rowptr, const int32_t *col, c
         for (int32_t k = 0; k < lc; ++k) Lcol[lb + k] = col[a + k];
         Ucnt[i] = rowptr[i + 1] - a - lc + 1;
     }
+}
+
+__global__ void k_fill_Lrow(int64_t n, const int32_t *Lrowptr, int32_t *Lrow)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        for (int32_t p = Lrowptr[i]; p < Lrowptr[i + 1]; ++p) Lrow[p] = (int32_t)i;
 }
 
 __global__ void k_fill_U(int64_t n, const int32_t *rowptr, const int32_t *col, const int32_t *Lrowptr,
@@ -327,6 +336,7 @@ int launch_persistent(gic_handle *h, const void *fn, int block, size_t smem, int
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    ++h->launches;
     GIC_CUDA_TRY(cudaLaunchKernelExC(&cfg, fn, args));
     return GIC_OK;
 }
@@ -344,6 +354,7 @@ static void free_pattern(Pattern &p)
     cudaFree(p.tperm);
     cudaFree(p.grp);
     cudaFree(p.level);
+    cudaFree(p.Lrow);
     p = Pattern();
 }
 
@@ -367,11 +378,13 @@ static int analyze_impl(gic_handle *h, int64_t n, int64_t nnz, const int32_t *ro
 #define CUDA_STEP(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { set_last_cuda_error(e_, #x, __FILE__, __LINE__); rc = GIC_ERR_CUDA; goto out; } } while (0)
     CUDA_STEP(cudaMemsetAsync(h->dev_err, 0, sizeof(unsigned), h->stream));
     CUDA_STEP(cudaMemsetAsync(stats, 0, sizeof(int32_t) * 8, h->stream));
+    ++h->launches;
     k_validate<<<gr, T_ROWS, 0, h->stream>>>(n, nnz, rowptr, col, Lcnt, same, h->dev_err);
     CUDA_STEP(cudaGetLastError());
     STEP(read_and_clear_dev_err(h, &flags));
     if (flags) { rc = GIC_ERR_INVALID_ARG; goto out; }
     // only once every row is known to be in bounds
+    ++h->launches;
     k_symcheck<<<gr, T_ROWS, 0, h->stream>>>(n, rowptr, col, h->dev_err);
     CUDA_STEP(cudaGetLastError());
     STEP(read_and_clear_dev_err(h, &flags));
@@ -381,23 +394,33 @@ static int analyze_impl(gic_handle *h, int64_t n, int64_t nnz, const int32_t *ro
     STEP(scan_i32<false>(h, Lcnt, n, P.Lrowptr, &tot));
     P.nnzL = tot;
     CUDA_STEP(cudaMalloc(&P.Lcol, sizeof(int32_t) * (size_t)(P.nnzL > 0 ? P.nnzL : 1)));
+    ++h->launches;
     k_fill_L<<<gr, T_ROWS, 0, h->stream>>>(n, rowptr, col, P.Lrowptr, P.Lcol, Ucnt);
     CUDA_STEP(cudaGetLastError());
+    CUDA_STEP(cudaMalloc(&P.Lrow, sizeof(int32_t) * (size_t)(P.nnzL > 0 ? P.nnzL : 1)));
+    ++h->launches;
+    k_fill_Lrow<<<gr, T_ROWS, 0, h->stream>>>(n, P.Lrowptr, P.Lrow);
     CUDA_STEP(cudaMalloc(&P.Urowptr, sizeof(int32_t) * (size_t)(n + 1)));
     STEP(scan_i32<false>(h, Ucnt, n, P.Urowptr, &tot));
     if (tot != P.nnzL) { rc = GIC_ERR_INVALID_ARG; goto out; }
     CUDA_STEP(cudaMalloc(&P.Ucol, sizeof(int32_t) * (size_t)(P.nnzL > 0 ? P.nnzL : 1)));
     CUDA_STEP(cudaMalloc(&P.tperm, sizeof(int32_t) * (size_t)(P.nnzL > 0 ? P.nnzL : 1)));
+    ++h->launches;
     k_fill_U<<<gr, T_ROWS, 0, h->stream>>>(n, rowptr, col, P.Lrowptr, P.Urowptr, P.Ucol, P.tperm);
     CUDA_STEP(cudaGetLastError());
 
+    ++h->launches;
+
     k_run_keys<<<gr, T_ROWS, 0, h->stream>>>(n, same, key);
     STEP(scan_i32<true>(h, key, n, runstart, nullptr));
+    ++h->launches;
     k_group_flags<<<gr, T_ROWS, 0, h->stream>>>(n, runstart, gflag);
     STEP(scan_i32<false>(h, gflag, n, gid, &tot));
     P.ngroups = (int32_t)tot;
     CUDA_STEP(cudaMalloc(&P.grp, sizeof(int32_t) * (size_t)(P.ngroups + 1)));
+    ++h->launches;
     k_group_starts<<<gr, T_ROWS, 0, h->stream>>>(n, gflag, gid, P.grp, P.ngroups);
+    ++h->launches;
     k_group_stats<<<grid_rows(h, P.ngroups), T_ROWS, 0, h->stream>>>(P.ngroups, P.grp, P.Lrowptr, P.Urowptr, stats);
     CUDA_STEP(cudaGetLastError());
 

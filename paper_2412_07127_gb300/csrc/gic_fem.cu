@@ -147,10 +147,12 @@ int gic_fem_hex_assemble(gic_handle *h, int N, double nu, int nb, const double *
     if (nb < 1 || !E || !rowptr || !col || !val || !(nu > -1.0 && nu < 0.5)) return GIC_ERR_INVALID_ARG;
     if (nnz1 * nb >= (1ll << 31)) return GIC_ERR_TOO_LARGE;
     double *Ke = (double *)h->dev_small;
+    ++h->launches;
     k_element_matrix<<<1, 576, 0, h->stream>>>(nu, 1.0 / N, Ke);
     int64_t rows = n1 * nb;
     int64_t blocks = (rows + 255) / 256;
     if (blocks > (int64_t)h->num_sms * 32) blocks = (int64_t)h->num_sms * 32;
+    ++h->launches;
     k_assemble<<<(unsigned)blocks, 256, 0, h->stream>>>(N, nb, E, Ke, rowptr, col, val, n1, nnz1);
     GIC_CUDA_TRY(cudaGetLastError());
     return GIC_OK;

@@ -204,6 +204,7 @@ static int ic0_once(gic_handle *h, const Pattern &P, const double *valA, double 
     unsigned long long *bad_dev = (unsigned long long *)((char *)h->dev_small + 60000);
     int64_t blocks = (P.n + 255) / 256;
     if (blocks > (int64_t)h->num_sms * 8) blocks = (int64_t)h->num_sms * 8;
+    ++h->launches;
     k_ic0_prepare<<<(unsigned)blocks, 256, 0, h->stream>>>(P.n, P.Lrowptr, valL, bad_dev);
     GIC_CUDA_TRY(cudaGetLastError());
     size_t smem = sizeof(IcWarpSmem) * IC_WARPS;

@@ -116,6 +116,7 @@ struct Pattern {
     // groups of consecutive rows with identical A patterns (<= GMAX rows)
     int32_t *grp = nullptr;   // ngroups+1 start rows
     int32_t *level = nullptr; // n row levels
+    int32_t *Lrow = nullptr;  // nnzL: row of every L entry (edge -> its row node)
     int device = 0;
 };
 
@@ -135,9 +136,14 @@ struct gic_handle {
     unsigned *dev_err = nullptr;   // device error flags
     void *dev_small = nullptr;     // 64 KiB of library scratch (scalars, Ke)
     void *host_pinned = nullptr;   // 4 KiB pinned readback area
+    long long launches = 0;        // kernels this handle has launched
 };
 
 namespace gic {
+size_t pcg_ws_bytes(int64_t n, int64_t nnzL, int l_dtype);
+size_t gnn_infer_ws_bytes(int64_t n, int64_t nnzL);
+int gnn_correct_inplace(gic_handle *h, const gic_pattern *P, const double *valA, const float *theta_host,
+                        double *L, void *ws, size_t ws_bytes, int *kept);
 int check_handle(gic_handle *h);
 int read_and_clear_dev_err(gic_handle *h, unsigned *flags);
 }

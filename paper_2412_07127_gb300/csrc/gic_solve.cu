@@ -444,6 +444,14 @@ static SolveWs carve(const Pattern &P, int l_dtype, void *ws)
     return o;
 }
 
+size_t pcg_ws_bytes(int64_t n, int64_t nnzL, int l_dtype)
+{
+    Pattern P;
+    P.n = n;
+    P.nnzL = nnzL;
+    return carve(P, l_dtype, nullptr).bytes;
+}
+
 static unsigned vec_grid(gic_handle *h, int64_t n, int block)
 {
     int64_t b = (n + block - 1) / block;
@@ -491,33 +499,58 @@ template <typename TL>
 static int setup_factor(gic_handle *h, const Pattern &P, const TL *Lval, TL *Uval, double *invd)
 {
     int64_t cnt = P.nnzL > P.n ? P.nnzL : P.n;
+    ++h->launches;
     k_transpose_vals<TL><<<vec_grid(h, cnt, 256), 256, 0, h->stream>>>(P.n, P.nnzL, P.tperm, P.Lrowptr, Lval, Uval, invd);
     GIC_CUDA_TRY(cudaGetLastError());
     return GIC_OK;
 }
 
-// Optional per-kernel-class timing of gic_pcg (CUDA events on the handle's
-// stream around every launch; the loop then synchronises every iteration).
+// Optional per-kernel-class timing: while enabled, a pair of CUDA events is
+// recorded on the handle's stream around every solve-path launch (no host
+// synchronisation), and the elapsed times are summed into the classes when a
+// call finishes (or the event pool fills).
 struct Prof {
     int on = 0;
-    cudaEvent_t ev[2] = {nullptr, nullptr};
+    int used = 0;
+    static constexpr int CAP = 8192;
+    cudaEvent_t ev[CAP] = {};
+    int cls[CAP / 2] = {};
     double ms[GIC_PROF_CLASSES] = {0};
     long long launches[GIC_PROF_CLASSES] = {0};
 };
-static Prof g_prof[64];
+static Prof *g_prof[64];
 
-static Prof &prof_of(gic_handle *h) { return g_prof[h->device & 63]; }
+static Prof &prof_of(gic_handle *h)
+{
+    Prof *&p = g_prof[h->device & 63];
+    if (!p) p = new Prof();
+    return *p;
+}
 
-#define PROF_BEGIN(cls)                                                                    \
-    if (pr.on) GIC_CUDA_TRY(cudaEventRecord(pr.ev[0], h->stream));
-#define PROF_END(cls)                                                                      \
-    if (pr.on) {                                                                           \
-        GIC_CUDA_TRY(cudaEventRecord(pr.ev[1], h->stream));                                \
-        GIC_CUDA_TRY(cudaEventSynchronize(pr.ev[1]));                                      \
-        float t_ = 0.f;                                                                    \
-        GIC_CUDA_TRY(cudaEventElapsedTime(&t_, pr.ev[0], pr.ev[1]));                       \
-        pr.ms[cls] += t_;                                                                  \
-        pr.launches[cls] += 1;                                                             \
+static int prof_flush(gic_handle *h, Prof &pr)
+{
+    if (pr.used == 0) return GIC_OK;
+    GIC_CUDA_TRY(cudaEventSynchronize(pr.ev[pr.used - 1]));
+    for (int k = 0; k + 1 < pr.used; k += 2) {
+        float t = 0.f;
+        GIC_CUDA_TRY(cudaEventElapsedTime(&t, pr.ev[k], pr.ev[k + 1]));
+        pr.ms[pr.cls[k / 2]] += t;
+        pr.launches[pr.cls[k / 2]] += 1;
+    }
+    pr.used = 0;
+    return GIC_OK;
+}
+
+#define PROF_BEGIN(c)                                                              \
+    if (pr.on) {                                                                   \
+        if (pr.used + 2 > Prof::CAP) GIC_TRY(prof_flush(h, pr));                   \
+        GIC_CUDA_TRY(cudaEventRecord(pr.ev[pr.used], h->stream));                  \
+        pr.cls[pr.used / 2] = (c);                                                 \
+    }
+#define PROF_END(c)                                                                \
+    if (pr.on) {                                                                   \
+        GIC_CUDA_TRY(cudaEventRecord(pr.ev[pr.used + 1], h->stream));              \
+        pr.used += 2;                                                              \
     }
 
 // One PCG iteration: lines 11-18 of Algorithm 1 and the stop test.
@@ -529,7 +562,9 @@ static int pcg_iteration(gic_handle *h, const Pattern &P, const double *valA, co
     Prof &pr = prof_of(h);
     if (ident) {
         PROF_BEGIN(GIC_PROF_VECTOR);
+        ++h->launches;
         k_ident_rz<<<vec_grid(h, n, VEC_BLOCK), VEC_BLOCK, 0, h->stream>>>(n, W.r, W.partials, W.sc);
+        ++h->launches;
         k_update_p<true><<<vec_grid(h, n, VEC_BLOCK), VEC_BLOCK, 0, h->stream>>>(n, W.z, W.p, W.r, W.partials, W.sc);
         GIC_CUDA_TRY(cudaGetLastError());
         PROF_END(GIC_PROF_VECTOR);
@@ -541,16 +576,19 @@ static int pcg_iteration(gic_handle *h, const Pattern &P, const double *valA, co
         GIC_TRY((launch_ltsolve<TL, true>(h, P, (const TL *)W.Uval, W.invd, W.y, W.z, W.r, W.partials, W.sc)));
         PROF_END(GIC_PROF_LTSOLVE);
         PROF_BEGIN(GIC_PROF_VECTOR);
+        ++h->launches;
         k_update_p<false><<<vec_grid(h, n, VEC_BLOCK), VEC_BLOCK, 0, h->stream>>>(n, W.z, W.p, W.r, W.partials, W.sc);
         GIC_CUDA_TRY(cudaGetLastError());
         PROF_END(GIC_PROF_VECTOR);
     }
     PROF_BEGIN(GIC_PROF_SPMV);
+    ++h->launches;
     k_spmv<1><<<spmv_grid(h, n), SPMV_BLOCK, 0, h->stream>>>(n, P.rowptr, P.col, valA, W.p, W.w, nullptr, W.partials,
                                                             nullptr, W.sc);
     GIC_CUDA_TRY(cudaGetLastError());
     PROF_END(GIC_PROF_SPMV);
     PROF_BEGIN(GIC_PROF_VECTOR);
+    ++h->launches;
     k_update_xr<<<vec_grid(h, n, VEC_BLOCK), VEC_BLOCK, 0, h->stream>>>(n, x, W.r, W.p, W.w, W.partials, W.sc);
     GIC_CUDA_TRY(cudaGetLastError());
     PROF_END(GIC_PROF_VECTOR);
@@ -563,12 +601,15 @@ static int pcg_run(gic_handle *h, const Pattern &P, const double *valA, const TL
 {
     const int64_t n = P.n;
     Prof &pr = prof_of(h);
+    ++h->launches;
     k_init_scalars<<<1, 1, 0, h->stream>>>(W.sc, rtol, maxit);
     if (!ident) {
         GIC_TRY(setup_factor<TL>(h, P, Lval, (TL *)W.Uval, W.invd));
+        ++h->launches;
         k_fill_sentinel<<<vec_grid(h, n, 256), 256, 0, h->stream>>>(n, W.y, W.z);
     }
     PROF_BEGIN(GIC_PROF_SPMV);
+    ++h->launches;
     k_spmv<2><<<spmv_grid(h, n), SPMV_BLOCK, 0, h->stream>>>(n, P.rowptr, P.col, valA, x, W.r, b, W.partials, nullptr,
                                                             W.sc);
     GIC_CUDA_TRY(cudaGetLastError());
@@ -605,6 +646,7 @@ static int pcg_run(gic_handle *h, const Pattern &P, const double *valA, const TL
     }
     cudaEventDestroy(ev_done);
     if (rc != GIC_OK) return rc;
+    GIC_TRY(prof_flush(h, pr));
     GIC_CUDA_TRY(cudaMemcpyAsync(hs, W.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream));
     GIC_CUDA_TRY(cudaStreamSynchronize(h->stream));
     Scalars out = *hs;
@@ -644,6 +686,7 @@ int gic_convert_f64_f32(gic_handle *h, int64_t count, const double *src, float *
     GIC_TRY(check_handle(h));
     if (count < 0 || (count > 0 && (!src || !dst))) return GIC_ERR_INVALID_ARG;
     if (count == 0) return GIC_OK;
+    ++h->launches;
     k_convert_f64_f32<<<vec_grid(h, count, 256), 256, 0, h->stream>>>(count, src, dst);
     GIC_CUDA_TRY(cudaGetLastError());
     return GIC_OK;
@@ -660,6 +703,7 @@ int gic_spmv(gic_handle *h, const gic_pattern *P, const double *valA, const doub
     unsigned grid = spmv_grid(h, p.n);
     if (xdoty && grid > (65536 - 1024) / 8) return GIC_ERR_UNSUPPORTED;
     if (xdoty) GIC_CUDA_TRY(cudaMemsetAsync(sc, 0, sizeof(Scalars), h->stream));
+    ++h->launches;
     k_spmv<0><<<grid, SPMV_BLOCK, 0, h->stream>>>(p.n, p.rowptr, p.col, valA, x, y, nullptr, partials, xdoty, sc);
     GIC_CUDA_TRY(cudaGetLastError());
     return GIC_OK;
@@ -673,6 +717,7 @@ int gic_lsolve(gic_handle *h, const gic_pattern *P, const void *valL, int l_dtyp
     const Pattern &p = P->p;
     SolveWs W = carve(p, l_dtype, ws);
     if (ws_bytes < W.bytes) return GIC_ERR_WORKSPACE;
+    ++h->launches;
     k_fill_sentinel<<<vec_grid(h, p.n, 256), 256, 0, h->stream>>>(p.n, y, nullptr);
     Prof &pr = prof_of(h);
     if (l_dtype == GIC_F64) {
@@ -697,6 +742,7 @@ int gic_ltsolve(gic_handle *h, const gic_pattern *P, const void *valL, int l_dty
     const Pattern &p = P->p;
     SolveWs W = carve(p, l_dtype, ws);
     if (ws_bytes < W.bytes) return GIC_ERR_WORKSPACE;
+    ++h->launches;
     k_fill_sentinel<<<vec_grid(h, p.n, 256), 256, 0, h->stream>>>(p.n, z, nullptr);
     Prof &pr = prof_of(h);
     double *yy = const_cast<double *>(y); // not written when PCG = false
@@ -743,10 +789,9 @@ int gic_profile_enable(gic_handle *h, int on)
 {
     GIC_TRY(check_handle(h));
     Prof &pr = prof_of(h);
-    if (on && !pr.ev[0]) {
-        GIC_CUDA_TRY(cudaEventCreate(&pr.ev[0]));
-        GIC_CUDA_TRY(cudaEventCreate(&pr.ev[1]));
-    }
+    GIC_TRY(prof_flush(h, pr));
+    if (on && !pr.ev[0])
+        for (int k = 0; k < Prof::CAP; ++k) GIC_CUDA_TRY(cudaEventCreate(&pr.ev[k]));
     pr.on = on ? 1 : 0;
     for (int k = 0; k < GIC_PROF_CLASSES; ++k) {
         pr.ms[k] = 0.0;
@@ -759,10 +804,18 @@ int gic_profile_read(gic_handle *h, double *ms, int64_t *launches)
 {
     GIC_TRY(check_handle(h));
     Prof &pr = prof_of(h);
+    GIC_TRY(prof_flush(h, pr));
     for (int k = 0; k < GIC_PROF_CLASSES; ++k) {
         if (ms) ms[k] = pr.ms[k];
         if (launches) launches[k] = pr.launches[k];
     }
+    return GIC_OK;
+}
+
+int gic_launch_count(gic_handle *h, int64_t *count)
+{
+    if (!h || !count) return GIC_ERR_INVALID_ARG;
+    *count = h->launches;
     return GIC_OK;
 }
 

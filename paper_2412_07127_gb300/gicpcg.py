@@ -61,6 +61,24 @@ _SIGS = {
     "gic_profile_enable": (_int, [_vp, _int]),
     "gic_profile_read": (_int, [_vp, C.POINTER(_dbl), C.POINTER(_i64)]),
     "gic_solve_error_flags": (_int, [_vp, C.POINTER(C.c_uint)]),
+    "gic_launch_count": (_int, [_vp, C.POINTER(_i64)]),
+    "gic_solve_host": (_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _int, _dbl, _int,
+                              C.POINTER(_i32), C.POINTER(_dbl), C.POINTER(_dbl), C.POINTER(_int),
+                              _vp, _sz]),
+    "gic_solve_host_workspace_size": (_int, [_vp, _i64, _i64, _int, _int, C.POINTER(_sz)]),
+    "gic_gnn_param_count": (_int, []),
+    "gic_features": (_int, [_vp, _vp, _int, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "gic_gnn_workspace_size": (_int, [_vp, _vp, _int, _int, C.POINTER(_sz)]),
+    "gic_gnn_forward": (_int, [_vp, _vp, _int, _vp, _vp, _vp, _vp, _vp, _sz]),
+    "gic_gnn_forward_train": (_int, [_vp, _vp, _int, _vp, _vp, _vp, _vp, _vp, _sz]),
+    "gic_gnn_backward": (_int, [_vp, _vp, _int, _vp, _vp, _vp, _vp, _vp, _vp, _sz]),
+    "gic_gnn_correct": (_int, [_vp, _vp, _int, _vp, _vp, _vp, _vp, C.POINTER(_int)]),
+    "gic_scale_factor": (_int, [_vp, _vp, _int, _vp, _vp, _vp]),
+    "gic_gnn_correct_scaled": (_int, [_vp, _vp, _vp, _vp, _vp]),
+    "gic_gnn_correct_backward": (_int, [_vp, _vp, _vp, _vp, _vp]),
+    "gic_probe_workspace_size": (_int, [_vp, _vp, _int, _int, C.POINTER(_sz)]),
+    "gic_probe_loss": (_int, [_vp, _vp, _int, _vp, _vp, _vp, _int, _vp, _vp, _vp, _sz]),
+    "gic_adam_step": (_int, [_vp, _i64, _vp, _vp, _vp, _vp, _int, _dbl]),
 }
 
 _lib = None
@@ -284,3 +302,128 @@ def error_flags(h: Handle):
     f = C.c_uint()
     _call("gic_solve_error_flags", h.h, C.byref(f))
     return f.value
+
+
+def launch_count(h: Handle):
+    c = _i64()
+    _call("gic_launch_count", h.h, C.byref(c))
+    return c.value
+
+
+def solve_host(h: Handle, rowptr, col, val, b, theta=None, l_dtype=GIC_F64, rtol=1e-8,
+               maxit=10000, ws=None, x=None):
+    """End-to-end solve from host (numpy or CPU torch) buffers; x returned on the host.
+    theta: None (plain IC(0)) or float32 host array of GNN parameters."""
+    import numpy as np
+    n, nnz = len(rowptr) - 1, len(col)
+    if ws is None:
+        ws = solve_host_workspace(h, n, nnz, theta is not None, l_dtype)
+    x = x if x is not None else np.zeros(n)
+    it, rr, a, used = _i32(), _dbl(), _dbl(), _int()
+
+    def hp(arr):
+        return None if arr is None else _vp(arr.ctypes.data if hasattr(arr, "ctypes") else arr.data_ptr())
+    st = lib().gic_solve_host(h.h, n, nnz, hp(rowptr), hp(col), hp(val), hp(b), hp(x), hp(theta),
+                              l_dtype, rtol, maxit, C.byref(it), C.byref(rr), C.byref(a),
+                              C.byref(used), _ptr(ws), ws.numel())
+    if st not in (GIC_OK, GIC_ERR_NO_CONVERGENCE):
+        raise GicError("gic_solve_host", st)
+    return dict(x=x, iters=it.value, relres=rr.value, alpha=a.value, used_gnn=used.value, status=st)
+
+
+def solve_host_workspace(h: Handle, n, nnz, with_gnn, l_dtype=GIC_F64, device=0):
+    b = _sz()
+    _call("gic_solve_host_workspace_size", h.h, n, nnz, 1 if with_gnn else 0, l_dtype, C.byref(b))
+    return torch.empty(b.value, dtype=torch.uint8, device=torch.device("cuda", device))
+
+
+# ------------------------------------------------------------------ GNN
+def gnn_param_count():
+    return lib().gic_gnn_param_count()
+
+
+def features(h: Handle, P: Pattern, valA, ngraphs=1, with_ahat=False):
+    """Returns (x9 (n,9) f32, e0 (nnzL) f32, scale (ngraphs) f64 device, Ahat or None)."""
+    dev = valA.device
+    x9 = torch.empty(P.n, 9, dtype=torch.float32, device=dev)
+    e0 = torch.empty(P.nnzL, dtype=torch.float32, device=dev)
+    Ahat = torch.empty(P.nnzA, dtype=torch.float32, device=dev) if with_ahat else None
+    scale = torch.empty(ngraphs, dtype=torch.float64, device=dev)
+    _call("gic_features", h.h, P.p, ngraphs, _ptr(valA), _ptr(x9), _ptr(e0), _ptr(Ahat),
+          _ptr(scale), None)
+    return x9, e0, scale, Ahat
+
+
+def gnn_workspace(h: Handle, P: Pattern, ngraphs=1, training=False):
+    b = _sz()
+    _call("gic_gnn_workspace_size", h.h, P.p, ngraphs, 1 if training else 0, C.byref(b))
+    return torch.empty(b.value, dtype=torch.uint8, device=P.rowptr.device)
+
+
+def gnn_forward(h: Handle, P: Pattern, theta, x9, e0, ngraphs=1, ws=None, g=None):
+    ws = ws if ws is not None else gnn_workspace(h, P, ngraphs, False)
+    g = g if g is not None else torch.empty(P.nnzL, dtype=torch.float32, device=x9.device)
+    _call("gic_gnn_forward", h.h, P.p, ngraphs, _ptr(theta), _ptr(x9), _ptr(e0), _ptr(g),
+          _ptr(ws), ws.numel())
+    return g
+
+
+def gnn_forward_train(h: Handle, P: Pattern, theta, x9, e0, ws, ngraphs=1, g=None):
+    g = g if g is not None else torch.empty(P.nnzL, dtype=torch.float32, device=x9.device)
+    _call("gic_gnn_forward_train", h.h, P.p, ngraphs, _ptr(theta), _ptr(x9), _ptr(e0), _ptr(g),
+          _ptr(ws), ws.numel())
+    return g
+
+
+def gnn_backward(h: Handle, P: Pattern, theta, x9, e0, dg, ws, ngraphs=1, dtheta=None):
+    dtheta = dtheta if dtheta is not None else torch.empty_like(theta)
+    _call("gic_gnn_backward", h.h, P.p, ngraphs, _ptr(theta), _ptr(x9), _ptr(e0), _ptr(dg),
+          _ptr(dtheta), _ptr(ws), ws.numel())
+    return dtheta
+
+
+def gnn_correct(h: Handle, P: Pattern, LIC, g, scale, ngraphs=1, out=None):
+    out = out if out is not None else torch.empty_like(LIC)
+    ok = _int()
+    _call("gic_gnn_correct", h.h, P.p, ngraphs, _ptr(LIC), _ptr(g), _ptr(scale), _ptr(out),
+          C.byref(ok))
+    return out, bool(ok.value)
+
+
+def scale_factor(h: Handle, P: Pattern, LIC, scale, ngraphs=1):
+    out = torch.empty(P.nnzL, dtype=torch.float32, device=LIC.device)
+    _call("gic_scale_factor", h.h, P.p, ngraphs, _ptr(LIC), _ptr(scale), _ptr(out))
+    return out
+
+
+def gnn_correct_scaled(h: Handle, P: Pattern, LIChat, g, out=None):
+    out = out if out is not None else torch.empty_like(LIChat)
+    _call("gic_gnn_correct_scaled", h.h, P.p, _ptr(LIChat), _ptr(g), _ptr(out))
+    return out
+
+
+def gnn_correct_backward(h: Handle, P: Pattern, Lhat, dLhat, out=None):
+    out = out if out is not None else torch.empty_like(Lhat)
+    _call("gic_gnn_correct_backward", h.h, P.p, _ptr(Lhat), _ptr(dLhat), _ptr(out))
+    return out
+
+
+def probe_workspace(h: Handle, P: Pattern, ngraphs, m):
+    b = _sz()
+    _call("gic_probe_workspace_size", h.h, P.p, ngraphs, m, C.byref(b))
+    return torch.empty(b.value, dtype=torch.uint8, device=P.rowptr.device)
+
+
+def probe_loss(h: Handle, P: Pattern, Ahat, Lhat, Z, ngraphs=1, grad=False, ws=None):
+    """Returns (loss (ngraphs+1) f32 device, dLhat or None)."""
+    m = Z.shape[0]
+    ws = ws if ws is not None else probe_workspace(h, P, ngraphs, m)
+    loss = torch.empty(ngraphs + 1, dtype=torch.float32, device=Z.device)
+    dL = torch.empty(P.nnzL, dtype=torch.float32, device=Z.device) if grad else None
+    _call("gic_probe_loss", h.h, P.p, ngraphs, _ptr(Ahat), _ptr(Lhat), _ptr(Z), m, _ptr(loss),
+          _ptr(dL), _ptr(ws), ws.numel())
+    return loss, dL
+
+
+def adam_step(h: Handle, theta, grad, m1, m2, t, lr):
+    _call("gic_adam_step", h.h, theta.numel(), _ptr(theta), _ptr(grad), _ptr(m1), _ptr(m2), t, lr)

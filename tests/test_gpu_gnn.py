@@ -1,0 +1,276 @@
+"""GPU parity of the GNN correction and its training path (A4-A6, A8-A10)
+against the FP64 oracle, through the C-ABI. The GPU computes in FP32: graph
+inputs to FP32 rounding, the GNN output g and the probe loss within 1e-5
+relative (norm-wise), gradients within 1e-4 (sums over many edges in FP32)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2412_07127_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_07127_gb300 import build, gicpcg
+    build.build()
+    return gicpcg
+
+
+@pytest.fixture(scope="module")
+def h(G):
+    return G.Handle(0)
+
+
+def _dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    return (t.to(dtype) if dtype is not None else t).to(DEV)
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _nrel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def _theta32(seed, scale=1.0):
+    """Parameters as the GPU holds them (float32); the oracle gets the same
+    values in float64."""
+    t = I.gnn_init(seed, out_scale=scale).astype(np.float32)
+    return t, t.astype(np.float64)
+
+
+def _batch(G, h, N, seeds, sigma=1.0):
+    Es = [I.material_field(N, s, sigma) for s in seeds]
+    rp, c, v = G.fem_hex_assemble(h, N, _dev(np.concatenate(Es)), nb=len(seeds))
+    P = G.Pattern(h, rp, c)
+    As = [O.fem_hex_assemble(N, E) for E in Es]
+    return P, v, As
+
+
+@pytest.mark.parametrize("N,nb", [(5, 1), (3, 2)])
+def test_features_match_oracle(G, h, N, nb):
+    P, v, As = _batch(G, h, N, range(nb))
+    x9, e0, scale, Ahat = G.features(h, P, v, ngraphs=nb, with_ahat=True)
+    x9, e0, scale, Ahat = _np(x9), _np(e0), _np(scale), _np(Ahat)
+    n, nnzL, nnzA = As[0].n, (As[0].nnz + As[0].n) // 2, As[0].nnz
+    for k, A in enumerate(As):
+        ox9, oe0, os_ = O.features(A)
+        assert abs(scale[k] - os_) <= 1e-13 * os_
+        assert _nrel(x9[k * n:(k + 1) * n], ox9) <= 1e-7
+        assert np.allclose(x9[k * n:(k + 1) * n], ox9, rtol=1e-6, atol=1e-6)
+        assert np.allclose(e0[k * nnzL:(k + 1) * nnzL], oe0, rtol=1e-6, atol=1e-7)
+        assert np.allclose(Ahat[k * nnzA:(k + 1) * nnzA], A.val / os_, rtol=1e-6, atol=1e-7)
+
+
+@pytest.mark.parametrize("N,nb", [(4, 1), (8, 1), (3, 2)])
+def test_gnn_forward_matches_oracle(G, h, N, nb):
+    P, v, As = _batch(G, h, N, [10 + k for k in range(nb)])
+    x9, e0, scale, _ = G.features(h, P, v, ngraphs=nb)
+    t32, t64 = _theta32(1)
+    g = _np(G.gnn_forward(h, P, _dev(t32), x9, e0, ngraphs=nb))
+    nnzL = (As[0].nnz + As[0].n) // 2
+    for k, A in enumerate(As):
+        T = O.lower(A)
+        ox9, oe0, _ = O.features(A)
+        og = O.gnn_forward(T, ox9, oe0, t64)
+        assert _nrel(g[k * nnzL:(k + 1) * nnzL], og) <= 1e-5
+        assert np.abs(g[k * nnzL:(k + 1) * nnzL] - og).max() <= 1e-4 * np.abs(og).max()
+
+
+def test_gnn_forward_train_equals_forward(G, h):
+    P, v, As = _batch(G, h, 4, [3])
+    x9, e0, scale, _ = G.features(h, P, v)
+    t32, _ = _theta32(2)
+    th = _dev(t32)
+    g1 = G.gnn_forward(h, P, th, x9, e0)
+    ws = G.gnn_workspace(h, P, 1, training=True)
+    g2 = G.gnn_forward_train(h, P, th, x9, e0, ws)
+    assert torch.equal(g1, g2)
+
+
+def test_correct_matches_oracle(G, h):
+    N = 6
+    P, v, As = _batch(G, h, N, [4])
+    A = As[0]
+    x9, e0, scale, _ = G.features(h, P, v)
+    t32, t64 = _theta32(3, scale=0.05)
+    g = G.gnn_forward(h, P, _dev(t32), x9, e0)
+    LIC, bad = G.ic0(h, P, v)
+    Lc, ok = G.gnn_correct(h, P, LIC, g, scale)
+    assert ok
+    T = O.lower(A)
+    ox9, oe0, os_ = O.features(A)
+    og = O.gnn_forward(T, ox9, oe0, t64)
+    Lo, _ = O.ic0(A)
+    ref = np.sqrt(os_) * O.correct(T, Lo.val / np.sqrt(os_), og)
+    assert _nrel(_np(Lc), ref) <= 1e-6
+    diag = T.rowptr[1:] - 1
+    assert np.all(_np(Lc)[diag] > 0)
+
+
+def test_correct_zero_output_is_ic0(G, h):
+    """W2 = 0 and b2 = 0 in the last block: g = 0, so L = L_IC exactly."""
+    N = 4
+    P, v, As = _batch(G, h, N, [5])
+    x9, e0, scale, _ = G.features(h, P, v)
+    t32, _ = _theta32(4)
+    sl = I.param_slices()
+    o, _ = sl["W2_2"]
+    t32[o:o + 32] = 0
+    t32[sl["b2_2"][0]] = 0
+    g = G.gnn_forward(h, P, _dev(t32), x9, e0)
+    assert torch.all(g == 0)
+    LIC, _ = G.ic0(h, P, v)
+    Lc, ok = G.gnn_correct(h, P, LIC, g, scale)
+    assert ok and torch.equal(Lc, LIC)
+
+
+def test_correct_flags_bad_diagonal(G, h):
+    N = 3
+    P, v, As = _batch(G, h, N, [6])
+    LIC, _ = G.ic0(h, P, v)
+    g = torch.zeros(P.nnzL, dtype=torch.float32, device=DEV)
+    g[P.nnzL - 1] = float("nan")
+    scale = torch.ones(1, dtype=torch.float64, device=DEV)
+    _, ok = G.gnn_correct(h, P, LIC, g, scale)
+    assert not ok
+
+
+def _scaled_inputs(G, h, P, v, As, nb, perturb_seed=0):
+    """Scaled Ahat (GPU from its own features) and a perturbed scaled factor
+    Lhat given to both sides (drawn here, not by the GPU)."""
+    x9, e0, scale, Ahat = G.features(h, P, v, ngraphs=nb, with_ahat=True)
+    rng = np.random.default_rng(perturb_seed)
+    Lhats = []
+    for A in As:
+        Lo, _ = O.ic0(A)
+        _, _, s = O.features(A)
+        Lh = Lo.val / np.sqrt(s) * (1 + 0.1 * rng.standard_normal(Lo.nnz))
+        Lhats.append(Lh.astype(np.float32))
+    return x9, e0, scale, Ahat, Lhats
+
+
+@pytest.mark.parametrize("N,nb", [(4, 1), (3, 2)])
+def test_probe_loss_and_gradient_match_oracle(G, h, N, nb):
+    P, v, As = _batch(G, h, N, [20 + k for k in range(nb)])
+    x9, e0, scale, Ahat, Lhats = _scaled_inputs(G, h, P, v, As, nb)
+    n = As[0].n
+    m = 8
+    Zs = [I.probes(m, n, 30 + k) for k in range(nb)]
+    Z = np.concatenate(Zs, axis=1)
+    loss, dL = G.probe_loss(h, P, Ahat, _dev(np.concatenate(Lhats)), _dev(Z), ngraphs=nb, grad=True)
+    loss, dL = _np(loss), _np(dL)
+    nnzL = len(Lhats[0])
+    olosses = []
+    for k, A in enumerate(As):
+        _, _, s = O.features(A)
+        Ah = O.CSR(A.rowptr, A.col, A.val / s)
+        T = O.lower(A)
+        Lh = O.CSR(T.rowptr, T.col, Lhats[k].astype(np.float64))
+        ol, odL = O.probe_loss(Ah, Lh, Zs[k].astype(np.float64), grad=True)
+        olosses.append(ol)
+        assert abs(loss[k] - ol) <= 1e-5 * abs(ol)
+        assert _nrel(dL[k * nnzL:(k + 1) * nnzL], odL / nb) <= 1e-4
+    assert abs(loss[nb] - np.mean(olosses)) <= 1e-5 * np.mean(olosses)
+
+
+@pytest.mark.parametrize("N,nb", [(3, 1), (2, 2)])
+def test_gnn_backward_matches_oracle(G, h, N, nb):
+    P, v, As = _batch(G, h, N, [40 + k for k in range(nb)])
+    x9, e0, scale, _ = G.features(h, P, v, ngraphs=nb)
+    t32, t64 = _theta32(5)
+    th = _dev(t32)
+    ws = G.gnn_workspace(h, P, nb, training=True)
+    G.gnn_forward_train(h, P, th, x9, e0, ws, ngraphs=nb)
+    nnzL = (As[0].nnz + As[0].n) // 2
+    dg = np.random.default_rng(7).standard_normal(nnzL * nb).astype(np.float32)
+    dth = _np(G.gnn_backward(h, P, th, x9, e0, _dev(dg), ws, ngraphs=nb))
+    ref = np.zeros(t64.size)
+    for k, A in enumerate(As):
+        T = O.lower(A)
+        ox9, oe0, _ = O.features(A)
+        ref += O.gnn_backward(T, ox9, oe0, t64, dg[k * nnzL:(k + 1) * nnzL].astype(np.float64))
+    assert _nrel(dth, ref) <= 1e-4
+    for name, (off, shape) in I.param_slices().items():
+        sz = int(np.prod(shape))
+        assert _nrel(dth[off:off + sz], ref[off:off + sz]) <= 2e-3, name
+
+
+def test_gnn_backward_deterministic(G, h):
+    P, v, As = _batch(G, h, 4, [8])
+    x9, e0, scale, _ = G.features(h, P, v)
+    t32, _ = _theta32(6)
+    th = _dev(t32)
+    ws = G.gnn_workspace(h, P, 1, training=True)
+    G.gnn_forward_train(h, P, th, x9, e0, ws)
+    dg = _dev(np.random.default_rng(1).standard_normal(P.nnzL).astype(np.float32))
+    d1 = G.gnn_backward(h, P, th, x9, e0, dg, ws).clone()
+    d2 = G.gnn_backward(h, P, th, x9, e0, dg, ws)
+    assert torch.equal(d1, d2)
+
+
+def test_adam_matches_oracle(G, h):
+    rng = np.random.default_rng(2)
+    th = rng.standard_normal(3504)
+    t_gpu = _dev(th.astype(np.float32))
+    m1g = torch.zeros_like(t_gpu)
+    m2g = torch.zeros_like(t_gpu)
+    th_o = th.astype(np.float32).astype(np.float64)
+    m1o, m2o = np.zeros(3504), np.zeros(3504)
+    for t in range(1, 6):
+        gr = rng.standard_normal(3504).astype(np.float32)
+        G.adam_step(h, t_gpu, _dev(gr), m1g, m2g, t, 0.005)
+        O.adam_step(th_o, gr.astype(np.float64), m1o, m2o, t, 0.005)
+    assert np.allclose(_np(t_gpu), th_o, rtol=1e-5, atol=1e-6)
+
+
+def test_training_steps_reduce_loss(G, h):
+    """Ten Adam steps on one fixed batch lower the probe loss (property)."""
+    nb, N = 2, 3
+    P, v, As = _batch(G, h, N, [50, 51])
+    x9, e0, scale, Ahat = G.features(h, P, v, ngraphs=nb, with_ahat=True)
+    LIC, bad = G.ic0(h, P, v)
+    assert bad == -1
+    LIChat = G.scale_factor(h, P, LIC, scale, ngraphs=nb)
+    Z = _dev(np.concatenate([I.probes(8, As[0].n, 60 + k) for k in range(nb)], axis=1))
+    t32, _ = _theta32(7, scale=0.01)
+    th = _dev(t32)
+    m1, m2 = torch.zeros_like(th), torch.zeros_like(th)
+    ws = G.gnn_workspace(h, P, nb, training=True)
+    losses = []
+    for t in range(1, 11):
+        g = G.gnn_forward_train(h, P, th, x9, e0, ws, ngraphs=nb)
+        Lhat = G.gnn_correct_scaled(h, P, LIChat, g)
+        loss, dL = G.probe_loss(h, P, Ahat, Lhat, Z, ngraphs=nb, grad=True)
+        dg = G.gnn_correct_backward(h, P, Lhat, dL)
+        dth = G.gnn_backward(h, P, th, x9, e0, dg, ws, ngraphs=nb)
+        G.adam_step(h, th, dth, m1, m2, t, 0.005)
+        losses.append(float(loss[nb]))
+    assert losses[-1] < losses[0]
+
+
+def test_solve_host_matches_oracle(G, h):
+    N = 5
+    E = I.material_field(N, 3)
+    A = O.fem_hex_assemble(N, E)
+    b = I.rhs(A.n, 3)
+    t32, t64 = _theta32(8, scale=0.02)
+    for theta in (None, t32):
+        r = G.solve_host(h, A.rowptr, A.col, A.val, b, theta=theta)
+        Lo, _ = O.ic0(A)
+        if theta is not None and r["used_gnn"]:
+            T = O.lower(A)
+            ox9, oe0, s = O.features(A)
+            og = O.gnn_forward(T, ox9, oe0, t64)
+            Lo = O.CSR(T.rowptr, T.col, np.sqrt(s) * O.correct(T, Lo.val / np.sqrt(s), og))
+        ro = O.pcg(A, b, Lo, tol=1e-8)
+        assert abs(r["iters"] - ro["iters"]) <= max(1, int(0.02 * ro["iters"]))
+        assert np.linalg.norm(r["x"] - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
