@@ -247,6 +247,14 @@ int gic_probe_loss(gic_handle *h, const gic_pattern *P, int ngraphs, const float
 int gic_adam_step(gic_handle *h, int64_t np, float *theta, const float *grad, float *m1,
                   float *m2, int t, double lr);
 
+/* Tuning of the triangular-solve schedule (no effect on results):
+ * GIC_TUNE_SOLVE_CHUNK = consecutive row groups one warp solves in order
+ * (0 = default 32, capped so a chunk holds at most 512 rows);
+ * GIC_TUNE_SOLVE_WARPS_PER_SM = cap on solve warps per SM (0 = none). */
+#define GIC_TUNE_SOLVE_CHUNK 0
+#define GIC_TUNE_SOLVE_WARPS_PER_SM 1
+int gic_set_tuning(gic_handle *h, int key, int value);
+
 /* Number of kernels this handle has launched so far (host output). */
 int gic_launch_count(gic_handle *h, int64_t *count);
 

@@ -56,6 +56,7 @@ def lib():
         L.or_round_bf16.restype = _dbl
         L.or_gnn_forward.argtypes = [_i64, _i32p, _i32p, _f64p, _f64p, _f64p, C.c_int, _f64p]
         L.or_correct.argtypes = [_i64, _i32p, _i32p, _f64p, _f64p, _f64p]
+        L.or_correct_backward.argtypes = [_i64, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p]
         L.or_gnn_backward.argtypes = [_i64, _i32p, _i32p, _f64p, _f64p, _f64p, C.c_int, _f64p, _f64p]
         L.or_probe_loss.argtypes = [_i64, _i32p, _i32p, _f64p, _i32p, _i32p, _f64p, _f64p,
                                     C.c_int, C.c_void_p]
@@ -255,6 +256,12 @@ def correct(T: CSR, LIC_val, g):
     out = np.zeros(T.nnz)
     lib().or_correct(T.n, T.rowptr, T.col, _c64(LIC_val), _c64(g), out)
     return out
+
+
+def correct_backward(T: CSR, LIC_val, g, dLout):
+    dg = np.zeros(T.nnz)
+    lib().or_correct_backward(T.n, T.rowptr, T.col, _c64(LIC_val), _c64(g), _c64(dLout), dg)
+    return dg
 
 
 def gnn_backward(T: CSR, x9, e0, theta, dg, bf16=False):

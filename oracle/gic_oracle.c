@@ -28,6 +28,7 @@
  *                             restatement. Against the paper itself the
  *                             architecture is parity unpinned (Figure 1 is
  *                             missing from the text; the layout is a reading).
+ *   or_correct(+backward)     pinned: g = 0 => L_IC; finite differences
  *   or_probe_loss(+grad)      pinned: unbiased vs dense ||LL^T-A||_F^2,
  *                             central finite differences
  *   or_gnn_backward           pinned: central finite differences
@@ -721,6 +722,16 @@ void or_correct(int64_t n, const int32_t *Lrowptr, const int32_t *Lcol, const do
     for (int64_t i = 0; i < n; ++i)
         for (int32_t p = Lrowptr[i]; p < Lrowptr[i + 1]; ++p)
             Lout[p] = (Lcol[p] == i) ? LIC[p] * exp(g[p] / 2.0) : LIC[p] + g[p];
+}
+
+/* Backward of or_correct: dg = dLout off the diagonal and
+ * dLout * LIC * exp(g/2) / 2 on it (the derivative of each output entry). */
+void or_correct_backward(int64_t n, const int32_t *Lrowptr, const int32_t *Lcol, const double *LIC,
+                         const double *g, const double *dLout, double *dg)
+{
+    for (int64_t i = 0; i < n; ++i)
+        for (int32_t p = Lrowptr[i]; p < Lrowptr[i + 1]; ++p)
+            dg[p] = (Lcol[p] == i) ? dLout[p] * LIC[p] * exp(g[p] / 2.0) / 2.0 : dLout[p];
 }
 
 /* Backward of the GNN for the gradient dg of the edge output g.

@@ -34,6 +34,7 @@ struct IcWarpSmem {
     double lg[GMAX][MAXDIM];     // external part of each group row
     double lin[GMAX][GMAX + 1];  // in-group part (and diagonal) of each group row
     int32_t J[MAXDIM];
+    int32_t rs[MAXDIM];          // start of row J[u] in L
     int32_t off[MAXDIM + 1];     // prefix of the gathered rows' lengths
 };
 
@@ -70,44 +71,59 @@ __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t ngroups, const in
         const int32_t b0 = Lrowptr[s];
         const int m = Lrowptr[s + 1] - b0 - 1; // external columns (host checked m <= MAXDIM)
 
-        // 1. external columns, their readiness, their row lengths
+        // 1. external columns, their readiness (relaxed polling, one fence
+        // after the last wait), their row starts and lengths
         for (int u = lane; u < m; u += 32) {
             int32_t j = Lcol[b0 + u];
             S.J[u] = j;
-            int32_t dpos = Lrowptr[j + 1] - 1;
-            double d = ld_acquire(Lval + dpos);
-            long long it = 0;
-            while (is_sentinel(d) && it < SPIN_LIMIT) {
-                if (it > 32) __nanosleep(it < 1024 ? 32 : 256);
-                d = ld_acquire(Lval + dpos);
-                ++it;
-                if ((it & 1023) == 0 && *((volatile unsigned *)err) != 0u) break;
-            }
-            if (is_sentinel(d)) atomicOr(err, ERR_TIMEOUT);
-            S.off[u + 1] = dpos + 1 - Lrowptr[j]; // length of row j (its diagonal included)
+            const int32_t rs = Lrowptr[j];
+            const int32_t dpos = Lrowptr[j + 1] - 1;
+            S.rs[u] = rs;
+            S.off[u + 1] = dpos + 1 - rs; // length of row j (its diagonal included)
+            wait_value(Lval + dpos, err);
         }
         __syncwarp();
+        fence_acq_rel(); // pairs with the producers' release of each diagonal
         if (lane == 0) {
             S.off[0] = 0;
             for (int u = 0; u < m; ++u) S.off[u + 1] += S.off[u];
         }
         for (int idx = lane; idx < m * m; idx += 32) S.M[(idx / m) * MAXDIM + (idx % m)] = 0.0;
         __syncwarp();
-        __threadfence(); // pairs with the producers' release of each diagonal
 
-        // gather M[u][v] = L_{J[u],J[v]} for the entries of row J[u] inside J
+        // gather M[u][v] = L_{J[u],J[v]} for the entries of row J[u] inside J,
+        // four independent (column, value) loads in flight per lane
         const int P = S.off[m];
         int u = 0;
-        for (int idx = lane; idx < P; idx += 32) {
-            while (S.off[u + 1] <= idx) ++u;
-            int32_t j = S.J[u];
-            int32_t q = Lrowptr[j] + (idx - S.off[u]);
-            int32_t c = Lcol[q];
-            int v = find_in(S.J, 0, u + 1, c);
-            if (v >= 0) {
-                double val = Lval[q];
-                S.M[u * MAXDIM + v] = val;
-                if (v == u) S.invd[u] = 1.0 / val;
+        for (int base = lane; base < P; base += 128) {
+            int32_t q[4], uu[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int idx = base + 32 * k;
+                if (idx < P) {
+                    while (S.off[u + 1] <= idx) ++u;
+                    uu[k] = u;
+                    q[k] = S.rs[u] + (idx - S.off[u]);
+                } else {
+                    uu[k] = -1;
+                    q[k] = 0;
+                }
+            }
+            int32_t cc[4];
+            double vv[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                cc[k] = (uu[k] >= 0) ? Lcol[q[k]] : -1;
+                vv[k] = (uu[k] >= 0) ? Lval[q[k]] : 0.0;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (uu[k] < 0) continue;
+                const int v = find_in(S.J, 0, uu[k] + 1, cc[k]);
+                if (v >= 0) {
+                    S.M[uu[k] * MAXDIM + v] = vv[k];
+                    if (v == uu[k]) S.invd[v] = 1.0 / vv[k];
+                }
             }
         }
         __syncwarp();

@@ -33,7 +33,7 @@ enum : unsigned { ERR_TIMEOUT = 1u, ERR_BOUNDS = 2u };
 // Spin-wait limits: polls of one word before a waiting warp gives up, sets
 // ERR_TIMEOUT and writes NaN so that everything downstream drains. With the
 // back-off below this is about a second of waiting.
-constexpr long long SPIN_LIMIT = 1ll << 22;
+constexpr long long SPIN_LIMIT = 1ll << 20;
 
 // A quiet-NaN bit pattern that arithmetic never produces (the GPU's
 // canonical NaN differs), used as "not written yet" in solve outputs.
@@ -77,21 +77,28 @@ __device__ __forceinline__ void st_release_i32(int *p, int v)
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Wait until *p is no longer the sentinel; bounded. On timeout sets the
-// error flag and returns NaN.
+// Wait until *p is no longer the sentinel; bounded. Polls with relaxed
+// loads (no cache invalidation per poll), backing off exponentially up to
+// about a microsecond. On timeout sets the error flag and returns NaN.
 __device__ __forceinline__ double wait_value(const double *p, unsigned *err)
 {
     double v = ld_relaxed(p);
     if (!is_sentinel(v)) return v;
+    unsigned ns = 8;
     for (long long it = 0; it < SPIN_LIMIT; ++it) {
-        if (it > 32) __nanosleep(it < 1024 ? 32 : 256);
+        if (it > 16) {
+            __nanosleep(ns);
+            if (ns < 1024) ns <<= 1;
+        }
         v = ld_relaxed(p);
         if (!is_sentinel(v)) return v;
-        if ((it & 1023) == 1023 && *((volatile unsigned *)err) != 0u) return __longlong_as_double(0x7ff8000000000000ll);
+        if ((it & 255) == 255 && *((volatile unsigned *)err) != 0u) return __longlong_as_double(0x7ff8000000000000ll);
     }
     atomicOr(err, ERR_TIMEOUT);
     return __longlong_as_double(0x7ff8000000000000ll);
 }
+
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v)
@@ -137,6 +144,8 @@ struct gic_handle {
     void *dev_small = nullptr;     // 64 KiB of library scratch (scalars, Ke)
     void *host_pinned = nullptr;   // 4 KiB pinned readback area
     long long launches = 0;        // kernels this handle has launched
+    int tune_chunk = 0;            // groups per warp chunk in the solves (0: default)
+    int tune_solve_warps_per_sm = 0; // cap on resident solve warps per SM (0: none)
 };
 
 namespace gic {

@@ -92,64 +92,117 @@ __global__ void k_transpose_vals(int64_t n, int64_t nnzL, const int32_t *tperm, 
 }
 
 // ------------------------------------------------------------ SpTRSV
+// A warp owns a chunk of `chunk` consecutive groups and solves them in
+// order, keeping the chunk's solution values in shared memory: a dependency
+// inside the chunk (for hex elasticity the neighbour along x) is read from
+// there, one outside it from global memory, waiting on the sentinel. Chunks
+// are dealt round-robin to a co-resident grid in dependency order. Every
+// index and factor value a group needs is loaded before its wait, so the
+// critical path after the last dependency lands is: FMAs, one warp
+// reduction, the dense in-group block, one store.
+constexpr int MAXCHUNK_ROWS = 512; // chunk * max group rows, per warp buffer
+
+// dependency j: from the warp's chunk buffer (rows [lo, hi), stored at
+// buf[j - base]) or from global memory, waiting on the sentinel
+__device__ __forceinline__ double get_dep(const double *y, const double *buf, int32_t j, int32_t lo, int32_t hi,
+                                          int32_t base, unsigned *err)
+{
+    if (j >= lo && j < hi) return buf[j - base];
+    return wait_value(y + j, err);
+}
+
 // Forward: y_i = (r_i - sum_{j<i} L_ij y_j) / L_ii. y must hold the sentinel.
-template <typename TL>
-__global__ void __launch_bounds__(SOLVE_BLOCK) k_lsolve(int32_t ngroups, const int32_t *__restrict__ grp,
+template <typename TL, int GM>
+__global__ void __launch_bounds__(SOLVE_BLOCK) k_lsolve(int32_t ngroups, int chunk, const int32_t *__restrict__ grp,
                                                         const int32_t *__restrict__ Lrowptr,
                                                         const int32_t *__restrict__ Lcol, const TL *__restrict__ Lval,
                                                         const double *__restrict__ invd, const double *__restrict__ r,
                                                         double *y, unsigned *err, const Scalars *sc)
 {
     if (sc && sc->done) return;
+    extern __shared__ double ybuf_all[];
     const int lane = threadIdx.x & 31;
+    double *ybuf = ybuf_all + (threadIdx.x >> 5) * MAXCHUNK_ROWS;
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t g = w; g < ngroups; g += nw) {
-        const int32_t s = grp[g];
-        const int G = grp[g + 1] - s;
-        const int32_t b0 = Lrowptr[s];
-        const int32_t m = Lrowptr[s + 1] - b0 - 1;
-        int32_t base[GMAX];
-        double acc[GMAX];
+    const int64_t nchunks = (ngroups + chunk - 1) / chunk;
+    for (int64_t c = w; c < nchunks; c += nw) {
+        const int64_t g0 = c * chunk;
+        const int64_t g1 = min(g0 + chunk, (int64_t)ngroups);
+        const int32_t row0 = grp[g0];
+        for (int64_t g = g0; g < g1; ++g) {
+            const int32_t s = grp[g];
+            const int G = grp[g + 1] - s;
+            const int32_t b0 = Lrowptr[s];
+            const int32_t m = Lrowptr[s + 1] - b0 - 1;
+            int32_t base[GM];
+            double acc[GM], rr[GM], iv[GM];
 #pragma unroll
-        for (int t = 0; t < GMAX; ++t) {
-            base[t] = (t < G) ? b0 + t * (m + 1) + (t * (t - 1)) / 2 : 0;
-            acc[t] = 0.0;
-        }
-        for (int32_t k = lane; k < m; k += 32) {
-            const int32_t j = Lcol[b0 + k];
-            const double yj = wait_value(y + j, err);
+            for (int t = 0; t < GM; ++t) {
+                base[t] = b0 + t * (m + 1) + (t * (t - 1)) / 2;
+                acc[t] = 0.0;
+                rr[t] = (t < G) ? r[s + t] : 0.0;
+                iv[t] = (t < G) ? invd[s + t] : 0.0;
+            }
+            // prefetch two columns per lane and their values in every row
+            const int32_t k0 = lane, k1 = lane + 32;
+            const int32_t j0 = (k0 < m) ? Lcol[b0 + k0] : -1;
+            const int32_t j1 = (k1 < m) ? Lcol[b0 + k1] : -1;
+            double v0[GM], v1[GM];
 #pragma unroll
-            for (int t = 0; t < GMAX; ++t)
-                if (t < G) acc[t] = fma((double)Lval[base[t] + k], yj, acc[t]);
-        }
+            for (int t = 0; t < GM; ++t) {
+                v0[t] = (t < G && j0 >= 0) ? (double)Lval[base[t] + k0] : 0.0;
+                v1[t] = (t < G && j1 >= 0) ? (double)Lval[base[t] + k1] : 0.0;
+            }
+            double lin[GM * (GM - 1) / 2 + 1];
 #pragma unroll
-        for (int t = 0; t < GMAX; ++t)
-            if (t < G) acc[t] = warp_sum(acc[t]);
-        if (lane == 0) {
-            double yl[GMAX];
+            for (int t = 1; t < GM; ++t)
 #pragma unroll
-            for (int t = 0; t < GMAX; ++t) {
-                if (t < G) {
-                    double v = r[s + t] - acc[t];
+                for (int u = 0; u < t; ++u)
+                    lin[t * (t - 1) / 2 + u] = (t < G) ? (double)Lval[base[t] + m + u] : 0.0;
+            // wait for the external values (in-chunk values come from smem)
+            const double y0 = (j0 >= 0) ? get_dep(y, ybuf, j0, row0, s, row0, err) : 0.0;
+            const double y1 = (j1 >= 0) ? get_dep(y, ybuf, j1, row0, s, row0, err) : 0.0;
 #pragma unroll
-                    for (int u = 0; u < t; ++u) v = fma(-(double)Lval[base[t] + m + u], yl[u], v);
-                    yl[t] = v * invd[s + t];
-                }
+            for (int t = 0; t < GM; ++t) acc[t] = fma(v1[t], y1, v0[t] * y0);
+            for (int32_t k = lane + 64; k < m; k += 32) { // rows longer than 64 external columns
+                const int32_t j = Lcol[b0 + k];
+                const double yj = get_dep(y, ybuf, j, row0, s, row0, err);
+#pragma unroll
+                for (int t = 0; t < GM; ++t)
+                    if (t < G) acc[t] = fma((double)Lval[base[t] + k], yj, acc[t]);
             }
 #pragma unroll
-            for (int t = 0; t < GMAX; ++t)
-                if (t < G) st_relaxed(y + s + t, yl[t]);
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int t = 0; t < GM; ++t)
+                    if (t < G) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+            if (lane == 0) {
+                double yl[GM];
+#pragma unroll
+                for (int t = 0; t < GM; ++t) {
+                    if (t < G) {
+                        double v = rr[t] - acc[t];
+#pragma unroll
+                        for (int u = 0; u < t; ++u) v = fma(-lin[t * (t - 1) / 2 + u], yl[u], v);
+                        yl[t] = v * iv[t];
+                        st_relaxed(y + s + t, yl[t]);
+                        ybuf[s - row0 + t] = yl[t];
+                    }
+                }
+            }
+            __syncwarp();
         }
     }
 }
 
 // Backward: z_i = (y_i - sum_{j>i} L_ji z_j) / L_ii on U = L^T. z must hold
-// the sentinel. Groups are visited from the last one down. With PCG != 0
-// the kernel also resets y to the sentinel (for the next forward solve) and
-// forms r^T z, then beta = r_k^T z_k / r_{k-1}^T z_{k-1} (Algorithm 1 line 13).
-template <typename TL, bool PCG>
-__global__ void __launch_bounds__(SOLVE_BLOCK) k_ltsolve(int32_t ngroups, const int32_t *__restrict__ grp,
+// the sentinel. Chunks and the groups inside them run from the last one
+// down. With PCG the kernel also resets y to the sentinel (for the next
+// forward solve) and forms r^T z, then beta = r_k^T z_k / r_{k-1}^T z_{k-1}
+// (Algorithm 1 line 13) in the last warp to finish.
+template <typename TL, bool PCG, int GM>
+__global__ void __launch_bounds__(SOLVE_BLOCK) k_ltsolve(int32_t ngroups, int chunk, const int32_t *__restrict__ grp,
                                                          const int32_t *__restrict__ Urowptr,
                                                          const int32_t *__restrict__ Ucol, const TL *__restrict__ Uval,
                                                          const double *__restrict__ invd, double *y, double *z,
@@ -157,58 +210,87 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_ltsolve(int32_t ngroups, const 
                                                          unsigned *err, Scalars *sc)
 {
     if (sc && sc->done) return;
+    extern __shared__ double zbuf_all[];
     const int lane = threadIdx.x & 31;
+    double *zbuf = zbuf_all + (threadIdx.x >> 5) * MAXCHUNK_ROWS;
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nchunks = (ngroups + chunk - 1) / chunk;
     double dot = 0.0;
-    for (int64_t gg = w; gg < ngroups; gg += nw) {
-        const int64_t g = ngroups - 1 - gg;
-        const int32_t s = grp[g];
-        const int G = grp[g + 1] - s;
-        const int32_t e = s + G - 1;
-        const int32_t be = Urowptr[e];
-        const int32_t mu = Urowptr[e + 1] - be - 1;
-        int32_t base[GMAX], ext[GMAX];
-        double acc[GMAX];
+    for (int64_t cc = w; cc < nchunks; cc += nw) {
+        const int64_t c = nchunks - 1 - cc;
+        const int64_t g0 = c * chunk;
+        const int64_t g1 = min(g0 + chunk, (int64_t)ngroups);
+        const int32_t row0 = grp[g0], rowEnd = grp[g1];
+        for (int64_t g = g1 - 1; g >= g0; --g) {
+            const int32_t s = grp[g];
+            const int G = grp[g + 1] - s;
+            const int32_t e = s + G - 1;
+            const int32_t be = Urowptr[e];
+            const int32_t mu = Urowptr[e + 1] - be - 1;
+            int32_t base[GM];
+            double acc[GM], yy[GM], rr[GM], iv[GM];
 #pragma unroll
-        for (int t = 0; t < GMAX; ++t) {
-            // row s+t of U holds G-t in-group entries (diagonal first), then mu
-            base[t] = (t < G) ? Urowptr[s + t] : 0;
-            ext[t] = base[t] + (G - t);
-            acc[t] = 0.0;
-        }
-        for (int32_t k = lane; k < mu; k += 32) {
-            const int32_t j = Ucol[be + 1 + k];
-            const double zj = wait_value(z + j, err);
+            for (int t = 0; t < GM; ++t) {
+                // row s+t of U: G-t in-group entries (diagonal first), then mu
+                base[t] = (t < G) ? Urowptr[s + t] : 0;
+                acc[t] = 0.0;
+                yy[t] = (t < G) ? y[s + t] : 0.0;
+                rr[t] = (PCG && t < G) ? r[s + t] : 0.0;
+                iv[t] = (t < G) ? invd[s + t] : 0.0;
+            }
+            const int32_t k0 = lane, k1 = lane + 32;
+            const int32_t j0 = (k0 < mu) ? Ucol[be + 1 + k0] : -1;
+            const int32_t j1 = (k1 < mu) ? Ucol[be + 1 + k1] : -1;
+            double v0[GM], v1[GM];
 #pragma unroll
-            for (int t = 0; t < GMAX; ++t)
-                if (t < G) acc[t] = fma((double)Uval[ext[t] + k], zj, acc[t]);
-        }
+            for (int t = 0; t < GM; ++t) {
+                const int32_t ext = base[t] + (G - t);
+                v0[t] = (t < G && j0 >= 0) ? (double)Uval[ext + k0] : 0.0;
+                v1[t] = (t < G && j1 >= 0) ? (double)Uval[ext + k1] : 0.0;
+            }
+            double lin[GM * (GM - 1) / 2 + 1]; // lin[u(u-1)/2 + t] = U[s+t][s+u], t < u
 #pragma unroll
-        for (int t = 0; t < GMAX; ++t)
-            if (t < G) acc[t] = warp_sum(acc[t]);
-        if (lane == 0) {
-            double zl[GMAX];
+            for (int u = 1; u < GM; ++u)
 #pragma unroll
-            for (int t = GMAX - 1; t >= 0; --t) {
-                if (t < G) {
-                    double v = y[s + t] - acc[t];
+                for (int t = 0; t < u; ++t)
+                    lin[u * (u - 1) / 2 + t] = (u < G) ? (double)Uval[base[t] + (u - t)] : 0.0;
+            const double z0 = (j0 >= 0) ? get_dep(z, zbuf, j0, e + 1, rowEnd, row0, err) : 0.0;
+            const double z1 = (j1 >= 0) ? get_dep(z, zbuf, j1, e + 1, rowEnd, row0, err) : 0.0;
 #pragma unroll
-                    for (int u = t + 1; u < GMAX; ++u)
-                        if (u < G) v = fma(-(double)Uval[base[t] + (u - t)], zl[u], v);
-                    zl[t] = v * invd[s + t];
-                }
+            for (int t = 0; t < GM; ++t) acc[t] = fma(v1[t], z1, v0[t] * z0);
+            for (int32_t k = lane + 64; k < mu; k += 32) {
+                const int32_t j = Ucol[be + 1 + k];
+                const double zj = get_dep(z, zbuf, j, e + 1, rowEnd, row0, err);
+#pragma unroll
+                for (int t = 0; t < GM; ++t)
+                    if (t < G) acc[t] = fma((double)Uval[base[t] + (G - t) + k], zj, acc[t]);
             }
 #pragma unroll
-            for (int t = 0; t < GMAX; ++t) {
-                if (t < G) {
-                    st_relaxed(z + s + t, zl[t]);
-                    if (PCG) {
-                        y[s + t] = sentinel_d();
-                        dot = fma(r[s + t], zl[t], dot);
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int t = 0; t < GM; ++t)
+                    if (t < G) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+            if (lane == 0) {
+                double zl[GM];
+#pragma unroll
+                for (int t = GM - 1; t >= 0; --t) {
+                    if (t < G) {
+                        double v = yy[t] - acc[t];
+#pragma unroll
+                        for (int u = t + 1; u < GM; ++u)
+                            if (u < G) v = fma(-lin[u * (u - 1) / 2 + t], zl[u], v);
+                        zl[t] = v * iv[t];
+                        st_relaxed(z + s + t, zl[t]);
+                        zbuf[s - row0 + t] = zl[t];
+                        if (PCG) {
+                            y[s + t] = sentinel_d();
+                            dot = fma(rr[t], zl[t], dot);
+                        }
                     }
                 }
             }
+            __syncwarp();
         }
     }
     if (PCG) {
@@ -257,8 +339,20 @@ __global__ void __launch_bounds__(SPMV_BLOCK) k_spmv(int64_t n, const int32_t *_
     double d1 = 0.0, d2 = 0.0;
     for (int64_t i = w; i < n; i += nw) {
         const int32_t a = rowptr[i], e = rowptr[i + 1];
-        double s = 0.0;
-        for (int32_t p = a + lane; p < e; p += 32) s = fma(val[p], __ldg(x + col[p]), s);
+        // all loads of up to 128 entries in flight before the first use
+        int32_t c[4];
+        double v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int32_t p = a + lane + 32 * k;
+            c[k] = (p < e) ? __ldg(col + p) : -1;
+            v[k] = (p < e) ? __ldg(val + p) : 0.0;
+        }
+        double xv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) xv[k] = (c[k] >= 0) ? __ldg(x + c[k]) : 0.0;
+        double s = fma(v[3], xv[3], fma(v[2], xv[2], fma(v[1], xv[1], v[0] * xv[0])));
+        for (int32_t p = a + lane + 128; p < e; p += 32) s = fma(val[p], __ldg(x + col[p]), s);
         s = warp_sum(s);
         if (lane == 0) {
             if (MODE == 2) {
@@ -471,28 +565,68 @@ static unsigned spmv_grid(gic_handle *h, int64_t n)
     return (unsigned)b;
 }
 
+static int solve_chunk(gic_handle *h, const Pattern &P)
+{
+    int g = P.max_group > 0 ? P.max_group : 1;
+    int c = h->tune_chunk > 0 ? h->tune_chunk : 32;
+    if (c * g > MAXCHUNK_ROWS) c = MAXCHUNK_ROWS / g;
+    return c < 1 ? 1 : c;
+}
+
+static int64_t solve_warps(gic_handle *h, const Pattern &P, int chunk)
+{
+    int64_t nchunks = ((int64_t)P.ngroups + chunk - 1) / chunk;
+    if (h->tune_solve_warps_per_sm > 0) {
+        int64_t cap = (int64_t)h->tune_solve_warps_per_sm * h->num_sms;
+        if (nchunks > cap) nchunks = cap;
+    }
+    return nchunks;
+}
+
+template <typename TL, int GM>
+static int launch_lsolve_g(gic_handle *h, const Pattern &P, const TL *Lval, const double *invd, const double *r,
+                           double *y, Scalars *sc)
+{
+    int32_t ng = P.ngroups;
+    int chunk = solve_chunk(h, P);
+    const int32_t *g = P.grp, *lr = P.Lrowptr, *lc = P.Lcol;
+    unsigned *er = h->dev_err;
+    void *args[] = {&ng, &chunk, &g, &lr, &lc, &Lval, &invd, &r, &y, &er, &sc};
+    size_t smem = (size_t)(SOLVE_BLOCK / 32) * MAXCHUNK_ROWS * sizeof(double);
+    return launch_persistent(h, (const void *)k_lsolve<TL, GM>, SOLVE_BLOCK, smem, solve_warps(h, P, chunk), args);
+}
+
 template <typename TL>
 static int launch_lsolve(gic_handle *h, const Pattern &P, const TL *Lval, const double *invd, const double *r,
                          double *y, Scalars *sc)
 {
+    if (P.max_group <= 1) return launch_lsolve_g<TL, 1>(h, P, Lval, invd, r, y, sc);
+    if (P.max_group <= 3) return launch_lsolve_g<TL, 3>(h, P, Lval, invd, r, y, sc);
+    return launch_lsolve_g<TL, GMAX>(h, P, Lval, invd, r, y, sc);
+}
+
+template <typename TL, bool PCG, int GM>
+static int launch_ltsolve_g(gic_handle *h, const Pattern &P, const TL *Uval, const double *invd, double *y, double *z,
+                            const double *r, double *partials, Scalars *sc)
+{
     int32_t ng = P.ngroups;
-    const int32_t *g = P.grp, *lr = P.Lrowptr, *lc = P.Lcol;
+    int chunk = solve_chunk(h, P);
+    const int32_t *g = P.grp, *ur = P.Urowptr, *uc = P.Ucol;
     unsigned *er = h->dev_err;
-    void *args[] = {&ng, &g, &lr, &lc, &Lval, &invd, &r, &y, &er, &sc};
-    return launch_persistent(h, (const void *)k_lsolve<TL>, SOLVE_BLOCK, 0, ng, args);
+    void *args[] = {&ng, &chunk, &g, &ur, &uc, &Uval, &invd, &y, &z, &r, &partials, &er, &sc};
+    int64_t need = solve_warps(h, P, chunk);
+    if (PCG && need > MAX_PARTIALS) need = MAX_PARTIALS; // grid warps <= partial slots
+    size_t smem = (size_t)(SOLVE_BLOCK / 32) * MAXCHUNK_ROWS * sizeof(double);
+    return launch_persistent(h, (const void *)k_ltsolve<TL, PCG, GM>, SOLVE_BLOCK, smem, need, args);
 }
 
 template <typename TL, bool PCG>
 static int launch_ltsolve(gic_handle *h, const Pattern &P, const TL *Uval, const double *invd, double *y, double *z,
                           const double *r, double *partials, Scalars *sc)
 {
-    int32_t ng = P.ngroups;
-    const int32_t *g = P.grp, *ur = P.Urowptr, *uc = P.Ucol;
-    unsigned *er = h->dev_err;
-    void *args[] = {&ng, &g, &ur, &uc, &Uval, &invd, &y, &z, &r, &partials, &er, &sc};
-    int64_t need = ng;
-    if (PCG && need > MAX_PARTIALS) need = MAX_PARTIALS; // grid warps <= partial slots
-    return launch_persistent(h, (const void *)k_ltsolve<TL, PCG>, SOLVE_BLOCK, 0, need, args);
+    if (P.max_group <= 1) return launch_ltsolve_g<TL, PCG, 1>(h, P, Uval, invd, y, z, r, partials, sc);
+    if (P.max_group <= 3) return launch_ltsolve_g<TL, PCG, 3>(h, P, Uval, invd, y, z, r, partials, sc);
+    return launch_ltsolve_g<TL, PCG, GMAX>(h, P, Uval, invd, y, z, r, partials, sc);
 }
 
 template <typename TL>
@@ -810,6 +944,16 @@ int gic_profile_read(gic_handle *h, double *ms, int64_t *launches)
         if (launches) launches[k] = pr.launches[k];
     }
     return GIC_OK;
+}
+
+int gic_set_tuning(gic_handle *h, int key, int value)
+{
+    if (!h || value < 0) return GIC_ERR_INVALID_ARG;
+    switch (key) {
+    case GIC_TUNE_SOLVE_CHUNK: h->tune_chunk = value; return GIC_OK;
+    case GIC_TUNE_SOLVE_WARPS_PER_SM: h->tune_solve_warps_per_sm = value; return GIC_OK;
+    default: return GIC_ERR_INVALID_ARG;
+    }
 }
 
 int gic_launch_count(gic_handle *h, int64_t *count)

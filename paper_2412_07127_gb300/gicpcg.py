@@ -62,6 +62,7 @@ _SIGS = {
     "gic_profile_read": (_int, [_vp, C.POINTER(_dbl), C.POINTER(_i64)]),
     "gic_solve_error_flags": (_int, [_vp, C.POINTER(C.c_uint)]),
     "gic_launch_count": (_int, [_vp, C.POINTER(_i64)]),
+    "gic_set_tuning": (_int, [_vp, _int, _int]),
     "gic_solve_host": (_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _int, _dbl, _int,
                               C.POINTER(_i32), C.POINTER(_dbl), C.POINTER(_dbl), C.POINTER(_int),
                               _vp, _sz]),
@@ -302,6 +303,13 @@ def error_flags(h: Handle):
     f = C.c_uint()
     _call("gic_solve_error_flags", h.h, C.byref(f))
     return f.value
+
+
+GIC_TUNE_SOLVE_CHUNK, GIC_TUNE_SOLVE_WARPS_PER_SM = 0, 1
+
+
+def set_tuning(h: Handle, key, value):
+    _call("gic_set_tuning", h.h, key, value)
 
 
 def launch_count(h: Handle):

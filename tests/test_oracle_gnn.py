@@ -111,6 +111,24 @@ def test_correction_keeps_positive_diagonal():
     assert np.allclose(Lc[diag], L.val[diag] * np.exp(g[diag] / 2), rtol=1e-15)
 
 
+def test_correct_backward_finite_differences():
+    N = 2
+    A = O.fem_hex_assemble(N, I.material_field(N, 2))
+    T = O.lower(A)
+    L, _ = O.ic0(A)
+    rng = np.random.default_rng(4)
+    g = rng.normal(0, 0.3, T.nnz)
+    c = rng.standard_normal(T.nnz)
+    dg = O.correct_backward(T, L.val, g, c)
+    h = 1e-6
+    for p in range(0, T.nnz, 7):
+        gp, gm = g.copy(), g.copy()
+        gp[p] += h
+        gm[p] -= h
+        fd = (c @ O.correct(T, L.val, gp) - c @ O.correct(T, L.val, gm)) / (2 * h)
+        assert np.isclose(dg[p], fd, rtol=1e-7, atol=1e-9)
+
+
 def test_probe_loss_single_probe_equals_dense():
     N = 2
     A = O.fem_hex_assemble(N, I.material_field(N, 8))
