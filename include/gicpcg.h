@@ -248,10 +248,8 @@ int gic_adam_step(gic_handle *h, int64_t np, float *theta, const float *grad, fl
                   float *m2, int t, double lr);
 
 /* Tuning of the triangular-solve schedule (no effect on results):
- * GIC_TUNE_SOLVE_CHUNK = consecutive row groups one warp solves in order
- * (0 = default 32, capped so a chunk holds at most 512 rows);
- * GIC_TUNE_SOLVE_WARPS_PER_SM = cap on solve warps per SM (0 = none). */
-#define GIC_TUNE_SOLVE_CHUNK 0
+ * GIC_TUNE_SOLVE_WARPS_PER_SM = cap on resident solve warps per SM
+ * (0 = no cap). */
 #define GIC_TUNE_SOLVE_WARPS_PER_SM 1
 int gic_set_tuning(gic_handle *h, int key, int value);
 

@@ -15,6 +15,9 @@
 #include <stdio.h>
 #include <stdlib.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "gic_internal.cuh"
 
 namespace gic {
@@ -302,6 +305,84 @@ __global__ void k_levels(int32_t ngroups, const int32_t *grp, const int32_t *Lro
     if (lane == 0) atomicMax(maxlev, mx_all);
 }
 
+// ------------------------------------------------------------ schedule
+__global__ void k_chunk_flags(int32_t ngroups, const int32_t *grp, const int32_t *level, int32_t *cflag)
+{
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += (int64_t)gridDim.x * blockDim.x)
+        cflag[g] = (g == 0) || (level[grp[g]] <= level[grp[g] - 1]);
+}
+
+__global__ void k_chunk_starts(int32_t ngroups, const int32_t *cflag, const int32_t *cid, int32_t *chunk_grp,
+                               int32_t nchunks)
+{
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += (int64_t)gridDim.x * blockDim.x)
+        if (cflag[g]) chunk_grp[cid[g]] = (int32_t)g;
+    if (blockIdx.x == 0 && threadIdx.x == 0) chunk_grp[nchunks] = ngroups;
+}
+
+// start and end level of every chunk
+__global__ void k_chunk_levels(int32_t nchunks, const int32_t *chunk_grp, const int32_t *grp, const int32_t *level,
+                               int32_t *lv_s, int32_t *lv_e)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks; c += (int64_t)gridDim.x * blockDim.x) {
+        lv_s[c] = level[grp[chunk_grp[c]]];
+        lv_e[c] = level[grp[chunk_grp[c + 1]] - 1];
+    }
+}
+
+__global__ void k_inverse_perm(int32_t cnt, const int32_t *ord, int32_t *pos)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += (int64_t)gridDim.x * blockDim.x)
+        pos[ord[k]] = (int32_t)k;
+}
+
+// row -> chunk position maps, then: every external dependency of a group
+// must sit in a chunk that comes earlier in the sweep's order
+__global__ void k_row_chunk(int32_t nchunks, const int32_t *chunk_grp, const int32_t *grp, int32_t *rowchunk)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks; c += (int64_t)gridDim.x * blockDim.x)
+        for (int32_t i = grp[chunk_grp[c]]; i < grp[chunk_grp[c + 1]]; ++i) rowchunk[i] = (int32_t)c;
+}
+
+__global__ void k_check_order(int32_t ngroups, const int32_t *grp, const int32_t *Lrowptr, const int32_t *Lcol,
+                              const int32_t *Urowptr, const int32_t *Ucol, const int32_t *rowchunk,
+                              const int32_t *pos_f, const int32_t *pos_b, unsigned *bad)
+{
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = grp[g], e = grp[g + 1] - 1;
+        const int32_t c = rowchunk[s];
+        for (int32_t p = Lrowptr[s]; p < Lrowptr[s + 1] - 1; ++p) {
+            const int32_t cj = rowchunk[Lcol[p]];
+            if (cj != c && pos_f[cj] >= pos_f[c]) atomicOr(bad, 1u);
+        }
+        for (int32_t q = Urowptr[e] + 1; q < Urowptr[e + 1]; ++q) {
+            const int32_t cj = rowchunk[Ucol[q]];
+            if (cj != c && pos_b[cj] >= pos_b[c]) atomicOr(bad, 2u);
+        }
+    }
+}
+
+// ------------------------------------------------------------ SELL-32
+__global__ void k_sell_widths(int64_t n, int64_t nslices, const int32_t *rowptr, int32_t *w)
+{
+    for (int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; sl < nslices; sl += (int64_t)gridDim.x * blockDim.x) {
+        int32_t m = 0;
+        for (int64_t i = sl * 32; i < min(n, sl * 32 + 32); ++i) m = max(m, rowptr[i + 1] - rowptr[i]);
+        w[sl] = m;
+    }
+}
+
+__global__ void k_sell_cols(int64_t n, const int32_t *rowptr, const int32_t *col, const int64_t *sptr,
+                            const int32_t *w, int32_t *scol)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t sl = i >> 5;
+        const int t = (int)(i & 31);
+        const int32_t a = rowptr[i], len = rowptr[i + 1] - a;
+        for (int32_t k = 0; k < w[sl]; ++k) scol[sptr[sl] + (int64_t)k * 32 + t] = (k < len) ? col[a + k] : (int32_t)i;
+    }
+}
+
 static const int T_ROWS = 256;
 
 static unsigned grid_rows(gic_handle *h, int64_t n)
@@ -355,7 +436,108 @@ static void free_pattern(Pattern &p)
     cudaFree(p.grp);
     cudaFree(p.level);
     cudaFree(p.Lrow);
+    cudaFree(p.chunk_grp);
+    cudaFree(p.ord_f);
+    cudaFree(p.ord_b);
+    cudaFree(p.sell_ptr);
+    cudaFree(p.sell_w);
+    cudaFree(p.sell_col);
     p = Pattern();
+}
+
+// Chunks, their sweep orders and the dependency check (see Pattern).
+static int build_schedule(gic_handle *h, Pattern &P, int32_t *cflag, int32_t *cid, int32_t *lv_s, int32_t *lv_e)
+{
+    const int32_t ng = P.ngroups;
+    unsigned gr = grid_rows(h, ng);
+    long long tot = 0;
+    ++h->launches;
+    k_chunk_flags<<<gr, T_ROWS, 0, h->stream>>>(ng, P.grp, P.level, cflag);
+    GIC_CUDA_TRY(cudaGetLastError());
+    GIC_TRY(scan_i32<false>(h, cflag, ng, cid, &tot));
+    int32_t nc = (int32_t)tot;
+    int32_t *rowchunk = nullptr, *pos = nullptr;
+    unsigned *bad = (unsigned *)((char *)h->dev_small + 62000);
+    std::vector<int32_t> hs, he, of, ob;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        // attempt 0: level-monotone runs; attempt 1: one group per chunk
+        cudaFree(P.chunk_grp); cudaFree(P.ord_f); cudaFree(P.ord_b);
+        P.chunk_grp = P.ord_f = P.ord_b = nullptr;
+        if (attempt == 1) nc = ng;
+        GIC_CUDA_TRY(cudaMalloc(&P.chunk_grp, sizeof(int32_t) * (size_t)(nc + 1)));
+        GIC_CUDA_TRY(cudaMalloc(&P.ord_f, sizeof(int32_t) * (size_t)nc));
+        GIC_CUDA_TRY(cudaMalloc(&P.ord_b, sizeof(int32_t) * (size_t)nc));
+        if (attempt == 0) {
+            ++h->launches;
+            k_chunk_starts<<<gr, T_ROWS, 0, h->stream>>>(ng, cflag, cid, P.chunk_grp, nc);
+        } else {
+            std::vector<int32_t> id(nc + 1);
+            for (int32_t k = 0; k <= nc; ++k) id[k] = k;
+            GIC_CUDA_TRY(cudaMemcpyAsync(P.chunk_grp, id.data(), sizeof(int32_t) * (size_t)(nc + 1),
+                                         cudaMemcpyHostToDevice, h->stream));
+        }
+        ++h->launches;
+        k_chunk_levels<<<grid_rows(h, nc), T_ROWS, 0, h->stream>>>(nc, P.chunk_grp, P.grp, P.level, lv_s, lv_e);
+        GIC_CUDA_TRY(cudaGetLastError());
+        hs.resize(nc); he.resize(nc); of.resize(nc); ob.resize(nc);
+        GIC_CUDA_TRY(cudaMemcpyAsync(hs.data(), lv_s, sizeof(int32_t) * (size_t)nc, cudaMemcpyDeviceToHost, h->stream));
+        GIC_CUDA_TRY(cudaMemcpyAsync(he.data(), lv_e, sizeof(int32_t) * (size_t)nc, cudaMemcpyDeviceToHost, h->stream));
+        GIC_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        for (int32_t k = 0; k < nc; ++k) of[k] = ob[k] = k;
+        std::stable_sort(of.begin(), of.end(), [&](int32_t a, int32_t b) { return hs[a] < hs[b]; });
+        std::stable_sort(ob.begin(), ob.end(), [&](int32_t a, int32_t b) { return he[a] > he[b]; });
+        GIC_CUDA_TRY(cudaMemcpyAsync(P.ord_f, of.data(), sizeof(int32_t) * (size_t)nc, cudaMemcpyHostToDevice, h->stream));
+        GIC_CUDA_TRY(cudaMemcpyAsync(P.ord_b, ob.data(), sizeof(int32_t) * (size_t)nc, cudaMemcpyHostToDevice, h->stream));
+        if (attempt == 1) break; // level order per group is always valid
+        GIC_CUDA_TRY(cudaMalloc(&rowchunk, sizeof(int32_t) * (size_t)P.n));
+        GIC_CUDA_TRY(cudaMalloc(&pos, sizeof(int32_t) * 2 * (size_t)nc));
+        ++h->launches;
+        k_row_chunk<<<grid_rows(h, nc), T_ROWS, 0, h->stream>>>(nc, P.chunk_grp, P.grp, rowchunk);
+        ++h->launches;
+        k_inverse_perm<<<grid_rows(h, nc), T_ROWS, 0, h->stream>>>(nc, P.ord_f, pos);
+        ++h->launches;
+        k_inverse_perm<<<grid_rows(h, nc), T_ROWS, 0, h->stream>>>(nc, P.ord_b, pos + nc);
+        GIC_CUDA_TRY(cudaMemsetAsync(bad, 0, 4, h->stream));
+        ++h->launches;
+        k_check_order<<<gr, T_ROWS, 0, h->stream>>>(ng, P.grp, P.Lrowptr, P.Lcol, P.Urowptr, P.Ucol, rowchunk, pos,
+                                                    pos + nc, bad);
+        unsigned hb = 1;
+        GIC_CUDA_TRY(cudaMemcpyAsync(&hb, bad, 4, cudaMemcpyDeviceToHost, h->stream));
+        GIC_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        cudaFree(rowchunk);
+        cudaFree(pos);
+        rowchunk = pos = nullptr;
+        if (hb == 0) break;
+    }
+    P.nchunks = nc;
+    P.chunked = (nc < ng) ? 1 : 0;
+    return GIC_OK;
+}
+
+static int build_sell(gic_handle *h, Pattern &P)
+{
+    P.nslices = (P.n + 31) / 32;
+    GIC_CUDA_TRY(cudaMalloc(&P.sell_w, sizeof(int32_t) * (size_t)P.nslices));
+    GIC_CUDA_TRY(cudaMalloc(&P.sell_ptr, sizeof(int64_t) * (size_t)(P.nslices + 1)));
+    ++h->launches;
+    k_sell_widths<<<grid_rows(h, P.nslices), T_ROWS, 0, h->stream>>>(P.n, P.nslices, P.rowptr, P.sell_w);
+    GIC_CUDA_TRY(cudaGetLastError());
+    std::vector<int32_t> w(P.nslices);
+    std::vector<int64_t> ptr(P.nslices + 1);
+    GIC_CUDA_TRY(cudaMemcpyAsync(w.data(), P.sell_w, sizeof(int32_t) * (size_t)P.nslices, cudaMemcpyDeviceToHost,
+                                 h->stream));
+    GIC_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    ptr[0] = 0;
+    for (int64_t k = 0; k < P.nslices; ++k) ptr[k + 1] = ptr[k] + 32 * (int64_t)w[k];
+    P.sell_nnz = ptr[P.nslices];
+    GIC_CUDA_TRY(cudaMemcpyAsync(P.sell_ptr, ptr.data(), sizeof(int64_t) * (size_t)(P.nslices + 1),
+                                 cudaMemcpyHostToDevice, h->stream));
+    GIC_CUDA_TRY(cudaMalloc(&P.sell_col, sizeof(int32_t) * (size_t)P.sell_nnz));
+    ++h->launches;
+    k_sell_cols<<<grid_rows(h, P.n), T_ROWS, 0, h->stream>>>(P.n, P.rowptr, P.col, P.sell_ptr, P.sell_w, P.sell_col);
+    GIC_CUDA_TRY(cudaGetLastError());
+    GIC_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return GIC_OK;
 }
 
 static int analyze_impl(gic_handle *h, int64_t n, int64_t nnz, const int32_t *rowptr, const int32_t *col, Pattern &P)
@@ -370,6 +552,7 @@ static int analyze_impl(gic_handle *h, int64_t n, int64_t nnz, const int32_t *ro
     int32_t *Lcnt = tmp, *same = tmp + (n + 1), *Ucnt = tmp + 2 * (n + 1), *key = tmp + 3 * (n + 1);
     int32_t *runstart = tmp + 4 * (n + 1), *gflag = tmp + 5 * (n + 1), *gid = tmp + 6 * (n + 1);
     int32_t *stats = tmp + 7 * (n + 1);
+    int32_t *tmp2_a = key, *tmp2_b = runstart; // free again once the groups are built
     int rc = GIC_OK;
     long long tot = 0;
     unsigned flags = 0;
@@ -445,6 +628,8 @@ static int analyze_impl(gic_handle *h, int64_t n, int64_t nnz, const int32_t *ro
     }
     STEP(read_and_clear_dev_err(h, &flags));
     if (flags & ERR_TIMEOUT) { rc = GIC_ERR_TIMEOUT; goto out; }
+    STEP(build_schedule(h, P, gflag, gid, tmp2_a, tmp2_b));
+    STEP(build_sell(h, P));
 out:
 #undef STEP
 #undef CUDA_STEP

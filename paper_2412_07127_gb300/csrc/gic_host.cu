@@ -32,7 +32,8 @@ static HostWs carve_host(int64_t n, int64_t nnz, int with_gnn, int l_dtype, void
     o.L32 = (float *)(c + off); off += (l_dtype == GIC_F32) ? al(4 * (size_t)nnzL) : 0;
     o.gnn_bytes = with_gnn ? gnn_infer_ws_bytes(n, nnzL) : 0;
     o.gnn = c + off; off += al(o.gnn_bytes);
-    o.pcg_bytes = pcg_ws_bytes(n, nnzL, l_dtype);
+    // SELL-32 padding: at most 31 entries of padding per row beyond A's own
+    o.pcg_bytes = pcg_ws_bytes(n, nnzL, nnz + 32 * n, l_dtype);
     o.pcg = c + off; off += al(o.pcg_bytes);
     o.bytes = off;
     return o;

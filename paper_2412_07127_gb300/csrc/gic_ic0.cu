@@ -50,7 +50,9 @@ __device__ __forceinline__ int find_in(const int32_t *J, int lo, int hi, int32_t
     return -1;
 }
 
-__global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t ngroups, const int32_t *__restrict__ grp,
+__global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t nchunks, const int32_t *__restrict__ ord,
+                                                       const int32_t *__restrict__ chunk_grp,
+                                                       const int32_t *__restrict__ grp,
                                                        const int32_t *__restrict__ Arowptr,
                                                        const double *__restrict__ valA,
                                                        const int32_t *__restrict__ Lrowptr,
@@ -65,7 +67,9 @@ __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t ngroups, const in
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const double qnan = __longlong_as_double(0x7ff8000000000000ll);
 
-    for (int64_t g = w; g < ngroups; g += nw) {
+    for (int64_t pos = w; pos < nchunks; pos += nw) {
+      const int32_t ch = ord[pos];
+      for (int32_t g = chunk_grp[ch]; g < chunk_grp[ch + 1]; ++g) {
         const int32_t s = grp[g];
         const int G = grp[g + 1] - s;
         const int32_t b0 = Lrowptr[s];
@@ -73,6 +77,7 @@ __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t ngroups, const in
 
         // 1. external columns, their readiness (relaxed polling, one fence
         // after the last wait), their row starts and lengths
+        int32_t dp0 = -1, dp1 = -1;
         for (int u = lane; u < m; u += 32) {
             int32_t j = Lcol[b0 + u];
             S.J[u] = j;
@@ -80,7 +85,12 @@ __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t ngroups, const in
             const int32_t dpos = Lrowptr[j + 1] - 1;
             S.rs[u] = rs;
             S.off[u + 1] = dpos + 1 - rs; // length of row j (its diagonal included)
-            wait_value(Lval + dpos, err);
+            if (u < 32) dp0 = dpos; else if (u < 64) dp1 = dpos;
+        }
+        {   // one lane at a time polls the diagonal written last
+            double d0 = (dp0 >= 0) ? ld_relaxed(Lval + dp0) : 0.0;
+            double d1 = (dp1 >= 0) ? ld_relaxed(Lval + dp1) : 0.0;
+            wait_deps<true>(Lval, dp0, dp1, d0, d1, err);
         }
         __syncwarp();
         fence_acq_rel(); // pairs with the producers' release of each diagonal
@@ -202,6 +212,7 @@ __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t ngroups, const in
             if (lane == 0) st_release(Lval + lb + m + t, piv);
             __syncwarp();
         }
+      }
     }
 }
 
@@ -229,11 +240,11 @@ static int ic0_once(gic_handle *h, const Pattern &P, const double *valA, double 
         GIC_CUDA_TRY(cudaFuncSetAttribute(k_ic0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr_set[h->device & 63] = 1;
     }
-    int32_t ng = P.ngroups;
-    const int32_t *g = P.grp, *ar = P.rowptr, *lr = P.Lrowptr, *lc = P.Lcol;
+    int32_t nc = P.nchunks;
+    const int32_t *ord = P.ord_f, *cg = P.chunk_grp, *g = P.grp, *ar = P.rowptr, *lr = P.Lrowptr, *lc = P.Lcol;
     unsigned *er = h->dev_err;
-    void *args[] = {&ng, &g, &ar, &valA, &lr, &lc, &valL, &alpha, &bad_dev, &er};
-    GIC_TRY(launch_persistent(h, (const void *)k_ic0, IC_WARPS * 32, smem, ng, args));
+    void *args[] = {&nc, &ord, &cg, &g, &ar, &valA, &lr, &lc, &valL, &alpha, &bad_dev, &er};
+    GIC_TRY(launch_persistent(h, (const void *)k_ic0, IC_WARPS * 32, smem, nc, args));
     unsigned long long *hb = (unsigned long long *)((char *)h->host_pinned + 2048);
     GIC_CUDA_TRY(cudaMemcpyAsync(hb, bad_dev, sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
     unsigned flags = 0;

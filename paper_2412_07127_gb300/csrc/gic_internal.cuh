@@ -2,6 +2,7 @@
 // Nothing here is visible through the C-ABI; include/gicpcg.h is the boundary.
 #pragma once
 #include <cuda_runtime.h>
+#include <limits.h>
 #include <stdint.h>
 #include <stddef.h>
 
@@ -100,6 +101,36 @@ __device__ __forceinline__ double wait_value(const double *p, unsigned *err)
 
 __device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
+// Wait until neither lane value is the sentinel: one polling lane at a
+// time, on the outstanding dependency produced last (the largest column in
+// the forward sweep, LAST_IS_MAX; the smallest in the backward sweep).
+template <bool LAST_IS_MAX>
+__device__ __forceinline__ void wait_deps(const double *y, int32_t j0, int32_t j1, double &y0, double &y1,
+                                          unsigned *err)
+{
+    bool p0 = j0 >= 0 && is_sentinel(y0), p1 = j1 >= 0 && is_sentinel(y1);
+    unsigned pend = __ballot_sync(0xffffffffu, p0 || p1);
+    for (int round = 0; pend && round < 130; ++round) {
+        int32_t mine, jm;
+        if (LAST_IS_MAX) {
+            mine = max(p0 ? j0 : -1, p1 ? j1 : -1);
+            jm = __reduce_max_sync(0xffffffffu, mine);
+        } else {
+            mine = min(p0 ? j0 : INT_MAX, p1 ? j1 : INT_MAX);
+            jm = __reduce_min_sync(0xffffffffu, mine);
+        }
+        if (mine == jm) wait_value(y + jm, err);
+        __syncwarp();
+        if (p0) { y0 = ld_relaxed(y + j0); p0 = is_sentinel(y0); }
+        if (p1) { y1 = ld_relaxed(y + j1); p1 = is_sentinel(y1); }
+        pend = __ballot_sync(0xffffffffu, p0 || p1);
+        if (pend && *((volatile unsigned *)err) != 0u) break;
+    }
+    if (p0) y0 = __longlong_as_double(0x7ff8000000000000ll);
+    if (p1) y1 = __longlong_as_double(0x7ff8000000000000ll);
+}
+
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v)
 {
@@ -124,6 +155,21 @@ struct Pattern {
     int32_t *grp = nullptr;   // ngroups+1 start rows
     int32_t *level = nullptr; // n row levels
     int32_t *Lrow = nullptr;  // nnzL: row of every L entry (edge -> its row node)
+    // Solve schedule: chunks = runs of consecutive groups with increasing
+    // levels (for hex elasticity the x-pencils), ordered by start level for
+    // the forward sweep and by end level (descending) for the backward one.
+    // Every cross-chunk dependency points to an earlier chunk in that order
+    // (checked; otherwise every group is its own chunk, in level order).
+    int32_t nchunks = 0;
+    int chunked = 0;
+    int32_t *chunk_grp = nullptr;     // nchunks+1 start groups
+    int32_t *ord_f = nullptr, *ord_b = nullptr;
+    // SELL-32 layout of A's pattern for SpMV: slices of 32 rows, column-major
+    // inside a slice, padded to the slice's longest row with the row itself.
+    int64_t nslices = 0, sell_nnz = 0;
+    int64_t *sell_ptr = nullptr;      // nslices+1 entry offsets
+    int32_t *sell_w = nullptr;        // nslices widths
+    int32_t *sell_col = nullptr;      // sell_nnz column indices
     int device = 0;
 };
 
@@ -144,12 +190,11 @@ struct gic_handle {
     void *dev_small = nullptr;     // 64 KiB of library scratch (scalars, Ke)
     void *host_pinned = nullptr;   // 4 KiB pinned readback area
     long long launches = 0;        // kernels this handle has launched
-    int tune_chunk = 0;            // groups per warp chunk in the solves (0: default)
     int tune_solve_warps_per_sm = 0; // cap on resident solve warps per SM (0: none)
 };
 
 namespace gic {
-size_t pcg_ws_bytes(int64_t n, int64_t nnzL, int l_dtype);
+size_t pcg_ws_bytes(int64_t n, int64_t nnzL, int64_t sell_nnz, int l_dtype);
 size_t gnn_infer_ws_bytes(int64_t n, int64_t nnzL);
 int gnn_correct_inplace(gic_handle *h, const gic_pattern *P, const double *valA, const float *theta_host,
                         double *L, void *ws, size_t ws_bytes, int *kept);

@@ -17,6 +17,7 @@
 // Every dot product is reduced deterministically: per-block (or per-warp)
 // partials in a fixed layout, summed in index order by the last block to
 // finish, which also computes alpha / beta and the stop test on the device.
+#include <limits.h>
 #include <math.h>
 #include <stdio.h>
 
@@ -92,59 +93,61 @@ __global__ void k_transpose_vals(int64_t n, int64_t nnzL, const int32_t *tperm, 
 }
 
 // ------------------------------------------------------------ SpTRSV
-// A warp owns a chunk of `chunk` consecutive groups and solves them in
-// order, keeping the chunk's solution values in shared memory: a dependency
-// inside the chunk (for hex elasticity the neighbour along x) is read from
-// there, one outside it from global memory, waiting on the sentinel. Chunks
-// are dealt round-robin to a co-resident grid in dependency order. Every
-// index and factor value a group needs is loaded before its wait, so the
-// critical path after the last dependency lands is: FMAs, one warp
-// reduction, the dense in-group block, one store.
-constexpr int MAXCHUNK_ROWS = 512; // chunk * max group rows, per warp buffer
+// Schedule: the pattern's chunks (runs of consecutive row groups with
+// increasing levels; for hex elasticity the x-pencils) are dealt round-robin
+// to a co-resident grid in an order where every cross-chunk dependency
+// points to an earlier chunk, so the first unfinished chunk can always
+// progress. One warp solves a chunk group by group; the last 64 rows it
+// produced stay in a shared-memory ring, so the dependency on the previous
+// group (the neighbour along x) never leaves the SM. Every index and factor
+// value a group needs is loaded before it waits; then one lane polls the
+// outstanding dependency with the largest column (the last one produced)
+// and the others reload once it lands. "Not yet computed" is a sentinel NaN
+// stored in the solution vector, so the flag and the datum are one word.
+constexpr int RING = 64;
 
-// dependency j: from the warp's chunk buffer (rows [lo, hi), stored at
-// buf[j - base]) or from global memory, waiting on the sentinel
-__device__ __forceinline__ double get_dep(const double *y, const double *buf, int32_t j, int32_t lo, int32_t hi,
-                                          int32_t base, unsigned *err)
+// value of dependency j: from the ring if this warp produced it recently,
+// else one relaxed load from global memory (may still be the sentinel)
+__device__ __forceinline__ double dep_first(const double *y, const double *ring, int32_t j, int32_t lo, int32_t hi)
 {
-    if (j >= lo && j < hi) return buf[j - base];
-    return wait_value(y + j, err);
+    if (j >= lo && j < hi) return ring[j & (RING - 1)];
+    return ld_relaxed(y + j);
 }
 
 // Forward: y_i = (r_i - sum_{j<i} L_ij y_j) / L_ii. y must hold the sentinel.
 template <typename TL, int GM>
-__global__ void __launch_bounds__(SOLVE_BLOCK) k_lsolve(int32_t ngroups, int chunk, const int32_t *__restrict__ grp,
+__global__ void __launch_bounds__(SOLVE_BLOCK) k_lsolve(int32_t nchunks, const int32_t *__restrict__ ord,
+                                                        const int32_t *__restrict__ chunk_grp,
+                                                        const int32_t *__restrict__ grp,
                                                         const int32_t *__restrict__ Lrowptr,
                                                         const int32_t *__restrict__ Lcol, const TL *__restrict__ Lval,
                                                         const double *__restrict__ invd, const double *__restrict__ r,
                                                         double *y, unsigned *err, const Scalars *sc)
 {
     if (sc && sc->done) return;
-    extern __shared__ double ybuf_all[];
+    __shared__ double ring_all[SOLVE_BLOCK / 32][RING];
     const int lane = threadIdx.x & 31;
-    double *ybuf = ybuf_all + (threadIdx.x >> 5) * MAXCHUNK_ROWS;
+    double *ring = ring_all[threadIdx.x >> 5];
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t nchunks = (ngroups + chunk - 1) / chunk;
-    for (int64_t c = w; c < nchunks; c += nw) {
-        const int64_t g0 = c * chunk;
-        const int64_t g1 = min(g0 + chunk, (int64_t)ngroups);
+    for (int64_t pos = w; pos < nchunks; pos += nw) {
+        const int32_t c = ord[pos];
+        const int32_t g0 = chunk_grp[c], g1 = chunk_grp[c + 1];
         const int32_t row0 = grp[g0];
-        for (int64_t g = g0; g < g1; ++g) {
+        for (int32_t g = g0; g < g1; ++g) {
             const int32_t s = grp[g];
             const int G = grp[g + 1] - s;
             const int32_t b0 = Lrowptr[s];
             const int32_t m = Lrowptr[s + 1] - b0 - 1;
+            const int32_t lo = max(row0, s - RING);
             int32_t base[GM];
             double acc[GM], rr[GM], iv[GM];
 #pragma unroll
             for (int t = 0; t < GM; ++t) {
                 base[t] = b0 + t * (m + 1) + (t * (t - 1)) / 2;
-                acc[t] = 0.0;
                 rr[t] = (t < G) ? r[s + t] : 0.0;
                 iv[t] = (t < G) ? invd[s + t] : 0.0;
             }
-            // prefetch two columns per lane and their values in every row
             const int32_t k0 = lane, k1 = lane + 32;
             const int32_t j0 = (k0 < m) ? Lcol[b0 + k0] : -1;
             const int32_t j1 = (k1 < m) ? Lcol[b0 + k1] : -1;
@@ -160,14 +163,15 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_lsolve(int32_t ngroups, int chu
 #pragma unroll
                 for (int u = 0; u < t; ++u)
                     lin[t * (t - 1) / 2 + u] = (t < G) ? (double)Lval[base[t] + m + u] : 0.0;
-            // wait for the external values (in-chunk values come from smem)
-            const double y0 = (j0 >= 0) ? get_dep(y, ybuf, j0, row0, s, row0, err) : 0.0;
-            const double y1 = (j1 >= 0) ? get_dep(y, ybuf, j1, row0, s, row0, err) : 0.0;
+            double y0 = (j0 >= 0) ? dep_first(y, ring, j0, lo, s) : 0.0;
+            double y1 = (j1 >= 0) ? dep_first(y, ring, j1, lo, s) : 0.0;
+            wait_deps<true>(y, j0, j1, y0, y1, err);
 #pragma unroll
             for (int t = 0; t < GM; ++t) acc[t] = fma(v1[t], y1, v0[t] * y0);
-            for (int32_t k = lane + 64; k < m; k += 32) { // rows longer than 64 external columns
+            for (int32_t k = lane + 64; k < m; k += 32) { // rows with more than 64 external columns
                 const int32_t j = Lcol[b0 + k];
-                const double yj = get_dep(y, ybuf, j, row0, s, row0, err);
+                double yj = dep_first(y, ring, j, lo, s), dummy = 0.0;
+                wait_deps<true>(y, j, -1, yj, dummy, err);
 #pragma unroll
                 for (int t = 0; t < GM; ++t)
                     if (t < G) acc[t] = fma((double)Lval[base[t] + k], yj, acc[t]);
@@ -187,7 +191,7 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_lsolve(int32_t ngroups, int chu
                         for (int u = 0; u < t; ++u) v = fma(-lin[t * (t - 1) / 2 + u], yl[u], v);
                         yl[t] = v * iv[t];
                         st_relaxed(y + s + t, yl[t]);
-                        ybuf[s - row0 + t] = yl[t];
+                        ring[(s + t) & (RING - 1)] = yl[t];
                     }
                 }
             }
@@ -197,12 +201,14 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_lsolve(int32_t ngroups, int chu
 }
 
 // Backward: z_i = (y_i - sum_{j>i} L_ji z_j) / L_ii on U = L^T. z must hold
-// the sentinel. Chunks and the groups inside them run from the last one
-// down. With PCG the kernel also resets y to the sentinel (for the next
-// forward solve) and forms r^T z, then beta = r_k^T z_k / r_{k-1}^T z_{k-1}
-// (Algorithm 1 line 13) in the last warp to finish.
+// the sentinel. Chunks run in the backward order and each one from its last
+// group down. With PCG the kernel also resets y to the sentinel (for the
+// next forward solve) and forms r^T z, then beta = r_k^T z_k /
+// r_{k-1}^T z_{k-1} (Algorithm 1 line 13) in the last warp to finish.
 template <typename TL, bool PCG, int GM>
-__global__ void __launch_bounds__(SOLVE_BLOCK) k_ltsolve(int32_t ngroups, int chunk, const int32_t *__restrict__ grp,
+__global__ void __launch_bounds__(SOLVE_BLOCK) k_ltsolve(int32_t nchunks, const int32_t *__restrict__ ord,
+                                                         const int32_t *__restrict__ chunk_grp,
+                                                         const int32_t *__restrict__ grp,
                                                          const int32_t *__restrict__ Urowptr,
                                                          const int32_t *__restrict__ Ucol, const TL *__restrict__ Uval,
                                                          const double *__restrict__ invd, double *y, double *z,
@@ -210,31 +216,29 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_ltsolve(int32_t ngroups, int ch
                                                          unsigned *err, Scalars *sc)
 {
     if (sc && sc->done) return;
-    extern __shared__ double zbuf_all[];
+    __shared__ double ring_all[SOLVE_BLOCK / 32][RING];
     const int lane = threadIdx.x & 31;
-    double *zbuf = zbuf_all + (threadIdx.x >> 5) * MAXCHUNK_ROWS;
+    double *ring = ring_all[threadIdx.x >> 5];
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t nchunks = (ngroups + chunk - 1) / chunk;
     double dot = 0.0;
-    for (int64_t cc = w; cc < nchunks; cc += nw) {
-        const int64_t c = nchunks - 1 - cc;
-        const int64_t g0 = c * chunk;
-        const int64_t g1 = min(g0 + chunk, (int64_t)ngroups);
-        const int32_t row0 = grp[g0], rowEnd = grp[g1];
-        for (int64_t g = g1 - 1; g >= g0; --g) {
+    for (int64_t pos = w; pos < nchunks; pos += nw) {
+        const int32_t c = ord[pos];
+        const int32_t g0 = chunk_grp[c], g1 = chunk_grp[c + 1];
+        const int32_t rowEnd = grp[g1];
+        for (int32_t g = g1 - 1; g >= g0; --g) {
             const int32_t s = grp[g];
             const int G = grp[g + 1] - s;
             const int32_t e = s + G - 1;
             const int32_t be = Urowptr[e];
             const int32_t mu = Urowptr[e + 1] - be - 1;
+            const int32_t hi = min(rowEnd, e + 1 + RING);
             int32_t base[GM];
             double acc[GM], yy[GM], rr[GM], iv[GM];
 #pragma unroll
             for (int t = 0; t < GM; ++t) {
                 // row s+t of U: G-t in-group entries (diagonal first), then mu
                 base[t] = (t < G) ? Urowptr[s + t] : 0;
-                acc[t] = 0.0;
                 yy[t] = (t < G) ? y[s + t] : 0.0;
                 rr[t] = (PCG && t < G) ? r[s + t] : 0.0;
                 iv[t] = (t < G) ? invd[s + t] : 0.0;
@@ -255,13 +259,15 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_ltsolve(int32_t ngroups, int ch
 #pragma unroll
                 for (int t = 0; t < u; ++t)
                     lin[u * (u - 1) / 2 + t] = (u < G) ? (double)Uval[base[t] + (u - t)] : 0.0;
-            const double z0 = (j0 >= 0) ? get_dep(z, zbuf, j0, e + 1, rowEnd, row0, err) : 0.0;
-            const double z1 = (j1 >= 0) ? get_dep(z, zbuf, j1, e + 1, rowEnd, row0, err) : 0.0;
+            double z0 = (j0 >= 0) ? dep_first(z, ring, j0, e + 1, hi) : 0.0;
+            double z1 = (j1 >= 0) ? dep_first(z, ring, j1, e + 1, hi) : 0.0;
+            wait_deps<false>(z, j0, j1, z0, z1, err);
 #pragma unroll
             for (int t = 0; t < GM; ++t) acc[t] = fma(v1[t], z1, v0[t] * z0);
             for (int32_t k = lane + 64; k < mu; k += 32) {
                 const int32_t j = Ucol[be + 1 + k];
-                const double zj = get_dep(z, zbuf, j, e + 1, rowEnd, row0, err);
+                double zj = dep_first(z, ring, j, e + 1, hi), dummy = 0.0;
+                wait_deps<false>(z, j, -1, zj, dummy, err);
 #pragma unroll
                 for (int t = 0; t < GM; ++t)
                     if (t < G) acc[t] = fma((double)Uval[base[t] + (G - t) + k], zj, acc[t]);
@@ -282,7 +288,7 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_ltsolve(int32_t ngroups, int ch
                             if (u < G) v = fma(-lin[u * (u - 1) / 2 + t], zl[u], v);
                         zl[t] = v * iv[t];
                         st_relaxed(z + s + t, zl[t]);
-                        zbuf[s - row0 + t] = zl[t];
+                        ring[(s + t) & (RING - 1)] = zl[t];
                         if (PCG) {
                             y[s + t] = sentinel_d();
                             dot = fma(rr[t], zl[t], dot);
@@ -386,6 +392,111 @@ __global__ void __launch_bounds__(SPMV_BLOCK) k_spmv(int64_t n, const int32_t *_
     if (MODE == 0) {
         *out_dot = t1;
     } else if (MODE == 1) {
+        sc->pw = t1;
+        if (!(t1 > 0.0) || !isfinite(t1)) {
+            sc->status = GIC_ERR_BREAKDOWN;
+            sc->done = 1;
+        } else {
+            sc->alpha = sc->rz / t1;
+        }
+    } else {
+        sc->rr = t1;
+        sc->bb = t2;
+        if (t2 == 0.0 || sqrt(t1) <= sc->tol * sqrt(t2)) {
+            sc->done = 1;
+            sc->status = GIC_OK;
+        }
+        if (!isfinite(t1)) {
+            sc->done = 1;
+            sc->status = GIC_ERR_BREAKDOWN;
+        }
+    }
+}
+
+// SELL-32 SpMV: one warp per slice of 32 rows, one row per lane, column-
+// major entries inside the slice, so every load is a coalesced 256-byte
+// (values) or 128-byte (columns) line and every FP64 instruction does up to
+// 32 useful multiply-adds with no cross-lane reduction (FP64 issue slots are
+// the scarce resource next to HBM on this part). Modes as k_spmv.
+__global__ void k_sell_vals(int64_t n, const int32_t *rowptr, const double *val, const int64_t *sptr, const int32_t *w,
+                            double *sval)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t sl = i >> 5;
+        const int t = (int)(i & 31);
+        const int32_t a = rowptr[i], len = rowptr[i + 1] - a;
+        for (int32_t k = 0; k < w[sl]; ++k) sval[sptr[sl] + (int64_t)k * 32 + t] = (k < len) ? val[a + k] : 0.0;
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(SPMV_BLOCK) k_spmv_sell(int64_t n, int64_t nslices, const int64_t *__restrict__ sptr,
+                                                          const int32_t *__restrict__ sw,
+                                                          const int32_t *__restrict__ scol,
+                                                          const double *__restrict__ sval,
+                                                          const double *__restrict__ x, double *__restrict__ y,
+                                                          const double *__restrict__ b, double *partials,
+                                                          Scalars *sc)
+{
+    if (sc->done) return;
+    __shared__ double sh[SPMV_BLOCK / 32];
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double d1 = 0.0, d2 = 0.0;
+    for (int64_t sl = w; sl < nslices; sl += nw) {
+        const int64_t i = sl * 32 + lane;
+        const int32_t width = sw[sl];
+        const int64_t o = sptr[sl] + lane;
+        double s0 = 0.0, s1 = 0.0;
+        int32_t k = 0;
+        for (; k + 4 <= width; k += 4) {
+            int32_t c[4];
+            double v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                c[u] = __ldg(scol + o + 32 * (int64_t)(k + u));
+                v[u] = __ldg(sval + o + 32 * (int64_t)(k + u));
+            }
+            double xv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) xv[u] = __ldg(x + c[u]);
+            s0 = fma(v[0], xv[0], s0);
+            s1 = fma(v[1], xv[1], s1);
+            s0 = fma(v[2], xv[2], s0);
+            s1 = fma(v[3], xv[3], s1);
+        }
+        for (; k < width; ++k) s0 = fma(__ldg(sval + o + 32 * (int64_t)k), __ldg(x + __ldg(scol + o + 32 * (int64_t)k)), s0);
+        const double s = s0 + s1;
+        if (i < n) {
+            if (MODE == 2) {
+                const double bi = b[i];
+                const double ri = bi - s;
+                y[i] = ri;
+                d1 = fma(ri, ri, d1);
+                d2 = fma(bi, bi, d2);
+            } else {
+                y[i] = s;
+                d1 = fma(x[i], s, d1);
+            }
+        }
+    }
+    double s1 = block_sum(d1, sh);
+    double s2 = (MODE == 2) ? block_sum(d2, sh) : 0.0;
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = s1;
+        if (MODE == 2) partials[gridDim.x + blockIdx.x] = s2;
+    }
+    __shared__ bool is_last;
+    if (threadIdx.x == 0) is_last = last_block(&sc->counter, gridDim.x);
+    __syncthreads();
+    if (!is_last || threadIdx.x >= 32) return;
+    __threadfence();
+    double t1 = warp_sum_partials(partials, gridDim.x);
+    double t2 = (MODE == 2) ? warp_sum_partials(partials + gridDim.x, gridDim.x) : 0.0;
+    if (lane != 0) return;
+    sc->counter = 0;
+    if (MODE == 1) {
         sc->pw = t1;
         if (!(t1 > 0.0) || !isfinite(t1)) {
             sc->status = GIC_ERR_BREAKDOWN;
@@ -518,6 +629,7 @@ struct SolveWs {
     void *Uval;
     double *invd, *r, *y, *z, *p, *w;
     double *partials;
+    double *sval; // A's values in the pattern's SELL-32 layout
     Scalars *sc;
     size_t bytes;
 };
@@ -532,17 +644,19 @@ static SolveWs carve(const Pattern &P, int l_dtype, void *ws)
     o.partials = (double *)(c + off); off += align_up(sizeof(double) * 2 * MAX_PARTIALS);
     o.Uval = c + off; off += (l_dtype == GIC_IDENTITY) ? 0 : align_up(es * (size_t)P.nnzL);
     o.invd = (double *)(c + off); off += (l_dtype == GIC_IDENTITY) ? 0 : align_up(8 * (size_t)P.n);
+    o.sval = (double *)(c + off); off += align_up(8 * (size_t)P.sell_nnz);
     double **vecs[5] = {&o.r, &o.y, &o.z, &o.p, &o.w};
     for (int k = 0; k < 5; ++k) { *vecs[k] = (double *)(c + off); off += align_up(8 * (size_t)P.n); }
     o.bytes = off;
     return o;
 }
 
-size_t pcg_ws_bytes(int64_t n, int64_t nnzL, int l_dtype)
+size_t pcg_ws_bytes(int64_t n, int64_t nnzL, int64_t sell_nnz, int l_dtype)
 {
     Pattern P;
     P.n = n;
     P.nnzL = nnzL;
+    P.sell_nnz = sell_nnz;
     return carve(P, l_dtype, nullptr).bytes;
 }
 
@@ -565,35 +679,25 @@ static unsigned spmv_grid(gic_handle *h, int64_t n)
     return (unsigned)b;
 }
 
-static int solve_chunk(gic_handle *h, const Pattern &P)
+static int64_t solve_warps(gic_handle *h, const Pattern &P)
 {
-    int g = P.max_group > 0 ? P.max_group : 1;
-    int c = h->tune_chunk > 0 ? h->tune_chunk : 32;
-    if (c * g > MAXCHUNK_ROWS) c = MAXCHUNK_ROWS / g;
-    return c < 1 ? 1 : c;
-}
-
-static int64_t solve_warps(gic_handle *h, const Pattern &P, int chunk)
-{
-    int64_t nchunks = ((int64_t)P.ngroups + chunk - 1) / chunk;
+    int64_t need = P.nchunks;
     if (h->tune_solve_warps_per_sm > 0) {
         int64_t cap = (int64_t)h->tune_solve_warps_per_sm * h->num_sms;
-        if (nchunks > cap) nchunks = cap;
+        if (need > cap) need = cap;
     }
-    return nchunks;
+    return need;
 }
 
 template <typename TL, int GM>
 static int launch_lsolve_g(gic_handle *h, const Pattern &P, const TL *Lval, const double *invd, const double *r,
                            double *y, Scalars *sc)
 {
-    int32_t ng = P.ngroups;
-    int chunk = solve_chunk(h, P);
-    const int32_t *g = P.grp, *lr = P.Lrowptr, *lc = P.Lcol;
+    int32_t nc = P.nchunks;
+    const int32_t *ord = P.ord_f, *cg = P.chunk_grp, *g = P.grp, *lr = P.Lrowptr, *lc = P.Lcol;
     unsigned *er = h->dev_err;
-    void *args[] = {&ng, &chunk, &g, &lr, &lc, &Lval, &invd, &r, &y, &er, &sc};
-    size_t smem = (size_t)(SOLVE_BLOCK / 32) * MAXCHUNK_ROWS * sizeof(double);
-    return launch_persistent(h, (const void *)k_lsolve<TL, GM>, SOLVE_BLOCK, smem, solve_warps(h, P, chunk), args);
+    void *args[] = {&nc, &ord, &cg, &g, &lr, &lc, &Lval, &invd, &r, &y, &er, &sc};
+    return launch_persistent(h, (const void *)k_lsolve<TL, GM>, SOLVE_BLOCK, 0, solve_warps(h, P), args);
 }
 
 template <typename TL>
@@ -609,15 +713,13 @@ template <typename TL, bool PCG, int GM>
 static int launch_ltsolve_g(gic_handle *h, const Pattern &P, const TL *Uval, const double *invd, double *y, double *z,
                             const double *r, double *partials, Scalars *sc)
 {
-    int32_t ng = P.ngroups;
-    int chunk = solve_chunk(h, P);
-    const int32_t *g = P.grp, *ur = P.Urowptr, *uc = P.Ucol;
+    int32_t nc = P.nchunks;
+    const int32_t *ord = P.ord_b, *cg = P.chunk_grp, *g = P.grp, *ur = P.Urowptr, *uc = P.Ucol;
     unsigned *er = h->dev_err;
-    void *args[] = {&ng, &chunk, &g, &ur, &uc, &Uval, &invd, &y, &z, &r, &partials, &er, &sc};
-    int64_t need = solve_warps(h, P, chunk);
+    void *args[] = {&nc, &ord, &cg, &g, &ur, &uc, &Uval, &invd, &y, &z, &r, &partials, &er, &sc};
+    int64_t need = solve_warps(h, P);
     if (PCG && need > MAX_PARTIALS) need = MAX_PARTIALS; // grid warps <= partial slots
-    size_t smem = (size_t)(SOLVE_BLOCK / 32) * MAXCHUNK_ROWS * sizeof(double);
-    return launch_persistent(h, (const void *)k_ltsolve<TL, PCG, GM>, SOLVE_BLOCK, smem, need, args);
+    return launch_persistent(h, (const void *)k_ltsolve<TL, PCG, GM>, SOLVE_BLOCK, 0, need, args);
 }
 
 template <typename TL, bool PCG>
@@ -717,8 +819,8 @@ static int pcg_iteration(gic_handle *h, const Pattern &P, const double *valA, co
     }
     PROF_BEGIN(GIC_PROF_SPMV);
     ++h->launches;
-    k_spmv<1><<<spmv_grid(h, n), SPMV_BLOCK, 0, h->stream>>>(n, P.rowptr, P.col, valA, W.p, W.w, nullptr, W.partials,
-                                                            nullptr, W.sc);
+    k_spmv_sell<1><<<spmv_grid(h, P.nslices), SPMV_BLOCK, 0, h->stream>>>(
+        n, P.nslices, P.sell_ptr, P.sell_w, P.sell_col, W.sval, W.p, W.w, nullptr, W.partials, W.sc);
     GIC_CUDA_TRY(cudaGetLastError());
     PROF_END(GIC_PROF_SPMV);
     PROF_BEGIN(GIC_PROF_VECTOR);
@@ -744,8 +846,10 @@ static int pcg_run(gic_handle *h, const Pattern &P, const double *valA, const TL
     }
     PROF_BEGIN(GIC_PROF_SPMV);
     ++h->launches;
-    k_spmv<2><<<spmv_grid(h, n), SPMV_BLOCK, 0, h->stream>>>(n, P.rowptr, P.col, valA, x, W.r, b, W.partials, nullptr,
-                                                            W.sc);
+    ++h->launches;
+    k_sell_vals<<<vec_grid(h, n, 256), 256, 0, h->stream>>>(n, P.rowptr, valA, P.sell_ptr, P.sell_w, W.sval);
+    k_spmv_sell<2><<<spmv_grid(h, P.nslices), SPMV_BLOCK, 0, h->stream>>>(
+        n, P.nslices, P.sell_ptr, P.sell_w, P.sell_col, W.sval, x, W.r, b, W.partials, W.sc);
     GIC_CUDA_TRY(cudaGetLastError());
     PROF_END(GIC_PROF_SPMV);
     // Iterations are enqueued in batches; the host reads the device flag of
@@ -950,7 +1054,6 @@ int gic_set_tuning(gic_handle *h, int key, int value)
 {
     if (!h || value < 0) return GIC_ERR_INVALID_ARG;
     switch (key) {
-    case GIC_TUNE_SOLVE_CHUNK: h->tune_chunk = value; return GIC_OK;
     case GIC_TUNE_SOLVE_WARPS_PER_SM: h->tune_solve_warps_per_sm = value; return GIC_OK;
     default: return GIC_ERR_INVALID_ARG;
     }

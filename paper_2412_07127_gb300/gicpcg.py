@@ -305,7 +305,7 @@ def error_flags(h: Handle):
     return f.value
 
 
-GIC_TUNE_SOLVE_CHUNK, GIC_TUNE_SOLVE_WARPS_PER_SM = 0, 1
+GIC_TUNE_SOLVE_WARPS_PER_SM = 1
 
 
 def set_tuning(h: Handle, key, value):
