@@ -114,6 +114,47 @@ __device__ __forceinline__ double dep_first(const double *y, const double *ring,
     return ld_relaxed(y + j);
 }
 
+// Everything a group needs before it can wait, in registers. The sweep keeps
+// two of these: the group being solved and the next one, whose loads are in
+// flight while the current group waits and computes.
+template <int GM>
+struct GroupRegs {
+    int32_t s, G, m, j0, j1;
+    double rr[GM], iv[GM], aux[GM]; // aux: y (backward sweep)
+    double v0[GM], v1[GM];
+    double lin[GM * (GM - 1) / 2 + 1];
+};
+
+// forward: row s+t of L holds m external entries, t in-group ones, the diagonal
+template <typename TL, int GM>
+__device__ __forceinline__ void load_group_L(GroupRegs<GM> &q, int32_t g, int32_t g1, const int32_t *grp,
+                                             const int32_t *Lrowptr, const int32_t *Lcol, const TL *Lval,
+                                             const double *invd, const double *r, int lane)
+{
+    q.G = 0;
+    q.j0 = q.j1 = -1;
+    if (g >= g1) return;
+    const int32_t s = grp[g];
+    const int G = grp[g + 1] - s;
+    const int32_t b0 = Lrowptr[s];
+    const int32_t m = Lrowptr[s + 1] - b0 - 1;
+    q.s = s;
+    q.G = G;
+    q.m = m;
+    q.j0 = (lane < m) ? Lcol[b0 + lane] : -1;
+    q.j1 = (lane + 32 < m) ? Lcol[b0 + lane + 32] : -1;
+#pragma unroll
+    for (int t = 0; t < GM; ++t) {
+        const int32_t base = b0 + t * (m + 1) + (t * (t - 1)) / 2;
+        q.rr[t] = (t < G) ? r[s + t] : 0.0;
+        q.iv[t] = (t < G) ? invd[s + t] : 0.0;
+        q.v0[t] = (t < G && lane < m) ? (double)Lval[base + lane] : 0.0;
+        q.v1[t] = (t < G && lane + 32 < m) ? (double)Lval[base + lane + 32] : 0.0;
+#pragma unroll
+        for (int u = 0; u < t; ++u) q.lin[t * (t - 1) / 2 + u] = (t < G) ? (double)Lval[base + m + u] : 0.0;
+    }
+}
+
 // Forward: y_i = (r_i - sum_{j<i} L_ij y_j) / L_ii. y must hold the sentinel.
 template <typename TL, int GM>
 __global__ void __launch_bounds__(SOLVE_BLOCK) k_lsolve(int32_t nchunks, const int32_t *__restrict__ ord,
@@ -130,51 +171,33 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_lsolve(int32_t nchunks, const i
     double *ring = ring_all[threadIdx.x >> 5];
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    GroupRegs<GM> cur, nxt;
     for (int64_t pos = w; pos < nchunks; pos += nw) {
         const int32_t c = ord[pos];
         const int32_t g0 = chunk_grp[c], g1 = chunk_grp[c + 1];
         const int32_t row0 = grp[g0];
+        load_group_L<TL, GM>(cur, g0, g1, grp, Lrowptr, Lcol, Lval, invd, r, lane);
         for (int32_t g = g0; g < g1; ++g) {
-            const int32_t s = grp[g];
-            const int G = grp[g + 1] - s;
-            const int32_t b0 = Lrowptr[s];
-            const int32_t m = Lrowptr[s + 1] - b0 - 1;
+            load_group_L<TL, GM>(nxt, g + 1, g1, grp, Lrowptr, Lcol, Lval, invd, r, lane);
+            const int32_t s = cur.s, m = cur.m;
+            const int G = cur.G;
             const int32_t lo = max(row0, s - RING);
-            int32_t base[GM];
-            double acc[GM], rr[GM], iv[GM];
+            double y0 = (cur.j0 >= 0) ? dep_first(y, ring, cur.j0, lo, s) : 0.0;
+            double y1 = (cur.j1 >= 0) ? dep_first(y, ring, cur.j1, lo, s) : 0.0;
+            wait_deps<true>(y, cur.j0, cur.j1, y0, y1, err);
+            double acc[GM];
 #pragma unroll
-            for (int t = 0; t < GM; ++t) {
-                base[t] = b0 + t * (m + 1) + (t * (t - 1)) / 2;
-                rr[t] = (t < G) ? r[s + t] : 0.0;
-                iv[t] = (t < G) ? invd[s + t] : 0.0;
-            }
-            const int32_t k0 = lane, k1 = lane + 32;
-            const int32_t j0 = (k0 < m) ? Lcol[b0 + k0] : -1;
-            const int32_t j1 = (k1 < m) ? Lcol[b0 + k1] : -1;
-            double v0[GM], v1[GM];
+            for (int t = 0; t < GM; ++t) acc[t] = fma(cur.v1[t], y1, cur.v0[t] * y0);
+            if (m > 64) { // rows with more than 64 external columns
+                const int32_t b0 = Lrowptr[s];
+                for (int32_t k = lane + 64; k < m; k += 32) {
+                    const int32_t j = Lcol[b0 + k];
+                    double yj = dep_first(y, ring, j, lo, s), dummy = 0.0;
+                    wait_deps<true>(y, j, -1, yj, dummy, err);
 #pragma unroll
-            for (int t = 0; t < GM; ++t) {
-                v0[t] = (t < G && j0 >= 0) ? (double)Lval[base[t] + k0] : 0.0;
-                v1[t] = (t < G && j1 >= 0) ? (double)Lval[base[t] + k1] : 0.0;
-            }
-            double lin[GM * (GM - 1) / 2 + 1];
-#pragma unroll
-            for (int t = 1; t < GM; ++t)
-#pragma unroll
-                for (int u = 0; u < t; ++u)
-                    lin[t * (t - 1) / 2 + u] = (t < G) ? (double)Lval[base[t] + m + u] : 0.0;
-            double y0 = (j0 >= 0) ? dep_first(y, ring, j0, lo, s) : 0.0;
-            double y1 = (j1 >= 0) ? dep_first(y, ring, j1, lo, s) : 0.0;
-            wait_deps<true>(y, j0, j1, y0, y1, err);
-#pragma unroll
-            for (int t = 0; t < GM; ++t) acc[t] = fma(v1[t], y1, v0[t] * y0);
-            for (int32_t k = lane + 64; k < m; k += 32) { // rows with more than 64 external columns
-                const int32_t j = Lcol[b0 + k];
-                double yj = dep_first(y, ring, j, lo, s), dummy = 0.0;
-                wait_deps<true>(y, j, -1, yj, dummy, err);
-#pragma unroll
-                for (int t = 0; t < GM; ++t)
-                    if (t < G) acc[t] = fma((double)Lval[base[t] + k], yj, acc[t]);
+                    for (int t = 0; t < GM; ++t)
+                        if (t < G) acc[t] = fma((double)Lval[b0 + t * (m + 1) + (t * (t - 1)) / 2 + k], yj, acc[t]);
+                }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1)
@@ -186,18 +209,58 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_lsolve(int32_t nchunks, const i
 #pragma unroll
                 for (int t = 0; t < GM; ++t) {
                     if (t < G) {
-                        double v = rr[t] - acc[t];
+                        double v = cur.rr[t] - acc[t];
 #pragma unroll
-                        for (int u = 0; u < t; ++u) v = fma(-lin[t * (t - 1) / 2 + u], yl[u], v);
-                        yl[t] = v * iv[t];
+                        for (int u = 0; u < t; ++u) v = fma(-cur.lin[t * (t - 1) / 2 + u], yl[u], v);
+                        yl[t] = v * cur.iv[t];
                         st_relaxed(y + s + t, yl[t]);
                         ring[(s + t) & (RING - 1)] = yl[t];
                     }
                 }
             }
             __syncwarp();
+            cur = nxt;
         }
     }
+}
+
+// backward: row s+t of U holds G-t in-group entries (diagonal first), then
+// the mu external ones shared by the group (those of row e = s+G-1)
+template <typename TL, bool PCG, int GM>
+__device__ __forceinline__ void load_group_U(GroupRegs<GM> &q, int32_t g, int32_t g0, const int32_t *grp,
+                                             const int32_t *Urowptr, const int32_t *Ucol, const TL *Uval,
+                                             const double *invd, const double *y, const double *r, int lane)
+{
+    q.G = 0;
+    q.j0 = q.j1 = -1;
+    if (g < g0) return;
+    const int32_t s = grp[g];
+    const int G = grp[g + 1] - s;
+    const int32_t e = s + G - 1;
+    const int32_t be = Urowptr[e];
+    const int32_t mu = Urowptr[e + 1] - be - 1;
+    q.s = s;
+    q.G = G;
+    q.m = mu;
+    q.j0 = (lane < mu) ? Ucol[be + 1 + lane] : -1;
+    q.j1 = (lane + 32 < mu) ? Ucol[be + 1 + lane + 32] : -1;
+    int32_t base[GM];
+#pragma unroll
+    for (int t = 0; t < GM; ++t) base[t] = be - (G - 1 - t) * (mu + 1) - ((G - 1 - t) * (G - t)) / 2;
+#pragma unroll
+    for (int t = 0; t < GM; ++t) {
+        const int32_t ext = base[t] + (G - t);
+        q.aux[t] = (t < G) ? y[s + t] : 0.0;
+        q.rr[t] = (PCG && t < G) ? r[s + t] : 0.0;
+        q.iv[t] = (t < G) ? invd[s + t] : 0.0;
+        q.v0[t] = (t < G && lane < mu) ? (double)Uval[ext + lane] : 0.0;
+        q.v1[t] = (t < G && lane + 32 < mu) ? (double)Uval[ext + lane + 32] : 0.0;
+    }
+#pragma unroll
+    for (int u = 1; u < GM; ++u)
+#pragma unroll
+        for (int t = 0; t < u; ++t)
+            q.lin[u * (u - 1) / 2 + t] = (u < G) ? (double)Uval[base[t] + (u - t)] : 0.0;
 }
 
 // Backward: z_i = (y_i - sum_{j>i} L_ji z_j) / L_ii on U = L^T. z must hold
@@ -222,55 +285,34 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_ltsolve(int32_t nchunks, const 
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double dot = 0.0;
+    GroupRegs<GM> cur, nxt;
     for (int64_t pos = w; pos < nchunks; pos += nw) {
         const int32_t c = ord[pos];
         const int32_t g0 = chunk_grp[c], g1 = chunk_grp[c + 1];
         const int32_t rowEnd = grp[g1];
+        load_group_U<TL, PCG, GM>(cur, g1 - 1, g0, grp, Urowptr, Ucol, Uval, invd, y, r, lane);
         for (int32_t g = g1 - 1; g >= g0; --g) {
-            const int32_t s = grp[g];
-            const int G = grp[g + 1] - s;
+            load_group_U<TL, PCG, GM>(nxt, g - 1, g0, grp, Urowptr, Ucol, Uval, invd, y, r, lane);
+            const int32_t s = cur.s, mu = cur.m;
+            const int G = cur.G;
             const int32_t e = s + G - 1;
-            const int32_t be = Urowptr[e];
-            const int32_t mu = Urowptr[e + 1] - be - 1;
             const int32_t hi = min(rowEnd, e + 1 + RING);
-            int32_t base[GM];
-            double acc[GM], yy[GM], rr[GM], iv[GM];
+            double z0 = (cur.j0 >= 0) ? dep_first(z, ring, cur.j0, e + 1, hi) : 0.0;
+            double z1 = (cur.j1 >= 0) ? dep_first(z, ring, cur.j1, e + 1, hi) : 0.0;
+            wait_deps<false>(z, cur.j0, cur.j1, z0, z1, err);
+            double acc[GM];
 #pragma unroll
-            for (int t = 0; t < GM; ++t) {
-                // row s+t of U: G-t in-group entries (diagonal first), then mu
-                base[t] = (t < G) ? Urowptr[s + t] : 0;
-                yy[t] = (t < G) ? y[s + t] : 0.0;
-                rr[t] = (PCG && t < G) ? r[s + t] : 0.0;
-                iv[t] = (t < G) ? invd[s + t] : 0.0;
-            }
-            const int32_t k0 = lane, k1 = lane + 32;
-            const int32_t j0 = (k0 < mu) ? Ucol[be + 1 + k0] : -1;
-            const int32_t j1 = (k1 < mu) ? Ucol[be + 1 + k1] : -1;
-            double v0[GM], v1[GM];
+            for (int t = 0; t < GM; ++t) acc[t] = fma(cur.v1[t], z1, cur.v0[t] * z0);
+            if (mu > 64) {
+                const int32_t be = Urowptr[e];
+                for (int32_t k = lane + 64; k < mu; k += 32) {
+                    const int32_t j = Ucol[be + 1 + k];
+                    double zj = dep_first(z, ring, j, e + 1, hi), dummy = 0.0;
+                    wait_deps<false>(z, j, -1, zj, dummy, err);
 #pragma unroll
-            for (int t = 0; t < GM; ++t) {
-                const int32_t ext = base[t] + (G - t);
-                v0[t] = (t < G && j0 >= 0) ? (double)Uval[ext + k0] : 0.0;
-                v1[t] = (t < G && j1 >= 0) ? (double)Uval[ext + k1] : 0.0;
-            }
-            double lin[GM * (GM - 1) / 2 + 1]; // lin[u(u-1)/2 + t] = U[s+t][s+u], t < u
-#pragma unroll
-            for (int u = 1; u < GM; ++u)
-#pragma unroll
-                for (int t = 0; t < u; ++t)
-                    lin[u * (u - 1) / 2 + t] = (u < G) ? (double)Uval[base[t] + (u - t)] : 0.0;
-            double z0 = (j0 >= 0) ? dep_first(z, ring, j0, e + 1, hi) : 0.0;
-            double z1 = (j1 >= 0) ? dep_first(z, ring, j1, e + 1, hi) : 0.0;
-            wait_deps<false>(z, j0, j1, z0, z1, err);
-#pragma unroll
-            for (int t = 0; t < GM; ++t) acc[t] = fma(v1[t], z1, v0[t] * z0);
-            for (int32_t k = lane + 64; k < mu; k += 32) {
-                const int32_t j = Ucol[be + 1 + k];
-                double zj = dep_first(z, ring, j, e + 1, hi), dummy = 0.0;
-                wait_deps<false>(z, j, -1, zj, dummy, err);
-#pragma unroll
-                for (int t = 0; t < GM; ++t)
-                    if (t < G) acc[t] = fma((double)Uval[base[t] + (G - t) + k], zj, acc[t]);
+                    for (int t = 0; t < GM; ++t)
+                        if (t < G) acc[t] = fma((double)Uval[Urowptr[s + t] + (G - t) + k], zj, acc[t]);
+                }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1)
@@ -282,21 +324,22 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_ltsolve(int32_t nchunks, const 
 #pragma unroll
                 for (int t = GM - 1; t >= 0; --t) {
                     if (t < G) {
-                        double v = yy[t] - acc[t];
+                        double v = cur.aux[t] - acc[t];
 #pragma unroll
                         for (int u = t + 1; u < GM; ++u)
-                            if (u < G) v = fma(-lin[u * (u - 1) / 2 + t], zl[u], v);
-                        zl[t] = v * iv[t];
+                            if (u < G) v = fma(-cur.lin[u * (u - 1) / 2 + t], zl[u], v);
+                        zl[t] = v * cur.iv[t];
                         st_relaxed(z + s + t, zl[t]);
                         ring[(s + t) & (RING - 1)] = zl[t];
                         if (PCG) {
                             y[s + t] = sentinel_d();
-                            dot = fma(rr[t], zl[t], dot);
+                            dot = fma(cur.rr[t], zl[t], dot);
                         }
                     }
                 }
             }
             __syncwarp();
+            cur = nxt;
         }
     }
     if (PCG) {

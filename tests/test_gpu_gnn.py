@@ -298,12 +298,15 @@ def test_training_step_gradient_matches_oracle(G, h):
 
 
 def test_training_small_step_descends(G, h):
-    """A small step against the GPU gradient lowers the GPU loss."""
+    """A small step against the GPU gradient of the MLP weights lowers the
+    GPU loss. (GraphNorm's shift alpha is left out: on these small meshes the
+    loss is extremely curved along it at initialisation.)"""
     f = _train_loss_fn(G, h)
     t32, _ = _theta32(7, scale=0.2)
     th = _dev(t32)
     l0, d = f(th)
-    l1, _ = f(th - (1e-4 / float(d.norm())) * d, grad=False)
+    d[:27] = 0
+    l1, _ = f(th - (1e-3 / float(d.norm())) * d, grad=False)
     assert l1 < l0, (l0, l1)
 
 
