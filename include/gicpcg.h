@@ -253,6 +253,12 @@ int gic_adam_step(gic_handle *h, int64_t np, float *theta, const float *grad, fl
 #define GIC_TUNE_SOLVE_WARPS_PER_SM 1
 int gic_set_tuning(gic_handle *h, int key, int value);
 
+/* Failure-path self-test of the bounded device waits: one warp waits on a
+ * word that nothing writes, giving up after `polls` polls (1..2^21). Returns
+ * GIC_ERR_TIMEOUT (the expected outcome: the wait ran out, was reported and
+ * the handle stays usable) or GIC_OK if the wait unexpectedly ended. */
+int gic_selftest_wait_timeout(gic_handle *h, int64_t polls);
+
 /* Number of kernels this handle has launched so far (host output). */
 int gic_launch_count(gic_handle *h, int64_t *count);
 

@@ -99,3 +99,31 @@ const char *gic_status_string(int s)
 const char *gic_last_cuda_error(void) { return gic::g_last_cuda_error; }
 
 }  // extern "C"
+
+namespace gic {
+// one warp waits on a word that nothing writes, with a caller-chosen limit
+__global__ void k_selftest_wait(double *cell, unsigned *err, long long limit)
+{
+    if (threadIdx.x == 0) wait_value(cell, err, limit);
+}
+__global__ void k_selftest_arm(double *cell) { *cell = sentinel_d(); }
+}  // namespace gic
+
+extern "C" {
+
+int gic_selftest_wait_timeout(gic_handle *h, int64_t polls)
+{
+    GIC_TRY(gic::check_handle(h));
+    if (polls < 1 || polls > (1ll << 21)) return GIC_ERR_INVALID_ARG;
+    double *cell = (double *)((char *)h->dev_small + 63000);
+    ++h->launches;
+    gic::k_selftest_arm<<<1, 1, 0, h->stream>>>(cell);
+    ++h->launches;
+    gic::k_selftest_wait<<<1, 32, 0, h->stream>>>(cell, h->dev_err, (long long)polls);
+    GIC_CUDA_TRY(cudaGetLastError());
+    unsigned flags = 0;
+    GIC_TRY(gic::read_and_clear_dev_err(h, &flags));
+    return (flags & gic::ERR_TIMEOUT) ? GIC_ERR_TIMEOUT : GIC_OK;
+}
+
+}  // extern "C"

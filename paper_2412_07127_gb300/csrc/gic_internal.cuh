@@ -31,10 +31,10 @@ void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int 
 // Device error flags (bit set in handle->dev_err).
 enum : unsigned { ERR_TIMEOUT = 1u, ERR_BOUNDS = 2u };
 
-// Spin-wait limits: polls of one word before a waiting warp gives up, sets
-// ERR_TIMEOUT and writes NaN so that everything downstream drains. With the
-// back-off below this is about a second of waiting.
-constexpr long long SPIN_LIMIT = 1ll << 20;
+// Spin-wait limit: polls of one word before a waiting warp gives up, sets
+// ERR_TIMEOUT and writes NaN so that everything downstream drains (about a
+// second: a poll is an L2 round trip, then sleeps after the first 2^16).
+constexpr long long SPIN_LIMIT = 1ll << 21;
 
 // A quiet-NaN bit pattern that arithmetic never produces (the GPU's
 // canonical NaN differs), used as "not written yet" in solve outputs.
@@ -78,19 +78,16 @@ __device__ __forceinline__ void st_release_i32(int *p, int v)
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Wait until *p is no longer the sentinel; bounded. Polls with relaxed
-// loads (no cache invalidation per poll), backing off exponentially up to
-// about a microsecond. On timeout sets the error flag and returns NaN.
-__device__ __forceinline__ double wait_value(const double *p, unsigned *err)
+// Wait until *p is no longer the sentinel; bounded. Tight polling with
+// relaxed loads (each poll is one L2 round trip, which paces it); only after
+// about 2^16 polls does the waiter start sleeping between polls. After
+// `limit` polls it gives up, sets ERR_TIMEOUT and returns NaN.
+__device__ __forceinline__ double wait_value(const double *p, unsigned *err, long long limit = SPIN_LIMIT)
 {
     double v = ld_relaxed(p);
     if (!is_sentinel(v)) return v;
-    unsigned ns = 8;
-    for (long long it = 0; it < SPIN_LIMIT; ++it) {
-        if (it > 16) {
-            __nanosleep(ns);
-            if (ns < 1024) ns <<= 1;
-        }
+    for (long long it = 0; it < limit; ++it) {
+        if (it > 65536) __nanosleep(128);
         v = ld_relaxed(p);
         if (!is_sentinel(v)) return v;
         if ((it & 255) == 255 && *((volatile unsigned *)err) != 0u) return __longlong_as_double(0x7ff8000000000000ll);
@@ -101,35 +98,15 @@ __device__ __forceinline__ double wait_value(const double *p, unsigned *err)
 
 __device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
-// Wait until neither lane value is the sentinel: one polling lane at a
-// time, on the outstanding dependency produced last (the largest column in
-// the forward sweep, LAST_IS_MAX; the smallest in the backward sweep).
+// Wait until neither of a lane's two dependency values is the sentinel:
+// every lane polls its own outstanding words concurrently.
 template <bool LAST_IS_MAX>
 __device__ __forceinline__ void wait_deps(const double *y, int32_t j0, int32_t j1, double &y0, double &y1,
                                           unsigned *err)
 {
-    bool p0 = j0 >= 0 && is_sentinel(y0), p1 = j1 >= 0 && is_sentinel(y1);
-    unsigned pend = __ballot_sync(0xffffffffu, p0 || p1);
-    for (int round = 0; pend && round < 130; ++round) {
-        int32_t mine, jm;
-        if (LAST_IS_MAX) {
-            mine = max(p0 ? j0 : -1, p1 ? j1 : -1);
-            jm = __reduce_max_sync(0xffffffffu, mine);
-        } else {
-            mine = min(p0 ? j0 : INT_MAX, p1 ? j1 : INT_MAX);
-            jm = __reduce_min_sync(0xffffffffu, mine);
-        }
-        if (mine == jm) wait_value(y + jm, err);
-        __syncwarp();
-        if (p0) { y0 = ld_relaxed(y + j0); p0 = is_sentinel(y0); }
-        if (p1) { y1 = ld_relaxed(y + j1); p1 = is_sentinel(y1); }
-        pend = __ballot_sync(0xffffffffu, p0 || p1);
-        if (pend && *((volatile unsigned *)err) != 0u) break;
-    }
-    if (p0) y0 = __longlong_as_double(0x7ff8000000000000ll);
-    if (p1) y1 = __longlong_as_double(0x7ff8000000000000ll);
+    if (j0 >= 0 && is_sentinel(y0)) y0 = wait_value(y + j0, err);
+    if (j1 >= 0 && is_sentinel(y1)) y1 = wait_value(y + j1, err);
 }
-
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v)

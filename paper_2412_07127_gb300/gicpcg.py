@@ -63,6 +63,7 @@ _SIGS = {
     "gic_solve_error_flags": (_int, [_vp, C.POINTER(C.c_uint)]),
     "gic_launch_count": (_int, [_vp, C.POINTER(_i64)]),
     "gic_set_tuning": (_int, [_vp, _int, _int]),
+    "gic_selftest_wait_timeout": (_int, [_vp, _i64]),
     "gic_solve_host": (_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _int, _dbl, _int,
                               C.POINTER(_i32), C.POINTER(_dbl), C.POINTER(_dbl), C.POINTER(_int),
                               _vp, _sz]),
@@ -310,6 +311,11 @@ GIC_TUNE_SOLVE_WARPS_PER_SM = 1
 
 def set_tuning(h: Handle, key, value):
     _call("gic_set_tuning", h.h, key, value)
+
+
+def selftest_wait_timeout(h: Handle, polls=4096):
+    """Status of a deliberately unsatisfiable bounded wait (GIC_ERR_TIMEOUT expected)."""
+    return lib().gic_selftest_wait_timeout(h.h, polls)
 
 
 def launch_count(h: Handle):

@@ -364,3 +364,20 @@ def test_full_size_40_cube(G, h):
     assert _iters_ok(res["iters"], ro["iters"]), (res["iters"], ro["iters"])
     x = _np(res["x"])
     assert np.linalg.norm(x - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
+
+
+def test_bounded_wait_times_out_and_handle_survives(G, h):
+    """A device wait on a flag that nothing sets runs out, is reported as
+    GIC_ERR_TIMEOUT, and the handle still solves correctly afterwards."""
+    assert G.selftest_wait_timeout(h, 4096) == G.GIC_ERR_TIMEOUT
+    assert G.error_flags(h) == 0
+    N = 3
+    A = O.fem_hex_assemble(N, I.material_field(N, 1))
+    b = I.rhs(A.n, 1)
+    rp, c, v = _upload(A)
+    P = G.Pattern(h, rp, c)
+    Lg, _ = G.ic0(h, P, v)
+    res = G.pcg(h, P, v, Lg, _dev(b))
+    Lo, _ = O.ic0(A)
+    ro = O.pcg(A, b, Lo)
+    assert _iters_ok(res["iters"], ro["iters"])
