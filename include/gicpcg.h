@@ -247,10 +247,12 @@ int gic_probe_loss(gic_handle *h, const gic_pattern *P, int ngraphs, const float
 int gic_adam_step(gic_handle *h, int64_t np, float *theta, const float *grad, float *m1,
                   float *m2, int t, double lr);
 
-/* Tuning of the triangular-solve schedule (no effect on results):
- * GIC_TUNE_SOLVE_WARPS_PER_SM = cap on resident solve warps per SM
- * (0 = no cap). */
+/* Tuning of the sync-free kernels (IC(0), triangular solves); no effect on
+ * results: GIC_TUNE_SOLVE_WARPS_PER_SM = cap on resident solve warps per SM
+ * (0 = no cap); GIC_TUNE_POLL = polling: low 16 bits = nanoseconds slept
+ * between polls, bit 16 set = one polling lane per warp (default 1<<16). */
 #define GIC_TUNE_SOLVE_WARPS_PER_SM 1
+#define GIC_TUNE_POLL 2
 int gic_set_tuning(gic_handle *h, int key, int value);
 
 /* Failure-path self-test of the bounded device waits: one warp waits on a

@@ -372,14 +372,18 @@ __global__ void k_sell_widths(int64_t n, int64_t nslices, const int32_t *rowptr,
     }
 }
 
-__global__ void k_sell_cols(int64_t n, const int32_t *rowptr, const int32_t *col, const int64_t *sptr,
-                            const int32_t *w, int32_t *scol)
+// every lane of every slice is written: padding of a real row points at the
+// row itself, lanes past the last row (partial last slice) at column 0
+__global__ void k_sell_cols(int64_t n, int64_t nslices, const int32_t *rowptr, const int32_t *col,
+                            const int64_t *sptr, const int32_t *w, int32_t *scol)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nslices * 32;
+         i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t sl = i >> 5;
         const int t = (int)(i & 31);
-        const int32_t a = rowptr[i], len = rowptr[i + 1] - a;
-        for (int32_t k = 0; k < w[sl]; ++k) scol[sptr[sl] + (int64_t)k * 32 + t] = (k < len) ? col[a + k] : (int32_t)i;
+        const int32_t a = (i < n) ? rowptr[i] : 0, len = (i < n) ? rowptr[i + 1] - a : 0;
+        const int32_t pad = (i < n) ? (int32_t)i : 0;
+        for (int32_t k = 0; k < w[sl]; ++k) scol[sptr[sl] + (int64_t)k * 32 + t] = (k < len) ? col[a + k] : pad;
     }
 }
 
@@ -534,7 +538,8 @@ static int build_sell(gic_handle *h, Pattern &P)
                                  cudaMemcpyHostToDevice, h->stream));
     GIC_CUDA_TRY(cudaMalloc(&P.sell_col, sizeof(int32_t) * (size_t)P.sell_nnz));
     ++h->launches;
-    k_sell_cols<<<grid_rows(h, P.n), T_ROWS, 0, h->stream>>>(P.n, P.rowptr, P.col, P.sell_ptr, P.sell_w, P.sell_col);
+    k_sell_cols<<<grid_rows(h, P.nslices * 32), T_ROWS, 0, h->stream>>>(P.n, P.nslices, P.rowptr, P.col, P.sell_ptr,
+                                                                        P.sell_w, P.sell_col);
     GIC_CUDA_TRY(cudaGetLastError());
     GIC_CUDA_TRY(cudaStreamSynchronize(h->stream));
     return GIC_OK;

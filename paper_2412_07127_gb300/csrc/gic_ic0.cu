@@ -57,7 +57,8 @@ __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t nchunks, const in
                                                        const double *__restrict__ valA,
                                                        const int32_t *__restrict__ Lrowptr,
                                                        const int32_t *__restrict__ Lcol, double *Lval,
-                                                       double alpha, unsigned long long *bad_row, unsigned *err)
+                                                       double alpha, unsigned long long *bad_row, unsigned *err,
+                                                       int poll)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -90,7 +91,7 @@ __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t nchunks, const in
         {   // one lane at a time polls the diagonal written last
             double d0 = (dp0 >= 0) ? ld_relaxed(Lval + dp0) : 0.0;
             double d1 = (dp1 >= 0) ? ld_relaxed(Lval + dp1) : 0.0;
-            wait_deps<true>(Lval, dp0, dp1, d0, d1, err);
+            wait_deps<true>(Lval, dp0, dp1, d0, d1, err, poll);
         }
         __syncwarp();
         fence_acq_rel(); // pairs with the producers' release of each diagonal
@@ -243,7 +244,8 @@ static int ic0_once(gic_handle *h, const Pattern &P, const double *valA, double 
     int32_t nc = P.nchunks;
     const int32_t *ord = P.ord_f, *cg = P.chunk_grp, *g = P.grp, *ar = P.rowptr, *lr = P.Lrowptr, *lc = P.Lcol;
     unsigned *er = h->dev_err;
-    void *args[] = {&nc, &ord, &cg, &g, &ar, &valA, &lr, &lc, &valL, &alpha, &bad_dev, &er};
+    int poll = h->tune_poll;
+    void *args[] = {&nc, &ord, &cg, &g, &ar, &valA, &lr, &lc, &valL, &alpha, &bad_dev, &er, &poll};
     GIC_TRY(launch_persistent(h, (const void *)k_ic0, IC_WARPS * 32, smem, nc, args));
     unsigned long long *hb = (unsigned long long *)((char *)h->host_pinned + 2048);
     GIC_CUDA_TRY(cudaMemcpyAsync(hb, bad_dev, sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));

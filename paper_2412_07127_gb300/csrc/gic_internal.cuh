@@ -78,16 +78,18 @@ __device__ __forceinline__ void st_release_i32(int *p, int v)
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Wait until *p is no longer the sentinel; bounded. Tight polling with
-// relaxed loads (each poll is one L2 round trip, which paces it); only after
-// about 2^16 polls does the waiter start sleeping between polls. After
-// `limit` polls it gives up, sets ERR_TIMEOUT and returns NaN.
-__device__ __forceinline__ double wait_value(const double *p, unsigned *err, long long limit = SPIN_LIMIT)
+// Wait until *p is no longer the sentinel; bounded. Polls with relaxed
+// loads (each poll is one L2 round trip), sleeping sleep_ns between polls
+// (0: none), and after 2^16 polls at least 128 ns. After `limit` polls it
+// gives up, sets ERR_TIMEOUT and returns NaN.
+__device__ __forceinline__ double wait_value(const double *p, unsigned *err, long long limit = SPIN_LIMIT,
+                                             unsigned sleep_ns = 0)
 {
     double v = ld_relaxed(p);
     if (!is_sentinel(v)) return v;
     for (long long it = 0; it < limit; ++it) {
         if (it > 65536) __nanosleep(128);
+        else if (sleep_ns) __nanosleep(sleep_ns);
         v = ld_relaxed(p);
         if (!is_sentinel(v)) return v;
         if ((it & 255) == 255 && *((volatile unsigned *)err) != 0u) return __longlong_as_double(0x7ff8000000000000ll);
@@ -96,16 +98,48 @@ __device__ __forceinline__ double wait_value(const double *p, unsigned *err, lon
     return __longlong_as_double(0x7ff8000000000000ll);
 }
 
+// Polling configuration of the sync-free kernels: low 16 bits = sleep
+// between polls in ns, POLL_ONE_LANE = only the lane holding the outstanding
+// dependency produced last polls, the others reload once it lands.
+constexpr int POLL_ONE_LANE = 1 << 16;
+
 __device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
-// Wait until neither of a lane's two dependency values is the sentinel:
-// every lane polls its own outstanding words concurrently.
+// Wait until neither of a lane's two dependency values is the sentinel.
+// With POLL_ONE_LANE one lane at a time polls, the one holding the
+// outstanding dependency produced last (the largest column in the forward
+// sweep, LAST_IS_MAX; the smallest in the backward one); otherwise every lane
+// polls its own words concurrently.
 template <bool LAST_IS_MAX>
 __device__ __forceinline__ void wait_deps(const double *y, int32_t j0, int32_t j1, double &y0, double &y1,
-                                          unsigned *err)
+                                          unsigned *err, int poll)
 {
-    if (j0 >= 0 && is_sentinel(y0)) y0 = wait_value(y + j0, err);
-    if (j1 >= 0 && is_sentinel(y1)) y1 = wait_value(y + j1, err);
+    const unsigned sl = (unsigned)(poll & 0xffff);
+    bool p0 = j0 >= 0 && is_sentinel(y0), p1 = j1 >= 0 && is_sentinel(y1);
+    if (!(poll & POLL_ONE_LANE)) {
+        if (p0) y0 = wait_value(y + j0, err, SPIN_LIMIT, sl);
+        if (p1) y1 = wait_value(y + j1, err, SPIN_LIMIT, sl);
+        return;
+    }
+    unsigned pend = __ballot_sync(0xffffffffu, p0 || p1);
+    for (int round = 0; pend && round < 130; ++round) {
+        int32_t mine, jm;
+        if (LAST_IS_MAX) {
+            mine = max(p0 ? j0 : -1, p1 ? j1 : -1);
+            jm = __reduce_max_sync(0xffffffffu, mine);
+        } else {
+            mine = min(p0 ? j0 : INT_MAX, p1 ? j1 : INT_MAX);
+            jm = __reduce_min_sync(0xffffffffu, mine);
+        }
+        if (mine == jm) wait_value(y + jm, err, SPIN_LIMIT, sl);
+        __syncwarp();
+        if (p0) { y0 = ld_relaxed(y + j0); p0 = is_sentinel(y0); }
+        if (p1) { y1 = ld_relaxed(y + j1); p1 = is_sentinel(y1); }
+        pend = __ballot_sync(0xffffffffu, p0 || p1);
+        if (pend && *((volatile unsigned *)err) != 0u) break;
+    }
+    if (p0) y0 = __longlong_as_double(0x7ff8000000000000ll);
+    if (p1) y1 = __longlong_as_double(0x7ff8000000000000ll);
 }
 
 template <typename T>
@@ -168,6 +202,7 @@ struct gic_handle {
     void *host_pinned = nullptr;   // 4 KiB pinned readback area
     long long launches = 0;        // kernels this handle has launched
     int tune_solve_warps_per_sm = 0; // cap on resident solve warps per SM (0: none)
+    int tune_poll = gic::POLL_ONE_LANE; // polling configuration of the sync-free kernels
 };
 
 namespace gic {

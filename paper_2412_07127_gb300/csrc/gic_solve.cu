@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_lsolve(int32_t nchunks, const i
                                                         const int32_t *__restrict__ Lrowptr,
                                                         const int32_t *__restrict__ Lcol, const TL *__restrict__ Lval,
                                                         const double *__restrict__ invd, const double *__restrict__ r,
-                                                        double *y, unsigned *err, const Scalars *sc)
+                                                        double *y, unsigned *err, int poll, const Scalars *sc)
 {
     if (sc && sc->done) return;
     __shared__ double ring_all[SOLVE_BLOCK / 32][RING];
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_lsolve(int32_t nchunks, const i
             const int32_t lo = max(row0, s - RING);
             double y0 = (cur.j0 >= 0) ? dep_first(y, ring, cur.j0, lo, s) : 0.0;
             double y1 = (cur.j1 >= 0) ? dep_first(y, ring, cur.j1, lo, s) : 0.0;
-            wait_deps<true>(y, cur.j0, cur.j1, y0, y1, err);
+            wait_deps<true>(y, cur.j0, cur.j1, y0, y1, err, poll);
             double acc[GM];
 #pragma unroll
             for (int t = 0; t < GM; ++t) acc[t] = fma(cur.v1[t], y1, cur.v0[t] * y0);
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_lsolve(int32_t nchunks, const i
                 for (int32_t k = lane + 64; k < m; k += 32) {
                     const int32_t j = Lcol[b0 + k];
                     double yj = dep_first(y, ring, j, lo, s), dummy = 0.0;
-                    wait_deps<true>(y, j, -1, yj, dummy, err);
+                    wait_deps<true>(y, j, -1, yj, dummy, err, poll);
 #pragma unroll
                     for (int t = 0; t < GM; ++t)
                         if (t < G) acc[t] = fma((double)Lval[b0 + t * (m + 1) + (t * (t - 1)) / 2 + k], yj, acc[t]);
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_ltsolve(int32_t nchunks, const 
                                                          const int32_t *__restrict__ Ucol, const TL *__restrict__ Uval,
                                                          const double *__restrict__ invd, double *y, double *z,
                                                          const double *__restrict__ r, double *partials,
-                                                         unsigned *err, Scalars *sc)
+                                                         unsigned *err, int poll, Scalars *sc)
 {
     if (sc && sc->done) return;
     __shared__ double ring_all[SOLVE_BLOCK / 32][RING];
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_ltsolve(int32_t nchunks, const 
             const int32_t hi = min(rowEnd, e + 1 + RING);
             double z0 = (cur.j0 >= 0) ? dep_first(z, ring, cur.j0, e + 1, hi) : 0.0;
             double z1 = (cur.j1 >= 0) ? dep_first(z, ring, cur.j1, e + 1, hi) : 0.0;
-            wait_deps<false>(z, cur.j0, cur.j1, z0, z1, err);
+            wait_deps<false>(z, cur.j0, cur.j1, z0, z1, err, poll);
             double acc[GM];
 #pragma unroll
             for (int t = 0; t < GM; ++t) acc[t] = fma(cur.v1[t], z1, cur.v0[t] * z0);
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_ltsolve(int32_t nchunks, const 
                 for (int32_t k = lane + 64; k < mu; k += 32) {
                     const int32_t j = Ucol[be + 1 + k];
                     double zj = dep_first(z, ring, j, e + 1, hi), dummy = 0.0;
-                    wait_deps<false>(z, j, -1, zj, dummy, err);
+                    wait_deps<false>(z, j, -1, zj, dummy, err, poll);
 #pragma unroll
                     for (int t = 0; t < GM; ++t)
                         if (t < G) acc[t] = fma((double)Uval[Urowptr[s + t] + (G - t) + k], zj, acc[t]);
@@ -461,13 +461,14 @@ __global__ void __launch_bounds__(SPMV_BLOCK) k_spmv(int64_t n, const int32_t *_
 // (values) or 128-byte (columns) line and every FP64 instruction does up to
 // 32 useful multiply-adds with no cross-lane reduction (FP64 issue slots are
 // the scarce resource next to HBM on this part). Modes as k_spmv.
-__global__ void k_sell_vals(int64_t n, const int32_t *rowptr, const double *val, const int64_t *sptr, const int32_t *w,
-                            double *sval)
+__global__ void k_sell_vals(int64_t n, int64_t nslices, const int32_t *rowptr, const double *val, const int64_t *sptr,
+                            const int32_t *w, double *sval)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nslices * 32;
+         i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t sl = i >> 5;
         const int t = (int)(i & 31);
-        const int32_t a = rowptr[i], len = rowptr[i + 1] - a;
+        const int32_t a = (i < n) ? rowptr[i] : 0, len = (i < n) ? rowptr[i + 1] - a : 0;
         for (int32_t k = 0; k < w[sl]; ++k) sval[sptr[sl] + (int64_t)k * 32 + t] = (k < len) ? val[a + k] : 0.0;
     }
 }
@@ -489,7 +490,7 @@ __global__ void __launch_bounds__(SPMV_BLOCK) k_spmv_sell(int64_t n, int64_t nsl
     double d1 = 0.0, d2 = 0.0;
     for (int64_t sl = w; sl < nslices; sl += nw) {
         const int64_t i = sl * 32 + lane;
-        const int32_t width = sw[sl];
+        const int32_t width = (i < n) ? sw[sl] : 0; // lanes past the last row load nothing
         const int64_t o = sptr[sl] + lane;
         double s0 = 0.0, s1 = 0.0;
         int32_t k = 0;
@@ -739,7 +740,8 @@ static int launch_lsolve_g(gic_handle *h, const Pattern &P, const TL *Lval, cons
     int32_t nc = P.nchunks;
     const int32_t *ord = P.ord_f, *cg = P.chunk_grp, *g = P.grp, *lr = P.Lrowptr, *lc = P.Lcol;
     unsigned *er = h->dev_err;
-    void *args[] = {&nc, &ord, &cg, &g, &lr, &lc, &Lval, &invd, &r, &y, &er, &sc};
+    int poll = h->tune_poll;
+    void *args[] = {&nc, &ord, &cg, &g, &lr, &lc, &Lval, &invd, &r, &y, &er, &poll, &sc};
     return launch_persistent(h, (const void *)k_lsolve<TL, GM>, SOLVE_BLOCK, 0, solve_warps(h, P), args);
 }
 
@@ -759,7 +761,8 @@ static int launch_ltsolve_g(gic_handle *h, const Pattern &P, const TL *Uval, con
     int32_t nc = P.nchunks;
     const int32_t *ord = P.ord_b, *cg = P.chunk_grp, *g = P.grp, *ur = P.Urowptr, *uc = P.Ucol;
     unsigned *er = h->dev_err;
-    void *args[] = {&nc, &ord, &cg, &g, &ur, &uc, &Uval, &invd, &y, &z, &r, &partials, &er, &sc};
+    int poll = h->tune_poll;
+    void *args[] = {&nc, &ord, &cg, &g, &ur, &uc, &Uval, &invd, &y, &z, &r, &partials, &er, &poll, &sc};
     int64_t need = solve_warps(h, P);
     if (PCG && need > MAX_PARTIALS) need = MAX_PARTIALS; // grid warps <= partial slots
     return launch_persistent(h, (const void *)k_ltsolve<TL, PCG, GM>, SOLVE_BLOCK, 0, need, args);
@@ -890,7 +893,8 @@ static int pcg_run(gic_handle *h, const Pattern &P, const double *valA, const TL
     PROF_BEGIN(GIC_PROF_SPMV);
     ++h->launches;
     ++h->launches;
-    k_sell_vals<<<vec_grid(h, n, 256), 256, 0, h->stream>>>(n, P.rowptr, valA, P.sell_ptr, P.sell_w, W.sval);
+    k_sell_vals<<<vec_grid(h, P.nslices * 32, 256), 256, 0, h->stream>>>(n, P.nslices, P.rowptr, valA, P.sell_ptr,
+                                                                          P.sell_w, W.sval);
     k_spmv_sell<2><<<spmv_grid(h, P.nslices), SPMV_BLOCK, 0, h->stream>>>(
         n, P.nslices, P.sell_ptr, P.sell_w, P.sell_col, W.sval, x, W.r, b, W.partials, W.sc);
     GIC_CUDA_TRY(cudaGetLastError());
@@ -1098,6 +1102,7 @@ int gic_set_tuning(gic_handle *h, int key, int value)
     if (!h || value < 0) return GIC_ERR_INVALID_ARG;
     switch (key) {
     case GIC_TUNE_SOLVE_WARPS_PER_SM: h->tune_solve_warps_per_sm = value; return GIC_OK;
+    case GIC_TUNE_POLL: h->tune_poll = value; return GIC_OK;
     default: return GIC_ERR_INVALID_ARG;
     }
 }

@@ -306,7 +306,8 @@ def error_flags(h: Handle):
     return f.value
 
 
-GIC_TUNE_SOLVE_WARPS_PER_SM = 1
+GIC_TUNE_SOLVE_WARPS_PER_SM, GIC_TUNE_POLL = 1, 2
+POLL_ONE_LANE = 1 << 16
 
 
 def set_tuning(h: Handle, key, value):
