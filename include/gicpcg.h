@@ -98,6 +98,11 @@ int gic_pattern_destroy(gic_pattern *P);
 /* Host outputs (any may be NULL). */
 int gic_pattern_info(const gic_pattern *P, int64_t *n, int64_t *nnzA, int64_t *nnzL,
                      int32_t *nlevels, int32_t *ngroups);
+/* Schedule of the sync-free kernels (host outputs, any may be NULL): number
+ * of chunks (runs of row groups one warp processes in order), whether they
+ * are multi-group runs (1) or single groups in level order (0), and the
+ * padded entry count of the SELL-32 copy of A used by the PCG SpMV. */
+int gic_pattern_schedule(const gic_pattern *P, int32_t *nchunks, int32_t *chunked, int64_t *sell_nnz);
 /* Copies of the analysis (device outputs, any may be NULL): Lrowptr (n+1),
  * Lcol (nnzL), level (n), group start rows (ngroups+1). */
 int gic_pattern_export(gic_handle *h, const gic_pattern *P, int32_t *Lrowptr, int32_t *Lcol,

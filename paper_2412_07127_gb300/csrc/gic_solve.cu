@@ -120,6 +120,7 @@ __device__ __forceinline__ double dep_first(const double *y, const double *ring,
 template <int GM>
 struct GroupRegs {
     int32_t s, G, m, j0, j1;
+    double d0, d1;                  // dependency values loaded early (may be the sentinel)
     double rr[GM], iv[GM], aux[GM]; // aux: y (backward sweep)
     double v0[GM], v1[GM];
     double lin[GM * (GM - 1) / 2 + 1];
@@ -129,7 +130,7 @@ struct GroupRegs {
 template <typename TL, int GM>
 __device__ __forceinline__ void load_group_L(GroupRegs<GM> &q, int32_t g, int32_t g1, const int32_t *grp,
                                              const int32_t *Lrowptr, const int32_t *Lcol, const TL *Lval,
-                                             const double *invd, const double *r, int lane)
+                                             const double *invd, const double *r, const double *y, int lane)
 {
     q.G = 0;
     q.j0 = q.j1 = -1;
@@ -143,6 +144,10 @@ __device__ __forceinline__ void load_group_L(GroupRegs<GM> &q, int32_t g, int32_
     q.m = m;
     q.j0 = (lane < m) ? Lcol[b0 + lane] : -1;
     q.j1 = (lane + 32 < m) ? Lcol[b0 + lane + 32] : -1;
+    // early look at the dependencies (the previous group's rows are not
+    // written yet; those are taken from the ring when this group runs)
+    q.d0 = (q.j0 >= 0) ? ld_relaxed(y + q.j0) : 0.0;
+    q.d1 = (q.j1 >= 0) ? ld_relaxed(y + q.j1) : 0.0;
 #pragma unroll
     for (int t = 0; t < GM; ++t) {
         const int32_t base = b0 + t * (m + 1) + (t * (t - 1)) / 2;
@@ -176,14 +181,14 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_lsolve(int32_t nchunks, const i
         const int32_t c = ord[pos];
         const int32_t g0 = chunk_grp[c], g1 = chunk_grp[c + 1];
         const int32_t row0 = grp[g0];
-        load_group_L<TL, GM>(cur, g0, g1, grp, Lrowptr, Lcol, Lval, invd, r, lane);
+        load_group_L<TL, GM>(cur, g0, g1, grp, Lrowptr, Lcol, Lval, invd, r, y, lane);
         for (int32_t g = g0; g < g1; ++g) {
-            load_group_L<TL, GM>(nxt, g + 1, g1, grp, Lrowptr, Lcol, Lval, invd, r, lane);
+            load_group_L<TL, GM>(nxt, g + 1, g1, grp, Lrowptr, Lcol, Lval, invd, r, y, lane);
             const int32_t s = cur.s, m = cur.m;
             const int G = cur.G;
             const int32_t lo = max(row0, s - RING);
-            double y0 = (cur.j0 >= 0) ? dep_first(y, ring, cur.j0, lo, s) : 0.0;
-            double y1 = (cur.j1 >= 0) ? dep_first(y, ring, cur.j1, lo, s) : 0.0;
+            double y0 = (cur.j0 >= lo && cur.j0 < s) ? ring[cur.j0 & (RING - 1)] : cur.d0;
+            double y1 = (cur.j1 >= lo && cur.j1 < s) ? ring[cur.j1 & (RING - 1)] : cur.d1;
             wait_deps<true>(y, cur.j0, cur.j1, y0, y1, err, poll);
             double acc[GM];
 #pragma unroll
@@ -229,7 +234,8 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_lsolve(int32_t nchunks, const i
 template <typename TL, bool PCG, int GM>
 __device__ __forceinline__ void load_group_U(GroupRegs<GM> &q, int32_t g, int32_t g0, const int32_t *grp,
                                              const int32_t *Urowptr, const int32_t *Ucol, const TL *Uval,
-                                             const double *invd, const double *y, const double *r, int lane)
+                                             const double *invd, const double *y, const double *r,
+                                             const double *z, int lane)
 {
     q.G = 0;
     q.j0 = q.j1 = -1;
@@ -244,6 +250,8 @@ __device__ __forceinline__ void load_group_U(GroupRegs<GM> &q, int32_t g, int32_
     q.m = mu;
     q.j0 = (lane < mu) ? Ucol[be + 1 + lane] : -1;
     q.j1 = (lane + 32 < mu) ? Ucol[be + 1 + lane + 32] : -1;
+    q.d0 = (q.j0 >= 0) ? ld_relaxed(z + q.j0) : 0.0;
+    q.d1 = (q.j1 >= 0) ? ld_relaxed(z + q.j1) : 0.0;
     int32_t base[GM];
 #pragma unroll
     for (int t = 0; t < GM; ++t) base[t] = be - (G - 1 - t) * (mu + 1) - ((G - 1 - t) * (G - t)) / 2;
@@ -290,15 +298,15 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_ltsolve(int32_t nchunks, const 
         const int32_t c = ord[pos];
         const int32_t g0 = chunk_grp[c], g1 = chunk_grp[c + 1];
         const int32_t rowEnd = grp[g1];
-        load_group_U<TL, PCG, GM>(cur, g1 - 1, g0, grp, Urowptr, Ucol, Uval, invd, y, r, lane);
+        load_group_U<TL, PCG, GM>(cur, g1 - 1, g0, grp, Urowptr, Ucol, Uval, invd, y, r, z, lane);
         for (int32_t g = g1 - 1; g >= g0; --g) {
-            load_group_U<TL, PCG, GM>(nxt, g - 1, g0, grp, Urowptr, Ucol, Uval, invd, y, r, lane);
+            load_group_U<TL, PCG, GM>(nxt, g - 1, g0, grp, Urowptr, Ucol, Uval, invd, y, r, z, lane);
             const int32_t s = cur.s, mu = cur.m;
             const int G = cur.G;
             const int32_t e = s + G - 1;
             const int32_t hi = min(rowEnd, e + 1 + RING);
-            double z0 = (cur.j0 >= 0) ? dep_first(z, ring, cur.j0, e + 1, hi) : 0.0;
-            double z1 = (cur.j1 >= 0) ? dep_first(z, ring, cur.j1, e + 1, hi) : 0.0;
+            double z0 = (cur.j0 > e && cur.j0 < hi) ? ring[cur.j0 & (RING - 1)] : cur.d0;
+            double z1 = (cur.j1 > e && cur.j1 < hi) ? ring[cur.j1 & (RING - 1)] : cur.d1;
             wait_deps<false>(z, cur.j0, cur.j1, z0, z1, err, poll);
             double acc[GM];
 #pragma unroll
@@ -1105,6 +1113,15 @@ int gic_set_tuning(gic_handle *h, int key, int value)
     case GIC_TUNE_POLL: h->tune_poll = value; return GIC_OK;
     default: return GIC_ERR_INVALID_ARG;
     }
+}
+
+int gic_pattern_schedule(const gic_pattern *P, int32_t *nchunks, int32_t *chunked, int64_t *sell_nnz)
+{
+    if (!P) return GIC_ERR_INVALID_ARG;
+    if (nchunks) *nchunks = P->p.nchunks;
+    if (chunked) *chunked = P->p.chunked;
+    if (sell_nnz) *sell_nnz = P->p.sell_nnz;
+    return GIC_OK;
 }
 
 int gic_launch_count(gic_handle *h, int64_t *count)

@@ -49,6 +49,7 @@ _SIGS = {
     "gic_pattern_info": (_int, [_vp, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64),
                                 C.POINTER(_i32), C.POINTER(_i32)]),
     "gic_pattern_export": (_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "gic_pattern_schedule": (_int, [_vp, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i64)]),
     "gic_ic0": (_int, [_vp, _vp, _vp, _vp, _dbl, C.POINTER(_i64)]),
     "gic_ic0_auto": (_int, [_vp, _vp, _vp, _vp, _int, C.POINTER(_dbl), C.POINTER(_i64)]),
     "gic_convert_f64_f32": (_int, [_vp, _i64, _vp, _vp]),
@@ -176,6 +177,9 @@ class Pattern:
         _call("gic_pattern_info", p, C.byref(n_), C.byref(nA), C.byref(nL), C.byref(nl), C.byref(ng))
         self.n, self.nnzA, self.nnzL = n_.value, nA.value, nL.value
         self.nlevels, self.ngroups = nl.value, ng.value
+        nc, ch, sn = _i32(), _i32(), _i64()
+        _call("gic_pattern_schedule", p, C.byref(nc), C.byref(ch), C.byref(sn))
+        self.nchunks, self.chunked, self.sell_nnz = nc.value, ch.value, sn.value
 
     def export(self, h: Handle):
         dev = self.rowptr.device
