@@ -114,36 +114,71 @@ __device__ __forceinline__ double dep_first(const double *y, const double *ring,
     return ld_relaxed(y + j);
 }
 
+// Per-warp shared staging of a window of WIN consecutive groups: their start
+// rows, sizes, row-pointer bases and external column lists. Loading a window
+// costs one dependent chain of global loads; inside it every address a group
+// needs comes from shared memory, so the loads for the next group really are
+// issued ahead (a warp stalls only when it uses a value).
+constexpr int WIN = 32;  // groups per window
+constexpr int WCOL = 48; // external columns per group kept in shared memory
+
+struct WarpStage {
+    int32_t s[WIN], G[WIN], b[WIN], m[WIN];
+    int32_t cols[WIN][WCOL];
+    double ring[RING];
+};
+
 // Everything a group needs before it can wait, in registers. The sweep keeps
 // two of these: the group being solved and the next one, whose loads are in
 // flight while the current group waits and computes.
 template <int GM>
 struct GroupRegs {
-    int32_t s, G, m, j0, j1;
+    int32_t s, G, m, b, j0, j1;
     double d0, d1;                  // dependency values loaded early (may be the sentinel)
     double rr[GM], iv[GM], aux[GM]; // aux: y (backward sweep)
     double v0[GM], v1[GM];
     double lin[GM * (GM - 1) / 2 + 1];
 };
 
-// forward: row s+t of L holds m external entries, t in-group ones, the diagonal
+// Forward window: group starts, L row-pointer bases, external counts and the
+// external columns of each group's first row (shared by the whole group).
+__device__ __forceinline__ void stage_window_L(WarpStage &W, int32_t w0, int32_t cnt, const int32_t *grp,
+                                               const int32_t *Lrowptr, const int32_t *Lcol, int lane)
+{
+    if (lane < cnt) {
+        const int32_t s = grp[w0 + lane];
+        const int32_t G = grp[w0 + lane + 1] - s;
+        const int32_t b0 = Lrowptr[s];
+        W.s[lane] = s;
+        W.G[lane] = G;
+        W.b[lane] = b0;
+        W.m[lane] = Lrowptr[s + 1] - b0 - 1;
+    }
+    __syncwarp();
+#pragma unroll 4
+    for (int k = 0; k < cnt; ++k) {
+        const int32_t m = W.m[k], b0 = W.b[k];
+        if (lane < m && lane < WCOL) W.cols[k][lane] = Lcol[b0 + lane];
+        if (lane + 32 < m && lane + 32 < WCOL) W.cols[k][lane + 32] = Lcol[b0 + lane + 32];
+    }
+    __syncwarp();
+}
+
 template <typename TL, int GM>
-__device__ __forceinline__ void load_group_L(GroupRegs<GM> &q, int32_t g, int32_t g1, const int32_t *grp,
-                                             const int32_t *Lrowptr, const int32_t *Lcol, const TL *Lval,
-                                             const double *invd, const double *r, const double *y, int lane)
+__device__ __forceinline__ void load_group_L(GroupRegs<GM> &q, const WarpStage &W, int k, int cnt,
+                                             const int32_t *Lcol, const TL *Lval, const double *invd,
+                                             const double *r, const double *y, int lane)
 {
     q.G = 0;
     q.j0 = q.j1 = -1;
-    if (g >= g1) return;
-    const int32_t s = grp[g];
-    const int G = grp[g + 1] - s;
-    const int32_t b0 = Lrowptr[s];
-    const int32_t m = Lrowptr[s + 1] - b0 - 1;
+    if (k >= cnt) return;
+    const int32_t s = W.s[k], G = W.G[k], b0 = W.b[k], m = W.m[k];
     q.s = s;
     q.G = G;
     q.m = m;
-    q.j0 = (lane < m) ? Lcol[b0 + lane] : -1;
-    q.j1 = (lane + 32 < m) ? Lcol[b0 + lane + 32] : -1;
+    q.b = b0;
+    q.j0 = (lane < m) ? ((lane < WCOL) ? W.cols[k][lane] : Lcol[b0 + lane]) : -1;
+    q.j1 = (lane + 32 < m) ? ((lane + 32 < WCOL) ? W.cols[k][lane + 32] : Lcol[b0 + lane + 32]) : -1;
     // early look at the dependencies (the previous group's rows are not
     // written yet; those are taken from the ring when this group runs)
     q.d0 = (q.j0 >= 0) ? ld_relaxed(y + q.j0) : 0.0;
@@ -171,9 +206,10 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_lsolve(int32_t nchunks, const i
                                                         double *y, unsigned *err, int poll, const Scalars *sc)
 {
     if (sc && sc->done) return;
-    __shared__ double ring_all[SOLVE_BLOCK / 32][RING];
+    extern __shared__ __align__(16) unsigned char stage_raw[];
     const int lane = threadIdx.x & 31;
-    double *ring = ring_all[threadIdx.x >> 5];
+    WarpStage &W = reinterpret_cast<WarpStage *>(stage_raw)[threadIdx.x >> 5];
+    double *ring = W.ring;
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     GroupRegs<GM> cur, nxt;
@@ -181,75 +217,100 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_lsolve(int32_t nchunks, const i
         const int32_t c = ord[pos];
         const int32_t g0 = chunk_grp[c], g1 = chunk_grp[c + 1];
         const int32_t row0 = grp[g0];
-        load_group_L<TL, GM>(cur, g0, g1, grp, Lrowptr, Lcol, Lval, invd, r, y, lane);
-        for (int32_t g = g0; g < g1; ++g) {
-            load_group_L<TL, GM>(nxt, g + 1, g1, grp, Lrowptr, Lcol, Lval, invd, r, y, lane);
-            const int32_t s = cur.s, m = cur.m;
-            const int G = cur.G;
-            const int32_t lo = max(row0, s - RING);
-            double y0 = (cur.j0 >= lo && cur.j0 < s) ? ring[cur.j0 & (RING - 1)] : cur.d0;
-            double y1 = (cur.j1 >= lo && cur.j1 < s) ? ring[cur.j1 & (RING - 1)] : cur.d1;
-            wait_deps<true>(y, cur.j0, cur.j1, y0, y1, err, poll);
-            double acc[GM];
+        for (int32_t w0 = g0; w0 < g1; w0 += WIN) {
+            const int cnt = min(WIN, g1 - w0);
+            stage_window_L(W, w0, cnt, grp, Lrowptr, Lcol, lane);
+            load_group_L<TL, GM>(cur, W, 0, cnt, Lcol, Lval, invd, r, y, lane);
+            for (int k = 0; k < cnt; ++k) {
+                load_group_L<TL, GM>(nxt, W, k + 1, cnt, Lcol, Lval, invd, r, y, lane);
+                const int32_t s = cur.s, m = cur.m;
+                const int G = cur.G;
+                const int32_t lo = max(row0, s - RING);
+                double y0 = (cur.j0 >= lo && cur.j0 < s) ? ring[cur.j0 & (RING - 1)] : cur.d0;
+                double y1 = (cur.j1 >= lo && cur.j1 < s) ? ring[cur.j1 & (RING - 1)] : cur.d1;
+                wait_deps<true>(y, cur.j0, cur.j1, y0, y1, err, poll);
+                double acc[GM];
 #pragma unroll
-            for (int t = 0; t < GM; ++t) acc[t] = fma(cur.v1[t], y1, cur.v0[t] * y0);
-            if (m > 64) { // rows with more than 64 external columns
-                const int32_t b0 = Lrowptr[s];
-                for (int32_t k = lane + 64; k < m; k += 32) {
-                    const int32_t j = Lcol[b0 + k];
-                    double yj = dep_first(y, ring, j, lo, s), dummy = 0.0;
-                    wait_deps<true>(y, j, -1, yj, dummy, err, poll);
+                for (int t = 0; t < GM; ++t) acc[t] = fma(cur.v1[t], y1, cur.v0[t] * y0);
+                if (m > 64) { // rows with more than 64 external columns
+                    const int32_t b0 = cur.b;
+                    for (int32_t kk = lane + 64; kk < m; kk += 32) {
+                        const int32_t j = Lcol[b0 + kk];
+                        double yj = (j >= lo && j < s) ? ring[j & (RING - 1)] : ld_relaxed(y + j), dummy = 0.0;
+                        wait_deps<true>(y, j, -1, yj, dummy, err, poll);
 #pragma unroll
-                    for (int t = 0; t < GM; ++t)
-                        if (t < G) acc[t] = fma((double)Lval[b0 + t * (m + 1) + (t * (t - 1)) / 2 + k], yj, acc[t]);
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-                for (int t = 0; t < GM; ++t)
-                    if (t < G) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
-            if (lane == 0) {
-                double yl[GM];
-#pragma unroll
-                for (int t = 0; t < GM; ++t) {
-                    if (t < G) {
-                        double v = cur.rr[t] - acc[t];
-#pragma unroll
-                        for (int u = 0; u < t; ++u) v = fma(-cur.lin[t * (t - 1) / 2 + u], yl[u], v);
-                        yl[t] = v * cur.iv[t];
-                        st_relaxed(y + s + t, yl[t]);
-                        ring[(s + t) & (RING - 1)] = yl[t];
+                        for (int t = 0; t < GM; ++t)
+                            if (t < G) acc[t] = fma((double)Lval[b0 + t * (m + 1) + (t * (t - 1)) / 2 + kk], yj, acc[t]);
                     }
                 }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                    for (int t = 0; t < GM; ++t)
+                        if (t < G) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+                if (lane == 0) {
+                    double yl[GM];
+#pragma unroll
+                    for (int t = 0; t < GM; ++t) {
+                        if (t < G) {
+                            double v = cur.rr[t] - acc[t];
+#pragma unroll
+                            for (int u = 0; u < t; ++u) v = fma(-cur.lin[t * (t - 1) / 2 + u], yl[u], v);
+                            yl[t] = v * cur.iv[t];
+                            st_relaxed(y + s + t, yl[t]);
+                            ring[(s + t) & (RING - 1)] = yl[t];
+                        }
+                    }
+                }
+                __syncwarp();
+                cur = nxt;
             }
-            __syncwarp();
-            cur = nxt;
         }
     }
+}
+
+// Backward window (groups w1-cnt+1 .. w1, staged in descending order): U row
+// bases, external counts and the external columns of each group's last row.
+__device__ __forceinline__ void stage_window_U(WarpStage &W, int32_t w1, int32_t cnt, const int32_t *grp,
+                                               const int32_t *Urowptr, const int32_t *Ucol, int lane)
+{
+    if (lane < cnt) {
+        const int32_t g = w1 - lane;
+        const int32_t s = grp[g];
+        const int32_t G = grp[g + 1] - s;
+        const int32_t be = Urowptr[s + G - 1];
+        W.s[lane] = s;
+        W.G[lane] = G;
+        W.b[lane] = be;
+        W.m[lane] = Urowptr[s + G] - be - 1;
+    }
+    __syncwarp();
+#pragma unroll 4
+    for (int k = 0; k < cnt; ++k) {
+        const int32_t m = W.m[k], be = W.b[k];
+        if (lane < m && lane < WCOL) W.cols[k][lane] = Ucol[be + 1 + lane];
+        if (lane + 32 < m && lane + 32 < WCOL) W.cols[k][lane + 32] = Ucol[be + 1 + lane + 32];
+    }
+    __syncwarp();
 }
 
 // backward: row s+t of U holds G-t in-group entries (diagonal first), then
 // the mu external ones shared by the group (those of row e = s+G-1)
 template <typename TL, bool PCG, int GM>
-__device__ __forceinline__ void load_group_U(GroupRegs<GM> &q, int32_t g, int32_t g0, const int32_t *grp,
-                                             const int32_t *Urowptr, const int32_t *Ucol, const TL *Uval,
-                                             const double *invd, const double *y, const double *r,
-                                             const double *z, int lane)
+__device__ __forceinline__ void load_group_U(GroupRegs<GM> &q, const WarpStage &W, int k, int cnt,
+                                             const int32_t *Ucol, const TL *Uval, const double *invd,
+                                             const double *y, const double *r, const double *z, int lane)
 {
     q.G = 0;
     q.j0 = q.j1 = -1;
-    if (g < g0) return;
-    const int32_t s = grp[g];
-    const int G = grp[g + 1] - s;
-    const int32_t e = s + G - 1;
-    const int32_t be = Urowptr[e];
-    const int32_t mu = Urowptr[e + 1] - be - 1;
+    if (k >= cnt) return;
+    const int32_t s = W.s[k], G = W.G[k], be = W.b[k], mu = W.m[k];
     q.s = s;
     q.G = G;
     q.m = mu;
-    q.j0 = (lane < mu) ? Ucol[be + 1 + lane] : -1;
-    q.j1 = (lane + 32 < mu) ? Ucol[be + 1 + lane + 32] : -1;
+    q.b = be;
+    q.j0 = (lane < mu) ? ((lane < WCOL) ? W.cols[k][lane] : Ucol[be + 1 + lane]) : -1;
+    q.j1 = (lane + 32 < mu) ? ((lane + 32 < WCOL) ? W.cols[k][lane + 32] : Ucol[be + 1 + lane + 32]) : -1;
     q.d0 = (q.j0 >= 0) ? ld_relaxed(z + q.j0) : 0.0;
     q.d1 = (q.j1 >= 0) ? ld_relaxed(z + q.j1) : 0.0;
     int32_t base[GM];
@@ -287,9 +348,10 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_ltsolve(int32_t nchunks, const 
                                                          unsigned *err, int poll, Scalars *sc)
 {
     if (sc && sc->done) return;
-    __shared__ double ring_all[SOLVE_BLOCK / 32][RING];
+    extern __shared__ __align__(16) unsigned char stage_raw[];
     const int lane = threadIdx.x & 31;
-    double *ring = ring_all[threadIdx.x >> 5];
+    WarpStage &W = reinterpret_cast<WarpStage *>(stage_raw)[threadIdx.x >> 5];
+    double *ring = W.ring;
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double dot = 0.0;
@@ -298,56 +360,60 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_ltsolve(int32_t nchunks, const 
         const int32_t c = ord[pos];
         const int32_t g0 = chunk_grp[c], g1 = chunk_grp[c + 1];
         const int32_t rowEnd = grp[g1];
-        load_group_U<TL, PCG, GM>(cur, g1 - 1, g0, grp, Urowptr, Ucol, Uval, invd, y, r, z, lane);
-        for (int32_t g = g1 - 1; g >= g0; --g) {
-            load_group_U<TL, PCG, GM>(nxt, g - 1, g0, grp, Urowptr, Ucol, Uval, invd, y, r, z, lane);
-            const int32_t s = cur.s, mu = cur.m;
-            const int G = cur.G;
-            const int32_t e = s + G - 1;
-            const int32_t hi = min(rowEnd, e + 1 + RING);
-            double z0 = (cur.j0 > e && cur.j0 < hi) ? ring[cur.j0 & (RING - 1)] : cur.d0;
-            double z1 = (cur.j1 > e && cur.j1 < hi) ? ring[cur.j1 & (RING - 1)] : cur.d1;
-            wait_deps<false>(z, cur.j0, cur.j1, z0, z1, err, poll);
-            double acc[GM];
+        for (int32_t w1 = g1 - 1; w1 >= g0; w1 -= WIN) {
+            const int cnt = min(WIN, w1 - g0 + 1);
+            stage_window_U(W, w1, cnt, grp, Urowptr, Ucol, lane);
+            load_group_U<TL, PCG, GM>(cur, W, 0, cnt, Ucol, Uval, invd, y, r, z, lane);
+            for (int k = 0; k < cnt; ++k) {
+                load_group_U<TL, PCG, GM>(nxt, W, k + 1, cnt, Ucol, Uval, invd, y, r, z, lane);
+                const int32_t s = cur.s, mu = cur.m;
+                const int G = cur.G;
+                const int32_t e = s + G - 1;
+                const int32_t hi = min(rowEnd, e + 1 + RING);
+                double z0 = (cur.j0 > e && cur.j0 < hi) ? ring[cur.j0 & (RING - 1)] : cur.d0;
+                double z1 = (cur.j1 > e && cur.j1 < hi) ? ring[cur.j1 & (RING - 1)] : cur.d1;
+                wait_deps<false>(z, cur.j0, cur.j1, z0, z1, err, poll);
+                double acc[GM];
 #pragma unroll
-            for (int t = 0; t < GM; ++t) acc[t] = fma(cur.v1[t], z1, cur.v0[t] * z0);
-            if (mu > 64) {
-                const int32_t be = Urowptr[e];
-                for (int32_t k = lane + 64; k < mu; k += 32) {
-                    const int32_t j = Ucol[be + 1 + k];
-                    double zj = dep_first(z, ring, j, e + 1, hi), dummy = 0.0;
-                    wait_deps<false>(z, j, -1, zj, dummy, err, poll);
+                for (int t = 0; t < GM; ++t) acc[t] = fma(cur.v1[t], z1, cur.v0[t] * z0);
+                if (mu > 64) {
+                    const int32_t be = cur.b;
+                    for (int32_t kk = lane + 64; kk < mu; kk += 32) {
+                        const int32_t j = Ucol[be + 1 + kk];
+                        double zj = (j > e && j < hi) ? ring[j & (RING - 1)] : ld_relaxed(z + j), dummy = 0.0;
+                        wait_deps<false>(z, j, -1, zj, dummy, err, poll);
+#pragma unroll
+                        for (int t = 0; t < GM; ++t)
+                            if (t < G) acc[t] = fma((double)Uval[Urowptr[s + t] + (G - t) + kk], zj, acc[t]);
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
                     for (int t = 0; t < GM; ++t)
-                        if (t < G) acc[t] = fma((double)Uval[Urowptr[s + t] + (G - t) + k], zj, acc[t]);
-                }
-            }
+                        if (t < G) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+                if (lane == 0) {
+                    double zl[GM];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
+                    for (int t = GM - 1; t >= 0; --t) {
+                        if (t < G) {
+                            double v = cur.aux[t] - acc[t];
 #pragma unroll
-                for (int t = 0; t < GM; ++t)
-                    if (t < G) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
-            if (lane == 0) {
-                double zl[GM];
-#pragma unroll
-                for (int t = GM - 1; t >= 0; --t) {
-                    if (t < G) {
-                        double v = cur.aux[t] - acc[t];
-#pragma unroll
-                        for (int u = t + 1; u < GM; ++u)
-                            if (u < G) v = fma(-cur.lin[u * (u - 1) / 2 + t], zl[u], v);
-                        zl[t] = v * cur.iv[t];
-                        st_relaxed(z + s + t, zl[t]);
-                        ring[(s + t) & (RING - 1)] = zl[t];
-                        if (PCG) {
-                            y[s + t] = sentinel_d();
-                            dot = fma(cur.rr[t], zl[t], dot);
+                            for (int u = t + 1; u < GM; ++u)
+                                if (u < G) v = fma(-cur.lin[u * (u - 1) / 2 + t], zl[u], v);
+                            zl[t] = v * cur.iv[t];
+                            st_relaxed(z + s + t, zl[t]);
+                            ring[(s + t) & (RING - 1)] = zl[t];
+                            if (PCG) {
+                                y[s + t] = sentinel_d();
+                                dot = fma(cur.rr[t], zl[t], dot);
+                            }
                         }
                     }
                 }
+                __syncwarp();
+                cur = nxt;
             }
-            __syncwarp();
-            cur = nxt;
         }
     }
     if (PCG) {
@@ -750,7 +816,14 @@ static int launch_lsolve_g(gic_handle *h, const Pattern &P, const TL *Lval, cons
     unsigned *er = h->dev_err;
     int poll = h->tune_poll;
     void *args[] = {&nc, &ord, &cg, &g, &lr, &lc, &Lval, &invd, &r, &y, &er, &poll, &sc};
-    return launch_persistent(h, (const void *)k_lsolve<TL, GM>, SOLVE_BLOCK, 0, solve_warps(h, P), args);
+    const size_t smem = sizeof(WarpStage) * (SOLVE_BLOCK / 32);
+    static bool attr_done[2][64] = {};
+    bool &ad = attr_done[sizeof(TL) == 4][h->device & 63];
+    if (!ad) {
+        GIC_CUDA_TRY(cudaFuncSetAttribute(k_lsolve<TL, GM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        ad = true;
+    }
+    return launch_persistent(h, (const void *)k_lsolve<TL, GM>, SOLVE_BLOCK, smem, solve_warps(h, P), args);
 }
 
 template <typename TL>
@@ -773,7 +846,15 @@ static int launch_ltsolve_g(gic_handle *h, const Pattern &P, const TL *Uval, con
     void *args[] = {&nc, &ord, &cg, &g, &ur, &uc, &Uval, &invd, &y, &z, &r, &partials, &er, &poll, &sc};
     int64_t need = solve_warps(h, P);
     if (PCG && need > MAX_PARTIALS) need = MAX_PARTIALS; // grid warps <= partial slots
-    return launch_persistent(h, (const void *)k_ltsolve<TL, PCG, GM>, SOLVE_BLOCK, 0, need, args);
+    const size_t smem = sizeof(WarpStage) * (SOLVE_BLOCK / 32);
+    static bool attr_done[2][2][64] = {};
+    bool &ad = attr_done[sizeof(TL) == 4][PCG][h->device & 63];
+    if (!ad) {
+        GIC_CUDA_TRY(cudaFuncSetAttribute(k_ltsolve<TL, PCG, GM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+        ad = true;
+    }
+    return launch_persistent(h, (const void *)k_ltsolve<TL, PCG, GM>, SOLVE_BLOCK, smem, need, args);
 }
 
 template <typename TL, bool PCG>
