@@ -258,6 +258,7 @@ int gic_adam_step(gic_handle *h, int64_t np, float *theta, const float *grad, fl
  * between polls, bit 16 set = one polling lane per warp (default 1<<16). */
 #define GIC_TUNE_SOLVE_WARPS_PER_SM 1
 #define GIC_TUNE_POLL 2
+#define GIC_TUNE_PIPELINE 3 /* 1 (default): staged triangular solves where they apply */
 int gic_set_tuning(gic_handle *h, int key, int value);
 
 /* Failure-path self-test of the bounded device waits: one warp waits on a

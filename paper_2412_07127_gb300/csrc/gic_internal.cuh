@@ -105,6 +105,28 @@ constexpr int POLL_ONE_LANE = 1 << 16;
 
 __device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
+// Asynchronous global -> shared copies (no register staging); a thread's
+// copies complete in commit-group order.
+__device__ __forceinline__ void cp_async_4(void *smem, const void *gmem)
+{
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_8(void *smem, const void *gmem)
+{
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+template <typename T>
+__device__ __forceinline__ void cp_async_t(T *smem, const T *gmem)
+{
+    if (sizeof(T) == 8) cp_async_8(smem, gmem);
+    else cp_async_4(smem, gmem);
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // Wait until neither of a lane's two dependency values is the sentinel.
 // With POLL_ONE_LANE one lane at a time polls, the one holding the
 // outstanding dependency produced last (the largest column in the forward
@@ -203,6 +225,7 @@ struct gic_handle {
     long long launches = 0;        // kernels this handle has launched
     int tune_solve_warps_per_sm = 0; // cap on resident solve warps per SM (0: none)
     int tune_poll = gic::POLL_ONE_LANE; // polling configuration of the sync-free kernels
+    int tune_pipeline = 1;              // staged (cp.async) triangular solves when the pattern fits
 };
 
 namespace gic {

@@ -443,6 +443,352 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_ltsolve(int32_t nchunks, const 
     }
 }
 
+// ------------------------------------------------------------ pipelined SpTRSV
+// Same schedule and arithmetic as k_lsolve / k_ltsolve, for patterns whose
+// groups have at most WCOL external columns. A warp stages the metadata of
+// its whole chunk (segments of CHMAX groups) in shared memory once, then
+// keeps NST groups in flight: each group's columns, factor values, right-hand
+// side and reciprocal diagonal are copied global -> shared with cp.async
+// NST-1 groups before the group runs, and its dependency values are read
+// two groups before it runs (polled again only if still the sentinel). The
+// per-group critical path is then the arithmetic plus genuine waits.
+constexpr int CHMAX = 160;
+constexpr int NST = 4;
+
+template <typename TL, int GM>
+struct PStage {
+    TL v[GM][WCOL];                 // external values of each row of the group
+    TL lin[GM * (GM - 1) / 2 + 1];  // in-group entries
+    double rr[GM], iv[GM], aux[GM]; // r (forward: rhs; backward: PCG dot), 1/L_ii, y (backward)
+    int32_t cols[WCOL];
+};
+
+template <typename TL, int GM>
+struct PWarp {
+    int32_t s[CHMAX], G[CHMAX], b[CHMAX], m[CHMAX];
+    PStage<TL, GM> st[NST];
+    double ring[RING];
+};
+
+// (t,u) of the q-th in-group entry, row-major lower triangle: t > u
+__device__ __forceinline__ void tri_index(int q, int &t, int &u)
+{
+    t = 1;
+    while (q >= t) { q -= t; ++t; }
+    u = q;
+}
+
+template <typename TL, int GM>
+__device__ __forceinline__ void fill_stage_L(PStage<TL, GM> &st, const PWarp<TL, GM> &W, int k, const int32_t *Lcol,
+                                             const TL *Lval, const double *r, const double *invd, int lane)
+{
+    const int32_t s = W.s[k], G = W.G[k], b0 = W.b[k], m = W.m[k];
+    if (lane < m) cp_async_4(&st.cols[lane], Lcol + b0 + lane);
+    if (lane + 32 < m) cp_async_4(&st.cols[lane + 32], Lcol + b0 + lane + 32);
+#pragma unroll
+    for (int t = 0; t < GM; ++t) {
+        if (t < G) {
+            const int32_t base = b0 + t * (m + 1) + (t * (t - 1)) / 2;
+            if (lane < m) cp_async_t(&st.v[t][lane], Lval + base + lane);
+            if (lane + 32 < m) cp_async_t(&st.v[t][lane + 32], Lval + base + lane + 32);
+        }
+    }
+    if (lane < G * (G - 1) / 2) {
+        int t, u;
+        tri_index(lane, t, u);
+        cp_async_t(&st.lin[lane], Lval + b0 + t * (m + 1) + (t * (t - 1)) / 2 + m + u);
+    }
+    if (lane < G) {
+        cp_async_8(&st.rr[lane], r + s + lane);
+        cp_async_8(&st.iv[lane], invd + s + lane);
+    }
+}
+
+template <typename TL, int GM>
+__global__ void __launch_bounds__(SOLVE_BLOCK) k_lsolve_p(int32_t nchunks, const int32_t *__restrict__ ord,
+                                                          const int32_t *__restrict__ chunk_grp,
+                                                          const int32_t *__restrict__ grp,
+                                                          const int32_t *__restrict__ Lrowptr,
+                                                          const int32_t *__restrict__ Lcol,
+                                                          const TL *__restrict__ Lval, const double *__restrict__ invd,
+                                                          const double *__restrict__ r, double *y, unsigned *err,
+                                                          int poll, const Scalars *sc)
+{
+    if (sc && sc->done) return;
+    extern __shared__ __align__(16) unsigned char pw_raw[];
+    const int lane = threadIdx.x & 31;
+    PWarp<TL, GM> &W = reinterpret_cast<PWarp<TL, GM> *>(pw_raw)[threadIdx.x >> 5];
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t pos = w; pos < nchunks; pos += nw) {
+        const int32_t c = ord[pos];
+        const int32_t g0 = chunk_grp[c], g1 = chunk_grp[c + 1];
+        const int32_t row0 = grp[g0];
+        for (int32_t seg = g0; seg < g1; seg += CHMAX) {
+            const int cnt = min(CHMAX, g1 - seg);
+            for (int k = lane; k < cnt; k += 32) {
+                const int32_t s = grp[seg + k];
+                const int32_t b0 = Lrowptr[s];
+                W.s[k] = s;
+                W.G[k] = grp[seg + k + 1] - s;
+                W.b[k] = b0;
+                W.m[k] = Lrowptr[s + 1] - b0 - 1;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int d = 0; d < NST; ++d) {
+                if (d < cnt) fill_stage_L<TL, GM>(W.st[d], W, d, Lcol, Lval, r, invd, lane);
+                cp_async_commit();
+            }
+            cp_async_wait<NST - 2>();
+            __syncwarp();
+            // dependency values of the next two groups, read early
+            double dA0 = 0.0, dA1 = 0.0, dB0 = 0.0, dB1 = 0.0;
+            {
+                const int32_t m0 = W.m[0];
+                const int32_t ja = (lane < m0) ? W.st[0].cols[lane] : -1, jb = (lane + 32 < m0) ? W.st[0].cols[lane + 32] : -1;
+                dA0 = (ja >= 0) ? ld_relaxed(y + ja) : 0.0;
+                dA1 = (jb >= 0) ? ld_relaxed(y + jb) : 0.0;
+                if (cnt > 1) {
+                    const int32_t m1 = W.m[1];
+                    const int32_t jc = (lane < m1) ? W.st[1].cols[lane] : -1, jd = (lane + 32 < m1) ? W.st[1].cols[lane + 32] : -1;
+                    dB0 = (jc >= 0) ? ld_relaxed(y + jc) : 0.0;
+                    dB1 = (jd >= 0) ? ld_relaxed(y + jd) : 0.0;
+                }
+            }
+            for (int k = 0; k < cnt; ++k) {
+                PStage<TL, GM> &st = W.st[k % NST];
+                const int32_t s = W.s[k], m = W.m[k];
+                const int G = W.G[k];
+                const int32_t lo = max(row0, s - RING);
+                const int32_t j0 = (lane < m) ? st.cols[lane] : -1;
+                const int32_t j1 = (lane + 32 < m) ? st.cols[lane + 32] : -1;
+                double y0 = (j0 >= lo && j0 < s) ? W.ring[j0 & (RING - 1)] : dA0;
+                double y1 = (j1 >= lo && j1 < s) ? W.ring[j1 & (RING - 1)] : dA1;
+                if (j0 < 0) y0 = 0.0;
+                if (j1 < 0) y1 = 0.0;
+                wait_deps<true>(y, j0, j1, y0, y1, err, poll);
+                double acc[GM];
+#pragma unroll
+                for (int t = 0; t < GM; ++t) {
+                    const double a0 = (t < G && j0 >= 0) ? (double)st.v[t][lane] : 0.0;
+                    const double a1 = (t < G && j1 >= 0) ? (double)st.v[t][lane + 32] : 0.0;
+                    acc[t] = fma(a1, y1, a0 * y0);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                    for (int t = 0; t < GM; ++t)
+                        if (t < G) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+                if (lane == 0) {
+                    double yl[GM];
+#pragma unroll
+                    for (int t = 0; t < GM; ++t) {
+                        if (t < G) {
+                            double v = st.rr[t] - acc[t];
+#pragma unroll
+                            for (int u = 0; u < t; ++u) v = fma(-(double)st.lin[t * (t - 1) / 2 + u], yl[u], v);
+                            yl[t] = v * st.iv[t];
+                            st_relaxed(y + s + t, yl[t]);
+                            W.ring[(s + t) & (RING - 1)] = yl[t];
+                        }
+                    }
+                }
+                __syncwarp();
+                // refill this stage with group k + NST, then ready group k + 2
+                if (k + NST < cnt) fill_stage_L<TL, GM>(st, W, k + NST, Lcol, Lval, r, invd, lane);
+                cp_async_commit();
+                cp_async_wait<NST - 2>();
+                __syncwarp();
+                dA0 = dB0;
+                dA1 = dB1;
+                if (k + 2 < cnt) {
+                    const PStage<TL, GM> &s2 = W.st[(k + 2) % NST];
+                    const int32_t m2 = W.m[k + 2];
+                    const int32_t jc = (lane < m2) ? s2.cols[lane] : -1, jd = (lane + 32 < m2) ? s2.cols[lane + 32] : -1;
+                    dB0 = (jc >= 0) ? ld_relaxed(y + jc) : 0.0;
+                    dB1 = (jd >= 0) ? ld_relaxed(y + jd) : 0.0;
+                }
+            }
+            cp_async_wait<0>();
+            __syncwarp();
+        }
+    }
+}
+
+template <typename TL, bool PCG, int GM>
+__device__ __forceinline__ void fill_stage_U(PStage<TL, GM> &st, const PWarp<TL, GM> &W, int k, const int32_t *Ucol,
+                                             const TL *Uval, const double *r, const double *invd, const double *y,
+                                             int lane)
+{
+    const int32_t s = W.s[k], G = W.G[k], be = W.b[k], mu = W.m[k];
+    if (lane < mu) cp_async_4(&st.cols[lane], Ucol + be + 1 + lane);
+    if (lane + 32 < mu) cp_async_4(&st.cols[lane + 32], Ucol + be + 1 + lane + 32);
+#pragma unroll
+    for (int t = 0; t < GM; ++t) {
+        if (t < G) {
+            const int32_t base = be - (G - 1 - t) * (mu + 1) - ((G - 1 - t) * (G - t)) / 2;
+            const int32_t ext = base + (G - t);
+            if (lane < mu) cp_async_t(&st.v[t][lane], Uval + ext + lane);
+            if (lane + 32 < mu) cp_async_t(&st.v[t][lane + 32], Uval + ext + lane + 32);
+        }
+    }
+    if (lane < G * (G - 1) / 2) { // lin[u(u-1)/2 + t] = U[s+t][s+u], t < u
+        int uu, t;
+        tri_index(lane, uu, t);
+        const int32_t base = be - (G - 1 - t) * (mu + 1) - ((G - 1 - t) * (G - t)) / 2;
+        cp_async_t(&st.lin[lane], Uval + base + (uu - t));
+    }
+    if (lane < G) {
+        if (PCG) cp_async_8(&st.rr[lane], r + s + lane);
+        cp_async_8(&st.iv[lane], invd + s + lane);
+        cp_async_8(&st.aux[lane], y + s + lane);
+    }
+}
+
+template <typename TL, bool PCG, int GM>
+__global__ void __launch_bounds__(SOLVE_BLOCK) k_ltsolve_p(int32_t nchunks, const int32_t *__restrict__ ord,
+                                                           const int32_t *__restrict__ chunk_grp,
+                                                           const int32_t *__restrict__ grp,
+                                                           const int32_t *__restrict__ Urowptr,
+                                                           const int32_t *__restrict__ Ucol,
+                                                           const TL *__restrict__ Uval, const double *__restrict__ invd,
+                                                           double *y, double *z, const double *__restrict__ r,
+                                                           double *partials, unsigned *err, int poll, Scalars *sc)
+{
+    if (sc && sc->done) return;
+    extern __shared__ __align__(16) unsigned char pw_raw[];
+    const int lane = threadIdx.x & 31;
+    PWarp<TL, GM> &W = reinterpret_cast<PWarp<TL, GM> *>(pw_raw)[threadIdx.x >> 5];
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double dot = 0.0;
+    for (int64_t pos = w; pos < nchunks; pos += nw) {
+        const int32_t c = ord[pos];
+        const int32_t g0 = chunk_grp[c], g1 = chunk_grp[c + 1];
+        const int32_t rowEnd = grp[g1];
+        for (int32_t segEnd = g1 - 1; segEnd >= g0; segEnd -= CHMAX) {
+            const int cnt = min(CHMAX, segEnd - g0 + 1);
+            for (int k = lane; k < cnt; k += 32) { // k-th group of the segment, from its end
+                const int32_t g = segEnd - k;
+                const int32_t s = grp[g];
+                const int32_t G = grp[g + 1] - s;
+                const int32_t be = Urowptr[s + G - 1];
+                W.s[k] = s;
+                W.G[k] = G;
+                W.b[k] = be;
+                W.m[k] = Urowptr[s + G] - be - 1;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int d = 0; d < NST; ++d) {
+                if (d < cnt) fill_stage_U<TL, PCG, GM>(W.st[d], W, d, Ucol, Uval, r, invd, y, lane);
+                cp_async_commit();
+            }
+            cp_async_wait<NST - 2>();
+            __syncwarp();
+            double dA0 = 0.0, dA1 = 0.0, dB0 = 0.0, dB1 = 0.0;
+            {
+                const int32_t m0 = W.m[0];
+                const int32_t ja = (lane < m0) ? W.st[0].cols[lane] : -1, jb = (lane + 32 < m0) ? W.st[0].cols[lane + 32] : -1;
+                dA0 = (ja >= 0) ? ld_relaxed(z + ja) : 0.0;
+                dA1 = (jb >= 0) ? ld_relaxed(z + jb) : 0.0;
+                if (cnt > 1) {
+                    const int32_t m1 = W.m[1];
+                    const int32_t jc = (lane < m1) ? W.st[1].cols[lane] : -1, jd = (lane + 32 < m1) ? W.st[1].cols[lane + 32] : -1;
+                    dB0 = (jc >= 0) ? ld_relaxed(z + jc) : 0.0;
+                    dB1 = (jd >= 0) ? ld_relaxed(z + jd) : 0.0;
+                }
+            }
+            for (int k = 0; k < cnt; ++k) {
+                PStage<TL, GM> &st = W.st[k % NST];
+                const int32_t s = W.s[k], mu = W.m[k];
+                const int G = W.G[k];
+                const int32_t e = s + G - 1;
+                const int32_t hi = min(rowEnd, e + 1 + RING);
+                const int32_t j0 = (lane < mu) ? st.cols[lane] : -1;
+                const int32_t j1 = (lane + 32 < mu) ? st.cols[lane + 32] : -1;
+                double z0 = (j0 > e && j0 < hi) ? W.ring[j0 & (RING - 1)] : dA0;
+                double z1 = (j1 > e && j1 < hi) ? W.ring[j1 & (RING - 1)] : dA1;
+                if (j0 < 0) z0 = 0.0;
+                if (j1 < 0) z1 = 0.0;
+                wait_deps<false>(z, j0, j1, z0, z1, err, poll);
+                double acc[GM];
+#pragma unroll
+                for (int t = 0; t < GM; ++t) {
+                    const double a0 = (t < G && j0 >= 0) ? (double)st.v[t][lane] : 0.0;
+                    const double a1 = (t < G && j1 >= 0) ? (double)st.v[t][lane + 32] : 0.0;
+                    acc[t] = fma(a1, z1, a0 * z0);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                    for (int t = 0; t < GM; ++t)
+                        if (t < G) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+                if (lane == 0) {
+                    double zl[GM];
+#pragma unroll
+                    for (int t = GM - 1; t >= 0; --t) {
+                        if (t < G) {
+                            double v = st.aux[t] - acc[t];
+#pragma unroll
+                            for (int u = t + 1; u < GM; ++u)
+                                if (u < G) v = fma(-(double)st.lin[u * (u - 1) / 2 + t], zl[u], v);
+                            zl[t] = v * st.iv[t];
+                            st_relaxed(z + s + t, zl[t]);
+                            W.ring[(s + t) & (RING - 1)] = zl[t];
+                            if (PCG) {
+                                y[s + t] = sentinel_d();
+                                dot = fma(st.rr[t], zl[t], dot);
+                            }
+                        }
+                    }
+                }
+                __syncwarp();
+                if (k + NST < cnt) fill_stage_U<TL, PCG, GM>(st, W, k + NST, Ucol, Uval, r, invd, y, lane);
+                cp_async_commit();
+                cp_async_wait<NST - 2>();
+                __syncwarp();
+                dA0 = dB0;
+                dA1 = dB1;
+                if (k + 2 < cnt) {
+                    const PStage<TL, GM> &s2 = W.st[(k + 2) % NST];
+                    const int32_t m2 = W.m[k + 2];
+                    const int32_t jc = (lane < m2) ? s2.cols[lane] : -1, jd = (lane + 32 < m2) ? s2.cols[lane + 32] : -1;
+                    dB0 = (jc >= 0) ? ld_relaxed(z + jc) : 0.0;
+                    dB1 = (jd >= 0) ? ld_relaxed(z + jd) : 0.0;
+                }
+            }
+            cp_async_wait<0>();
+            __syncwarp();
+        }
+    }
+    if (PCG) {
+        if (lane == 0) partials[w] = dot;
+        __syncwarp();
+        unsigned last = 0;
+        if (lane == 0) {
+            __threadfence();
+            last = (atomicAdd(&sc->counter, 1u) == (unsigned)nw - 1u);
+        }
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (last) {
+            __threadfence();
+            double rz = warp_sum_partials(partials, (int)nw);
+            if (lane == 0) {
+                sc->counter = 0;
+                if (!(rz > 0.0) || !isfinite(rz)) {
+                    sc->status = GIC_ERR_BREAKDOWN;
+                    sc->done = 1;
+                } else {
+                    sc->beta = (sc->iter == 0) ? 0.0 : rz / sc->rz;
+                    sc->rz = rz;
+                }
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------ SpMV
 // MODE 0: y = A x (optional x^T y into *out_dot)
 // MODE 1: y = A p, pw = p^T y, alpha = rz / pw          (Algorithm 1 lines 15-16)
@@ -826,10 +1172,37 @@ static int launch_lsolve_g(gic_handle *h, const Pattern &P, const TL *Lval, cons
     return launch_persistent(h, (const void *)k_lsolve<TL, GM>, SOLVE_BLOCK, smem, solve_warps(h, P), args);
 }
 
+template <typename TL, int GM>
+static int launch_lsolve_pg(gic_handle *h, const Pattern &P, const TL *Lval, const double *invd, const double *r,
+                            double *y, Scalars *sc)
+{
+    int32_t nc = P.nchunks;
+    const int32_t *ord = P.ord_f, *cg = P.chunk_grp, *g = P.grp, *lr = P.Lrowptr, *lc = P.Lcol;
+    unsigned *er = h->dev_err;
+    int poll = h->tune_poll;
+    void *args[] = {&nc, &ord, &cg, &g, &lr, &lc, &Lval, &invd, &r, &y, &er, &poll, &sc};
+    const size_t smem = sizeof(PWarp<TL, GM>) * (SOLVE_BLOCK / 32);
+    static bool ad[64] = {};
+    if (!ad[h->device & 63]) {
+        GIC_CUDA_TRY(cudaFuncSetAttribute(k_lsolve_p<TL, GM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        ad[h->device & 63] = true;
+    }
+    return launch_persistent(h, (const void *)k_lsolve_p<TL, GM>, SOLVE_BLOCK, smem, solve_warps(h, P), args);
+}
+
+static bool pipelined_ok(gic_handle *h, const Pattern &P)
+{
+    return h->tune_pipeline && P.max_group <= 3 && P.max_ext_lower <= WCOL && P.max_ext_upper <= WCOL;
+}
+
 template <typename TL>
 static int launch_lsolve(gic_handle *h, const Pattern &P, const TL *Lval, const double *invd, const double *r,
                          double *y, Scalars *sc)
 {
+    if (pipelined_ok(h, P)) {
+        if (P.max_group <= 1) return launch_lsolve_pg<TL, 1>(h, P, Lval, invd, r, y, sc);
+        return launch_lsolve_pg<TL, 3>(h, P, Lval, invd, r, y, sc);
+    }
     if (P.max_group <= 1) return launch_lsolve_g<TL, 1>(h, P, Lval, invd, r, y, sc);
     if (P.max_group <= 3) return launch_lsolve_g<TL, 3>(h, P, Lval, invd, r, y, sc);
     return launch_lsolve_g<TL, GMAX>(h, P, Lval, invd, r, y, sc);
@@ -857,10 +1230,35 @@ static int launch_ltsolve_g(gic_handle *h, const Pattern &P, const TL *Uval, con
     return launch_persistent(h, (const void *)k_ltsolve<TL, PCG, GM>, SOLVE_BLOCK, smem, need, args);
 }
 
+template <typename TL, bool PCG, int GM>
+static int launch_ltsolve_pg(gic_handle *h, const Pattern &P, const TL *Uval, const double *invd, double *y, double *z,
+                             const double *r, double *partials, Scalars *sc)
+{
+    int32_t nc = P.nchunks;
+    const int32_t *ord = P.ord_b, *cg = P.chunk_grp, *g = P.grp, *ur = P.Urowptr, *uc = P.Ucol;
+    unsigned *er = h->dev_err;
+    int poll = h->tune_poll;
+    void *args[] = {&nc, &ord, &cg, &g, &ur, &uc, &Uval, &invd, &y, &z, &r, &partials, &er, &poll, &sc};
+    int64_t need = solve_warps(h, P);
+    if (PCG && need > MAX_PARTIALS) need = MAX_PARTIALS;
+    const size_t smem = sizeof(PWarp<TL, GM>) * (SOLVE_BLOCK / 32);
+    static bool ad[64] = {};
+    if (!ad[h->device & 63]) {
+        GIC_CUDA_TRY(cudaFuncSetAttribute(k_ltsolve_p<TL, PCG, GM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+        ad[h->device & 63] = true;
+    }
+    return launch_persistent(h, (const void *)k_ltsolve_p<TL, PCG, GM>, SOLVE_BLOCK, smem, need, args);
+}
+
 template <typename TL, bool PCG>
 static int launch_ltsolve(gic_handle *h, const Pattern &P, const TL *Uval, const double *invd, double *y, double *z,
                           const double *r, double *partials, Scalars *sc)
 {
+    if (pipelined_ok(h, P)) {
+        if (P.max_group <= 1) return launch_ltsolve_pg<TL, PCG, 1>(h, P, Uval, invd, y, z, r, partials, sc);
+        return launch_ltsolve_pg<TL, PCG, 3>(h, P, Uval, invd, y, z, r, partials, sc);
+    }
     if (P.max_group <= 1) return launch_ltsolve_g<TL, PCG, 1>(h, P, Uval, invd, y, z, r, partials, sc);
     if (P.max_group <= 3) return launch_ltsolve_g<TL, PCG, 3>(h, P, Uval, invd, y, z, r, partials, sc);
     return launch_ltsolve_g<TL, PCG, GMAX>(h, P, Uval, invd, y, z, r, partials, sc);
@@ -1192,6 +1590,7 @@ int gic_set_tuning(gic_handle *h, int key, int value)
     switch (key) {
     case GIC_TUNE_SOLVE_WARPS_PER_SM: h->tune_solve_warps_per_sm = value; return GIC_OK;
     case GIC_TUNE_POLL: h->tune_poll = value; return GIC_OK;
+    case GIC_TUNE_PIPELINE: h->tune_pipeline = value; return GIC_OK;
     default: return GIC_ERR_INVALID_ARG;
     }
 }

@@ -310,7 +310,7 @@ def error_flags(h: Handle):
     return f.value
 
 
-GIC_TUNE_SOLVE_WARPS_PER_SM, GIC_TUNE_POLL = 1, 2
+GIC_TUNE_SOLVE_WARPS_PER_SM, GIC_TUNE_POLL, GIC_TUNE_PIPELINE = 1, 2, 3
 POLL_ONE_LANE = 1 << 16
 
 
