@@ -105,6 +105,77 @@ constexpr int POLL_ONE_LANE = 1 << 16;
 
 __device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
+// float flavour of the sentinel machinery (FP32 preconditioner vectors)
+constexpr unsigned SENTINEL_BITS_F = 0x7fa0beefu; // signalling-NaN payload
+__device__ __forceinline__ float sentinel_f() { return __uint_as_float(SENTINEL_BITS_F); }
+__device__ __forceinline__ bool is_sentinel(float v) { return __float_as_uint(v) == SENTINEL_BITS_F; }
+__device__ __forceinline__ float ld_relaxed(const float *p)
+{
+    float v;
+    asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(float *p, float v)
+{
+    asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+template <typename T> __device__ __forceinline__ T sentinel_of();
+template <> __device__ __forceinline__ double sentinel_of<double>() { return sentinel_d(); }
+template <> __device__ __forceinline__ float sentinel_of<float>() { return sentinel_f(); }
+template <typename T> __device__ __forceinline__ T qnan_of();
+template <> __device__ __forceinline__ double qnan_of<double>() { return __longlong_as_double(0x7ff8000000000000ll); }
+template <> __device__ __forceinline__ float qnan_of<float>() { return __uint_as_float(0x7fc00000u); }
+
+// generic bounded wait (same policy as wait_value)
+template <typename T>
+__device__ __forceinline__ T wait_word(const T *p, unsigned *err, unsigned sleep_ns)
+{
+    T v = ld_relaxed(p);
+    if (!is_sentinel(v)) return v;
+    for (long long it = 0; it < SPIN_LIMIT; ++it) {
+        if (it > 65536) __nanosleep(128);
+        else if (sleep_ns) __nanosleep(sleep_ns);
+        v = ld_relaxed(p);
+        if (!is_sentinel(v)) return v;
+        if ((it & 255) == 255 && *((volatile unsigned *)err) != 0u) return qnan_of<T>();
+    }
+    atomicOr(err, ERR_TIMEOUT);
+    return qnan_of<T>();
+}
+
+// outstanding dependencies of a lane (at most two words): one polling lane
+// at a time (the one holding the dependency produced last), or all lanes
+template <bool LAST_IS_MAX, typename T>
+__device__ __forceinline__ void wait_pair(const T *y, int32_t j0, int32_t j1, T &y0, T &y1, unsigned *err, int poll)
+{
+    const unsigned sl = (unsigned)(poll & 0xffff);
+    bool p0 = j0 >= 0 && is_sentinel(y0), p1 = j1 >= 0 && is_sentinel(y1);
+    if (!(poll & POLL_ONE_LANE)) {
+        if (p0) y0 = wait_word(y + j0, err, sl);
+        if (p1) y1 = wait_word(y + j1, err, sl);
+        return;
+    }
+    unsigned pend = __ballot_sync(0xffffffffu, p0 || p1);
+    for (int round = 0; pend && round < 130; ++round) {
+        int32_t mine, jm;
+        if (LAST_IS_MAX) {
+            mine = max(p0 ? j0 : -1, p1 ? j1 : -1);
+            jm = __reduce_max_sync(0xffffffffu, mine);
+        } else {
+            mine = min(p0 ? j0 : INT_MAX, p1 ? j1 : INT_MAX);
+            jm = __reduce_min_sync(0xffffffffu, mine);
+        }
+        if (mine == jm) wait_word(y + jm, err, sl);
+        __syncwarp();
+        if (p0) { y0 = ld_relaxed(y + j0); p0 = is_sentinel(y0); }
+        if (p1) { y1 = ld_relaxed(y + j1); p1 = is_sentinel(y1); }
+        pend = __ballot_sync(0xffffffffu, p0 || p1);
+        if (pend && *((volatile unsigned *)err) != 0u) break;
+    }
+    if (p0) y0 = qnan_of<T>();
+    if (p1) y1 = qnan_of<T>();
+}
+
 // Asynchronous global -> shared copies (no register staging); a thread's
 // copies complete in commit-group order.
 __device__ __forceinline__ void cp_async_4(void *smem, const void *gmem)

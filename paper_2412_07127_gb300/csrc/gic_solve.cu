@@ -73,25 +73,6 @@ __device__ __forceinline__ double warp_sum_partials(const double *partials, int 
     return warp_sum(s);
 }
 
-__global__ void k_fill_sentinel(int64_t n, double *a, double *b)
-{
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        a[i] = sentinel_d();
-        if (b) b[i] = sentinel_d();
-    }
-}
-
-// U values (transpose of L in U's CSR order) and reciprocal diagonal.
-template <typename TL>
-__global__ void k_transpose_vals(int64_t n, int64_t nnzL, const int32_t *tperm, const int32_t *Lrowptr, const TL *Lval,
-                                 TL *Uval, double *invd)
-{
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nnzL; q += stride) Uval[q] = Lval[tperm[q]];
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-        invd[i] = 1.0 / (double)Lval[Lrowptr[i + 1] - 1];
-}
-
 // ------------------------------------------------------------ SpTRSV
 // Schedule: the pattern's chunks (runs of consecutive row groups with
 // increasing levels; for hex elasticity the x-pencils) are dealt round-robin
@@ -444,33 +425,43 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_ltsolve(int32_t nchunks, const 
 }
 
 // ------------------------------------------------------------ pipelined SpTRSV
-// Same schedule and arithmetic as k_lsolve / k_ltsolve, for patterns whose
-// groups have at most WCOL external columns. A warp stages the metadata of
-// its whole chunk (segments of CHMAX groups) in shared memory once, then
-// keeps NST groups in flight: each group's columns, factor values, right-hand
-// side and reciprocal diagonal are copied global -> shared with cp.async
-// NST-1 groups before the group runs, and its dependency values are read
-// two groups before it runs (polled again only if still the sentinel). The
-// per-group critical path is then the arithmetic plus genuine waits.
+// Same schedule as k_lsolve / k_ltsolve, for patterns whose row groups have
+// at most 3 rows and at most WCOL external columns, in arithmetic type T
+// (double: the FP64 solve; float: the FP32 preconditioner apply, factor,
+// vectors and sums all in FP32). Per chunk a warp:
+//  * stages the metadata of the chunk (segments of CHMAX groups) once;
+//  * keeps NST groups in flight: columns, factor values, right-hand side and
+//    reciprocal diagonal copied global -> shared by cp.async NST-1 groups
+//    before the group runs;
+//  * splits each group's sum: the part over dependencies not produced by
+//    the previous group of the chunk is reduced one group early, as soon as
+//    those values are there (read two groups early, polled only if still
+//    the sentinel); when the previous group finishes, every lane adds its
+//    at most 3x3 contribution from registers and solves the dense in-group
+//    block. The in-chunk step (the x-neighbour for hex elasticity) then
+//    costs a few dependent FMAs instead of a warp reduction.
+// Arithmetic on this part: a dependent FP64 FMA is ~65 cycles and FP64
+// issue is ~1.6 lanes/clock/SM, so the reduction also keeps FP64
+// instructions few (three rows reduced in 6 adds, not 15).
 constexpr int CHMAX = 160;
 constexpr int NST = 4;
 
-template <typename TL, int GM>
+template <typename T, int GM>
 struct PStage {
-    TL v[GM][WCOL];                 // external values of each row of the group
-    TL lin[GM * (GM - 1) / 2 + 1];  // in-group entries
-    double rr[GM], iv[GM], aux[GM]; // r (forward: rhs; backward: PCG dot), 1/L_ii, y (backward)
+    double rd[GM];                 // r in FP64 (PCG dot of the backward sweep)
+    T v[GM][WCOL];                 // external values of each row of the group
+    T lin[GM * (GM - 1) / 2 + 1];  // in-group entries
+    T rr[GM], iv[GM], aux[GM];     // right-hand side (forward), 1/L_ii, y (backward)
     int32_t cols[WCOL];
 };
 
-template <typename TL, int GM>
+template <typename T, int GM>
 struct PWarp {
     int32_t s[CHMAX], G[CHMAX], b[CHMAX], m[CHMAX];
-    PStage<TL, GM> st[NST];
-    double ring[RING];
+    PStage<T, GM> st[NST];
 };
 
-// (t,u) of the q-th in-group entry, row-major lower triangle: t > u
+// (t,u) of the q-th entry of a strictly lower triangle stored row by row
 __device__ __forceinline__ void tri_index(int q, int &t, int &u)
 {
     t = 1;
@@ -478,9 +469,42 @@ __device__ __forceinline__ void tri_index(int q, int &t, int &u)
     u = q;
 }
 
-template <typename TL, int GM>
-__device__ __forceinline__ void fill_stage_L(PStage<TL, GM> &st, const PWarp<TL, GM> &W, int k, const int32_t *Lcol,
-                                             const TL *Lval, const double *r, const double *invd, int lane)
+// Warp sum of GM values, result in every lane. For three values the first
+// two butterfly levels exchange halves so each lane adds 2, then 1 value.
+template <typename T, int GM>
+__device__ __forceinline__ void warp_sum_n(T (&a)[GM], int lane)
+{
+    if (GM == 3) {
+        const bool hi16 = lane & 16;
+        // level 16: lanes < 16 keep {0,1}, lanes >= 16 keep {2, pad}
+        T k0 = hi16 ? a[2] : a[0], k1 = hi16 ? (T)0 : a[1];
+        T s0 = hi16 ? a[0] : a[2], s1 = hi16 ? a[1] : (T)0;
+        k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+        k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+        // level 8: bit3 = 0 keeps k0, bit3 = 1 keeps k1
+        const bool b8 = lane & 8;
+        T kk = b8 ? k1 : k0, ss = b8 ? k0 : k1;
+        kk += __shfl_xor_sync(0xffffffffu, ss, 8);
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) kk += __shfl_xor_sync(0xffffffffu, kk, o);
+        // totals: lanes 0-7 row 0, 8-15 row 1, 16-23 row 2
+        a[0] = __shfl_sync(0xffffffffu, kk, 0);
+        a[1] = __shfl_sync(0xffffffffu, kk, 8);
+        a[2] = __shfl_sync(0xffffffffu, kk, 16);
+    } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int t = 0; t < GM; ++t) a[t] += __shfl_xor_sync(0xffffffffu, a[t], o);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T pick3(int idx, T a, T b, T c) { return idx == 0 ? a : (idx == 1 ? b : c); }
+
+template <typename T, int GM>
+__device__ __forceinline__ void fill_stage_L(PStage<T, GM> &st, const PWarp<T, GM> &W, int k, const int32_t *Lcol,
+                                             const T *Lval, const T *r, const T *invd, int lane)
 {
     const int32_t s = W.s[k], G = W.G[k], b0 = W.b[k], m = W.m[k];
     if (lane < m) cp_async_4(&st.cols[lane], Lcol + b0 + lane);
@@ -499,31 +523,65 @@ __device__ __forceinline__ void fill_stage_L(PStage<TL, GM> &st, const PWarp<TL,
         cp_async_t(&st.lin[lane], Lval + b0 + t * (m + 1) + (t * (t - 1)) / 2 + m + u);
     }
     if (lane < G) {
-        cp_async_8(&st.rr[lane], r + s + lane);
-        cp_async_8(&st.iv[lane], invd + s + lane);
+        cp_async_t(&st.rr[lane], r + s + lane);
+        cp_async_t(&st.iv[lane], invd + s + lane);
     }
 }
 
-template <typename TL, int GM>
+// early read of the dependencies of stage-resident group k that lie below
+// `ps` (everything not produced by the group before it)
+template <typename T, int GM>
+__device__ __forceinline__ void early_L(const PStage<T, GM> &st, int32_t m, int32_t ps, const T *y, int lane, T &d0, T &d1)
+{
+    const int32_t j0 = (lane < m) ? st.cols[lane] : -1, j1 = (lane + 32 < m) ? st.cols[lane + 32] : -1;
+    d0 = (j0 >= 0 && j0 < ps) ? ld_relaxed(y + j0) : (T)0;
+    d1 = (j1 >= 0 && j1 < ps) ? ld_relaxed(y + j1) : (T)0;
+}
+
+// the part of group k's sums over dependencies below ps
+template <typename T, int GM>
+__device__ __forceinline__ void ext_sum_L(T (&S)[GM], const PStage<T, GM> &st, int32_t m, int G, int32_t ps,
+                                          const T *y, T d0, T d1, unsigned *err, int poll, int lane)
+{
+    int32_t j0 = (lane < m) ? st.cols[lane] : -1, j1 = (lane + 32 < m) ? st.cols[lane + 32] : -1;
+    if (j0 >= ps) j0 = -1;
+    if (j1 >= ps) j1 = -1;
+    wait_pair<true, T>(y, j0, j1, d0, d1, err, poll);
+    if (j0 < 0) d0 = (T)0;
+    if (j1 < 0) d1 = (T)0;
+#pragma unroll
+    for (int t = 0; t < GM; ++t) {
+        const T a0 = (t < G && j0 >= 0) ? st.v[t][lane] : (T)0;
+        const T a1 = (t < G && j1 >= 0) ? st.v[t][lane + 32] : (T)0;
+        S[t] = fma(a1, d1, a0 * d0);
+    }
+    warp_sum_n<T, GM>(S, lane);
+}
+
+// Forward: y_i = (r_i - sum_{j<i} L_ij y_j) / L_ii. y must hold the sentinel.
+template <typename T, int GM>
 __global__ void __launch_bounds__(SOLVE_BLOCK) k_lsolve_p(int32_t nchunks, const int32_t *__restrict__ ord,
                                                           const int32_t *__restrict__ chunk_grp,
                                                           const int32_t *__restrict__ grp,
                                                           const int32_t *__restrict__ Lrowptr,
                                                           const int32_t *__restrict__ Lcol,
-                                                          const TL *__restrict__ Lval, const double *__restrict__ invd,
-                                                          const double *__restrict__ r, double *y, unsigned *err,
-                                                          int poll, const Scalars *sc)
+                                                          const T *__restrict__ Lval, const T *__restrict__ invd,
+                                                          const T *__restrict__ r, T *y, unsigned *err, int poll,
+                                                          const Scalars *sc)
 {
     if (sc && sc->done) return;
     extern __shared__ __align__(16) unsigned char pw_raw[];
     const int lane = threadIdx.x & 31;
-    PWarp<TL, GM> &W = reinterpret_cast<PWarp<TL, GM> *>(pw_raw)[threadIdx.x >> 5];
+    PWarp<T, GM> &W = reinterpret_cast<PWarp<T, GM> *>(pw_raw)[threadIdx.x >> 5];
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t pos = w; pos < nchunks; pos += nw) {
         const int32_t c = ord[pos];
         const int32_t g0 = chunk_grp[c], g1 = chunk_grp[c + 1];
-        const int32_t row0 = grp[g0];
+        T yprev[GM];
+#pragma unroll
+        for (int t = 0; t < GM; ++t) yprev[t] = (T)0;
+        int32_t prev_s = INT_MAX; // rows of the previous group: [prev_s, prev_s + G)
         for (int32_t seg = g0; seg < g1; seg += CHMAX) {
             const int cnt = min(CHMAX, g1 - seg);
             for (int k = lane; k < cnt; k += 32) {
@@ -537,78 +595,58 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_lsolve_p(int32_t nchunks, const
             __syncwarp();
 #pragma unroll
             for (int d = 0; d < NST; ++d) {
-                if (d < cnt) fill_stage_L<TL, GM>(W.st[d], W, d, Lcol, Lval, r, invd, lane);
+                if (d < cnt) fill_stage_L<T, GM>(W.st[d], W, d, Lcol, Lval, r, invd, lane);
                 cp_async_commit();
             }
             cp_async_wait<NST - 2>();
             __syncwarp();
-            // dependency values of the next two groups, read early
-            double dA0 = 0.0, dA1 = 0.0, dB0 = 0.0, dB1 = 0.0;
+            T Sx[GM], dB0 = 0, dB1 = 0;
             {
-                const int32_t m0 = W.m[0];
-                const int32_t ja = (lane < m0) ? W.st[0].cols[lane] : -1, jb = (lane + 32 < m0) ? W.st[0].cols[lane + 32] : -1;
-                dA0 = (ja >= 0) ? ld_relaxed(y + ja) : 0.0;
-                dA1 = (jb >= 0) ? ld_relaxed(y + jb) : 0.0;
-                if (cnt > 1) {
-                    const int32_t m1 = W.m[1];
-                    const int32_t jc = (lane < m1) ? W.st[1].cols[lane] : -1, jd = (lane + 32 < m1) ? W.st[1].cols[lane + 32] : -1;
-                    dB0 = (jc >= 0) ? ld_relaxed(y + jc) : 0.0;
-                    dB1 = (jd >= 0) ? ld_relaxed(y + jd) : 0.0;
-                }
+                T d0, d1;
+                early_L<T, GM>(W.st[0], W.m[0], prev_s, y, lane, d0, d1);
+                ext_sum_L<T, GM>(Sx, W.st[0], W.m[0], W.G[0], prev_s, y, d0, d1, err, poll, lane);
+                if (cnt > 1) early_L<T, GM>(W.st[1], W.m[1], W.s[0], y, lane, dB0, dB1);
             }
             for (int k = 0; k < cnt; ++k) {
-                PStage<TL, GM> &st = W.st[k % NST];
+                const PStage<T, GM> &st = W.st[k % NST];
                 const int32_t s = W.s[k], m = W.m[k];
                 const int G = W.G[k];
-                const int32_t lo = max(row0, s - RING);
-                const int32_t j0 = (lane < m) ? st.cols[lane] : -1;
-                const int32_t j1 = (lane + 32 < m) ? st.cols[lane + 32] : -1;
-                double y0 = (j0 >= lo && j0 < s) ? W.ring[j0 & (RING - 1)] : dA0;
-                double y1 = (j1 >= lo && j1 < s) ? W.ring[j1 & (RING - 1)] : dA1;
-                if (j0 < 0) y0 = 0.0;
-                if (j1 < 0) y1 = 0.0;
-                wait_deps<true>(y, j0, j1, y0, y1, err, poll);
-                double acc[GM];
+                // contribution of the previous group (its rows are the
+                // largest external columns) and the dense in-group solve
+                T tot[GM];
 #pragma unroll
-                for (int t = 0; t < GM; ++t) {
-                    const double a0 = (t < G && j0 >= 0) ? (double)st.v[t][lane] : 0.0;
-                    const double a1 = (t < G && j1 >= 0) ? (double)st.v[t][lane + 32] : 0.0;
-                    acc[t] = fma(a1, y1, a0 * y0);
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1)
+                for (int t = 0; t < GM; ++t) tot[t] = Sx[t];
+                for (int e = m - 1; e >= 0 && e >= m - GM; --e) {
+                    const int32_t j = st.cols[e];
+                    if (j < prev_s) break;
+                    const T yp = pick3<T>(j - prev_s, yprev[0], yprev[GM > 1 ? 1 : 0], yprev[GM > 2 ? 2 : 0]);
 #pragma unroll
                     for (int t = 0; t < GM; ++t)
-                        if (t < G) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
-                if (lane == 0) {
-                    double yl[GM];
+                        if (t < G) tot[t] = fma(st.v[t][e], yp, tot[t]);
+                }
+                T yl[GM];
 #pragma unroll
-                    for (int t = 0; t < GM; ++t) {
-                        if (t < G) {
-                            double v = st.rr[t] - acc[t];
+                for (int t = 0; t < GM; ++t) {
+                    T v = st.rr[t] - tot[t];
 #pragma unroll
-                            for (int u = 0; u < t; ++u) v = fma(-(double)st.lin[t * (t - 1) / 2 + u], yl[u], v);
-                            yl[t] = v * st.iv[t];
-                            st_relaxed(y + s + t, yl[t]);
-                            W.ring[(s + t) & (RING - 1)] = yl[t];
-                        }
-                    }
+                    for (int u = 0; u < t; ++u) v = fma(-st.lin[t * (t - 1) / 2 + u], yl[u], v);
+                    yl[t] = (t < G) ? v * st.iv[t] : (T)0;
+                }
+                if (lane < G) st_relaxed(y + s + lane, pick3<T>(lane, yl[0], yl[GM > 1 ? 1 : 0], yl[GM > 2 ? 2 : 0]));
+#pragma unroll
+                for (int t = 0; t < GM; ++t) yprev[t] = yl[t];
+                prev_s = s;
+                // the part of the next group's sums not involving this group
+                if (k + 1 < cnt) {
+                    const int kn = k + 1;
+                    ext_sum_L<T, GM>(Sx, W.st[kn % NST], W.m[kn], W.G[kn], s, y, dB0, dB1, err, poll, lane);
                 }
                 __syncwarp();
-                // refill this stage with group k + NST, then ready group k + 2
-                if (k + NST < cnt) fill_stage_L<TL, GM>(st, W, k + NST, Lcol, Lval, r, invd, lane);
+                if (k + NST < cnt) fill_stage_L<T, GM>(W.st[k % NST], W, k + NST, Lcol, Lval, r, invd, lane);
                 cp_async_commit();
                 cp_async_wait<NST - 2>();
                 __syncwarp();
-                dA0 = dB0;
-                dA1 = dB1;
-                if (k + 2 < cnt) {
-                    const PStage<TL, GM> &s2 = W.st[(k + 2) % NST];
-                    const int32_t m2 = W.m[k + 2];
-                    const int32_t jc = (lane < m2) ? s2.cols[lane] : -1, jd = (lane + 32 < m2) ? s2.cols[lane + 32] : -1;
-                    dB0 = (jc >= 0) ? ld_relaxed(y + jc) : 0.0;
-                    dB1 = (jd >= 0) ? ld_relaxed(y + jd) : 0.0;
-                }
+                if (k + 2 < cnt) early_L<T, GM>(W.st[(k + 2) % NST], W.m[k + 2], W.s[k + 1], y, lane, dB0, dB1);
             }
             cp_async_wait<0>();
             __syncwarp();
@@ -616,10 +654,9 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_lsolve_p(int32_t nchunks, const
     }
 }
 
-template <typename TL, bool PCG, int GM>
-__device__ __forceinline__ void fill_stage_U(PStage<TL, GM> &st, const PWarp<TL, GM> &W, int k, const int32_t *Ucol,
-                                             const TL *Uval, const double *r, const double *invd, const double *y,
-                                             int lane)
+template <typename T, bool PCG, int GM>
+__device__ __forceinline__ void fill_stage_U(PStage<T, GM> &st, const PWarp<T, GM> &W, int k, const int32_t *Ucol,
+                                             const T *Uval, const double *rd, const T *invd, const T *y, int lane)
 {
     const int32_t s = W.s[k], G = W.G[k], be = W.b[k], mu = W.m[k];
     if (lane < mu) cp_async_4(&st.cols[lane], Ucol + be + 1 + lane);
@@ -640,33 +677,70 @@ __device__ __forceinline__ void fill_stage_U(PStage<TL, GM> &st, const PWarp<TL,
         cp_async_t(&st.lin[lane], Uval + base + (uu - t));
     }
     if (lane < G) {
-        if (PCG) cp_async_8(&st.rr[lane], r + s + lane);
-        cp_async_8(&st.iv[lane], invd + s + lane);
-        cp_async_8(&st.aux[lane], y + s + lane);
+        if (PCG) cp_async_8(&st.rd[lane], rd + s + lane);
+        cp_async_t(&st.iv[lane], invd + s + lane);
+        cp_async_t(&st.aux[lane], y + s + lane);
     }
 }
 
-template <typename TL, bool PCG, int GM>
+// dependencies of group k above `pe` (everything not produced by the group
+// processed before it, which sits just above)
+template <typename T, int GM>
+__device__ __forceinline__ void early_U(const PStage<T, GM> &st, int32_t mu, int32_t pe, const T *z, int lane, T &d0, T &d1)
+{
+    const int32_t j0 = (lane < mu) ? st.cols[lane] : -1, j1 = (lane + 32 < mu) ? st.cols[lane + 32] : -1;
+    d0 = (j0 >= 0 && j0 > pe) ? ld_relaxed(z + j0) : (T)0;
+    d1 = (j1 >= 0 && j1 > pe) ? ld_relaxed(z + j1) : (T)0;
+}
+
+template <typename T, int GM>
+__device__ __forceinline__ void ext_sum_U(T (&S)[GM], const PStage<T, GM> &st, int32_t mu, int G, int32_t pe,
+                                          const T *z, T d0, T d1, unsigned *err, int poll, int lane)
+{
+    int32_t j0 = (lane < mu) ? st.cols[lane] : -1, j1 = (lane + 32 < mu) ? st.cols[lane + 32] : -1;
+    if (j0 >= 0 && j0 <= pe) j0 = -1;
+    if (j1 >= 0 && j1 <= pe) j1 = -1;
+    wait_pair<false, T>(z, j0, j1, d0, d1, err, poll);
+    if (j0 < 0) d0 = (T)0;
+    if (j1 < 0) d1 = (T)0;
+#pragma unroll
+    for (int t = 0; t < GM; ++t) {
+        const T a0 = (t < G && j0 >= 0) ? st.v[t][lane] : (T)0;
+        const T a1 = (t < G && j1 >= 0) ? st.v[t][lane + 32] : (T)0;
+        S[t] = fma(a1, d1, a0 * d0);
+    }
+    warp_sum_n<T, GM>(S, lane);
+}
+
+// Backward: z_i = (y_i - sum_{j>i} L_ji z_j) / L_ii on U = L^T. z must hold
+// the sentinel. Chunks run in the backward order and each one from its last
+// group down. With PCG the kernel also resets y to the sentinel (for the
+// next forward solve) and forms r^T z in FP64, then beta = r_k^T z_k /
+// r_{k-1}^T z_{k-1} (Algorithm 1 line 13) in the last warp to finish.
+template <typename T, bool PCG, int GM>
 __global__ void __launch_bounds__(SOLVE_BLOCK) k_ltsolve_p(int32_t nchunks, const int32_t *__restrict__ ord,
                                                            const int32_t *__restrict__ chunk_grp,
                                                            const int32_t *__restrict__ grp,
                                                            const int32_t *__restrict__ Urowptr,
                                                            const int32_t *__restrict__ Ucol,
-                                                           const TL *__restrict__ Uval, const double *__restrict__ invd,
-                                                           double *y, double *z, const double *__restrict__ r,
+                                                           const T *__restrict__ Uval, const T *__restrict__ invd,
+                                                           T *y, T *z, const double *__restrict__ rd,
                                                            double *partials, unsigned *err, int poll, Scalars *sc)
 {
     if (sc && sc->done) return;
     extern __shared__ __align__(16) unsigned char pw_raw[];
     const int lane = threadIdx.x & 31;
-    PWarp<TL, GM> &W = reinterpret_cast<PWarp<TL, GM> *>(pw_raw)[threadIdx.x >> 5];
+    PWarp<T, GM> &W = reinterpret_cast<PWarp<T, GM> *>(pw_raw)[threadIdx.x >> 5];
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double dot = 0.0;
     for (int64_t pos = w; pos < nchunks; pos += nw) {
         const int32_t c = ord[pos];
         const int32_t g0 = chunk_grp[c], g1 = chunk_grp[c + 1];
-        const int32_t rowEnd = grp[g1];
+        T zprev[GM];
+#pragma unroll
+        for (int t = 0; t < GM; ++t) zprev[t] = (T)0;
+        int32_t prev_s = INT_MIN, prev_e = INT_MIN; // rows of the group processed before
         for (int32_t segEnd = g1 - 1; segEnd >= g0; segEnd -= CHMAX) {
             const int cnt = min(CHMAX, segEnd - g0 + 1);
             for (int k = lane; k < cnt; k += 32) { // k-th group of the segment, from its end
@@ -682,88 +756,74 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_ltsolve_p(int32_t nchunks, cons
             __syncwarp();
 #pragma unroll
             for (int d = 0; d < NST; ++d) {
-                if (d < cnt) fill_stage_U<TL, PCG, GM>(W.st[d], W, d, Ucol, Uval, r, invd, y, lane);
+                if (d < cnt) fill_stage_U<T, PCG, GM>(W.st[d], W, d, Ucol, Uval, rd, invd, y, lane);
                 cp_async_commit();
             }
             cp_async_wait<NST - 2>();
             __syncwarp();
-            double dA0 = 0.0, dA1 = 0.0, dB0 = 0.0, dB1 = 0.0;
+            T Sx[GM], dB0 = 0, dB1 = 0;
             {
-                const int32_t m0 = W.m[0];
-                const int32_t ja = (lane < m0) ? W.st[0].cols[lane] : -1, jb = (lane + 32 < m0) ? W.st[0].cols[lane + 32] : -1;
-                dA0 = (ja >= 0) ? ld_relaxed(z + ja) : 0.0;
-                dA1 = (jb >= 0) ? ld_relaxed(z + jb) : 0.0;
-                if (cnt > 1) {
-                    const int32_t m1 = W.m[1];
-                    const int32_t jc = (lane < m1) ? W.st[1].cols[lane] : -1, jd = (lane + 32 < m1) ? W.st[1].cols[lane + 32] : -1;
-                    dB0 = (jc >= 0) ? ld_relaxed(z + jc) : 0.0;
-                    dB1 = (jd >= 0) ? ld_relaxed(z + jd) : 0.0;
-                }
+                T d0, d1;
+                early_U<T, GM>(W.st[0], W.m[0], prev_e, z, lane, d0, d1);
+                ext_sum_U<T, GM>(Sx, W.st[0], W.m[0], W.G[0], prev_e, z, d0, d1, err, poll, lane);
+                if (cnt > 1) early_U<T, GM>(W.st[1], W.m[1], W.s[0] + W.G[0] - 1, z, lane, dB0, dB1);
             }
             for (int k = 0; k < cnt; ++k) {
-                PStage<TL, GM> &st = W.st[k % NST];
+                const PStage<T, GM> &st = W.st[k % NST];
                 const int32_t s = W.s[k], mu = W.m[k];
                 const int G = W.G[k];
                 const int32_t e = s + G - 1;
-                const int32_t hi = min(rowEnd, e + 1 + RING);
-                const int32_t j0 = (lane < mu) ? st.cols[lane] : -1;
-                const int32_t j1 = (lane + 32 < mu) ? st.cols[lane + 32] : -1;
-                double z0 = (j0 > e && j0 < hi) ? W.ring[j0 & (RING - 1)] : dA0;
-                double z1 = (j1 > e && j1 < hi) ? W.ring[j1 & (RING - 1)] : dA1;
-                if (j0 < 0) z0 = 0.0;
-                if (j1 < 0) z1 = 0.0;
-                wait_deps<false>(z, j0, j1, z0, z1, err, poll);
-                double acc[GM];
+                T tot[GM];
 #pragma unroll
-                for (int t = 0; t < GM; ++t) {
-                    const double a0 = (t < G && j0 >= 0) ? (double)st.v[t][lane] : 0.0;
-                    const double a1 = (t < G && j1 >= 0) ? (double)st.v[t][lane + 32] : 0.0;
-                    acc[t] = fma(a1, z1, a0 * z0);
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1)
+                for (int t = 0; t < GM; ++t) tot[t] = Sx[t];
+                // the previous group's rows are the smallest external columns
+                for (int q = 0; q < mu && q < GM; ++q) {
+                    const int32_t j = st.cols[q];
+                    if (j > prev_e) break;
+                    const T zp = pick3<T>(j - prev_s, zprev[0], zprev[GM > 1 ? 1 : 0], zprev[GM > 2 ? 2 : 0]);
 #pragma unroll
                     for (int t = 0; t < GM; ++t)
-                        if (t < G) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
-                if (lane == 0) {
-                    double zl[GM];
+                        if (t < G) tot[t] = fma(st.v[t][q], zp, tot[t]);
+                }
+                T zl[GM];
 #pragma unroll
-                    for (int t = GM - 1; t >= 0; --t) {
-                        if (t < G) {
-                            double v = st.aux[t] - acc[t];
+                for (int t = GM - 1; t >= 0; --t) {
+                    T v = st.aux[t] - tot[t];
 #pragma unroll
-                            for (int u = t + 1; u < GM; ++u)
-                                if (u < G) v = fma(-(double)st.lin[u * (u - 1) / 2 + t], zl[u], v);
-                            zl[t] = v * st.iv[t];
-                            st_relaxed(z + s + t, zl[t]);
-                            W.ring[(s + t) & (RING - 1)] = zl[t];
-                            if (PCG) {
-                                y[s + t] = sentinel_d();
-                                dot = fma(st.rr[t], zl[t], dot);
-                            }
-                        }
+                    for (int u = t + 1; u < GM; ++u)
+                        if (u < G) v = fma(-st.lin[u * (u - 1) / 2 + t], zl[u], v);
+                    zl[t] = (t < G) ? v * st.iv[t] : (T)0;
+                }
+                if (lane < G) {
+                    const T zv = pick3<T>(lane, zl[0], zl[GM > 1 ? 1 : 0], zl[GM > 2 ? 2 : 0]);
+                    st_relaxed(z + s + lane, zv);
+                    if (PCG) {
+                        y[s + lane] = sentinel_of<T>();
+                        dot = fma(st.rd[lane], (double)zv, dot);
                     }
                 }
+#pragma unroll
+                for (int t = 0; t < GM; ++t) zprev[t] = zl[t];
+                prev_s = s;
+                prev_e = e;
+                if (k + 1 < cnt) {
+                    const int kn = k + 1;
+                    ext_sum_U<T, GM>(Sx, W.st[kn % NST], W.m[kn], W.G[kn], e, z, dB0, dB1, err, poll, lane);
+                }
                 __syncwarp();
-                if (k + NST < cnt) fill_stage_U<TL, PCG, GM>(st, W, k + NST, Ucol, Uval, r, invd, y, lane);
+                if (k + NST < cnt) fill_stage_U<T, PCG, GM>(W.st[k % NST], W, k + NST, Ucol, Uval, rd, invd, y, lane);
                 cp_async_commit();
                 cp_async_wait<NST - 2>();
                 __syncwarp();
-                dA0 = dB0;
-                dA1 = dB1;
-                if (k + 2 < cnt) {
-                    const PStage<TL, GM> &s2 = W.st[(k + 2) % NST];
-                    const int32_t m2 = W.m[k + 2];
-                    const int32_t jc = (lane < m2) ? s2.cols[lane] : -1, jd = (lane + 32 < m2) ? s2.cols[lane + 32] : -1;
-                    dB0 = (jc >= 0) ? ld_relaxed(z + jc) : 0.0;
-                    dB1 = (jd >= 0) ? ld_relaxed(z + jd) : 0.0;
-                }
+                if (k + 2 < cnt)
+                    early_U<T, GM>(W.st[(k + 2) % NST], W.m[k + 2], W.s[k + 1] + W.G[k + 1] - 1, z, lane, dB0, dB1);
             }
             cp_async_wait<0>();
             __syncwarp();
         }
     }
     if (PCG) {
+        dot = warp_sum(dot); // lanes < G held the products
         if (lane == 0) partials[w] = dot;
         __syncwarp();
         unsigned last = 0;
@@ -982,12 +1042,11 @@ __global__ void __launch_bounds__(SPMV_BLOCK) k_spmv_sell(int64_t n, int64_t nsl
     }
 }
 
-// p = z + beta p (p = z on the first step); z back to the sentinel.
-// With IDENT the preconditioner is the identity: z is r itself, and r^T z is
-// formed here (the solves are skipped).
-template <bool IDENT>
-__global__ void __launch_bounds__(VEC_BLOCK) k_update_p(int64_t n, double *z, double *p, const double *r,
-                                                        double *partials, Scalars *sc)
+// p = z + beta p (p = z on the first step); z back to the sentinel (ZT:
+// float for the FP32 preconditioner vectors). With IDENT the preconditioner
+// is the identity and z is r itself.
+template <bool IDENT, typename ZT>
+__global__ void __launch_bounds__(VEC_BLOCK) k_update_p(int64_t n, ZT *z, double *p, const double *r, Scalars *sc)
 {
     if (sc->done) return;
     const int first = (sc->iter == 0);
@@ -997,9 +1056,9 @@ __global__ void __launch_bounds__(VEC_BLOCK) k_update_p(int64_t n, double *z, do
             const double zi = r[i];
             p[i] = first ? zi : fma(beta, p[i], zi);
         } else {
-            const double zi = z[i];
+            const double zi = (double)z[i];
             p[i] = first ? zi : fma(beta, p[i], zi);
-            z[i] = sentinel_d();
+            z[i] = sentinel_of<ZT>();
         }
     }
 }
@@ -1032,8 +1091,9 @@ __global__ void __launch_bounds__(VEC_BLOCK) k_ident_rz(int64_t n, const double 
 }
 
 // x += alpha p, r -= alpha w, rr = r^T r; iteration count and stop test.
+// r32 (nullable) receives float(r) for the FP32 preconditioner.
 __global__ void __launch_bounds__(VEC_BLOCK) k_update_xr(int64_t n, double *x, double *r, const double *p,
-                                                         const double *w, double *partials, Scalars *sc)
+                                                         const double *w, float *r32, double *partials, Scalars *sc)
 {
     if (sc->done) return;
     __shared__ double sh[VEC_BLOCK / 32];
@@ -1043,6 +1103,7 @@ __global__ void __launch_bounds__(VEC_BLOCK) k_update_xr(int64_t n, double *x, d
         x[i] = fma(alpha, p[i], x[i]);
         const double ri = fma(-alpha, w[i], r[i]);
         r[i] = ri;
+        if (r32) r32[i] = (float)ri;
         d = fma(ri, ri, d);
     }
     double s = block_sum(d, sh);
@@ -1084,21 +1145,68 @@ __global__ void k_convert_f64_f32(int64_t cnt, const double *src, float *dst)
         dst[i] = (float)src[i];
 }
 
+__global__ void k_convert_f32_f64(int64_t cnt, const float *src, double *dst)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (double)src[i];
+}
+
+template <typename T>
+__global__ void k_fill_sentinel_t(int64_t n, T *a, T *b)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        a[i] = sentinel_of<T>();
+        if (b) b[i] = sentinel_of<T>();
+    }
+}
+
+// U values (transpose of L in U's CSR order) and reciprocal diagonal (TI).
+template <typename TL, typename TI>
+__global__ void k_factor_setup(int64_t n, int64_t nnzL, const int32_t *tperm, const int32_t *Lrowptr, const TL *Lval,
+                               TL *Uval, TI *invd)
+{
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nnzL; q += stride) Uval[q] = Lval[tperm[q]];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        invd[i] = (TI)(1.0 / (double)Lval[Lrowptr[i + 1] - 1]);
+}
+
 // ------------------------------------------------------------ host side
 int launch_persistent(gic_handle *h, const void *fn, int block, size_t smem, int64_t warps_needed, void **args);
 
 static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
+// How the solves of one factor run: generic (any pattern, FP64 vectors and
+// sums) or pipelined (groups of <= 3 rows, <= WCOL external columns), each
+// with an FP64 or an FP32 factor. The pipelined FP32 mode keeps its vectors
+// and sums in FP32 too.
+enum SolveMode { MODE_GEN64, MODE_GEN32, MODE_P64, MODE_P32, MODE_IDENT };
+
 struct SolveWs {
     void *Uval;
-    double *invd, *r, *y, *z, *p, *w;
+    double *invd;                 // generic modes and P64
+    float *invd32, *r32, *y32, *z32; // P32
+    double *r, *y, *z, *p, *w;
     double *partials;
     double *sval; // A's values in the pattern's SELL-32 layout
     Scalars *sc;
     size_t bytes;
 };
 
-static SolveWs carve(const Pattern &P, int l_dtype, void *ws)
+static bool pipelined_fits(const Pattern &P)
+{
+    return P.max_group <= 3 && P.max_ext_lower <= WCOL && P.max_ext_upper <= WCOL;
+}
+
+static SolveMode solve_mode(const gic_handle *h, const Pattern &P, int l_dtype)
+{
+    if (l_dtype == GIC_IDENTITY) return MODE_IDENT;
+    const bool pipe = h->tune_pipeline && pipelined_fits(P);
+    if (l_dtype == GIC_F32) return pipe ? MODE_P32 : MODE_GEN32;
+    return pipe ? MODE_P64 : MODE_GEN64;
+}
+
+static SolveWs carve(const Pattern &P, int l_dtype, bool p32, void *ws)
 {
     SolveWs o = {};
     char *c = (char *)ws;
@@ -1108,6 +1216,10 @@ static SolveWs carve(const Pattern &P, int l_dtype, void *ws)
     o.partials = (double *)(c + off); off += align_up(sizeof(double) * 2 * MAX_PARTIALS);
     o.Uval = c + off; off += (l_dtype == GIC_IDENTITY) ? 0 : align_up(es * (size_t)P.nnzL);
     o.invd = (double *)(c + off); off += (l_dtype == GIC_IDENTITY) ? 0 : align_up(8 * (size_t)P.n);
+    if (p32) {
+        float **fv[4] = {&o.invd32, &o.r32, &o.y32, &o.z32};
+        for (int k = 0; k < 4; ++k) { *fv[k] = (float *)(c + off); off += align_up(4 * (size_t)P.n); }
+    }
     o.sval = (double *)(c + off); off += align_up(8 * (size_t)P.sell_nnz);
     double **vecs[5] = {&o.r, &o.y, &o.z, &o.p, &o.w};
     for (int k = 0; k < 5; ++k) { *vecs[k] = (double *)(c + off); off += align_up(8 * (size_t)P.n); }
@@ -1121,7 +1233,7 @@ size_t pcg_ws_bytes(int64_t n, int64_t nnzL, int64_t sell_nnz, int l_dtype)
     P.n = n;
     P.nnzL = nnzL;
     P.sell_nnz = sell_nnz;
-    return carve(P, l_dtype, nullptr).bytes;
+    return carve(P, l_dtype, l_dtype == GIC_F32, nullptr).bytes;
 }
 
 static unsigned vec_grid(gic_handle *h, int64_t n, int block)
@@ -1153,6 +1265,7 @@ static int64_t solve_warps(gic_handle *h, const Pattern &P)
     return need;
 }
 
+// ---- generic kernels (FP64 vectors)
 template <typename TL, int GM>
 static int launch_lsolve_g(gic_handle *h, const Pattern &P, const TL *Lval, const double *invd, const double *r,
                            double *y, Scalars *sc)
@@ -1163,46 +1276,18 @@ static int launch_lsolve_g(gic_handle *h, const Pattern &P, const TL *Lval, cons
     int poll = h->tune_poll;
     void *args[] = {&nc, &ord, &cg, &g, &lr, &lc, &Lval, &invd, &r, &y, &er, &poll, &sc};
     const size_t smem = sizeof(WarpStage) * (SOLVE_BLOCK / 32);
-    static bool attr_done[2][64] = {};
-    bool &ad = attr_done[sizeof(TL) == 4][h->device & 63];
-    if (!ad) {
+    static bool ad[64] = {};
+    if (!ad[h->device & 63]) {
         GIC_CUDA_TRY(cudaFuncSetAttribute(k_lsolve<TL, GM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        ad = true;
+        ad[h->device & 63] = true;
     }
     return launch_persistent(h, (const void *)k_lsolve<TL, GM>, SOLVE_BLOCK, smem, solve_warps(h, P), args);
 }
 
-template <typename TL, int GM>
-static int launch_lsolve_pg(gic_handle *h, const Pattern &P, const TL *Lval, const double *invd, const double *r,
-                            double *y, Scalars *sc)
-{
-    int32_t nc = P.nchunks;
-    const int32_t *ord = P.ord_f, *cg = P.chunk_grp, *g = P.grp, *lr = P.Lrowptr, *lc = P.Lcol;
-    unsigned *er = h->dev_err;
-    int poll = h->tune_poll;
-    void *args[] = {&nc, &ord, &cg, &g, &lr, &lc, &Lval, &invd, &r, &y, &er, &poll, &sc};
-    const size_t smem = sizeof(PWarp<TL, GM>) * (SOLVE_BLOCK / 32);
-    static bool ad[64] = {};
-    if (!ad[h->device & 63]) {
-        GIC_CUDA_TRY(cudaFuncSetAttribute(k_lsolve_p<TL, GM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        ad[h->device & 63] = true;
-    }
-    return launch_persistent(h, (const void *)k_lsolve_p<TL, GM>, SOLVE_BLOCK, smem, solve_warps(h, P), args);
-}
-
-static bool pipelined_ok(gic_handle *h, const Pattern &P)
-{
-    return h->tune_pipeline && P.max_group <= 3 && P.max_ext_lower <= WCOL && P.max_ext_upper <= WCOL;
-}
-
 template <typename TL>
-static int launch_lsolve(gic_handle *h, const Pattern &P, const TL *Lval, const double *invd, const double *r,
-                         double *y, Scalars *sc)
+static int launch_lsolve_gen(gic_handle *h, const Pattern &P, const TL *Lval, const double *invd, const double *r,
+                             double *y, Scalars *sc)
 {
-    if (pipelined_ok(h, P)) {
-        if (P.max_group <= 1) return launch_lsolve_pg<TL, 1>(h, P, Lval, invd, r, y, sc);
-        return launch_lsolve_pg<TL, 3>(h, P, Lval, invd, r, y, sc);
-    }
     if (P.max_group <= 1) return launch_lsolve_g<TL, 1>(h, P, Lval, invd, r, y, sc);
     if (P.max_group <= 3) return launch_lsolve_g<TL, 3>(h, P, Lval, invd, r, y, sc);
     return launch_lsolve_g<TL, GMAX>(h, P, Lval, invd, r, y, sc);
@@ -1220,56 +1305,94 @@ static int launch_ltsolve_g(gic_handle *h, const Pattern &P, const TL *Uval, con
     int64_t need = solve_warps(h, P);
     if (PCG && need > MAX_PARTIALS) need = MAX_PARTIALS; // grid warps <= partial slots
     const size_t smem = sizeof(WarpStage) * (SOLVE_BLOCK / 32);
-    static bool attr_done[2][2][64] = {};
-    bool &ad = attr_done[sizeof(TL) == 4][PCG][h->device & 63];
-    if (!ad) {
+    static bool ad[64] = {};
+    if (!ad[h->device & 63]) {
         GIC_CUDA_TRY(cudaFuncSetAttribute(k_ltsolve<TL, PCG, GM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
-        ad = true;
+        ad[h->device & 63] = true;
     }
     return launch_persistent(h, (const void *)k_ltsolve<TL, PCG, GM>, SOLVE_BLOCK, smem, need, args);
 }
 
-template <typename TL, bool PCG, int GM>
-static int launch_ltsolve_pg(gic_handle *h, const Pattern &P, const TL *Uval, const double *invd, double *y, double *z,
-                             const double *r, double *partials, Scalars *sc)
-{
-    int32_t nc = P.nchunks;
-    const int32_t *ord = P.ord_b, *cg = P.chunk_grp, *g = P.grp, *ur = P.Urowptr, *uc = P.Ucol;
-    unsigned *er = h->dev_err;
-    int poll = h->tune_poll;
-    void *args[] = {&nc, &ord, &cg, &g, &ur, &uc, &Uval, &invd, &y, &z, &r, &partials, &er, &poll, &sc};
-    int64_t need = solve_warps(h, P);
-    if (PCG && need > MAX_PARTIALS) need = MAX_PARTIALS;
-    const size_t smem = sizeof(PWarp<TL, GM>) * (SOLVE_BLOCK / 32);
-    static bool ad[64] = {};
-    if (!ad[h->device & 63]) {
-        GIC_CUDA_TRY(cudaFuncSetAttribute(k_ltsolve_p<TL, PCG, GM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-        ad[h->device & 63] = true;
-    }
-    return launch_persistent(h, (const void *)k_ltsolve_p<TL, PCG, GM>, SOLVE_BLOCK, smem, need, args);
-}
-
 template <typename TL, bool PCG>
-static int launch_ltsolve(gic_handle *h, const Pattern &P, const TL *Uval, const double *invd, double *y, double *z,
-                          const double *r, double *partials, Scalars *sc)
+static int launch_ltsolve_gen(gic_handle *h, const Pattern &P, const TL *Uval, const double *invd, double *y,
+                              double *z, const double *r, double *partials, Scalars *sc)
 {
-    if (pipelined_ok(h, P)) {
-        if (P.max_group <= 1) return launch_ltsolve_pg<TL, PCG, 1>(h, P, Uval, invd, y, z, r, partials, sc);
-        return launch_ltsolve_pg<TL, PCG, 3>(h, P, Uval, invd, y, z, r, partials, sc);
-    }
     if (P.max_group <= 1) return launch_ltsolve_g<TL, PCG, 1>(h, P, Uval, invd, y, z, r, partials, sc);
     if (P.max_group <= 3) return launch_ltsolve_g<TL, PCG, 3>(h, P, Uval, invd, y, z, r, partials, sc);
     return launch_ltsolve_g<TL, PCG, GMAX>(h, P, Uval, invd, y, z, r, partials, sc);
 }
 
-template <typename TL>
-static int setup_factor(gic_handle *h, const Pattern &P, const TL *Lval, TL *Uval, double *invd)
+// ---- pipelined kernels (vectors and sums in T)
+template <typename T, int GM>
+static int launch_lsolve_pg(gic_handle *h, const Pattern &P, const T *Lval, const T *invd, const T *r, T *y,
+                            Scalars *sc)
+{
+    int32_t nc = P.nchunks;
+    const int32_t *ord = P.ord_f, *cg = P.chunk_grp, *g = P.grp, *lr = P.Lrowptr, *lc = P.Lcol;
+    unsigned *er = h->dev_err;
+    int poll = h->tune_poll;
+    void *args[] = {&nc, &ord, &cg, &g, &lr, &lc, &Lval, &invd, &r, &y, &er, &poll, &sc};
+    const size_t smem = sizeof(PWarp<T, GM>) * (SOLVE_BLOCK / 32);
+    static bool ad[64] = {};
+    if (!ad[h->device & 63]) {
+        GIC_CUDA_TRY(cudaFuncSetAttribute(k_lsolve_p<T, GM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        ad[h->device & 63] = true;
+    }
+    return launch_persistent(h, (const void *)k_lsolve_p<T, GM>, SOLVE_BLOCK, smem, solve_warps(h, P), args);
+}
+
+template <typename T>
+static int launch_lsolve_p(gic_handle *h, const Pattern &P, const T *Lval, const T *invd, const T *r, T *y, Scalars *sc)
+{
+    if (P.max_group <= 1) return launch_lsolve_pg<T, 1>(h, P, Lval, invd, r, y, sc);
+    return launch_lsolve_pg<T, 3>(h, P, Lval, invd, r, y, sc);
+}
+
+template <typename T, bool PCG, int GM>
+static int launch_ltsolve_pg(gic_handle *h, const Pattern &P, const T *Uval, const T *invd, T *y, T *z,
+                             const double *rd, double *partials, Scalars *sc)
+{
+    int32_t nc = P.nchunks;
+    const int32_t *ord = P.ord_b, *cg = P.chunk_grp, *g = P.grp, *ur = P.Urowptr, *uc = P.Ucol;
+    unsigned *er = h->dev_err;
+    int poll = h->tune_poll;
+    void *args[] = {&nc, &ord, &cg, &g, &ur, &uc, &Uval, &invd, &y, &z, &rd, &partials, &er, &poll, &sc};
+    int64_t need = solve_warps(h, P);
+    if (PCG && need > MAX_PARTIALS) need = MAX_PARTIALS;
+    const size_t smem = sizeof(PWarp<T, GM>) * (SOLVE_BLOCK / 32);
+    static bool ad[64] = {};
+    if (!ad[h->device & 63]) {
+        GIC_CUDA_TRY(cudaFuncSetAttribute(k_ltsolve_p<T, PCG, GM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+        ad[h->device & 63] = true;
+    }
+    return launch_persistent(h, (const void *)k_ltsolve_p<T, PCG, GM>, SOLVE_BLOCK, smem, need, args);
+}
+
+template <typename T, bool PCG>
+static int launch_ltsolve_p(gic_handle *h, const Pattern &P, const T *Uval, const T *invd, T *y, T *z,
+                            const double *rd, double *partials, Scalars *sc)
+{
+    if (P.max_group <= 1) return launch_ltsolve_pg<T, PCG, 1>(h, P, Uval, invd, y, z, rd, partials, sc);
+    return launch_ltsolve_pg<T, PCG, 3>(h, P, Uval, invd, y, z, rd, partials, sc);
+}
+
+// Transposed values and reciprocal diagonal for the mode.
+static int setup_factor(gic_handle *h, const Pattern &P, SolveMode mode, const void *Lval, const SolveWs &W)
 {
     int64_t cnt = P.nnzL > P.n ? P.nnzL : P.n;
+    unsigned gr = vec_grid(h, cnt, 256);
     ++h->launches;
-    k_transpose_vals<TL><<<vec_grid(h, cnt, 256), 256, 0, h->stream>>>(P.n, P.nnzL, P.tperm, P.Lrowptr, Lval, Uval, invd);
+    if (mode == MODE_GEN64 || mode == MODE_P64)
+        k_factor_setup<double, double><<<gr, 256, 0, h->stream>>>(P.n, P.nnzL, P.tperm, P.Lrowptr,
+                                                                   (const double *)Lval, (double *)W.Uval, W.invd);
+    else if (mode == MODE_GEN32)
+        k_factor_setup<float, double><<<gr, 256, 0, h->stream>>>(P.n, P.nnzL, P.tperm, P.Lrowptr,
+                                                                  (const float *)Lval, (float *)W.Uval, W.invd);
+    else if (mode == MODE_P32)
+        k_factor_setup<float, float><<<gr, 256, 0, h->stream>>>(P.n, P.nnzL, P.tperm, P.Lrowptr, (const float *)Lval,
+                                                                 (float *)W.Uval, W.invd32);
     GIC_CUDA_TRY(cudaGetLastError());
     return GIC_OK;
 }
@@ -1322,31 +1445,63 @@ static int prof_flush(gic_handle *h, Prof &pr)
         pr.used += 2;                                                              \
     }
 
+// Forward then backward solve of one PCG step for the mode (z in W.z or W.z32).
+static int precondition(gic_handle *h, const Pattern &P, SolveMode mode, const void *Lval, const SolveWs &W)
+{
+    Prof &pr = prof_of(h);
+    PROF_BEGIN(GIC_PROF_LSOLVE);
+    switch (mode) {
+    case MODE_GEN64: GIC_TRY(launch_lsolve_gen<double>(h, P, (const double *)Lval, W.invd, W.r, W.y, W.sc)); break;
+    case MODE_GEN32: GIC_TRY(launch_lsolve_gen<float>(h, P, (const float *)Lval, W.invd, W.r, W.y, W.sc)); break;
+    case MODE_P64: GIC_TRY(launch_lsolve_p<double>(h, P, (const double *)Lval, W.invd, W.r, W.y, W.sc)); break;
+    case MODE_P32: GIC_TRY(launch_lsolve_p<float>(h, P, (const float *)Lval, W.invd32, W.r32, W.y32, W.sc)); break;
+    default: break;
+    }
+    PROF_END(GIC_PROF_LSOLVE);
+    PROF_BEGIN(GIC_PROF_LTSOLVE);
+    switch (mode) {
+    case MODE_GEN64:
+        GIC_TRY((launch_ltsolve_gen<double, true>(h, P, (const double *)W.Uval, W.invd, W.y, W.z, W.r, W.partials, W.sc)));
+        break;
+    case MODE_GEN32:
+        GIC_TRY((launch_ltsolve_gen<float, true>(h, P, (const float *)W.Uval, W.invd, W.y, W.z, W.r, W.partials, W.sc)));
+        break;
+    case MODE_P64:
+        GIC_TRY((launch_ltsolve_p<double, true>(h, P, (const double *)W.Uval, W.invd, W.y, W.z, W.r, W.partials, W.sc)));
+        break;
+    case MODE_P32:
+        GIC_TRY((launch_ltsolve_p<float, true>(h, P, (const float *)W.Uval, W.invd32, W.y32, W.z32, W.r, W.partials,
+                                               W.sc)));
+        break;
+    default: break;
+    }
+    PROF_END(GIC_PROF_LTSOLVE);
+    return GIC_OK;
+}
+
 // One PCG iteration: lines 11-18 of Algorithm 1 and the stop test.
-template <typename TL>
-static int pcg_iteration(gic_handle *h, const Pattern &P, const double *valA, const TL *Lval, const SolveWs &W,
-                         double *x, int ident)
+static int pcg_iteration(gic_handle *h, const Pattern &P, SolveMode mode, const double *valA, const void *Lval,
+                         const SolveWs &W, double *x)
 {
     const int64_t n = P.n;
     Prof &pr = prof_of(h);
-    if (ident) {
+    const unsigned vg = vec_grid(h, n, VEC_BLOCK);
+    if (mode == MODE_IDENT) {
         PROF_BEGIN(GIC_PROF_VECTOR);
         ++h->launches;
-        k_ident_rz<<<vec_grid(h, n, VEC_BLOCK), VEC_BLOCK, 0, h->stream>>>(n, W.r, W.partials, W.sc);
+        k_ident_rz<<<vg, VEC_BLOCK, 0, h->stream>>>(n, W.r, W.partials, W.sc);
         ++h->launches;
-        k_update_p<true><<<vec_grid(h, n, VEC_BLOCK), VEC_BLOCK, 0, h->stream>>>(n, W.z, W.p, W.r, W.partials, W.sc);
+        k_update_p<true, double><<<vg, VEC_BLOCK, 0, h->stream>>>(n, W.z, W.p, W.r, W.sc);
         GIC_CUDA_TRY(cudaGetLastError());
         PROF_END(GIC_PROF_VECTOR);
     } else {
-        PROF_BEGIN(GIC_PROF_LSOLVE);
-        GIC_TRY(launch_lsolve<TL>(h, P, Lval, W.invd, W.r, W.y, W.sc));
-        PROF_END(GIC_PROF_LSOLVE);
-        PROF_BEGIN(GIC_PROF_LTSOLVE);
-        GIC_TRY((launch_ltsolve<TL, true>(h, P, (const TL *)W.Uval, W.invd, W.y, W.z, W.r, W.partials, W.sc)));
-        PROF_END(GIC_PROF_LTSOLVE);
+        GIC_TRY(precondition(h, P, mode, Lval, W));
         PROF_BEGIN(GIC_PROF_VECTOR);
         ++h->launches;
-        k_update_p<false><<<vec_grid(h, n, VEC_BLOCK), VEC_BLOCK, 0, h->stream>>>(n, W.z, W.p, W.r, W.partials, W.sc);
+        if (mode == MODE_P32)
+            k_update_p<false, float><<<vg, VEC_BLOCK, 0, h->stream>>>(n, W.z32, W.p, W.r, W.sc);
+        else
+            k_update_p<false, double><<<vg, VEC_BLOCK, 0, h->stream>>>(n, W.z, W.p, W.r, W.sc);
         GIC_CUDA_TRY(cudaGetLastError());
         PROF_END(GIC_PROF_VECTOR);
     }
@@ -1358,34 +1513,40 @@ static int pcg_iteration(gic_handle *h, const Pattern &P, const double *valA, co
     PROF_END(GIC_PROF_SPMV);
     PROF_BEGIN(GIC_PROF_VECTOR);
     ++h->launches;
-    k_update_xr<<<vec_grid(h, n, VEC_BLOCK), VEC_BLOCK, 0, h->stream>>>(n, x, W.r, W.p, W.w, W.partials, W.sc);
+    k_update_xr<<<vg, VEC_BLOCK, 0, h->stream>>>(n, x, W.r, W.p, W.w, mode == MODE_P32 ? W.r32 : nullptr, W.partials,
+                                                 W.sc);
     GIC_CUDA_TRY(cudaGetLastError());
     PROF_END(GIC_PROF_VECTOR);
     return GIC_OK;
 }
 
-template <typename TL>
-static int pcg_run(gic_handle *h, const Pattern &P, const double *valA, const TL *Lval, int ident, const double *b,
-                   double *x, double rtol, int maxit, int32_t *iters, double *relres, const SolveWs &W)
+static int pcg_run(gic_handle *h, const Pattern &P, SolveMode mode, const double *valA, const void *Lval,
+                   const double *b, double *x, double rtol, int maxit, int32_t *iters, double *relres, const SolveWs &W)
 {
     const int64_t n = P.n;
     Prof &pr = prof_of(h);
+    const unsigned vg = vec_grid(h, n, 256);
     ++h->launches;
     k_init_scalars<<<1, 1, 0, h->stream>>>(W.sc, rtol, maxit);
-    if (!ident) {
-        GIC_TRY(setup_factor<TL>(h, P, Lval, (TL *)W.Uval, W.invd));
+    if (mode != MODE_IDENT) {
+        GIC_TRY(setup_factor(h, P, mode, Lval, W));
         ++h->launches;
-        k_fill_sentinel<<<vec_grid(h, n, 256), 256, 0, h->stream>>>(n, W.y, W.z);
+        if (mode == MODE_P32) k_fill_sentinel_t<float><<<vg, 256, 0, h->stream>>>(n, W.y32, W.z32);
+        else k_fill_sentinel_t<double><<<vg, 256, 0, h->stream>>>(n, W.y, W.z);
     }
-    PROF_BEGIN(GIC_PROF_SPMV);
-    ++h->launches;
     ++h->launches;
     k_sell_vals<<<vec_grid(h, P.nslices * 32, 256), 256, 0, h->stream>>>(n, P.nslices, P.rowptr, valA, P.sell_ptr,
                                                                           P.sell_w, W.sval);
+    PROF_BEGIN(GIC_PROF_SPMV);
+    ++h->launches;
     k_spmv_sell<2><<<spmv_grid(h, P.nslices), SPMV_BLOCK, 0, h->stream>>>(
         n, P.nslices, P.sell_ptr, P.sell_w, P.sell_col, W.sval, x, W.r, b, W.partials, W.sc);
     GIC_CUDA_TRY(cudaGetLastError());
     PROF_END(GIC_PROF_SPMV);
+    if (mode == MODE_P32) {
+        ++h->launches;
+        k_convert_f64_f32<<<vg, 256, 0, h->stream>>>(n, W.r, W.r32);
+    }
     // Iterations are enqueued in batches; the host reads the device flag of
     // the previous batch while the next one runs (finished kernels exit at
     // once when done is set), so the GPU does not idle on the check.
@@ -1398,7 +1559,7 @@ static int pcg_run(gic_handle *h, const Pattern &P, const double *valA, const TL
     while (true) {
         int todo = BATCH;
         if (enq + todo > maxit) todo = maxit - enq;
-        for (int k = 0; k < todo && rc == GIC_OK; ++k) rc = pcg_iteration<TL>(h, P, valA, Lval, W, x, ident);
+        for (int k = 0; k < todo && rc == GIC_OK; ++k) rc = pcg_iteration(h, P, mode, valA, Lval, W, x);
         if (rc != GIC_OK) break;
         enq += todo;
         if (pending) {
@@ -1431,6 +1592,64 @@ static int pcg_run(gic_handle *h, const Pattern &P, const double *valA, const TL
     return out.status;
 }
 
+// Standalone forward / backward solve (gic_lsolve, gic_ltsolve).
+static int standalone_solve(gic_handle *h, const Pattern &p, const void *valL, int l_dtype, const double *in,
+                            double *out, void *ws, size_t ws_bytes, bool forward)
+{
+    const SolveMode mode = solve_mode(h, p, l_dtype);
+    SolveWs W = carve(p, l_dtype, mode == MODE_P32, ws);
+    if (ws_bytes < W.bytes) return GIC_ERR_WORKSPACE;
+    const unsigned vg = vec_grid(h, p.n, 256);
+    GIC_TRY(setup_factor(h, p, mode, valL, W));
+    Prof &pr = prof_of(h);
+    if (mode == MODE_P32) {
+        ++h->launches;
+        k_convert_f64_f32<<<vg, 256, 0, h->stream>>>(p.n, in, W.r32); // the input, whichever sweep
+        ++h->launches;
+        k_fill_sentinel_t<float><<<vg, 256, 0, h->stream>>>(p.n, W.y32, nullptr);
+    } else {
+        ++h->launches;
+        k_fill_sentinel_t<double><<<vg, 256, 0, h->stream>>>(p.n, out, nullptr);
+    }
+    if (forward) {
+        PROF_BEGIN(GIC_PROF_LSOLVE);
+        switch (mode) {
+        case MODE_GEN64: GIC_TRY(launch_lsolve_gen<double>(h, p, (const double *)valL, W.invd, in, out, nullptr)); break;
+        case MODE_GEN32: GIC_TRY(launch_lsolve_gen<float>(h, p, (const float *)valL, W.invd, in, out, nullptr)); break;
+        case MODE_P64: GIC_TRY(launch_lsolve_p<double>(h, p, (const double *)valL, W.invd, in, out, nullptr)); break;
+        case MODE_P32: GIC_TRY(launch_lsolve_p<float>(h, p, (const float *)valL, W.invd32, W.r32, W.y32, nullptr)); break;
+        default: break;
+        }
+        PROF_END(GIC_PROF_LSOLVE);
+    } else {
+        double *yy = const_cast<double *>(in); // not written when PCG = false
+        PROF_BEGIN(GIC_PROF_LTSOLVE);
+        switch (mode) {
+        case MODE_GEN64:
+            GIC_TRY((launch_ltsolve_gen<double, false>(h, p, (const double *)W.Uval, W.invd, yy, out, nullptr, nullptr, nullptr)));
+            break;
+        case MODE_GEN32:
+            GIC_TRY((launch_ltsolve_gen<float, false>(h, p, (const float *)W.Uval, W.invd, yy, out, nullptr, nullptr, nullptr)));
+            break;
+        case MODE_P64:
+            GIC_TRY((launch_ltsolve_p<double, false>(h, p, (const double *)W.Uval, W.invd, yy, out, nullptr, nullptr, nullptr)));
+            break;
+        case MODE_P32:
+            GIC_TRY((launch_ltsolve_p<float, false>(h, p, (const float *)W.Uval, W.invd32, W.r32, W.y32, nullptr, nullptr,
+                                                   nullptr)));
+            break;
+        default: break;
+        }
+        PROF_END(GIC_PROF_LTSOLVE);
+    }
+    if (mode == MODE_P32) {
+        ++h->launches;
+        k_convert_f32_f64<<<vg, 256, 0, h->stream>>>(p.n, W.y32, out);
+    }
+    GIC_CUDA_TRY(cudaGetLastError());
+    return GIC_OK;
+}
+
 }  // namespace gic
 
 using namespace gic;
@@ -1449,7 +1668,7 @@ int gic_workspace_size(gic_handle *h, const gic_pattern *P, int op, int l_dtype,
     GIC_TRY(check_pattern(h, P));
     if (!bytes || (l_dtype != GIC_F64 && l_dtype != GIC_F32 && l_dtype != GIC_IDENTITY)) return GIC_ERR_INVALID_ARG;
     if (op != GIC_WS_SOLVE && op != GIC_WS_PCG) return GIC_ERR_INVALID_ARG;
-    *bytes = carve(P->p, l_dtype, nullptr).bytes;
+    *bytes = carve(P->p, l_dtype, l_dtype == GIC_F32, nullptr).bytes;
     return GIC_OK;
 }
 
@@ -1486,24 +1705,7 @@ int gic_lsolve(gic_handle *h, const gic_pattern *P, const void *valL, int l_dtyp
 {
     GIC_TRY(check_pattern(h, P));
     if (!valL || !r || !y || !ws || (l_dtype != GIC_F64 && l_dtype != GIC_F32)) return GIC_ERR_INVALID_ARG;
-    const Pattern &p = P->p;
-    SolveWs W = carve(p, l_dtype, ws);
-    if (ws_bytes < W.bytes) return GIC_ERR_WORKSPACE;
-    ++h->launches;
-    k_fill_sentinel<<<vec_grid(h, p.n, 256), 256, 0, h->stream>>>(p.n, y, nullptr);
-    Prof &pr = prof_of(h);
-    if (l_dtype == GIC_F64) {
-        GIC_TRY(setup_factor<double>(h, p, (const double *)valL, (double *)W.Uval, W.invd));
-        PROF_BEGIN(GIC_PROF_LSOLVE);
-        GIC_TRY(launch_lsolve<double>(h, p, (const double *)valL, W.invd, r, y, nullptr));
-        PROF_END(GIC_PROF_LSOLVE);
-    } else {
-        GIC_TRY(setup_factor<float>(h, p, (const float *)valL, (float *)W.Uval, W.invd));
-        PROF_BEGIN(GIC_PROF_LSOLVE);
-        GIC_TRY(launch_lsolve<float>(h, p, (const float *)valL, W.invd, r, y, nullptr));
-        PROF_END(GIC_PROF_LSOLVE);
-    }
-    return GIC_OK;
+    return standalone_solve(h, P->p, valL, l_dtype, r, y, ws, ws_bytes, true);
 }
 
 int gic_ltsolve(gic_handle *h, const gic_pattern *P, const void *valL, int l_dtype, const double *y, double *z,
@@ -1511,25 +1713,7 @@ int gic_ltsolve(gic_handle *h, const gic_pattern *P, const void *valL, int l_dty
 {
     GIC_TRY(check_pattern(h, P));
     if (!valL || !y || !z || !ws || (l_dtype != GIC_F64 && l_dtype != GIC_F32)) return GIC_ERR_INVALID_ARG;
-    const Pattern &p = P->p;
-    SolveWs W = carve(p, l_dtype, ws);
-    if (ws_bytes < W.bytes) return GIC_ERR_WORKSPACE;
-    ++h->launches;
-    k_fill_sentinel<<<vec_grid(h, p.n, 256), 256, 0, h->stream>>>(p.n, z, nullptr);
-    Prof &pr = prof_of(h);
-    double *yy = const_cast<double *>(y); // not written when PCG = false
-    if (l_dtype == GIC_F64) {
-        GIC_TRY(setup_factor<double>(h, p, (const double *)valL, (double *)W.Uval, W.invd));
-        PROF_BEGIN(GIC_PROF_LTSOLVE);
-        GIC_TRY((launch_ltsolve<double, false>(h, p, (const double *)W.Uval, W.invd, yy, z, nullptr, nullptr, nullptr)));
-        PROF_END(GIC_PROF_LTSOLVE);
-    } else {
-        GIC_TRY(setup_factor<float>(h, p, (const float *)valL, (float *)W.Uval, W.invd));
-        PROF_BEGIN(GIC_PROF_LTSOLVE);
-        GIC_TRY((launch_ltsolve<float, false>(h, p, (const float *)W.Uval, W.invd, yy, z, nullptr, nullptr, nullptr)));
-        PROF_END(GIC_PROF_LTSOLVE);
-    }
-    return GIC_OK;
+    return standalone_solve(h, P->p, valL, l_dtype, y, z, ws, ws_bytes, false);
 }
 
 int gic_solve_error_flags(gic_handle *h, unsigned *flags)
@@ -1547,14 +1731,12 @@ int gic_pcg(gic_handle *h, const gic_pattern *P, const double *valA, const void 
     if (l_dtype != GIC_IDENTITY && !valL) return GIC_ERR_INVALID_ARG;
     if (l_dtype != GIC_F64 && l_dtype != GIC_F32 && l_dtype != GIC_IDENTITY) return GIC_ERR_INVALID_ARG;
     const Pattern &p = P->p;
-    SolveWs W = carve(p, l_dtype, ws);
+    const SolveMode mode = solve_mode(h, p, l_dtype);
+    SolveWs W = carve(p, l_dtype, l_dtype == GIC_F32, ws);
     if (ws_bytes < W.bytes) return GIC_ERR_WORKSPACE;
-    if (p.ngroups > 0 && (spmv_grid(h, p.n) > MAX_PARTIALS || vec_grid(h, p.n, VEC_BLOCK) > MAX_PARTIALS))
+    if (p.ngroups > 0 && (spmv_grid(h, p.nslices) > MAX_PARTIALS || vec_grid(h, p.n, VEC_BLOCK) > MAX_PARTIALS))
         return GIC_ERR_UNSUPPORTED;
-    if (l_dtype == GIC_F32)
-        return pcg_run<float>(h, p, valA, (const float *)valL, 0, b, x, rtol, maxit, iters, relres, W);
-    return pcg_run<double>(h, p, valA, (const double *)valL, l_dtype == GIC_IDENTITY, b, x, rtol, maxit, iters,
-                           relres, W);
+    return pcg_run(h, p, mode, valA, valL, b, x, rtol, maxit, iters, relres, W);
 }
 
 int gic_profile_enable(gic_handle *h, int on)

@@ -233,11 +233,17 @@ def test_spmv_matches_oracle(G, h):
     assert abs(_np(d)[0] - x @ yo) <= 1e-12 * abs(x @ yo)
 
 
+@pytest.mark.parametrize("pipeline", [1, 0])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-@pytest.mark.parametrize("case", ["fem8", "random", "tridiag"])
-def test_triangular_solves_match_oracle(G, h, dtype, case):
+@pytest.mark.parametrize("case", ["fem8", "fem5", "random", "tridiag"])
+def test_triangular_solves_match_oracle(G, h, dtype, case, pipeline):
+    """Both solve paths (pipelined where the pattern allows, generic) against
+    the oracle on the same factor."""
+    G.set_tuning(h, G.GIC_TUNE_PIPELINE, pipeline)
     if case == "fem8":
         A = O.fem_hex_assemble(8, I.material_field(8, 5))
+    elif case == "fem5":
+        A = O.fem_hex_assemble(5, I.material_field(5, 6))
     elif case == "random":
         A = O.csr_from_dense(_spd_pattern(300, 0.02, 1))
     else:
@@ -254,9 +260,14 @@ def test_triangular_solves_match_oracle(G, h, dtype, case):
     z = G.ltsolve(h, P, Ld, y)
     yo = O.lsolve(Lref, r)
     zo = O.ltsolve(Lref, yo)
-    assert _rel(_np(y), yo) <= 1e-11
-    assert _rel(_np(z), zo) <= 1e-11
+    if dtype == torch.float64:
+        assert _rel(_np(y), yo) <= 1e-11
+        assert _rel(_np(z), zo) <= 1e-11
+    else:  # the FP32 preconditioner apply sums in FP32
+        nrel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
+        assert nrel(_np(y), yo) <= 1e-5 and nrel(_np(z), zo) <= 1e-5
     assert G.error_flags(h) == 0
+    G.set_tuning(h, G.GIC_TUNE_PIPELINE, 1)
 
 
 # ---------------------------------------------------------------- A7 PCG
@@ -293,7 +304,9 @@ def test_plain_cg_matches_oracle(G, h):
     assert np.linalg.norm(x - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
 
 
-def test_pcg_f32_factor(G, h):
+@pytest.mark.parametrize("pipeline", [1, 0])
+def test_pcg_f32_factor(G, h, pipeline):
+    G.set_tuning(h, G.GIC_TUNE_PIPELINE, pipeline)
     N = 8
     A = O.fem_hex_assemble(N, I.material_field(N, 9))
     b = I.rhs(A.n, 9)
@@ -303,6 +316,7 @@ def test_pcg_f32_factor(G, h):
     P = G.Pattern(h, rp, c)
     Lg, _ = G.ic0(h, P, v)
     res = G.pcg(h, P, v, G.to_f32(h, Lg), _dev(b), rtol=1e-8)
+    G.set_tuning(h, G.GIC_TUNE_PIPELINE, 1)
     ro = O.pcg(A, b, L32, tol=1e-8)
     assert _iters_ok(res["iters"], ro["iters"]), (res["iters"], ro["iters"])
     x = _np(res["x"])
