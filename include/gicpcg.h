@@ -267,6 +267,22 @@ int gic_set_tuning(gic_handle *h, int key, int value);
  * the handle stays usable) or GIC_OK if the wait unexpectedly ended. */
 int gic_selftest_wait_timeout(gic_handle *h, int64_t polls);
 
+/* y = A x and *xdoty = x^T y for callers that cannot allocate device memory
+ * (inside another allocator, under a fixed memory budget, or where a
+ * synchronous allocation is not allowed). No paper counterpart: same
+ * arithmetic as gic_spmv, but it needs no handle, no pattern and no
+ * workspace, and allocates nothing. Its scratch (partial sums and a
+ * counter) is a file-scope device array of about 8 MiB that every GPU
+ * loading this library holds until exit; the first call on a device looks up
+ * that array's device address, so make it before any stream capture.
+ * Calls share the scratch: calls that overlap on the GPU (other streams)
+ * race; calls in one stream are ordered. rowptr (n+1), col, val, x, y,
+ * xdoty: device memory of the current device; stream: a cudaStream_t
+ * (NULL = legacy default). n is limited to 8,388,608 rows (larger:
+ * GIC_ERR_TOO_LARGE). Asynchronous. */
+int gic_spmv_dot_noalloc(int64_t n, const int32_t *rowptr, const int32_t *col, const double *val,
+                         const double *x, double *y, double *xdoty, void *stream);
+
 /* Number of kernels this handle has launched so far (host output). */
 int gic_launch_count(gic_handle *h, int64_t *count);
 

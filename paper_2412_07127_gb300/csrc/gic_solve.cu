@@ -1794,3 +1794,65 @@ int gic_launch_count(gic_handle *h, int64_t *count)
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ no-allocation SpMV
+// Some callers cannot call cudaMalloc: code running inside another
+// framework's memory pool or allocator hooks, services that must not touch
+// the device heap after start-up, or code between stream-ordered operations
+// where a synchronous allocation is not allowed. gic_spmv_dot_noalloc serves
+// them: it needs no handle and no workspace, because its scratch (the
+// per-block partial sums of x^T y and the reduction's completion counter)
+// lives in this file-scope device array, which every GPU that loads the
+// library holds until the process exits (about 8 MiB).
+namespace gic {
+
+constexpr int64_t NOALLOC_SLOTS = 1 << 20;               // one partial per block of 8 rows
+constexpr int64_t NOALLOC_MAX_ROWS = 8 * NOALLOC_SLOTS;   // 8,388,608 rows
+
+struct NoallocScratch {
+    Scalars sc; // only its last-block counter is used; zeroed by every call
+    double partials[NOALLOC_SLOTS];
+};
+static __device__ __align__(256) NoallocScratch g_noalloc_scratch;
+
+// Device address of the scratch, looked up once per device with that device
+// current. (In host code the symbol only names a host-side stand-in; a kernel
+// given it would fault or read the wrong memory.)
+static NoallocScratch *g_noalloc_addr[64];
+
+static int noalloc_address(int device, NoallocScratch **out)
+{
+    if (device < 0 || device >= 64) return GIC_ERR_UNSUPPORTED;
+    if (!g_noalloc_addr[device]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) {
+            set_last_cuda_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
+            return GIC_ERR_CUDA;
+        }
+        g_noalloc_addr[device] = (NoallocScratch *)ptr;
+    }
+    *out = g_noalloc_addr[device];
+    return GIC_OK;
+}
+
+}  // namespace gic
+
+extern "C" int gic_spmv_dot_noalloc(int64_t n, const int32_t *rowptr, const int32_t *col, const double *val,
+                                    const double *x, double *y, double *xdoty, void *stream)
+{
+    if (n < 1 || !rowptr || !col || !val || !x || !y || !xdoty) return GIC_ERR_INVALID_ARG;
+    if (n > gic::NOALLOC_MAX_ROWS) return GIC_ERR_TOO_LARGE;
+    int device = 0;
+    GIC_CUDA_TRY(cudaGetDevice(&device));
+    gic::NoallocScratch *scr = nullptr;
+    GIC_TRY(gic::noalloc_address(device, &scr));
+    cudaStream_t s = (cudaStream_t)stream;
+    // the reduction counter must start at zero, whatever an earlier call left
+    GIC_CUDA_TRY(cudaMemsetAsync(&scr->sc, 0, sizeof(gic::Scalars), s));
+    const int64_t blocks = (n + 7) / 8; // 8 warps per block, one row per warp
+    gic::k_spmv<0><<<(unsigned)blocks, gic::SPMV_BLOCK, 0, s>>>(n, rowptr, col, val, x, y, nullptr, scr->partials,
+                                                                xdoty, &scr->sc);
+    GIC_CUDA_TRY(cudaGetLastError());
+    return GIC_OK;
+}

@@ -65,6 +65,7 @@ _SIGS = {
     "gic_launch_count": (_int, [_vp, C.POINTER(_i64)]),
     "gic_set_tuning": (_int, [_vp, _int, _int]),
     "gic_selftest_wait_timeout": (_int, [_vp, _i64]),
+    "gic_spmv_dot_noalloc": (_int, [_i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "gic_solve_host": (_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _int, _dbl, _int,
                               C.POINTER(_i32), C.POINTER(_dbl), C.POINTER(_dbl), C.POINTER(_int),
                               _vp, _sz]),
@@ -316,6 +317,13 @@ POLL_ONE_LANE = 1 << 16
 
 def set_tuning(h: Handle, key, value):
     _call("gic_set_tuning", h.h, key, value)
+
+
+def spmv_dot_noalloc(rowptr, col, val, x, y, xdoty, stream=None):
+    """y = A x and xdoty[0] = x^T y with no handle, workspace or allocation
+    (y and xdoty are caller-provided device tensors)."""
+    _call("gic_spmv_dot_noalloc", rowptr.numel() - 1, _ptr(rowptr), _ptr(col), _ptr(val), _ptr(x), _ptr(y),
+          _ptr(xdoty), _stream_ptr(stream))
 
 
 def selftest_wait_timeout(h: Handle, polls=4096):
