@@ -37,6 +37,7 @@ def parse():
     ap.add_argument("--ldtype", default="f64", choices=["f64", "f32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-f32", action="store_true", help="skip the FP32-apply comparison")
     return ap.parse_args()
 
 
@@ -64,13 +65,16 @@ def workload_sizes(N):
 
 
 def kernel_bytes(N, ldtype):
-    """Algorithmic bytes per launch of each kernel class."""
+    """Algorithmic bytes per launch of each kernel class:
+    factor values + int32 columns once, row pointers, the vectors read and
+    written once. FP32 apply: 4-byte factor values and vectors."""
     n, nnz, nnzL, _ = workload_sizes(N)
     lv = 8 if ldtype == "f64" else 4
+    vb = 8 if ldtype == "f64" else 4
     return {
         "spmv": 12 * nnz + 4 * (n + 1) + 16 * n,
-        "lsolve": (lv + 4) * nnzL + 4 * (n + 1) + 16 * n,
-        "ltsolve": (lv + 4) * nnzL + 4 * (n + 1) + 24 * n,
+        "lsolve": (lv + 4) * nnzL + 4 * (n + 1) + 2 * vb * n,
+        "ltsolve": (lv + 4) * nnzL + 4 * (n + 1) + 2 * vb * n + 8 * n,
         "vector": 40 * n,  # mean of the two vector kernels (32n and 48n)
     }
 
@@ -246,9 +250,13 @@ def run_ours(args, rank, world, local):
     x = torch.empty_like(b)
 
     ev = lambda: torch.cuda.Event(enable_timing=True)
+    ws_pcg32 = G.workspace(h, P, G.GIC_WS_PCG, G.GIC_F32)
 
-    def step():
+    def step(ldt_run):
+        """IC(0), features + GNN + correction, PCG with the corrected factor,
+        PCG with the plain IC(0) factor; factor precision ldt_run."""
         e = [ev() for _ in range(6)]
+        wsp = ws_pcg if ldt_run == G.GIC_F64 else ws_pcg32
         e[0].record(stream)
         _, alpha, bad = G.ic0_auto(h, P, valA, out=LIC)
         e[1].record(stream)
@@ -256,18 +264,24 @@ def run_ours(args, rank, world, local):
         G.gnn_forward(h, P, theta, x9, e0, ws=ws_gnn, g=g)
         _, ok = G.gnn_correct(h, P, LIC, g, scale, out=Lg)
         Luse = Lg if ok else LIC
+        Lrun = Luse if ldt_run == G.GIC_F64 else G.to_f32(h, Luse)
         e[2].record(stream)
         x.zero_()
-        r_g = G.pcg(h, P, valA, Luse if ldt == G.GIC_F64 else G.to_f32(h, Luse), b, x=x, ws=ws_pcg)
+        r_g = G.pcg(h, P, valA, Lrun, b, x=x, ws=wsp)
         e[3].record(stream)
+        L0 = LIC if ldt_run == G.GIC_F64 else G.to_f32(h, LIC)
         x.zero_()
         e[4].record(stream)
-        r_i = G.pcg(h, P, valA, LIC if ldt == G.GIC_F64 else G.to_f32(h, LIC), b, x=x, ws=ws_pcg)
+        r_i = G.pcg(h, P, valA, L0, b, x=x, ws=wsp)
         e[5].record(stream)
         return e, r_g, r_i, ok, alpha
 
+    def phases(recs):
+        ph = np.array([[r[0][k].elapsed_time(r[0][k + 1]) for k in range(5)] for r in recs]) / 1e3
+        return ph.mean(0)
+
     for _ in range(args.warmup):
-        step()
+        step(ldt)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -278,7 +292,7 @@ def run_ours(args, rank, world, local):
     t_start, t_end = ev(), ev()
     torch.cuda.synchronize()
     t_start.record(stream)
-    recs = [step() for _ in range(args.steps)]
+    recs = [step(ldt) for _ in range(args.steps)]
     t_end.record(stream)
     torch.cuda.synchronize()
     launches = G.launch_count(h) - launches0
@@ -286,14 +300,35 @@ def run_ours(args, rank, world, local):
     G.profile_enable(h, False)
     clk = clocks.stop()
     total_ms = t_start.elapsed_time(t_end)
-    ph = np.array([[r[0][k].elapsed_time(r[0][k + 1]) for k in range(5)] for r in recs]) / 1e3
-    ic0_s, gnn_s, cg_g_s, _, cg_i_s = ph.mean(0)
+    ic0_s, gnn_s, cg_g_s, _, cg_i_s = phases(recs)
     value = ic0_s + gnn_s + cg_g_s
     if world > 1:
         tt = torch.tensor([total_ms, value], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         total_ms, value = float(tt[0]), float(tt[1])
     r_g, r_i = recs[-1][1], recs[-1][2]
+
+    # the same steps with the FP32 preconditioner apply (FP64 CG), after the
+    # timed region, with their own per-kernel profile
+    other = None
+    if args.ldtype == "f64" and not args.no_f32:
+        for _ in range(2):
+            step(G.GIC_F32)
+        torch.cuda.synchronize()
+        G.profile_enable(h, True)
+        recs32 = [step(G.GIC_F32) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        prof32 = G.profile_read(h)
+        G.profile_enable(h, False)
+        a, b_, c, _, d = phases(recs32)
+        kb32 = kernel_bytes(N, "f32")
+        other = {"value_s": a + b_ + c, "phase_s": {"ic0": a, "features_gnn_correct": b_, "cg_gnn_ic": c, "cg_ic0": d,
+                                                    "ic0_pcg_total": a + d},
+                 "iters": {"gnn_ic": recs32[-1][1]["iters"], "ic0": recs32[-1][2]["iters"]},
+                 "relres": {"gnn_ic": recs32[-1][1]["relres"], "ic0": recs32[-1][2]["relres"]},
+                 "kernels": {k: {"launches": v["launches"], "avg_us": v["ms"] / v["launches"] * 1e3,
+                                 "GB_s": kb32[k] / (v["ms"] / v["launches"] / 1e3) / 1e9}
+                             for k, v in prof32.items() if v["launches"]}}
 
     # kernel classes: achieved GB/s from algorithmic bytes / mean launch time
     kb = kernel_bytes(N, args.ldtype)
@@ -328,7 +363,10 @@ def run_ours(args, rank, world, local):
            "relres": {"gnn_ic": r_g["relres"], "ic0": r_i["relres"]},
            "gnn_kept": bool(recs[-1][3]), "ic0_shift": recs[-1][4],
            "kernels": kern, "roofline": roof, "spmv_roofline": spmv_roof, "clocks": clk,
-           "gpu_launches": launches}
+           "gpu_launches": launches,
+           "schedule": {"chunks": P.nchunks, "multi_group_chunks": bool(P.chunked), "sell_padding":
+                        P.sell_nnz / P.nnzA - 1.0},
+           "f32_apply": other}
 
     if not args.no_e2e:
         # end to end through the C-ABI with host buffers (pinned)
