@@ -48,6 +48,43 @@ def dist_env():
     return rank, world, local
 
 
+def rank_seed(seed, rank):
+    """Weak scaling by replicas: every rank solves its own seeded system."""
+    return seed + rank
+
+
+def sync_all(world, dev=None):
+    """Device synchronise, then a barrier over the ranks (taken on both sides
+    of the timed region)."""
+    import torch
+    if dev is not None and dev.type == "cuda":
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(vals, world, dev):
+    """Element-wise maximum of a list of floats over the ranks."""
+    if world == 1:
+        return [float(v) for v in vals]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def workload_config(N, theta_src, ldtype):
+    n, nnz, nnzL, lev = workload_sizes(N)
+    return {"workload": f"hex elasticity {N}^3 elements ({n} dofs, {nnz} nnz), E=exp(N(0,1)), "
+                        f"nu=0.3, GNN-IC vs IC(0) PCG to 1e-8",
+            "N": N, "n": n, "nnz": nnz, "nnzL": nnzL, "levels": lev,
+            "gnn_weights": theta_src, "l_dtype": ldtype,
+            "l2": (f"inputs larger than L2 (A {12 * nnz / 1e6:.0f} MB, L {12 * nnzL / 1e6:.0f} MB "
+                   f"in FP64); no flush" if 12 * nnzL > 129e6 else "inputs smaller than L2; no flush")}
+
+
 def load_theta(N_PARAMS):
     import numpy as np
     from paper_2412_07127_gb300 import inputs as I
@@ -194,7 +231,7 @@ def run_reference(args, rank, world):
     from paper_2412_07127_gb300 import inputs as I
     if rank != 0:
         return
-    theta, _ = load_theta(I.N_PARAMS)
+    theta, theta_src = load_theta(I.N_PARAMS)
     th64 = theta.astype(np.float64)
     for _ in range(args.warmup):
         oracle_solve_seconds(args.N, args.seed, th64)
@@ -203,13 +240,12 @@ def run_reference(args, rank, world):
         v, det = oracle_solve_seconds(args.N, args.seed, th64)
         vals.append(v)
     val = float(np.mean(vals))
-    n, nnz, nnzL, lev = workload_sizes(args.N)
     sample = (f"CPU oracle, 1 thread: IC(0), features, correction, full PCG on the {args.N}^3 system; "
               f"GNN forward timed on 20^3 and scaled by edge count ({det['cpu_work_s']:.1f} s CPU work per step)")
     out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": val * 1e3,
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": f"hex elasticity {args.N}^3 elements", "n": n, "nnz": nnz},
+           "data": "synthetic", "config": workload_config(args.N, theta_src, args.ldtype),
            "iters": det["iters"],
            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": val, "unit": "s"},
            "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -232,7 +268,7 @@ def run_ours(args, rank, world, local):
     stream = torch.cuda.current_stream()
     h = G.Handle(local, stream)
     N = args.N
-    seed = args.seed + rank  # weak scaling: every rank solves its own system
+    seed = rank_seed(args.seed, rank)
     theta_np, theta_src = load_theta(I.N_PARAMS)
     theta = torch.from_numpy(theta_np).to(dev)
     ldt = G.GIC_F64 if args.ldtype == "f64" else G.GIC_F32
@@ -282,9 +318,7 @@ def run_ours(args, rank, world, local):
 
     for _ in range(args.warmup):
         step(ldt)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    sync_all(world, dev)
     clocks = ClockSampler(local)
     clocks.start()
     G.profile_enable(h, True)
@@ -294,7 +328,7 @@ def run_ours(args, rank, world, local):
     t_start.record(stream)
     recs = [step(ldt) for _ in range(args.steps)]
     t_end.record(stream)
-    torch.cuda.synchronize()
+    sync_all(world, dev)
     launches = G.launch_count(h) - launches0
     prof = G.profile_read(h)
     G.profile_enable(h, False)
@@ -302,10 +336,7 @@ def run_ours(args, rank, world, local):
     total_ms = t_start.elapsed_time(t_end)
     ic0_s, gnn_s, cg_g_s, _, cg_i_s = phases(recs)
     value = ic0_s + gnn_s + cg_g_s
-    if world > 1:
-        tt = torch.tensor([total_ms, value], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms, value = float(tt[0]), float(tt[1])
+    total_ms, value = max_over_ranks([total_ms, value], world, dev)
     r_g, r_i = recs[-1][1], recs[-1][2]
 
     # the same steps with the FP32 preconditioner apply (FP64 CG), after the
@@ -352,11 +383,7 @@ def run_ours(args, rank, world, local):
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.ldtype == "f64" else "f64+f32L",
            "data": "synthetic",
-           "config": {"workload": f"hex elasticity {N}^3 elements ({P.n} dofs, {P.nnzA} nnz), E=exp(N(0,1)), "
-                                  f"nu=0.3, GNN-IC vs IC(0) PCG to 1e-8",
-                      "N": N, "n": P.n, "nnz": P.nnzA, "nnzL": P.nnzL, "levels": P.nlevels,
-                      "gnn_weights": theta_src, "l_dtype": args.ldtype,
-                      "l2": "inputs larger than L2 (A 187 MB, L 94 MB at N=40); no flush"},
+           "config": workload_config(N, theta_src, args.ldtype),
            "iters": {"gnn_ic": r_g["iters"], "ic0": r_i["iters"]},
            "phase_s": {"ic0": ic0_s, "features_gnn_correct": gnn_s, "cg_gnn_ic": cg_g_s, "cg_ic0": cg_i_s,
                        "ic0_pcg_total": ic0_s + cg_i_s},
@@ -386,10 +413,7 @@ def run_ours(args, rank, world, local):
             re = G.solve_host(h, rp_np, c_np, v_np, b_hn, theta=th_hn, l_dtype=ldt, ws=ws_h, x=x_hn)
             ts.append(time.perf_counter() - t0)
         e2e = float(np.mean(ts))
-        if world > 1:
-            tt = torch.tensor([e2e], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e = float(tt[0])
+        e2e = max_over_ranks([e2e], world, dev)[0]
         out["e2e"] = {"value": e2e, "unit": "s",
                       "h2d_bytes_per_step": int(A_rp.numel() * 4 + A_c.numel() * 4 + A_v.numel() * 8
                                                 + b_h.numel() * 8 + th_h.numel() * 4),

@@ -1,0 +1,163 @@
+"""Training driver of the GNN correction (Section 3: probe-vector loss of
+Eq. 4-5, Adam with warm-up; Section 4's setting of many small generated
+systems). Every arithmetic step runs in the library's CUDA kernels; this
+module only draws the seeded inputs and sequences the calls.
+
+One step on a batch of B independent N^3 systems (one block-diagonal pattern):
+  assemble A (per-system log-normal E, sigma ~ U[0.5, 2]) -> IC(0) with the
+  diagonal-shift rule -> features, scale s, A/s -> GNN forward (kept tape) ->
+  L_hat = corrected L_IC/sqrt(s) -> probe loss and dL_hat -> correction
+  backward -> GNN backward -> Adam.
+The batch's pattern is the same at every step, so it is analysed once.
+
+Usage: python -m paper_2412_07127_gb300.train --steps 2000 --out theta.npy
+"""
+import argparse
+import json
+import os
+import time
+
+import numpy as np
+import torch
+
+from . import gicpcg as G
+from . import inputs as I
+
+
+def lr_at(t, warm, lr_max):
+    """Linear warm-up over the first `warm` steps (t counted from 0), then constant."""
+    if warm <= 0 or t >= warm:
+        return lr_max
+    return lr_max * t / warm
+
+
+class Trainer:
+    def __init__(self, h, N=20, batch=16, probes=8, seed0=1000, sigma_lo=0.5, sigma_hi=2.0,
+                 device="cuda:0"):
+        self.h, self.N, self.B, self.m = h, N, batch, probes
+        self.seed0, self.lo, self.hi = seed0, sigma_lo, sigma_hi
+        self.dev = torch.device(device)
+        self.n = I.fem_sizes(N)[0]
+        rp, col, _ = self._assemble(0)
+        self.rp, self.col = rp, col          # kept alive: the pattern borrows them
+        self.P = G.Pattern(h, rp, col)
+        self.ws = G.gnn_workspace(h, self.P, batch, training=True)
+        self.pws = G.probe_workspace(h, self.P, batch, probes)
+        self.shifts = []
+
+    def _seeds(self, k):
+        return [self.seed0 + k * self.B + j for j in range(self.B)]
+
+    def _assemble(self, k):
+        Es = [I.material_field(self.N, s, I.training_sigma(s, self.lo, self.hi)) for s in self._seeds(k)]
+        E = torch.from_numpy(np.concatenate(Es)).to(self.dev)
+        return G.fem_hex_assemble(self.h, self.N, E, nb=self.B)
+
+    def batch(self, k):
+        """Device inputs of batch k: (x9, e0, A_hat, L_IC_hat, Z)."""
+        _, _, v = self._assemble(k)
+        LIC, alpha, bad = G.ic0_auto(self.h, self.P, v)
+        if bad != -1:
+            raise RuntimeError(f"IC(0) failed on batch {k} even with shifts")
+        self.shifts.append(alpha)
+        x9, e0, scale, Ahat = G.features(self.h, self.P, v, ngraphs=self.B, with_ahat=True)
+        LIChat = G.scale_factor(self.h, self.P, LIC, scale, ngraphs=self.B)
+        Z = np.concatenate([I.probes(self.m, self.n, s) for s in self._seeds(k)], axis=1)
+        return x9, e0, Ahat, LIChat, torch.from_numpy(Z).to(self.dev)
+
+    def loss_grad(self, theta, data, grad=True):
+        x9, e0, Ahat, LIChat, Z = data
+        h, P, B = self.h, self.P, self.B
+        g = G.gnn_forward_train(h, P, theta, x9, e0, self.ws, ngraphs=B)
+        Lhat = G.gnn_correct_scaled(h, P, LIChat, g)
+        loss, dL = G.probe_loss(h, P, Ahat, Lhat, Z, ngraphs=B, grad=grad, ws=self.pws)
+        if not grad:
+            return loss, None
+        dg = G.gnn_correct_backward(h, P, Lhat, dL)
+        return loss, G.gnn_backward(h, P, theta, x9, e0, dg, self.ws, ngraphs=B)
+
+    def ic0_loss(self, data):
+        """Probe loss of the uncorrected factor (g = 0) on the same batch."""
+        x9, e0, Ahat, LIChat, Z = data
+        loss, _ = G.probe_loss(self.h, self.P, Ahat, LIChat, Z, ngraphs=self.B, ws=self.pws)
+        return loss
+
+
+def validate(h, theta, N=20, seeds=range(9000, 9016), sigma=1.0, l_dtype=torch.float64):
+    """PCG iterations to 1e-8 with plain IC(0) and with the corrected factor."""
+    out = []
+    dev = theta.device
+    for s in seeds:
+        E = torch.from_numpy(I.material_field(N, s, sigma)).to(dev)
+        rp, col, v = G.fem_hex_assemble(h, N, E)
+        P = G.Pattern(h, rp, col)
+        b = torch.from_numpy(I.rhs(P.n, s)).to(dev)
+        LIC, alpha, _ = G.ic0_auto(h, P, v)
+        x9, e0, scale, _ = G.features(h, P, v)
+        g = G.gnn_forward(h, P, theta, x9, e0)
+        L, ok = G.gnn_correct(h, P, LIC, g, scale)
+        r0 = G.pcg(h, P, v, LIC.to(l_dtype), b)
+        r1 = G.pcg(h, P, v, L.to(l_dtype), b) if ok else dict(iters=-1)
+        out.append(dict(seed=s, ic0=r0["iters"], gnn=r1["iters"], positive=ok, shift=alpha))
+        P.close()
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--N", type=int, default=20)
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--probes", type=int, default=8)
+    ap.add_argument("--lr", type=float, default=0.005)
+    ap.add_argument("--warmup-frac", type=float, default=0.05)
+    ap.add_argument("--init-seed", type=int, default=0)
+    ap.add_argument("--init-out-scale", type=float, default=0.02)
+    ap.add_argument("--seed0", type=int, default=1000)
+    ap.add_argument("--time-limit", type=float, default=1e9, help="seconds; stop early")
+    ap.add_argument("--val-every", type=int, default=0)
+    ap.add_argument("--val-N", type=int, default=20)
+    ap.add_argument("--out", required=True)
+    ap.add_argument("--log", default=None)
+    a = ap.parse_args(argv)
+
+    h = G.Handle(0)
+    tr = Trainer(h, a.N, a.batch, a.probes, a.seed0)
+    dev = tr.dev
+    theta = torch.from_numpy(I.gnn_init(a.init_seed, a.init_out_scale).astype(np.float32)).to(dev)
+    m1, m2 = torch.zeros_like(theta), torch.zeros_like(theta)
+    warm = int(a.warmup_frac * a.steps)
+    log = dict(args=vars(a), steps=[], val=[])
+    t0 = time.time()
+    for t in range(a.steps):
+        data = tr.batch(t)
+        loss, grad = tr.loss_grad(theta, data)
+        G.adam_step(h, theta, grad, m1, m2, t + 1, lr_at(t, warm, a.lr))
+        if t % 20 == 0 or t == a.steps - 1:
+            l_ic = float(tr.ic0_loss(data)[a.batch])
+            rec = dict(step=t, loss=float(loss[a.batch]), loss_ic0=l_ic, ratio=float(loss[a.batch]) / l_ic,
+                       gnorm=float(grad.norm()), wall=time.time() - t0)
+            log["steps"].append(rec)
+            print(json.dumps(rec), flush=True)
+        if a.val_every and (t + 1) % a.val_every == 0:
+            v = validate(h, theta, N=a.val_N, seeds=range(9000, 9004))
+            log["val"].append(dict(step=t + 1, runs=v))
+            print(json.dumps(dict(step=t + 1, val=v)), flush=True)
+        if time.time() - t0 > a.time_limit:
+            break
+    torch.cuda.synchronize()
+    log["train_seconds"] = time.time() - t0
+    log["steps_done"] = t + 1
+    log["ic0_shifts"] = sorted(set(tr.shifts))
+    os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
+    np.save(a.out, theta.cpu().numpy())
+    v = validate(h, theta, N=a.val_N)
+    log["final_val"] = v
+    print(json.dumps(dict(final_val=v)), flush=True)
+    if a.log:
+        with open(a.log, "w") as f:
+            json.dump(log, f, indent=1)
+
+
+if __name__ == "__main__":
+    main()
