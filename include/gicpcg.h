@@ -252,13 +252,21 @@ int gic_probe_loss(gic_handle *h, const gic_pattern *P, int ngraphs, const float
 int gic_adam_step(gic_handle *h, int64_t np, float *theta, const float *grad, float *m1,
                   float *m2, int t, double lr);
 
-/* Tuning of the sync-free kernels (IC(0), triangular solves); no effect on
- * results: GIC_TUNE_SOLVE_WARPS_PER_SM = cap on resident solve warps per SM
- * (0 = no cap); GIC_TUNE_POLL = polling: low 16 bits = nanoseconds slept
- * between polls, bit 16 set = one polling lane per warp (default 1<<16). */
+/* Tuning of the sync-free kernels (IC(0), triangular solves); results agree
+ * to round-off across settings: GIC_TUNE_SOLVE_WARPS_PER_SM = cap on resident
+ * solve warps (warp pairs for the warp-specialised solves) per SM (0 = no
+ * cap); GIC_TUNE_POLL = polling: low 16 bits = nanoseconds slept between
+ * polls, bit 16 set = one polling lane per warp (default 1<<16);
+ * GIC_TUNE_PIPELINE = triangular-solve kernels: 2 (default) warp-specialised
+ * solves on premultiplied row-group blocks where the pattern allows (groups
+ * of <= 3 rows, <= 61 external columns), else 1 = staged one-warp solves
+ * (<= 3 rows, <= 48 columns), else 0 = generic; GIC_TUNE_QDELTA = level
+ * window of the dependencies the warp-specialised solves treat as "late"
+ * (read by gic_analyze; default 6). */
 #define GIC_TUNE_SOLVE_WARPS_PER_SM 1
 #define GIC_TUNE_POLL 2
-#define GIC_TUNE_PIPELINE 3 /* 1 (default): staged triangular solves where they apply */
+#define GIC_TUNE_PIPELINE 3
+#define GIC_TUNE_QDELTA 4
 int gic_set_tuning(gic_handle *h, int key, int value);
 
 /* Failure-path self-test of the bounded device waits: one warp waits on a

@@ -387,6 +387,91 @@ __global__ void k_sell_cols(int64_t n, int64_t nslices, const int32_t *rowptr, c
     }
 }
 
+// ------------------------------------------------------------ warp-specialised solve schedule
+__global__ void k_group_chunk(int32_t nchunks, const int32_t *chunk_grp, int32_t *gchunk)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks; c += (int64_t)gridDim.x * blockDim.x)
+        for (int32_t g = chunk_grp[c]; g < chunk_grp[c + 1]; ++g) gchunk[g] = (int32_t)c;
+}
+
+// Classify and order the m external columns (cols[0..m)) of one group.
+// prev: rows [prev_lo, prev_hi); late: key[j] within the window (forward:
+// level >= lev - delta; backward: level <= lev + delta). At most QLATE late
+// columns are kept, those closest in level; the order written is early
+// (original order), late (farthest level first, i.e. expected arrival
+// order), prev (original order).
+__device__ void q_classify(int m, const int32_t *cols, const int32_t *level, int32_t lev, int delta, bool forward,
+                           int32_t prev_lo, int32_t prev_hi, int32_t *qcol, uint8_t *qpos, int32_t *counts)
+{
+    unsigned long long late = 0, prev = 0;
+    int nl = 0, np = 0;
+    for (int j = 0; j < m; ++j) {
+        const int32_t c = cols[j];
+        if (c >= prev_lo && c < prev_hi) { prev |= 1ull << j; ++np; continue; }
+        const int32_t lc = level[c];
+        if (forward ? (lc >= lev - delta) : (lc <= lev + delta)) { late |= 1ull << j; ++nl; }
+    }
+    while (nl > QLATE) { // demote the late column farthest in level
+        int worst = -1;
+        int32_t wl = 0;
+        for (int j = 0; j < m; ++j) {
+            if (!((late >> j) & 1ull)) continue;
+            const int32_t lc = level[cols[j]];
+            if (worst < 0 || (forward ? lc < wl : lc > wl)) { worst = j; wl = lc; }
+        }
+        late &= ~(1ull << worst);
+        --nl;
+    }
+    int k = 0;
+    for (int j = 0; j < m; ++j)
+        if (!(((late | prev) >> j) & 1ull)) { qcol[k] = cols[j]; qpos[k] = (uint8_t)j; ++k; }
+    const int ne = k;
+    unsigned long long left = late;
+    while (left) { // selection by level: farthest first
+        int best = -1;
+        int32_t bl = 0;
+        for (int j = 0; j < m; ++j) {
+            if (!((left >> j) & 1ull)) continue;
+            const int32_t lc = level[cols[j]];
+            if (best < 0 || (forward ? lc < bl : lc > bl)) { best = j; bl = lc; }
+        }
+        left &= ~(1ull << best);
+        qcol[k] = cols[best];
+        qpos[k] = (uint8_t)best;
+        ++k;
+    }
+    for (int j = 0; j < m; ++j)
+        if ((prev >> j) & 1ull) { qcol[k] = cols[j]; qpos[k] = (uint8_t)j; ++k; }
+    counts[0] = ne;
+    counts[1] = nl;
+    counts[2] = np;
+}
+
+__global__ void k_qsched(int32_t ngroups, const int32_t *grp, const int32_t *Lrowptr, const int32_t *Lcol,
+                         const int32_t *Urowptr, const int32_t *Ucol, const int32_t *level, const int32_t *chunk_grp,
+                         const int32_t *gchunk, int delta, int32_t *qf_col, uint8_t *qf_pos, int32_t *qf_cnt,
+                         int32_t *qb_col, uint8_t *qb_pos, int32_t *qb_cnt)
+{
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = grp[g], G = grp[g + 1] - s, e = s + G - 1;
+        const int32_t c = gchunk[g];
+        const bool first = chunk_grp[c] == (int32_t)g, last = chunk_grp[c + 1] == (int32_t)g + 1;
+        int cnt[3];
+        // forward: external columns of row s, prev = the group before in the chunk
+        const int32_t b0 = Lrowptr[s];
+        const int m = Lrowptr[s + 1] - b0 - 1;
+        q_classify(m, Lcol + b0, level, level[s], delta, true, first ? 0 : grp[g - 1], first ? 0 : s,
+                   qf_col + b0, qf_pos + b0, cnt);
+        qf_cnt[g] = cnt[0] | (cnt[1] << 8) | (cnt[2] << 16) | (G << 24);
+        // backward: external columns of U row e, prev = the group after in the chunk
+        const int32_t be = Urowptr[e], bu = Urowptr[s];
+        const int mu = Urowptr[e + 1] - be - 1;
+        q_classify(mu, Ucol + be + 1, level, level[e], delta, false, last ? 0 : grp[g + 1], last ? 0 : grp[g + 2],
+                   qb_col + bu, qb_pos + bu, cnt);
+        qb_cnt[g] = cnt[0] | (cnt[1] << 8) | (cnt[2] << 16) | (G << 24);
+    }
+}
+
 static const int T_ROWS = 256;
 
 static unsigned grid_rows(gic_handle *h, int64_t n)
@@ -446,6 +531,12 @@ static void free_pattern(Pattern &p)
     cudaFree(p.sell_ptr);
     cudaFree(p.sell_w);
     cudaFree(p.sell_col);
+    cudaFree(p.qf_col);
+    cudaFree(p.qb_col);
+    cudaFree(p.qf_pos);
+    cudaFree(p.qb_pos);
+    cudaFree(p.qf_cnt);
+    cudaFree(p.qb_cnt);
     p = Pattern();
 }
 
@@ -545,6 +636,40 @@ static int build_sell(gic_handle *h, Pattern &P)
     return GIC_OK;
 }
 
+// Schedule of the warp-specialised solves, where every group fits them.
+static int build_qsched(gic_handle *h, Pattern &P)
+{
+    P.qready = 0;
+    // a group's early columns and its own right-hand side share the 64 lane slots
+    if (P.ngroups == 0 || P.max_group > 3 || P.max_ext_lower > QCOL - 3 || P.max_ext_upper > QCOL - 3) return GIC_OK;
+    const size_t nL = (size_t)(P.nnzL > 0 ? P.nnzL : 1);
+    GIC_CUDA_TRY(cudaMalloc(&P.qf_col, sizeof(int32_t) * nL));
+    GIC_CUDA_TRY(cudaMalloc(&P.qb_col, sizeof(int32_t) * nL));
+    GIC_CUDA_TRY(cudaMalloc(&P.qf_pos, nL));
+    GIC_CUDA_TRY(cudaMalloc(&P.qb_pos, nL));
+    GIC_CUDA_TRY(cudaMalloc(&P.qf_cnt, sizeof(int32_t) * (size_t)P.ngroups));
+    GIC_CUDA_TRY(cudaMalloc(&P.qb_cnt, sizeof(int32_t) * (size_t)P.ngroups));
+    int32_t *gchunk = nullptr;
+    GIC_CUDA_TRY(cudaMalloc(&gchunk, sizeof(int32_t) * (size_t)P.ngroups));
+    ++h->launches;
+    k_group_chunk<<<grid_rows(h, P.nchunks), T_ROWS, 0, h->stream>>>(P.nchunks, P.chunk_grp, gchunk);
+    ++h->launches;
+    k_qsched<<<grid_rows(h, P.ngroups), T_ROWS, 0, h->stream>>>(P.ngroups, P.grp, P.Lrowptr, P.Lcol, P.Urowptr, P.Ucol,
+                                                                 P.level, P.chunk_grp, gchunk, h->tune_qdelta,
+                                                                 P.qf_col, P.qf_pos, P.qf_cnt, P.qb_col, P.qb_pos,
+                                                                 P.qb_cnt);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(gchunk);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e, "build_qsched", __FILE__, __LINE__);
+        return GIC_ERR_CUDA;
+    }
+    P.qdelta = h->tune_qdelta;
+    P.qready = 1;
+    return GIC_OK;
+}
+
 static int analyze_impl(gic_handle *h, int64_t n, int64_t nnz, const int32_t *rowptr, const int32_t *col, Pattern &P)
 {
     P.n = n;
@@ -635,6 +760,7 @@ static int analyze_impl(gic_handle *h, int64_t n, int64_t nnz, const int32_t *ro
     if (flags & ERR_TIMEOUT) { rc = GIC_ERR_TIMEOUT; goto out; }
     STEP(build_schedule(h, P, gflag, gid, tmp2_a, tmp2_b));
     STEP(build_sell(h, P));
+    STEP(build_qsched(h, P));
 out:
 #undef STEP
 #undef CUDA_STEP

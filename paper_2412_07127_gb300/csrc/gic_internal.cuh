@@ -274,8 +274,24 @@ struct Pattern {
     int64_t *sell_ptr = nullptr;      // nslices+1 entry offsets
     int32_t *sell_w = nullptr;        // nslices widths
     int32_t *sell_col = nullptr;      // sell_nnz column indices
+    // Schedule of the warp-specialised solves (groups of <= 3 rows with at
+    // most QCOL - 3 external columns): every group's external columns in the
+    // order [early | late | prev] -- prev: rows of the group solved just
+    // before it in its chunk; late: columns within qdelta levels of the
+    // group (finished shortly before it); early: the rest -- with the
+    // original position of each column in the group's rows. Forward data
+    // sit at the group's first L offset (Lrowptr[s]), backward data at its
+    // first U offset (Urowptr[s]); qf_cnt / qb_cnt pack the counts as
+    // ne | nl << 8 | np << 16 | G << 24.
+    int qready = 0, qdelta = 0;
+    int32_t *qf_col = nullptr, *qb_col = nullptr;
+    uint8_t *qf_pos = nullptr, *qb_pos = nullptr;
+    int32_t *qf_cnt = nullptr, *qb_cnt = nullptr;
     int device = 0;
 };
+
+constexpr int QCOL = 64;   // external columns of a group in the warp-specialised solves
+constexpr int QLATE = 16;  // at most this many late columns per group
 
 constexpr int GMAX = 8;    // rows per group
 constexpr int MAXDIM = 48; // max lower entries of a row handled by IC(0)
@@ -296,7 +312,8 @@ struct gic_handle {
     long long launches = 0;        // kernels this handle has launched
     int tune_solve_warps_per_sm = 0; // cap on resident solve warps per SM (0: none)
     int tune_poll = gic::POLL_ONE_LANE; // polling configuration of the sync-free kernels
-    int tune_pipeline = 1;              // staged (cp.async) triangular solves when the pattern fits
+    int tune_pipeline = 2;              // 2: warp-specialised solves, 1: staged solves, 0: generic
+    int tune_qdelta = 6;                // level window of the "late" columns (pattern analysis)
 };
 
 namespace gic {

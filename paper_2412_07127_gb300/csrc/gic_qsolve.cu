@@ -1,0 +1,443 @@
+// gic_qsolve.cu -- A7b: warp-specialised sync-free triangular solves for
+// patterns whose row groups have at most 3 rows and at most QCOL - 3
+// external columns (the hex-element systems: one group per node, x-pencil chunks).
+//
+// Forward substitution (Eq. (11) read as y_i = (r_i - sum_{j<i} L_ij y_j) /
+// L_ii) is done one row group at a time. With D the group's dense lower
+// diagonal block and M = D^-1, the group's rows are
+//     y_g = M r_g - (M L_ext) y_ext,
+// so once the premultiplied coefficients K = M L_ext are formed for a factor
+// (q_setup, once per PCG run), every row of a group is an independent dot
+// product: no in-group substitution chain is left on the critical path.
+// Backward (L^T z = y) uses z_g = M^T y_g - (M^T U_ext) z_ext on U = L^T.
+//
+// Two warps share one chunk (a run of groups solved in order):
+//  * the producer stages a group's columns and coefficients in shared memory
+//    (cp.async, QD groups ahead, a ring of QR slots), loads the "early"
+//    dependencies (finished well before the group), reduces their part of
+//    the dot products across lanes and leaves base = M r_g - K_early y_early;
+//  * the finisher (lanes 0..G-1, one row each) adds the contribution of the
+//    previous group of the chunk from registers and of the few "late"
+//    dependencies (within a level window of the group), waiting only for
+//    those, and publishes y.
+// The producer's lane-parallel work runs while the finisher waits, so the
+// chain from one group to the next is a handful of FMAs plus the latency of
+// the dependencies themselves. Readiness is the solution word itself (a
+// signalling-NaN sentinel until written), every wait is bounded, and the
+// chunk order guarantees that the earliest unfinished chunk can always run.
+#include <limits.h>
+#include <math.h>
+
+#include "gic_internal.cuh"
+#include "gic_solve.cuh"
+
+namespace gic {
+
+constexpr int QR = 4;                    // ring slots per warp pair
+constexpr int QD = 2;                    // groups staged ahead by the producer
+constexpr int QPAIRS = SOLVE_BLOCK / 64; // warp pairs per block
+constexpr unsigned FULL = 0xffffffffu;
+
+template <typename T>
+struct QSlot {
+    T K[3][QCOL];      // premultiplied external coefficients, columns [early | late | prev]
+    T Mv[6];           // M = D^-1, packed lower triangle (t, u <= t) at t(t+1)/2 + u
+    T rr[3];           // right-hand side rows (forward: r, backward: y)
+    T base[3];         // M rr - early part, written by the producer
+    double rd[3];      // backward with PCG: r in FP64 for the fused r^T z
+    int32_t cols[QCOL];
+    int32_t s, cw;     // first row, packed counts
+};
+
+template <typename T>
+struct QPair {
+    QSlot<T> slot[QR];
+    int full, freed; // groups produced / finished by the pair so far
+};
+
+__device__ __forceinline__ int ld_vol(const int *p) { return *(volatile const int *)p; }
+__device__ __forceinline__ void st_vol(int *p, int v) { *(volatile int *)p = v; }
+
+// Bounded wait (one lane) until the shared counter *p reaches target.
+__device__ __forceinline__ bool wait_seq(const int *p, int target, unsigned *err)
+{
+    if (ld_vol(p) >= target) return true;
+    for (long long it = 0; it < SPIN_LIMIT; ++it) {
+        if (ld_vol(p) >= target) return true;
+        if ((it & 255) == 255 && *((volatile unsigned *)err) != 0u) return false;
+    }
+    atomicOr(err, ERR_TIMEOUT);
+    return false;
+}
+
+// the warp waits on a counter through lane 0; true in every lane when reached
+__device__ __forceinline__ bool warp_wait_seq(const int *p, int target, unsigned *err, int lane)
+{
+    int r = 1;
+    if (lane == 0) r = wait_seq(p, target, err) ? 1 : 0;
+    return __shfl_sync(FULL, r, 0) != 0;
+}
+
+template <typename T>
+__device__ __forceinline__ void q_stage(QSlot<T> &S, int32_t s, int32_t cw, int64_t b0, const int32_t *qcol,
+                                        const T *Kv, const T *rhs, const double *rd, int lane)
+{
+    const int m = (cw & 255) + ((cw >> 8) & 255) + ((cw >> 16) & 255), G = cw >> 24;
+    if (lane == 0) {
+        S.s = s;
+        S.cw = cw;
+    }
+    if (lane < m) cp_async_4(&S.cols[lane], qcol + b0 + lane);
+    if (lane + 32 < m) cp_async_4(&S.cols[lane + 32], qcol + b0 + lane + 32);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        if (t < G) {
+            const T *row = Kv + b0 + (int64_t)t * m;
+            if (lane < m) cp_async_t(&S.K[t][lane], row + lane);
+            if (lane + 32 < m) cp_async_t(&S.K[t][lane + 32], row + lane + 32);
+        }
+    }
+    if (lane < G * (G + 1) / 2) cp_async_t(&S.Mv[lane], Kv + b0 + (int64_t)G * m + lane);
+    if (lane < G) cp_async_t(&S.rr[lane], rhs + s + lane);
+    if (rd && lane < G) cp_async_8(&S.rd[lane], rd + s + lane);
+}
+
+// -M coefficient of right-hand-side entry u in row t of the group (forward:
+// y_t gets sum_{u<=t} M_tu r_u; backward: z_t gets sum_{u>=t} M_ut y_u)
+template <typename T, bool FWD>
+__device__ __forceinline__ T q_mcoef(const QSlot<T> &S, int t, int u, int G)
+{
+    if (u < 0 || u >= G) return (T)0;
+    if (FWD) return (u <= t) ? -S.Mv[t * (t + 1) / 2 + u] : (T)0;
+    return (u >= t) ? -S.Mv[u * (u + 1) / 2 + t] : (T)0;
+}
+
+// Producer of one chunk (groups in sweep order k = 0..cnt-1).
+template <typename T, bool FWD>
+__device__ __forceinline__ bool q_produce(QPair<T> &Q, int seq, int32_t g0, int32_t g1, const int32_t *grp,
+                                          const int32_t *rowptr, const int32_t *qcol, const int32_t *qcnt,
+                                          const T *Kv, const T *rhs, const T *x, const double *rd, unsigned *err,
+                                          int poll, int lane)
+{
+    const int cnt = g1 - g0;
+    int32_t hs = 0, hc = 0, hb = 0; // headers of 32 groups, one per lane
+    int wbase = -64;
+    bool ok = true;
+    auto stage = [&](int k) {
+        if (k - wbase >= 32) {
+            wbase = k;
+            const int kk = k + lane;
+            if (kk < cnt) {
+                const int32_t g = FWD ? g0 + kk : g1 - 1 - kk;
+                hs = grp[g];
+                hc = qcnt[g];
+                hb = rowptr[hs];
+            }
+        }
+        const int32_t s = __shfl_sync(FULL, hs, k - wbase), cw = __shfl_sync(FULL, hc, k - wbase);
+        const int32_t b0 = __shfl_sync(FULL, hb, k - wbase);
+        if (!warp_wait_seq(&Q.freed, seq + k - QR + 1, err, lane)) {
+            ok = false;
+            return;
+        }
+        q_stage<T>(Q.slot[(seq + k) % QR], s, cw, b0, qcol, Kv, rhs, rd, lane);
+    };
+#pragma unroll
+    for (int d = 0; d < QD; ++d) {
+        if (d < cnt && ok) stage(d);
+        cp_async_commit();
+    }
+    // early dependency values of the group about to be reduced (loaded one
+    // group ahead so their latency overlaps the previous reduction)
+    T v0 = 0, v1 = 0;
+    int32_t j0 = -1, j1 = -1;
+    auto load_early = [&](int k) {
+        cp_async_wait<QD - 1>();
+        __syncwarp();
+        const QSlot<T> &S = Q.slot[(seq + k) % QR];
+        const int ne = S.cw & 255;
+        j0 = (lane < ne) ? S.cols[lane] : -1;
+        j1 = (lane + 32 < ne) ? S.cols[lane + 32] : -1;
+        v0 = (j0 >= 0) ? ld_relaxed(x + j0) : (T)0;
+        v1 = (j1 >= 0) ? ld_relaxed(x + j1) : (T)0;
+    };
+    if (cnt > 0 && ok) load_early(0);
+    for (int k = 0; k < cnt && ok; ++k) {
+        if (k + QD < cnt) stage(k + QD);
+        cp_async_commit();
+        QSlot<T> &S = Q.slot[(seq + k) % QR];
+        const int ne = S.cw & 255, G = S.cw >> 24;
+        wait_pair<FWD, T>(x, j0, j1, v0, v1, err, poll);
+        // positions p < ne: early columns (K, y); ne <= p < ne + G: the
+        // group's own right-hand side (-M, rr), so a = K y_early - M rr
+        const int u0 = lane - ne, u1 = lane + 32 - ne;
+        const T w0 = (j0 >= 0) ? v0 : ((u0 >= 0 && u0 < G) ? S.rr[u0] : (T)0);
+        const T w1 = (j1 >= 0) ? v1 : ((u1 >= 0 && u1 < G) ? S.rr[u1] : (T)0);
+        const bool two = ne + G > 32; // uniform over the warp
+        T a[3];
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const T c0 = (t < G) ? ((j0 >= 0) ? S.K[t][lane] : q_mcoef<T, FWD>(S, t, u0, G)) : (T)0;
+            if (two) {
+                const T c1 = (t < G) ? ((j1 >= 0) ? S.K[t][lane + 32] : q_mcoef<T, FWD>(S, t, u1, G)) : (T)0;
+                a[t] = fma(c1, w1, c0 * w0);
+            } else {
+                a[t] = c0 * w0;
+            }
+        }
+        if (k + 1 < cnt) load_early(k + 1);
+        warp_sum_n<T, 3>(a, lane);
+        if (lane < G) S.base[lane] = -pick3<T>(lane, a[0], a[1], a[2]);
+        __threadfence_block();
+        __syncwarp();
+        if (lane == 0) st_vol(&Q.full, seq + k + 1);
+    }
+    cp_async_wait<0>();
+    __syncwarp();
+    return ok;
+}
+
+// Finisher of one chunk: lanes t < G own row t of the group.
+template <typename T, bool PCG>
+__device__ __forceinline__ bool q_finish(QPair<T> &Q, int seq, int cnt, T *x, T *yreset, unsigned *err, int lane,
+                                         double &dot)
+{
+    T yp = 0;          // lane t: row t of the previous group of the chunk
+    int32_t prev_s = 0;
+    for (int k = 0; k < cnt; ++k) {
+        if (!warp_wait_seq(&Q.full, seq + k + 1, err, lane)) return false;
+        __threadfence_block();
+        const QSlot<T> &S = Q.slot[(seq + k) % QR];
+        const int32_t cw = S.cw, s = S.s;
+        const int ne = cw & 255, nl = (cw >> 8) & 255, np = (cw >> 16) & 255, G = cw >> 24;
+        const T p0 = __shfl_sync(FULL, yp, 0), p1 = __shfl_sync(FULL, yp, 1), p2 = __shfl_sync(FULL, yp, 2);
+        T yv = 0;
+        if (lane < G) {
+            const int t = lane;
+            T lv[QLATE];
+#pragma unroll
+            for (int j = 0; j < QLATE; ++j) lv[j] = (j < nl) ? ld_relaxed(x + S.cols[ne + j]) : (T)0;
+            T acc = S.base[t], acc2 = 0;
+            for (int j = 0; j < np; ++j) {
+                const int32_t cc = S.cols[ne + nl + j];
+                acc = fma(-S.K[t][ne + nl + j], pick3<T>(cc - prev_s, p0, p1, p2), acc);
+            }
+#pragma unroll
+            for (int j = 0; j < QLATE; ++j) {
+                if (j < nl) {
+                    T v = lv[j];
+                    if (is_sentinel(v)) v = wait_word(x + S.cols[ne + j], err, 0);
+                    if (j & 1) acc2 = fma(-S.K[t][ne + j], v, acc2);
+                    else acc = fma(-S.K[t][ne + j], v, acc);
+                }
+            }
+            yv = acc + acc2;
+            st_relaxed(x + s + t, yv);
+            if (PCG) {
+                yreset[s + t] = sentinel_of<T>();
+                dot = fma(S.rd[t], (double)yv, dot);
+            }
+        }
+        yp = yv;
+        __threadfence_block();
+        __syncwarp();
+        if (lane == 0) st_vol(&Q.freed, seq + k + 1);
+        prev_s = s;
+    }
+    return true;
+}
+
+// FWD: L y = r (x = y, rhs = r). Backward: L^T z = y (x = z, rhs = y); with
+// PCG it also resets y to the sentinel for the next forward sweep and forms
+// r^T z in FP64, then beta = r_k^T z_k / r_{k-1}^T z_{k-1} (Algorithm 1) in
+// the last warp to finish. x must hold the sentinel.
+template <typename T, bool FWD, bool PCG>
+__global__ void __launch_bounds__(SOLVE_BLOCK) k_qsolve(int32_t nchunks, const int32_t *__restrict__ ord,
+                                                        const int32_t *__restrict__ chunk_grp,
+                                                        const int32_t *__restrict__ grp,
+                                                        const int32_t *__restrict__ rowptr,
+                                                        const int32_t *__restrict__ qcol,
+                                                        const int32_t *__restrict__ qcnt, const T *__restrict__ Kv,
+                                                        const T *rhs, T *x, T *yreset, const double *__restrict__ rd,
+                                                        double *partials, unsigned *err, int poll, Scalars *sc)
+{
+    if (sc && sc->done) return;
+    extern __shared__ __align__(16) unsigned char q_raw[];
+    QPair<T> *pairs = reinterpret_cast<QPair<T> *>(q_raw);
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const bool producer = (wib & 1) == 0;
+    QPair<T> &Q = pairs[wib >> 1];
+    if (producer && lane == 0) {
+        Q.full = 0;
+        Q.freed = 0;
+    }
+    __syncthreads();
+    const int64_t gpair = (int64_t)blockIdx.x * QPAIRS + (wib >> 1);
+    const int64_t npair = (int64_t)gridDim.x * QPAIRS;
+    int seq = 0;
+    double dot = 0.0;
+    bool ok = true;
+    for (int64_t pos = gpair; pos < nchunks && ok; pos += npair) {
+        const int32_t c = ord[pos];
+        const int32_t g0 = chunk_grp[c], g1 = chunk_grp[c + 1];
+        if (producer)
+            ok = q_produce<T, FWD>(Q, seq, g0, g1, grp, rowptr, qcol, qcnt, Kv, rhs, x, PCG ? rd : nullptr, err, poll,
+                                   lane);
+        else
+            ok = q_finish<T, PCG>(Q, seq, g1 - g0, x, yreset, err, lane, dot);
+        seq += g1 - g0;
+    }
+    if (PCG) {
+        dot = warp_sum(dot);
+        const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+        if (lane == 0) partials[w] = dot;
+        __syncwarp();
+        unsigned last = 0;
+        if (lane == 0) {
+            __threadfence();
+            last = (atomicAdd(&sc->counter, 1u) == (unsigned)nw - 1u);
+        }
+        last = __shfl_sync(FULL, last, 0);
+        if (last) {
+            __threadfence();
+            const double rz = warp_sum_partials(partials, (int)nw);
+            if (lane == 0) {
+                sc->counter = 0;
+                if (!(rz > 0.0) || !isfinite(rz)) {
+                    sc->status = GIC_ERR_BREAKDOWN;
+                    sc->done = 1;
+                } else {
+                    sc->beta = (sc->iter == 0) ? 0.0 : rz / sc->rz;
+                    sc->rz = rz;
+                }
+            }
+        }
+    }
+}
+
+// Premultiplied group blocks of a factor, computed in FP64 and stored in TL:
+// forward K = M L_ext in the L layout (rows t of the group at
+// Lrowptr[s] + t m, columns in the schedule's order, then M packed), backward
+// K = M^T U_ext in the U layout at Urowptr[s].
+template <typename TL>
+__global__ void k_qsetup(int32_t ngroups, const int32_t *__restrict__ grp, const int32_t *__restrict__ Lrowptr,
+                         const int32_t *__restrict__ Urowptr, const int32_t *__restrict__ tperm,
+                         const uint8_t *__restrict__ qf_pos, const uint8_t *__restrict__ qb_pos,
+                         const TL *__restrict__ Lval, TL *__restrict__ Kf, TL *__restrict__ Kb)
+{
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = grp[g], G = grp[g + 1] - s, e = s + G - 1;
+        const int64_t b0 = Lrowptr[s];
+        const int m = (int)(Lrowptr[s + 1] - b0 - 1);
+        double D[3][3] = {}, M[3][3] = {};
+        for (int t = 0; t < G; ++t)
+            for (int u = 0; u <= t; ++u) D[t][u] = (double)Lval[Lrowptr[s + t] + m + u];
+        for (int t = 0; t < G; ++t) {
+            M[t][t] = 1.0 / D[t][t];
+            for (int u = 0; u < t; ++u) {
+                double a = 0.0;
+                for (int v = u; v < t; ++v) a = fma(D[t][v], M[v][u], a);
+                M[t][u] = -a * M[t][t];
+            }
+        }
+        for (int k = 0; k < m; ++k) {
+            const int j = qf_pos[b0 + k];
+            for (int t = 0; t < G; ++t) {
+                double a = 0.0;
+                for (int u = 0; u <= t; ++u) a = fma(M[t][u], (double)Lval[Lrowptr[s + u] + j], a);
+                Kf[b0 + (int64_t)t * m + k] = (TL)a;
+            }
+        }
+        const int64_t bu = Urowptr[s];
+        const int mu = (int)(Urowptr[e + 1] - Urowptr[e] - 1);
+        for (int k = 0; k < mu; ++k) {
+            const int j = qb_pos[bu + k];
+            for (int t = 0; t < G; ++t) {
+                double a = 0.0;
+                for (int u = t; u < G; ++u) a = fma(M[u][t], (double)Lval[tperm[Urowptr[s + u] + (G - u) + j]], a);
+                Kb[bu + (int64_t)t * mu + k] = (TL)a;
+            }
+        }
+        for (int t = 0; t < G; ++t)
+            for (int u = 0; u <= t; ++u) {
+                Kf[b0 + (int64_t)G * m + t * (t + 1) / 2 + u] = (TL)M[t][u];
+                Kb[bu + (int64_t)G * mu + t * (t + 1) / 2 + u] = (TL)M[t][u];
+            }
+    }
+}
+
+int q_setup(gic_handle *h, const Pattern &P, bool f32, const void *Lval, void *Kf, void *Kb)
+{
+    if (!P.qready) return GIC_ERR_UNSUPPORTED;
+    int64_t b = (P.ngroups + 127) / 128, cap = (int64_t)h->num_sms * 8;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    ++h->launches;
+    if (f32)
+        k_qsetup<float><<<(unsigned)b, 128, 0, h->stream>>>(P.ngroups, P.grp, P.Lrowptr, P.Urowptr, P.tperm, P.qf_pos,
+                                                            P.qb_pos, (const float *)Lval, (float *)Kf, (float *)Kb);
+    else
+        k_qsetup<double><<<(unsigned)b, 128, 0, h->stream>>>(P.ngroups, P.grp, P.Lrowptr, P.Urowptr, P.tperm, P.qf_pos,
+                                                             P.qb_pos, (const double *)Lval, (double *)Kf, (double *)Kb);
+    GIC_CUDA_TRY(cudaGetLastError());
+    return GIC_OK;
+}
+
+template <typename T, bool FWD, bool PCG>
+static int q_launch(gic_handle *h, const Pattern &P, const T *Kv, const T *rhs, T *x, T *yreset, const double *rd,
+                    double *partials, Scalars *sc)
+{
+    if (!P.qready) return GIC_ERR_UNSUPPORTED;
+    int32_t nc = P.nchunks;
+    const int32_t *ord = FWD ? P.ord_f : P.ord_b, *cg = P.chunk_grp, *g = P.grp;
+    const int32_t *rp = FWD ? P.Lrowptr : P.Urowptr;
+    const int32_t *qc = FWD ? P.qf_col : P.qb_col, *qn = FWD ? P.qf_cnt : P.qb_cnt;
+    unsigned *er = h->dev_err;
+    int poll = h->tune_poll;
+    void *args[] = {&nc, &ord, &cg, &g, &rp, &qc, &qn, &Kv, &rhs, &x, &yreset, &rd, &partials, &er, &poll, &sc};
+    int64_t need = 2 * (int64_t)nc; // warps: one pair per chunk
+    if (h->tune_solve_warps_per_sm > 0) {
+        const int64_t cap = 2 * (int64_t)h->tune_solve_warps_per_sm * h->num_sms;
+        if (need > cap) need = cap;
+    }
+    if (PCG && need > MAX_PARTIALS) need = MAX_PARTIALS; // grid warps <= partial slots
+    const size_t smem = sizeof(QPair<T>) * QPAIRS;
+    static bool ad[64] = {};
+    if (!ad[h->device & 63]) {
+        GIC_CUDA_TRY(cudaFuncSetAttribute(k_qsolve<T, FWD, PCG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+        ad[h->device & 63] = true;
+    }
+    return launch_persistent(h, (const void *)k_qsolve<T, FWD, PCG>, SOLVE_BLOCK, smem, need, args);
+}
+
+int q_lsolve(gic_handle *h, const Pattern &P, bool f32, const void *Kf, const void *r, void *y, const Scalars *sc)
+{
+    Scalars *s = const_cast<Scalars *>(sc);
+    if (f32)
+        return q_launch<float, true, false>(h, P, (const float *)Kf, (const float *)r, (float *)y, nullptr, nullptr,
+                                            nullptr, s);
+    return q_launch<double, true, false>(h, P, (const double *)Kf, (const double *)r, (double *)y, nullptr, nullptr,
+                                         nullptr, s);
+}
+
+int q_ltsolve(gic_handle *h, const Pattern &P, bool f32, bool pcg, const void *Kb, void *y, void *z,
+              const double *rd, double *partials, Scalars *sc)
+{
+    if (f32) {
+        if (pcg)
+            return q_launch<float, false, true>(h, P, (const float *)Kb, (const float *)y, (float *)z, (float *)y, rd,
+                                                partials, sc);
+        return q_launch<float, false, false>(h, P, (const float *)Kb, (const float *)y, (float *)z, nullptr, nullptr,
+                                             nullptr, sc);
+    }
+    if (pcg)
+        return q_launch<double, false, true>(h, P, (const double *)Kb, (const double *)y, (double *)z, (double *)y, rd,
+                                             partials, sc);
+    return q_launch<double, false, false>(h, P, (const double *)Kb, (const double *)y, (double *)z, nullptr, nullptr,
+                                          nullptr, sc);
+}
+
+}  // namespace gic

@@ -22,24 +22,12 @@
 #include <stdio.h>
 
 #include "gic_internal.cuh"
+#include "gic_solve.cuh"
 
 namespace gic {
 
-struct Scalars {
-    double rz;    // r_k^T z_k
-    double pw;    // p^T A p
-    double alpha, beta;
-    double rr, bb; // ||r||^2, ||b||^2
-    double tol;
-    int iter, maxit, done, status;
-    unsigned counter; // last-block ticket
-    unsigned pad;
-};
-
 constexpr int SPMV_BLOCK = 256;
 constexpr int VEC_BLOCK = 256;
-constexpr int SOLVE_BLOCK = 256;
-constexpr int MAX_PARTIALS = 1 << 16;
 
 // ------------------------------------------------------------ helpers
 __device__ __forceinline__ double block_sum(double v, double *sh)
@@ -64,14 +52,6 @@ __device__ __forceinline__ bool last_block(unsigned *counter, unsigned count)
     return t == count - 1;
 }
 
-// deterministic sum of partials[0..count) by one warp (lane-strided, then tree)
-__device__ __forceinline__ double warp_sum_partials(const double *partials, int count)
-{
-    int lane = threadIdx.x & 31;
-    double s = 0.0;
-    for (int k = lane; k < count; k += 32) s += ((volatile const double *)partials)[k];
-    return warp_sum(s);
-}
 
 // ------------------------------------------------------------ SpTRSV
 // Schedule: the pattern's chunks (runs of consecutive row groups with
@@ -468,39 +448,6 @@ __device__ __forceinline__ void tri_index(int q, int &t, int &u)
     while (q >= t) { q -= t; ++t; }
     u = q;
 }
-
-// Warp sum of GM values, result in every lane. For three values the first
-// two butterfly levels exchange halves so each lane adds 2, then 1 value.
-template <typename T, int GM>
-__device__ __forceinline__ void warp_sum_n(T (&a)[GM], int lane)
-{
-    if (GM == 3) {
-        const bool hi16 = lane & 16;
-        // level 16: lanes < 16 keep {0,1}, lanes >= 16 keep {2, pad}
-        T k0 = hi16 ? a[2] : a[0], k1 = hi16 ? (T)0 : a[1];
-        T s0 = hi16 ? a[0] : a[2], s1 = hi16 ? a[1] : (T)0;
-        k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
-        k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
-        // level 8: bit3 = 0 keeps k0, bit3 = 1 keeps k1
-        const bool b8 = lane & 8;
-        T kk = b8 ? k1 : k0, ss = b8 ? k0 : k1;
-        kk += __shfl_xor_sync(0xffffffffu, ss, 8);
-#pragma unroll
-        for (int o = 4; o > 0; o >>= 1) kk += __shfl_xor_sync(0xffffffffu, kk, o);
-        // totals: lanes 0-7 row 0, 8-15 row 1, 16-23 row 2
-        a[0] = __shfl_sync(0xffffffffu, kk, 0);
-        a[1] = __shfl_sync(0xffffffffu, kk, 8);
-        a[2] = __shfl_sync(0xffffffffu, kk, 16);
-    } else {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-            for (int t = 0; t < GM; ++t) a[t] += __shfl_xor_sync(0xffffffffu, a[t], o);
-    }
-}
-
-template <typename T>
-__device__ __forceinline__ T pick3(int idx, T a, T b, T c) { return idx == 0 ? a : (idx == 1 ? b : c); }
 
 template <typename T, int GM>
 __device__ __forceinline__ void fill_stage_L(PStage<T, GM> &st, const PWarp<T, GM> &W, int k, const int32_t *Lcol,
@@ -1172,18 +1119,22 @@ __global__ void k_factor_setup(int64_t n, int64_t nnzL, const int32_t *tperm, co
 }
 
 // ------------------------------------------------------------ host side
-int launch_persistent(gic_handle *h, const void *fn, int block, size_t smem, int64_t warps_needed, void **args);
 
 static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // How the solves of one factor run: generic (any pattern, FP64 vectors and
-// sums) or pipelined (groups of <= 3 rows, <= WCOL external columns), each
-// with an FP64 or an FP32 factor. The pipelined FP32 mode keeps its vectors
+// sums), pipelined (groups of <= 3 rows, <= WCOL external columns) or
+// warp-specialised on premultiplied group blocks (gic_qsolve.cu; groups of
+// <= 3 rows, <= QCOL external columns), each with an FP64 or an FP32
+// factor. The pipelined and warp-specialised FP32 modes keep their vectors
 // and sums in FP32 too.
-enum SolveMode { MODE_GEN64, MODE_GEN32, MODE_P64, MODE_P32, MODE_IDENT };
+enum SolveMode { MODE_GEN64, MODE_GEN32, MODE_P64, MODE_P32, MODE_Q64, MODE_Q32, MODE_IDENT };
+
+static bool f32_vectors(SolveMode m) { return m == MODE_P32 || m == MODE_Q32; }
 
 struct SolveWs {
-    void *Uval;
+    void *Uval;                   // U values (generic, pipelined) or backward blocks (warp-specialised)
+    void *Qf;                     // forward premultiplied blocks (warp-specialised)
     double *invd;                 // generic modes and P64
     float *invd32, *r32, *y32, *z32; // P32
     double *r, *y, *z, *p, *w;
@@ -1201,6 +1152,7 @@ static bool pipelined_fits(const Pattern &P)
 static SolveMode solve_mode(const gic_handle *h, const Pattern &P, int l_dtype)
 {
     if (l_dtype == GIC_IDENTITY) return MODE_IDENT;
+    if (h->tune_pipeline >= 2 && P.qready) return (l_dtype == GIC_F32) ? MODE_Q32 : MODE_Q64;
     const bool pipe = h->tune_pipeline && pipelined_fits(P);
     if (l_dtype == GIC_F32) return pipe ? MODE_P32 : MODE_GEN32;
     return pipe ? MODE_P64 : MODE_GEN64;
@@ -1215,6 +1167,7 @@ static SolveWs carve(const Pattern &P, int l_dtype, bool p32, void *ws)
     o.sc = (Scalars *)(c + off); off += align_up(sizeof(Scalars));
     o.partials = (double *)(c + off); off += align_up(sizeof(double) * 2 * MAX_PARTIALS);
     o.Uval = c + off; off += (l_dtype == GIC_IDENTITY) ? 0 : align_up(es * (size_t)P.nnzL);
+    o.Qf = c + off; off += (l_dtype == GIC_IDENTITY) ? 0 : align_up(es * (size_t)P.nnzL);
     o.invd = (double *)(c + off); off += (l_dtype == GIC_IDENTITY) ? 0 : align_up(8 * (size_t)P.n);
     if (p32) {
         float **fv[4] = {&o.invd32, &o.r32, &o.y32, &o.z32};
@@ -1381,6 +1334,7 @@ static int launch_ltsolve_p(gic_handle *h, const Pattern &P, const T *Uval, cons
 // Transposed values and reciprocal diagonal for the mode.
 static int setup_factor(gic_handle *h, const Pattern &P, SolveMode mode, const void *Lval, const SolveWs &W)
 {
+    if (mode == MODE_Q64 || mode == MODE_Q32) return q_setup(h, P, mode == MODE_Q32, Lval, W.Qf, W.Uval);
     int64_t cnt = P.nnzL > P.n ? P.nnzL : P.n;
     unsigned gr = vec_grid(h, cnt, 256);
     ++h->launches;
@@ -1455,6 +1409,8 @@ static int precondition(gic_handle *h, const Pattern &P, SolveMode mode, const v
     case MODE_GEN32: GIC_TRY(launch_lsolve_gen<float>(h, P, (const float *)Lval, W.invd, W.r, W.y, W.sc)); break;
     case MODE_P64: GIC_TRY(launch_lsolve_p<double>(h, P, (const double *)Lval, W.invd, W.r, W.y, W.sc)); break;
     case MODE_P32: GIC_TRY(launch_lsolve_p<float>(h, P, (const float *)Lval, W.invd32, W.r32, W.y32, W.sc)); break;
+    case MODE_Q64: GIC_TRY(q_lsolve(h, P, false, W.Qf, W.r, W.y, W.sc)); break;
+    case MODE_Q32: GIC_TRY(q_lsolve(h, P, true, W.Qf, W.r32, W.y32, W.sc)); break;
     default: break;
     }
     PROF_END(GIC_PROF_LSOLVE);
@@ -1473,6 +1429,8 @@ static int precondition(gic_handle *h, const Pattern &P, SolveMode mode, const v
         GIC_TRY((launch_ltsolve_p<float, true>(h, P, (const float *)W.Uval, W.invd32, W.y32, W.z32, W.r, W.partials,
                                                W.sc)));
         break;
+    case MODE_Q64: GIC_TRY(q_ltsolve(h, P, false, true, W.Uval, W.y, W.z, W.r, W.partials, W.sc)); break;
+    case MODE_Q32: GIC_TRY(q_ltsolve(h, P, true, true, W.Uval, W.y32, W.z32, W.r, W.partials, W.sc)); break;
     default: break;
     }
     PROF_END(GIC_PROF_LTSOLVE);
@@ -1498,7 +1456,7 @@ static int pcg_iteration(gic_handle *h, const Pattern &P, SolveMode mode, const 
         GIC_TRY(precondition(h, P, mode, Lval, W));
         PROF_BEGIN(GIC_PROF_VECTOR);
         ++h->launches;
-        if (mode == MODE_P32)
+        if (f32_vectors(mode))
             k_update_p<false, float><<<vg, VEC_BLOCK, 0, h->stream>>>(n, W.z32, W.p, W.r, W.sc);
         else
             k_update_p<false, double><<<vg, VEC_BLOCK, 0, h->stream>>>(n, W.z, W.p, W.r, W.sc);
@@ -1513,7 +1471,7 @@ static int pcg_iteration(gic_handle *h, const Pattern &P, SolveMode mode, const 
     PROF_END(GIC_PROF_SPMV);
     PROF_BEGIN(GIC_PROF_VECTOR);
     ++h->launches;
-    k_update_xr<<<vg, VEC_BLOCK, 0, h->stream>>>(n, x, W.r, W.p, W.w, mode == MODE_P32 ? W.r32 : nullptr, W.partials,
+    k_update_xr<<<vg, VEC_BLOCK, 0, h->stream>>>(n, x, W.r, W.p, W.w, f32_vectors(mode) ? W.r32 : nullptr, W.partials,
                                                  W.sc);
     GIC_CUDA_TRY(cudaGetLastError());
     PROF_END(GIC_PROF_VECTOR);
@@ -1531,7 +1489,7 @@ static int pcg_run(gic_handle *h, const Pattern &P, SolveMode mode, const double
     if (mode != MODE_IDENT) {
         GIC_TRY(setup_factor(h, P, mode, Lval, W));
         ++h->launches;
-        if (mode == MODE_P32) k_fill_sentinel_t<float><<<vg, 256, 0, h->stream>>>(n, W.y32, W.z32);
+        if (f32_vectors(mode)) k_fill_sentinel_t<float><<<vg, 256, 0, h->stream>>>(n, W.y32, W.z32);
         else k_fill_sentinel_t<double><<<vg, 256, 0, h->stream>>>(n, W.y, W.z);
     }
     ++h->launches;
@@ -1543,7 +1501,7 @@ static int pcg_run(gic_handle *h, const Pattern &P, SolveMode mode, const double
         n, P.nslices, P.sell_ptr, P.sell_w, P.sell_col, W.sval, x, W.r, b, W.partials, W.sc);
     GIC_CUDA_TRY(cudaGetLastError());
     PROF_END(GIC_PROF_SPMV);
-    if (mode == MODE_P32) {
+    if (f32_vectors(mode)) {
         ++h->launches;
         k_convert_f64_f32<<<vg, 256, 0, h->stream>>>(n, W.r, W.r32);
     }
@@ -1597,12 +1555,12 @@ static int standalone_solve(gic_handle *h, const Pattern &p, const void *valL, i
                             double *out, void *ws, size_t ws_bytes, bool forward)
 {
     const SolveMode mode = solve_mode(h, p, l_dtype);
-    SolveWs W = carve(p, l_dtype, mode == MODE_P32, ws);
+    SolveWs W = carve(p, l_dtype, f32_vectors(mode), ws);
     if (ws_bytes < W.bytes) return GIC_ERR_WORKSPACE;
     const unsigned vg = vec_grid(h, p.n, 256);
     GIC_TRY(setup_factor(h, p, mode, valL, W));
     Prof &pr = prof_of(h);
-    if (mode == MODE_P32) {
+    if (f32_vectors(mode)) {
         ++h->launches;
         k_convert_f64_f32<<<vg, 256, 0, h->stream>>>(p.n, in, W.r32); // the input, whichever sweep
         ++h->launches;
@@ -1618,6 +1576,8 @@ static int standalone_solve(gic_handle *h, const Pattern &p, const void *valL, i
         case MODE_GEN32: GIC_TRY(launch_lsolve_gen<float>(h, p, (const float *)valL, W.invd, in, out, nullptr)); break;
         case MODE_P64: GIC_TRY(launch_lsolve_p<double>(h, p, (const double *)valL, W.invd, in, out, nullptr)); break;
         case MODE_P32: GIC_TRY(launch_lsolve_p<float>(h, p, (const float *)valL, W.invd32, W.r32, W.y32, nullptr)); break;
+        case MODE_Q64: GIC_TRY(q_lsolve(h, p, false, W.Qf, in, out, nullptr)); break;
+        case MODE_Q32: GIC_TRY(q_lsolve(h, p, true, W.Qf, W.r32, W.y32, nullptr)); break;
         default: break;
         }
         PROF_END(GIC_PROF_LSOLVE);
@@ -1638,11 +1598,13 @@ static int standalone_solve(gic_handle *h, const Pattern &p, const void *valL, i
             GIC_TRY((launch_ltsolve_p<float, false>(h, p, (const float *)W.Uval, W.invd32, W.r32, W.y32, nullptr, nullptr,
                                                    nullptr)));
             break;
+        case MODE_Q64: GIC_TRY(q_ltsolve(h, p, false, false, W.Uval, yy, out, nullptr, nullptr, nullptr)); break;
+        case MODE_Q32: GIC_TRY(q_ltsolve(h, p, true, false, W.Uval, W.r32, W.y32, nullptr, nullptr, nullptr)); break;
         default: break;
         }
         PROF_END(GIC_PROF_LTSOLVE);
     }
-    if (mode == MODE_P32) {
+    if (f32_vectors(mode)) {
         ++h->launches;
         k_convert_f32_f64<<<vg, 256, 0, h->stream>>>(p.n, W.y32, out);
     }
@@ -1773,6 +1735,7 @@ int gic_set_tuning(gic_handle *h, int key, int value)
     case GIC_TUNE_SOLVE_WARPS_PER_SM: h->tune_solve_warps_per_sm = value; return GIC_OK;
     case GIC_TUNE_POLL: h->tune_poll = value; return GIC_OK;
     case GIC_TUNE_PIPELINE: h->tune_pipeline = value; return GIC_OK;
+    case GIC_TUNE_QDELTA: h->tune_qdelta = value; return GIC_OK;
     default: return GIC_ERR_INVALID_ARG;
     }
 }

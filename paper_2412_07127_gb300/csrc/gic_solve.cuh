@@ -1,0 +1,76 @@
+// gic_solve.cuh -- pieces shared by the PCG driver (gic_solve.cu) and the
+// warp-specialised triangular solves (gic_qsolve.cu).
+#pragma once
+#include "gic_internal.cuh"
+
+namespace gic {
+
+// Device-resident scalars of one PCG run (Supplementary Algorithm 1).
+struct Scalars {
+    double rz;    // r_k^T z_k
+    double pw;    // p^T A p
+    double alpha, beta;
+    double rr, bb; // ||r||^2, ||b||^2
+    double tol;
+    int iter, maxit, done, status;
+    unsigned counter; // last-block ticket
+    unsigned pad;
+};
+
+constexpr int SOLVE_BLOCK = 256;
+constexpr int MAX_PARTIALS = 1 << 16;
+
+// deterministic sum of partials[0..count) by one warp (lane-strided, then tree)
+__device__ __forceinline__ double warp_sum_partials(const double *partials, int count)
+{
+    int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int k = lane; k < count; k += 32) s += ((volatile const double *)partials)[k];
+    return warp_sum(s);
+}
+
+// Warp sum of GM values, result in every lane. For three values the first
+// two butterfly levels exchange halves so each lane adds 2, then 1 value.
+template <typename T, int GM>
+__device__ __forceinline__ void warp_sum_n(T (&a)[GM], int lane)
+{
+    if (GM == 3) {
+        const bool hi16 = lane & 16;
+        // level 16: lanes < 16 keep {0,1}, lanes >= 16 keep {2, pad}
+        T k0 = hi16 ? a[2] : a[0], k1 = hi16 ? (T)0 : a[1];
+        T s0 = hi16 ? a[0] : a[2], s1 = hi16 ? a[1] : (T)0;
+        k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+        k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+        // level 8: bit3 = 0 keeps k0, bit3 = 1 keeps k1
+        const bool b8 = lane & 8;
+        T kk = b8 ? k1 : k0, ss = b8 ? k0 : k1;
+        kk += __shfl_xor_sync(0xffffffffu, ss, 8);
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) kk += __shfl_xor_sync(0xffffffffu, kk, o);
+        // totals: lanes 0-7 row 0, 8-15 row 1, 16-23 row 2
+        a[0] = __shfl_sync(0xffffffffu, kk, 0);
+        a[1] = __shfl_sync(0xffffffffu, kk, 8);
+        a[2] = __shfl_sync(0xffffffffu, kk, 16);
+    } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int t = 0; t < GM; ++t) a[t] += __shfl_xor_sync(0xffffffffu, a[t], o);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T pick3(int idx, T a, T b, T c) { return idx == 0 ? a : (idx == 1 ? b : c); }
+
+
+int launch_persistent(gic_handle *h, const void *fn, int block, size_t smem, int64_t warps_needed, void **args);
+
+// Warp-specialised solves (gic_qsolve.cu). q_setup writes the premultiplied
+// group blocks of a factor (TL = double or float) into Kf (forward, L
+// layout) and Kb (backward, U layout); the solves then run on them.
+int q_setup(gic_handle *h, const Pattern &P, bool f32, const void *Lval, void *Kf, void *Kb);
+int q_lsolve(gic_handle *h, const Pattern &P, bool f32, const void *Kf, const void *r, void *y, const Scalars *sc);
+int q_ltsolve(gic_handle *h, const Pattern &P, bool f32, bool pcg, const void *Kb, void *y, void *z,
+              const double *rd, double *partials, Scalars *sc);
+
+}  // namespace gic

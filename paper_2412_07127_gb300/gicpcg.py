@@ -311,7 +311,7 @@ def error_flags(h: Handle):
     return f.value
 
 
-GIC_TUNE_SOLVE_WARPS_PER_SM, GIC_TUNE_POLL, GIC_TUNE_PIPELINE = 1, 2, 3
+GIC_TUNE_SOLVE_WARPS_PER_SM, GIC_TUNE_POLL, GIC_TUNE_PIPELINE, GIC_TUNE_QDELTA = 1, 2, 3, 4
 POLL_ONE_LANE = 1 << 16
 
 

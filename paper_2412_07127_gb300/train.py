@@ -41,6 +41,10 @@ class Trainer:
         rp, col, _ = self._assemble(0)
         self.rp, self.col = rp, col          # kept alive: the pattern borrows them
         self.P = G.Pattern(h, rp, col)
+        # one system's pattern: IC(0) and its shift rule run per system
+        _, self.nnz1 = G.fem_hex_sizes(N)
+        self.rp1, self.col1 = rp[:self.n + 1].clone(), col[:self.nnz1].clone()
+        self.P1 = G.Pattern(h, self.rp1, self.col1)
         self.ws = G.gnn_workspace(h, self.P, batch, training=True)
         self.pws = G.probe_workspace(h, self.P, batch, probes)
         self.shifts = []
@@ -56,10 +60,14 @@ class Trainer:
     def batch(self, k):
         """Device inputs of batch k: (x9, e0, A_hat, L_IC_hat, Z)."""
         _, _, v = self._assemble(k)
-        LIC, alpha, bad = G.ic0_auto(self.h, self.P, v)
-        if bad != -1:
-            raise RuntimeError(f"IC(0) failed on batch {k} even with shifts")
-        self.shifts.append(alpha)
+        LIC = torch.empty(self.P.nnzL, dtype=torch.float64, device=self.dev)
+        nL = self.P1.nnzL
+        for j in range(self.B):   # the batch's L is the concatenation of the systems' L
+            _, alpha, bad = G.ic0_auto(self.h, self.P1, v[j * self.nnz1:(j + 1) * self.nnz1],
+                                       out=LIC[j * nL:(j + 1) * nL])
+            if bad != -1:
+                raise RuntimeError(f"IC(0) failed on batch {k} even with shifts")
+            self.shifts.append(alpha)
         x9, e0, scale, Ahat = G.features(self.h, self.P, v, ngraphs=self.B, with_ahat=True)
         LIChat = G.scale_factor(self.h, self.P, LIC, scale, ngraphs=self.B)
         Z = np.concatenate([I.probes(self.m, self.n, s) for s in self._seeds(k)], axis=1)
