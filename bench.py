@@ -82,17 +82,31 @@ def workload_config(N, theta_src, ldtype):
             "N": N, "n": n, "nnz": nnz, "nnzL": nnzL, "levels": lev,
             "gnn_weights": theta_src, "l_dtype": ldtype,
             "l2": (f"inputs larger than L2 (A {12 * nnz / 1e6:.0f} MB, L {12 * nnzL / 1e6:.0f} MB "
-                   f"in FP64); no flush" if 12 * nnzL > 129e6 else "inputs smaller than L2; no flush")}
+                   f"in FP64); no flush" if 12 * nnz > 129e6 else "inputs smaller than L2; no flush")}
 
 
 def load_theta(N_PARAMS):
     import numpy as np
     from paper_2412_07127_gb300 import inputs as I
+    from paper_2412_07127_gb300.train import load_weights
     if os.path.exists(WEIGHTS):
-        th = np.load(WEIGHTS).astype(np.float32)
+        th, _ = load_weights(WEIGHTS)
         assert th.size == N_PARAMS
         return th, "trained (" + os.path.relpath(WEIGHTS, ROOT) + ")"
     return I.gnn_init(0, out_scale=0.02).astype(np.float32), "random init (seed 0, last layer x0.02)"
+
+
+def gnn_policy():
+    """The shipped weights' validation record and fallback decision."""
+    from paper_2412_07127_gb300.train import load_weights
+    if not os.path.exists(WEIGHTS):
+        return None
+    _, meta = load_weights(WEIGHTS)
+    if not meta:
+        return None
+    v = meta["validation"]
+    return {"use_gnn": meta["use_gnn"], "validation_iters_ic0": v["iters_ic0_mean"],
+            "validation_iters_gnn": v["iters_gnn_mean"], "validation": v["systems"]}
 
 
 def workload_sizes(N):
@@ -388,7 +402,7 @@ def run_ours(args, rank, world, local):
            "phase_s": {"ic0": ic0_s, "features_gnn_correct": gnn_s, "cg_gnn_ic": cg_g_s, "cg_ic0": cg_i_s,
                        "ic0_pcg_total": ic0_s + cg_i_s},
            "relres": {"gnn_ic": r_g["relres"], "ic0": r_i["relres"]},
-           "gnn_kept": bool(recs[-1][3]), "ic0_shift": recs[-1][4],
+           "gnn_kept": bool(recs[-1][3]), "ic0_shift": recs[-1][4], "gnn_policy": gnn_policy(),
            "kernels": kern, "roofline": roof, "spmv_roofline": spmv_roof, "clocks": clk,
            "gpu_launches": launches,
            "schedule": {"chunks": P.nchunks, "multi_group_chunks": bool(P.chunked), "sell_padding":

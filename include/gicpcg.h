@@ -103,6 +103,11 @@ int gic_pattern_info(const gic_pattern *P, int64_t *n, int64_t *nnzA, int64_t *n
  * are multi-group runs (1) or single groups in level order (0), and the
  * padded entry count of the SELL-32 copy of A used by the PCG SpMV. */
 int gic_pattern_schedule(const gic_pattern *P, int32_t *nchunks, int32_t *chunked, int64_t *sell_nnz);
+/* Which triangular-solve kernels the pattern admits (host outputs, any may be
+ * NULL): warp-specialised (1/0), SM-local blocks (1/0) and the rows the
+ * largest block mirrors in shared memory. */
+int gic_pattern_solve_kernels(const gic_pattern *P, int32_t *warp_specialised, int32_t *sm_local,
+                              int32_t *mirror_rows);
 /* Copies of the analysis (device outputs, any may be NULL): Lrowptr (n+1),
  * Lcol (nnzL), level (n), group start rows (ngroups+1). */
 int gic_pattern_export(gic_handle *h, const gic_pattern *P, int32_t *Lrowptr, int32_t *Lcol,
@@ -257,10 +262,12 @@ int gic_adam_step(gic_handle *h, int64_t np, float *theta, const float *grad, fl
  * solve warps (warp pairs for the warp-specialised solves) per SM (0 = no
  * cap); GIC_TUNE_POLL = polling: low 16 bits = nanoseconds slept between
  * polls, bit 16 set = one polling lane per warp (default 1<<16);
- * GIC_TUNE_PIPELINE = triangular-solve kernels: 2 (default) warp-specialised
- * solves on premultiplied row-group blocks where the pattern allows (groups
- * of <= 3 rows, <= 61 external columns), else 1 = staged one-warp solves
- * (<= 3 rows, <= 48 columns), else 0 = generic; GIC_TUNE_QDELTA = level
+ * GIC_TUNE_PIPELINE = triangular-solve kernels: 3 (default) SM-local solves
+ * (blocks of 16 neighbouring chunks per CTA, intra-block dependencies in
+ * shared memory) where the pattern's block order allows, else 2 =
+ * warp-specialised solves on premultiplied row-group blocks (groups of <= 3
+ * rows, <= 61 external columns), else 1 = staged one-warp solves (<= 3 rows,
+ * <= 48 columns), else 0 = generic; a lower value caps the choice; GIC_TUNE_QDELTA = level
  * window of the dependencies the warp-specialised solves treat as "late"
  * (read by gic_analyze; default 6). */
 #define GIC_TUNE_SOLVE_WARPS_PER_SM 1

@@ -287,8 +287,18 @@ struct Pattern {
     int32_t *qf_col = nullptr, *qb_col = nullptr;
     uint8_t *qf_pos = nullptr, *qb_pos = nullptr;
     int32_t *qf_cnt = nullptr, *qb_cnt = nullptr;
+    // Block schedule of the SM-local solves: chunk blocks = runs of BCHUNKS
+    // consecutive chunks (one CTA each, one warp per chunk, a shared-memory
+    // mirror of the block's rows), in index order (forward) and reverse
+    // index order (backward); every dependency on another chunk block points
+    // to an earlier one in that order (checked).
+    int bready = 0;
+    int32_t ncb = 0, mirror_rows = 0;
+    int32_t *cb_ord_f = nullptr, *cb_ord_b = nullptr;
     int device = 0;
 };
+
+constexpr int BCHUNKS = 16; // chunks (warps) per block of the SM-local solves
 
 constexpr int QCOL = 64;   // external columns of a group in the warp-specialised solves
 constexpr int QLATE = 16;  // at most this many late columns per group
@@ -312,7 +322,7 @@ struct gic_handle {
     long long launches = 0;        // kernels this handle has launched
     int tune_solve_warps_per_sm = 0; // cap on resident solve warps per SM (0: none)
     int tune_poll = gic::POLL_ONE_LANE; // polling configuration of the sync-free kernels
-    int tune_pipeline = 2;              // 2: warp-specialised solves, 1: staged solves, 0: generic
+    int tune_pipeline = 3;              // 3: SM-local, 2: warp-specialised, 1: staged, 0: generic solves
     int tune_qdelta = 6;                // level window of the "late" columns (pattern analysis)
 };
 

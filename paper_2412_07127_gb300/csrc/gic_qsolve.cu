@@ -49,34 +49,51 @@ struct QSlot {
     int32_t s, cw;     // first row, packed counts
 };
 
+// Slot i of the ring serves groups q = i, i + QR, ...; its j-th use (j =
+// q / QR) completes phase j of full[i] (producer -> finisher: staged data
+// and base are in place) and phase j of freed[i] (finisher -> producer: the
+// slot may be refilled). Waiting threads are suspended by the hardware
+// (mbarrier try_wait) instead of spinning on shared memory.
 template <typename T>
 struct QPair {
     QSlot<T> slot[QR];
-    int full, freed; // groups produced / finished by the pair so far
+    unsigned long long full[QR], freed[QR];
 };
 
-__device__ __forceinline__ int ld_vol(const int *p) { return *(volatile const int *)p; }
-__device__ __forceinline__ void st_vol(int *p, int v) { *(volatile int *)p = v; }
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
-// Bounded wait (one lane) until the shared counter *p reaches target.
-__device__ __forceinline__ bool wait_seq(const int *p, int target, unsigned *err)
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
 {
-    if (ld_vol(p) >= target) return true;
-    for (long long it = 0; it < SPIN_LIMIT; ++it) {
-        if (ld_vol(p) >= target) return true;
-        if ((it & 255) == 255 && *((volatile unsigned *)err) != 0u) return false;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Bounded wait for the completion of the phase with the given parity; every
+// calling thread waits (and acquires). False after the limit (error flag
+// set) or once another thread has flagged an error.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, unsigned *err)
+{
+    const unsigned a = smem_addr(bar);
+    for (long long it = 0; it < (SPIN_LIMIT >> 2); ++it) {
+        unsigned done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(a), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        if ((it & 63) == 63 && *((volatile unsigned *)err) != 0u) return false;
     }
     atomicOr(err, ERR_TIMEOUT);
     return false;
 }
 
-// the warp waits on a counter through lane 0; true in every lane when reached
-__device__ __forceinline__ bool warp_wait_seq(const int *p, int target, unsigned *err, int lane)
-{
-    int r = 1;
-    if (lane == 0) r = wait_seq(p, target, err) ? 1 : 0;
-    return __shfl_sync(FULL, r, 0) != 0;
-}
+__device__ __forceinline__ bool warp_all(bool v) { return __all_sync(FULL, v) != 0; }
 
 template <typename T>
 __device__ __forceinline__ void q_stage(QSlot<T> &S, int32_t s, int32_t cw, int64_t b0, const int32_t *qcol,
@@ -136,7 +153,8 @@ __device__ __forceinline__ bool q_produce(QPair<T> &Q, int seq, int32_t g0, int3
         }
         const int32_t s = __shfl_sync(FULL, hs, k - wbase), cw = __shfl_sync(FULL, hc, k - wbase);
         const int32_t b0 = __shfl_sync(FULL, hb, k - wbase);
-        if (!warp_wait_seq(&Q.freed, seq + k - QR + 1, err, lane)) {
+        const int q = seq + k, use = q / QR;
+        if (use > 0 && !warp_all(mbar_wait(&Q.freed[q % QR], (unsigned)(use - 1) & 1u, err))) {
             ok = false;
             return;
         }
@@ -190,7 +208,7 @@ __device__ __forceinline__ bool q_produce(QPair<T> &Q, int seq, int32_t g0, int3
         if (lane < G) S.base[lane] = -pick3<T>(lane, a[0], a[1], a[2]);
         __threadfence_block();
         __syncwarp();
-        if (lane == 0) st_vol(&Q.full, seq + k + 1);
+        if (lane == 0) mbar_arrive(&Q.full[(seq + k) % QR]);
     }
     cp_async_wait<0>();
     __syncwarp();
@@ -205,9 +223,9 @@ __device__ __forceinline__ bool q_finish(QPair<T> &Q, int seq, int cnt, T *x, T 
     T yp = 0;          // lane t: row t of the previous group of the chunk
     int32_t prev_s = 0;
     for (int k = 0; k < cnt; ++k) {
-        if (!warp_wait_seq(&Q.full, seq + k + 1, err, lane)) return false;
-        __threadfence_block();
-        const QSlot<T> &S = Q.slot[(seq + k) % QR];
+        const int q = seq + k;
+        if (!warp_all(mbar_wait(&Q.full[q % QR], (unsigned)(q / QR) & 1u, err))) return false;
+        const QSlot<T> &S = Q.slot[q % QR];
         const int32_t cw = S.cw, s = S.s;
         const int ne = cw & 255, nl = (cw >> 8) & 255, np = (cw >> 16) & 255, G = cw >> 24;
         const T p0 = __shfl_sync(FULL, yp, 0), p1 = __shfl_sync(FULL, yp, 1), p2 = __shfl_sync(FULL, yp, 2);
@@ -241,7 +259,7 @@ __device__ __forceinline__ bool q_finish(QPair<T> &Q, int seq, int cnt, T *x, T 
         yp = yv;
         __threadfence_block();
         __syncwarp();
-        if (lane == 0) st_vol(&Q.freed, seq + k + 1);
+        if (lane == 0) mbar_arrive(&Q.freed[q % QR]);
         prev_s = s;
     }
     return true;
@@ -252,7 +270,7 @@ __device__ __forceinline__ bool q_finish(QPair<T> &Q, int seq, int cnt, T *x, T 
 // r^T z in FP64, then beta = r_k^T z_k / r_{k-1}^T z_{k-1} (Algorithm 1) in
 // the last warp to finish. x must hold the sentinel.
 template <typename T, bool FWD, bool PCG>
-__global__ void __launch_bounds__(SOLVE_BLOCK) k_qsolve(int32_t nchunks, const int32_t *__restrict__ ord,
+__global__ void __launch_bounds__(SOLVE_BLOCK, 2) k_qsolve(int32_t nchunks, const int32_t *__restrict__ ord,
                                                         const int32_t *__restrict__ chunk_grp,
                                                         const int32_t *__restrict__ grp,
                                                         const int32_t *__restrict__ rowptr,
@@ -268,9 +286,9 @@ __global__ void __launch_bounds__(SOLVE_BLOCK) k_qsolve(int32_t nchunks, const i
     const int wib = threadIdx.x >> 5;
     const bool producer = (wib & 1) == 0;
     QPair<T> &Q = pairs[wib >> 1];
-    if (producer && lane == 0) {
-        Q.full = 0;
-        Q.freed = 0;
+    if (producer && lane < QR) {
+        mbar_init(&Q.full[lane], 1);
+        mbar_init(&Q.freed[lane], 1);
     }
     __syncthreads();
     const int64_t gpair = (int64_t)blockIdx.x * QPAIRS + (wib >> 1);

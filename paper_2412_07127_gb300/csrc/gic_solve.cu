@@ -1128,9 +1128,12 @@ static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 // <= 3 rows, <= QCOL external columns), each with an FP64 or an FP32
 // factor. The pipelined and warp-specialised FP32 modes keep their vectors
 // and sums in FP32 too.
-enum SolveMode { MODE_GEN64, MODE_GEN32, MODE_P64, MODE_P32, MODE_Q64, MODE_Q32, MODE_IDENT };
+// SM-local (gic_bsolve.cu) on the same blocks where the pattern's chunk
+// blocks allow it.
+enum SolveMode { MODE_GEN64, MODE_GEN32, MODE_P64, MODE_P32, MODE_Q64, MODE_Q32, MODE_B64, MODE_B32, MODE_IDENT };
 
-static bool f32_vectors(SolveMode m) { return m == MODE_P32 || m == MODE_Q32; }
+static bool f32_vectors(SolveMode m) { return m == MODE_P32 || m == MODE_Q32 || m == MODE_B32; }
+static bool premultiplied(SolveMode m) { return m == MODE_Q64 || m == MODE_Q32 || m == MODE_B64 || m == MODE_B32; }
 
 struct SolveWs {
     void *Uval;                   // U values (generic, pipelined) or backward blocks (warp-specialised)
@@ -1152,6 +1155,7 @@ static bool pipelined_fits(const Pattern &P)
 static SolveMode solve_mode(const gic_handle *h, const Pattern &P, int l_dtype)
 {
     if (l_dtype == GIC_IDENTITY) return MODE_IDENT;
+    if (h->tune_pipeline >= 3 && P.bready) return (l_dtype == GIC_F32) ? MODE_B32 : MODE_B64;
     if (h->tune_pipeline >= 2 && P.qready) return (l_dtype == GIC_F32) ? MODE_Q32 : MODE_Q64;
     const bool pipe = h->tune_pipeline && pipelined_fits(P);
     if (l_dtype == GIC_F32) return pipe ? MODE_P32 : MODE_GEN32;
@@ -1334,7 +1338,7 @@ static int launch_ltsolve_p(gic_handle *h, const Pattern &P, const T *Uval, cons
 // Transposed values and reciprocal diagonal for the mode.
 static int setup_factor(gic_handle *h, const Pattern &P, SolveMode mode, const void *Lval, const SolveWs &W)
 {
-    if (mode == MODE_Q64 || mode == MODE_Q32) return q_setup(h, P, mode == MODE_Q32, Lval, W.Qf, W.Uval);
+    if (premultiplied(mode)) return q_setup(h, P, f32_vectors(mode), Lval, W.Qf, W.Uval);
     int64_t cnt = P.nnzL > P.n ? P.nnzL : P.n;
     unsigned gr = vec_grid(h, cnt, 256);
     ++h->launches;
@@ -1411,6 +1415,8 @@ static int precondition(gic_handle *h, const Pattern &P, SolveMode mode, const v
     case MODE_P32: GIC_TRY(launch_lsolve_p<float>(h, P, (const float *)Lval, W.invd32, W.r32, W.y32, W.sc)); break;
     case MODE_Q64: GIC_TRY(q_lsolve(h, P, false, W.Qf, W.r, W.y, W.sc)); break;
     case MODE_Q32: GIC_TRY(q_lsolve(h, P, true, W.Qf, W.r32, W.y32, W.sc)); break;
+    case MODE_B64: GIC_TRY(b_lsolve(h, P, false, W.Qf, W.r, W.y, W.sc)); break;
+    case MODE_B32: GIC_TRY(b_lsolve(h, P, true, W.Qf, W.r32, W.y32, W.sc)); break;
     default: break;
     }
     PROF_END(GIC_PROF_LSOLVE);
@@ -1431,6 +1437,8 @@ static int precondition(gic_handle *h, const Pattern &P, SolveMode mode, const v
         break;
     case MODE_Q64: GIC_TRY(q_ltsolve(h, P, false, true, W.Uval, W.y, W.z, W.r, W.partials, W.sc)); break;
     case MODE_Q32: GIC_TRY(q_ltsolve(h, P, true, true, W.Uval, W.y32, W.z32, W.r, W.partials, W.sc)); break;
+    case MODE_B64: GIC_TRY(b_ltsolve(h, P, false, true, W.Uval, W.y, W.z, W.r, W.partials, W.sc)); break;
+    case MODE_B32: GIC_TRY(b_ltsolve(h, P, true, true, W.Uval, W.y32, W.z32, W.r, W.partials, W.sc)); break;
     default: break;
     }
     PROF_END(GIC_PROF_LTSOLVE);
@@ -1578,6 +1586,8 @@ static int standalone_solve(gic_handle *h, const Pattern &p, const void *valL, i
         case MODE_P32: GIC_TRY(launch_lsolve_p<float>(h, p, (const float *)valL, W.invd32, W.r32, W.y32, nullptr)); break;
         case MODE_Q64: GIC_TRY(q_lsolve(h, p, false, W.Qf, in, out, nullptr)); break;
         case MODE_Q32: GIC_TRY(q_lsolve(h, p, true, W.Qf, W.r32, W.y32, nullptr)); break;
+        case MODE_B64: GIC_TRY(b_lsolve(h, p, false, W.Qf, in, out, nullptr)); break;
+        case MODE_B32: GIC_TRY(b_lsolve(h, p, true, W.Qf, W.r32, W.y32, nullptr)); break;
         default: break;
         }
         PROF_END(GIC_PROF_LSOLVE);
@@ -1600,6 +1610,8 @@ static int standalone_solve(gic_handle *h, const Pattern &p, const void *valL, i
             break;
         case MODE_Q64: GIC_TRY(q_ltsolve(h, p, false, false, W.Uval, yy, out, nullptr, nullptr, nullptr)); break;
         case MODE_Q32: GIC_TRY(q_ltsolve(h, p, true, false, W.Uval, W.r32, W.y32, nullptr, nullptr, nullptr)); break;
+        case MODE_B64: GIC_TRY(b_ltsolve(h, p, false, false, W.Uval, yy, out, nullptr, nullptr, nullptr)); break;
+        case MODE_B32: GIC_TRY(b_ltsolve(h, p, true, false, W.Uval, W.r32, W.y32, nullptr, nullptr, nullptr)); break;
         default: break;
         }
         PROF_END(GIC_PROF_LTSOLVE);

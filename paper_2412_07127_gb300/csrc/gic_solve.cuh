@@ -73,4 +73,9 @@ int q_lsolve(gic_handle *h, const Pattern &P, bool f32, const void *Kf, const vo
 int q_ltsolve(gic_handle *h, const Pattern &P, bool f32, bool pcg, const void *Kb, void *y, void *z,
               const double *rd, double *partials, Scalars *sc);
 
+// SM-local solves (gic_bsolve.cu) on the same premultiplied blocks.
+int b_lsolve(gic_handle *h, const Pattern &P, bool f32, const void *Kf, const void *r, void *y, const Scalars *sc);
+int b_ltsolve(gic_handle *h, const Pattern &P, bool f32, bool pcg, const void *Kb, void *y, void *z,
+              const double *rd, double *partials, Scalars *sc);
+
 }  // namespace gic

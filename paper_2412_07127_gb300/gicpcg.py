@@ -50,6 +50,7 @@ _SIGS = {
                                 C.POINTER(_i32), C.POINTER(_i32)]),
     "gic_pattern_export": (_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "gic_pattern_schedule": (_int, [_vp, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i64)]),
+    "gic_pattern_solve_kernels": (_int, [_vp, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i32)]),
     "gic_ic0": (_int, [_vp, _vp, _vp, _vp, _dbl, C.POINTER(_i64)]),
     "gic_ic0_auto": (_int, [_vp, _vp, _vp, _vp, _int, C.POINTER(_dbl), C.POINTER(_i64)]),
     "gic_convert_f64_f32": (_int, [_vp, _i64, _vp, _vp]),
@@ -181,6 +182,9 @@ class Pattern:
         nc, ch, sn = _i32(), _i32(), _i64()
         _call("gic_pattern_schedule", p, C.byref(nc), C.byref(ch), C.byref(sn))
         self.nchunks, self.chunked, self.sell_nnz = nc.value, ch.value, sn.value
+        q, b, mr = _i32(), _i32(), _i32()
+        _call("gic_pattern_solve_kernels", p, C.byref(q), C.byref(b), C.byref(mr))
+        self.warp_specialised, self.sm_local, self.mirror_rows = q.value, b.value, mr.value
 
     def export(self, h: Handle):
         dev = self.rowptr.device

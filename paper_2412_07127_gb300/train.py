@@ -111,6 +111,41 @@ def validate(h, theta, N=20, seeds=range(9000, 9016), sigma=1.0, l_dtype=torch.f
     return out
 
 
+def weights_meta(log):
+    """Metadata stored beside trained weights: training record, validation
+    PCG iterations against plain IC(0), and the fallback decision (the
+    corrected factor is used only if it lowers the validation iterations)."""
+    a = log["args"]
+    v = log["final_val"]
+    ic0 = float(np.mean([r["ic0"] for r in v]))
+    gnn = float(np.mean([r["gnn"] if r["gnn"] >= 0 else np.inf for r in v]))
+    st = log["steps"]
+    return {
+        "about": "GNN correction weights (3504 float32) trained by paper_2412_07127_gb300.train on the GPU "
+                 "with the library's own forward/backward kernels",
+        "training": {"systems": f"{a['batch']} x {a['N']}^3-element hex elasticity per batch, sigma ~ U[0.5, 2] "
+                                f"per system, seeds {a['seed0']}+",
+                     "probes": f"{a['probes']} Gaussian per system", "steps_done": log["steps_done"],
+                     "seconds": round(log["train_seconds"], 1), "lr": a["lr"], "warmup_frac": a["warmup_frac"],
+                     "ic0_shifts_seen": log["ic0_shifts"],
+                     "loss_ratio_to_ic0_first": round(st[0]["ratio"], 4),
+                     "loss_ratio_to_ic0_last": round(st[-1]["ratio"], 4)},
+        "validation": {"systems": f"{a['val_N']}^3-element hex elasticity, sigma = 1, seeds 9000-9015, "
+                                  f"PCG to 1e-8, FP64", "iters_ic0_mean": ic0, "iters_gnn_mean": gnn, "runs": v},
+        "use_gnn": bool(gnn < ic0),
+        "policy": "the corrected factor is used only when its validation iteration count is below plain "
+                  "IC(0)'s; otherwise plain IC(0) is the fallback",
+    }
+
+
+def load_weights(path):
+    """(theta float32, metadata dict or None) of a weights file."""
+    th = np.load(path).astype(np.float32)
+    meta_path = os.path.splitext(path)[0] + ".json"
+    meta = json.load(open(meta_path)) if os.path.exists(meta_path) else None
+    return th, meta
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--steps", type=int, default=2000)
@@ -162,6 +197,8 @@ def main(argv=None):
     v = validate(h, theta, N=a.val_N)
     log["final_val"] = v
     print(json.dumps(dict(final_val=v)), flush=True)
+    with open(os.path.splitext(a.out)[0] + ".json", "w") as f:
+        json.dump(weights_meta(log), f, indent=1)
     if a.log:
         with open(a.log, "w") as f:
             json.dump(log, f, indent=1)

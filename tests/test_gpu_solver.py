@@ -99,6 +99,8 @@ def test_analysis_fem(G, h, N):
     assert np.array_equal(grp, _expected_groups(A))
     if N >= 2:  # then every group is the 3 dofs of one node
         assert P.ngroups == A.n // 3 and np.array_equal(grp, np.arange(0, A.n + 1, 3))
+        # the hex systems admit the fastest solve kernels (so the tests run them)
+        assert P.warp_specialised == 1 and P.sm_local == 1
 
 
 def _expected_groups(A):
@@ -233,12 +235,12 @@ def test_spmv_matches_oracle(G, h):
     assert abs(_np(d)[0] - x @ yo) <= 1e-12 * abs(x @ yo)
 
 
-@pytest.mark.parametrize("pipeline", [2, 1, 0])
+@pytest.mark.parametrize("pipeline", [3, 2, 1, 0])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("case", ["fem8", "fem5", "random", "tridiag"])
 def test_triangular_solves_match_oracle(G, h, dtype, case, pipeline):
-    """Every solve path (warp-specialised and pipelined where the pattern
-    allows, generic) against the oracle on the same factor."""
+    """Every solve path (SM-local, warp-specialised and pipelined where the
+    pattern allows, generic) against the oracle on the same factor."""
     G.set_tuning(h, G.GIC_TUNE_PIPELINE, pipeline)
     if case == "fem8":
         A = O.fem_hex_assemble(8, I.material_field(8, 5))
@@ -267,11 +269,12 @@ def test_triangular_solves_match_oracle(G, h, dtype, case, pipeline):
         nrel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
         assert nrel(_np(y), yo) <= 1e-5 and nrel(_np(z), zo) <= 1e-5
     assert G.error_flags(h) == 0
-    G.set_tuning(h, G.GIC_TUNE_PIPELINE, 2)
+    G.set_tuning(h, G.GIC_TUNE_PIPELINE, 3)
 
 
+@pytest.mark.parametrize("pipeline", [3, 2])
 @pytest.mark.parametrize("qdelta", [0, 3, 30])
-def test_solve_late_window_variants(G, h, qdelta):
+def test_solve_late_window_variants(G, h, qdelta, pipeline):
     """The split of a group's dependencies into early and late ones only
     changes when the solve waits, not its result."""
     G.set_tuning(h, G.GIC_TUNE_QDELTA, qdelta)
@@ -280,6 +283,7 @@ def test_solve_late_window_variants(G, h, qdelta):
     rp, c, v = _upload(A)
     P = G.Pattern(h, rp, c)
     G.set_tuning(h, G.GIC_TUNE_QDELTA, 6)
+    G.set_tuning(h, G.GIC_TUNE_PIPELINE, pipeline)
     r = np.random.default_rng(3).uniform(-1, 1, A.n)
     y = G.lsolve(h, P, _dev(Lo.val), _dev(r))
     z = G.ltsolve(h, P, _dev(Lo.val), y)
@@ -287,6 +291,7 @@ def test_solve_late_window_variants(G, h, qdelta):
     assert _rel(_np(y), yo) <= 1e-11
     assert _rel(_np(z), O.ltsolve(Lo, yo)) <= 1e-11
     assert G.error_flags(h) == 0
+    G.set_tuning(h, G.GIC_TUNE_PIPELINE, 3)
 
 
 # ---------------------------------------------------------------- A7 PCG
@@ -323,7 +328,7 @@ def test_plain_cg_matches_oracle(G, h):
     assert np.linalg.norm(x - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
 
 
-@pytest.mark.parametrize("pipeline", [2, 1, 0])
+@pytest.mark.parametrize("pipeline", [3, 2, 1, 0])
 def test_pcg_f32_factor(G, h, pipeline):
     G.set_tuning(h, G.GIC_TUNE_PIPELINE, pipeline)
     N = 8
@@ -335,7 +340,7 @@ def test_pcg_f32_factor(G, h, pipeline):
     P = G.Pattern(h, rp, c)
     Lg, _ = G.ic0(h, P, v)
     res = G.pcg(h, P, v, G.to_f32(h, Lg), _dev(b), rtol=1e-8)
-    G.set_tuning(h, G.GIC_TUNE_PIPELINE, 2)
+    G.set_tuning(h, G.GIC_TUNE_PIPELINE, 3)
     ro = O.pcg(A, b, L32, tol=1e-8)
     assert _iters_ok(res["iters"], ro["iters"]), (res["iters"], ro["iters"])
     x = _np(res["x"])
