@@ -162,6 +162,41 @@ int gic_ltsolve(gic_handle *h, const gic_pattern *P, const void *valL, int l_dty
 int gic_pcg(gic_handle *h, const gic_pattern *P, const double *valA, const void *valL,
             int l_dtype, const double *b, double *x, double rtol, int maxit, int32_t *iters,
             double *relres, void *ws, size_t ws_bytes);
+/* PCG as gic_pcg with the factor on a pattern of its own: the SpMV runs on
+ * PA (the matrix), the triangular solves on the lower triangle of PL (same n),
+ * for instance a factor thinned by gic_dropout. ws: device workspace of
+ * gic_workspace_size_split bytes. Same outputs and status codes as gic_pcg. */
+int gic_workspace_size_split(gic_handle *h, const gic_pattern *PA, const gic_pattern *PL,
+                             int l_dtype, size_t *bytes);
+int gic_pcg_split(gic_handle *h, const gic_pattern *PA, const double *valA, const gic_pattern *PL,
+                  const void *valL, int l_dtype, const double *b, double *x, double rtol, int maxit,
+                  int32_t *iters, double *relres, void *ws, size_t ws_bytes);
+
+/* --------------------------- fill-in dropout, deviation, direct prediction
+ * Fill-in dropout (Supplementary 5, Eq. (10)): off-diagonal factor entries
+ * with |L_ij| <= threshold become zero and leave the pattern; the diagonal is
+ * always kept. Eq. (10)'s epsilon applies to the scaled factor L/sqrt(s), so
+ * threshold = epsilon * sqrt(s). valL: device float64, nnzL values on P.
+ * Outputs (caller-owned device memory): the symmetric pattern S = L' + L'^T
+ * of the kept factor, Srowptr (n+1) and Scol (capacity nnzA), ready for
+ * gic_analyze; Lval_out (capacity nnzL) = the kept values in the CSR order
+ * of tril(S). Host outputs: *nnzS, *nnzL_out. */
+int gic_dropout(gic_handle *h, const gic_pattern *P, const double *valL, double threshold,
+                int32_t *Srowptr, int32_t *Scol, double *Lval_out, int64_t *nnzS, int64_t *nnzL_out);
+/* Deviation of a factor from the IC(0) factor (the diagnostic of the paper's
+ * Figure 5): |Lpred_ij - LIC_ij| / |LIC_ij| over entries with LIC_ij != 0.
+ * LIC, Lpred: device float64 on P. out (host, 6 values): mean and maximum on
+ * the diagonal, mean and maximum off the diagonal, the two entry counts. */
+int gic_factor_deviation(gic_handle *h, const gic_pattern *P, const double *LIC, const double *Lpred,
+                         double *out);
+/* Base factor of the direct prediction L = GNN(A) (Eq. (1), the paper's
+ * "NIC" ablation): correcting it with gic_gnn_correct (or, scaled, with
+ * gic_gnn_correct_scaled) gives off-diagonal g and diagonal exp(g/2).
+ * Writes (device, nnzL values, either may be NULL): L = sqrt(s_k) on the
+ * diagonal of graph k and 0 elsewhere (scale: device float64 [ngraphs] from
+ * gic_features), Lhat = 1 on the diagonal and 0 elsewhere (float32). */
+int gic_identity_factor(gic_handle *h, const gic_pattern *P, int ngraphs, const double *scale, double *L,
+                        float *Lhat);
 
 /* Per-kernel-class device time of the solve calls, measured with CUDA
  * events on the handle's stream around every launch while enabled (the PCG
@@ -262,9 +297,9 @@ int gic_adam_step(gic_handle *h, int64_t np, float *theta, const float *grad, fl
  * solve warps (warp pairs for the warp-specialised solves) per SM (0 = no
  * cap); GIC_TUNE_POLL = polling: low 16 bits = nanoseconds slept between
  * polls, bit 16 set = one polling lane per warp (default 1<<16);
- * GIC_TUNE_PIPELINE = triangular-solve kernels: 3 (default) SM-local solves
- * (blocks of 16 neighbouring chunks per CTA, intra-block dependencies in
- * shared memory) where the pattern's block order allows, else 2 =
+ * GIC_TUNE_PIPELINE = triangular-solve kernels: 3 = SM-local solves (blocks
+ * of 16 neighbouring chunks per CTA, intra-block dependencies in shared
+ * memory) where the pattern's block order allows, else 2 (default) =
  * warp-specialised solves on premultiplied row-group blocks (groups of <= 3
  * rows, <= 61 external columns), else 1 = staged one-warp solves (<= 3 rows,
  * <= 48 columns), else 0 = generic; a lower value caps the choice; GIC_TUNE_QDELTA = level

@@ -62,6 +62,9 @@ def lib():
                                     C.c_int, C.c_void_p]
         L.or_probe_loss.restype = _dbl
         L.or_adam_step.argtypes = [_i64, _f64p, _f64p, _f64p, _f64p, C.c_int, _dbl]
+        L.or_dropout.argtypes = [_i64, _i32p, _i32p, _f64p, _dbl, _i32p, _i32p, _f64p]
+        L.or_dropout.restype = _i64
+        L.or_factor_deviation.argtypes = [_i64, _i32p, _i32p, _f64p, _f64p, _f64p]
         L.or_lr_at.argtypes = [C.c_int, C.c_int, _dbl]
         L.or_lr_at.restype = _dbl
         _lib = L
@@ -288,3 +291,20 @@ def adam_step(theta, grad, m1, m2, t, lr):
 
 def lr_at(t, warm, lr_max=0.005):
     return lib().or_lr_at(t, warm, lr_max)
+
+
+# ---------------------------------------------------------------- Eq. (10), Figure 5
+def dropout(L: CSR, thr):
+    """Fill-in dropout of the factor: off-diagonal |L_ij| <= thr removed."""
+    rp = np.zeros(L.n + 1, np.int32)
+    col = np.zeros(len(L.col), np.int32)
+    val = np.zeros(len(L.col))
+    k = lib().or_dropout(L.n, L.rowptr, L.col, np.ascontiguousarray(L.val, np.float64), thr, rp, col, val)
+    return CSR(rp, col[:k].copy(), val[:k].copy())
+
+
+def factor_deviation(L: CSR, LIC_val, Lpred_val):
+    out = np.zeros(6)
+    lib().or_factor_deviation(L.n, L.rowptr, L.col, np.ascontiguousarray(LIC_val, np.float64),
+                              np.ascontiguousarray(Lpred_val, np.float64), out)
+    return out

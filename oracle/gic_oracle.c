@@ -33,6 +33,9 @@
  *                             central finite differences
  *   or_gnn_backward           pinned: central finite differences
  *   or_adam_step              pinned: closed form of the first steps
+ *   or_dropout                pinned: eps = 0 keeps L, a huge eps keeps the
+ *                             diagonal only, hand-built 3x3 case
+ *   or_factor_deviation       pinned: zero for equal factors, hand-built case
  */
 #include <math.h>
 #include <stdint.h>
@@ -937,4 +940,62 @@ double or_lr_at(int t, int warm, double lr_max)
 {
     if (warm <= 0 || t >= warm) return lr_max;
     return lr_max * (double)t / (double)warm;
+}
+
+/* ======================================================================
+ * Fill-in dropout (Supplementary 5, Eq. (10)): an off-diagonal entry of the
+ * factor whose absolute value is at most thr is set to zero and removed from
+ * the pattern; the diagonal always stays. Writes the kept factor as CSR
+ * (out_rowptr n+1, out_col/out_val capacity nnz(L)); returns its nnz.
+ * ====================================================================== */
+int64_t or_dropout(int64_t n, const int32_t *Lrowptr, const int32_t *Lcol, const double *Lval, double thr,
+                   int32_t *out_rowptr, int32_t *out_col, double *out_val)
+{
+    int64_t k = 0;
+    out_rowptr[0] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int32_t p = Lrowptr[i]; p < Lrowptr[i + 1]; ++p) {
+            int keep = (Lcol[p] == i) || (fabs(Lval[p]) > thr);
+            if (keep) {
+                out_col[k] = Lcol[p];
+                out_val[k] = Lval[p];
+                ++k;
+            }
+        }
+        out_rowptr[i + 1] = (int32_t)k;
+    }
+    return k;
+}
+
+/* ======================================================================
+ * Deviation of a factor from the IC(0) factor (the diagnostic of the
+ * paper's Figure 5): r = |Lpred - LIC| / |LIC| over the entries with
+ * LIC != 0. out: mean and max of r on the diagonal, mean and max off the
+ * diagonal, the diagonal and off-diagonal entry counts.
+ * ====================================================================== */
+void or_factor_deviation(int64_t n, const int32_t *Lrowptr, const int32_t *Lcol, const double *LIC,
+                         const double *Lpred, double *out)
+{
+    double sd = 0.0, md = 0.0, so = 0.0, mo = 0.0, cd = 0.0, co = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int32_t p = Lrowptr[i]; p < Lrowptr[i + 1]; ++p) {
+            if (LIC[p] == 0.0) continue;
+            double r = fabs(Lpred[p] - LIC[p]) / fabs(LIC[p]);
+            if (Lcol[p] == i) {
+                sd += r;
+                if (r > md) md = r;
+                cd += 1.0;
+            } else {
+                so += r;
+                if (r > mo) mo = r;
+                co += 1.0;
+            }
+        }
+    }
+    out[0] = cd > 0.0 ? sd / cd : 0.0;
+    out[1] = md;
+    out[2] = co > 0.0 ? so / co : 0.0;
+    out[3] = mo;
+    out[4] = cd;
+    out[5] = co;
 }

@@ -135,6 +135,11 @@ static int scan_i32(gic_handle *h, const int32_t *in, int64_t n, int32_t *out, l
     return GIC_OK;
 }
 
+int scan_excl_i32(gic_handle *h, const int32_t *in, int64_t n, int32_t *out, long long *total)
+{
+    return scan_i32<false>(h, in, n, out, total);
+}
+
 // ---------------------------------------------------------------- checks
 // Per row: bounds, strictly increasing columns, stored diagonal; Lcnt[i] =
 // number of entries with column <= i; same[i] = row i has the same columns

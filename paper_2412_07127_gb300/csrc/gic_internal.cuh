@@ -322,7 +322,7 @@ struct gic_handle {
     long long launches = 0;        // kernels this handle has launched
     int tune_solve_warps_per_sm = 0; // cap on resident solve warps per SM (0: none)
     int tune_poll = gic::POLL_ONE_LANE; // polling configuration of the sync-free kernels
-    int tune_pipeline = 3;              // 3: SM-local, 2: warp-specialised, 1: staged, 0: generic solves
+    int tune_pipeline = 2;              // 3: SM-local, 2: warp-specialised, 1: staged, 0: generic solves
     int tune_qdelta = 6;                // level window of the "late" columns (pattern analysis)
 };
 
@@ -332,5 +332,7 @@ size_t gnn_infer_ws_bytes(int64_t n, int64_t nnzL);
 int gnn_correct_inplace(gic_handle *h, const gic_pattern *P, const double *valA, const float *theta_host,
                         double *L, void *ws, size_t ws_bytes, int *kept);
 int check_handle(gic_handle *h);
+// exclusive prefix sum of n int32 counts into out[0..n] (out[n] = total)
+int scan_excl_i32(gic_handle *h, const int32_t *in, int64_t n, int32_t *out, long long *total);
 int read_and_clear_dev_err(gic_handle *h, unsigned *flags);
 }

@@ -1162,8 +1162,15 @@ static SolveMode solve_mode(const gic_handle *h, const Pattern &P, int l_dtype)
     return pipe ? MODE_P64 : MODE_GEN64;
 }
 
-static SolveWs carve(const Pattern &P, int l_dtype, bool p32, void *ws)
+// Workspace layout for a PCG whose SpMV runs on pattern PA and whose solves
+// run on the factor pattern PL (the same object unless the factor's pattern
+// was thinned, e.g. by fill-in dropout).
+static SolveWs carve(const Pattern &PA, const Pattern &PL, int l_dtype, bool p32, void *ws)
 {
+    Pattern P;
+    P.n = PA.n;
+    P.nnzL = PL.nnzL;
+    P.sell_nnz = PA.sell_nnz;
     SolveWs o = {};
     char *c = (char *)ws;
     size_t off = 0;
@@ -1190,7 +1197,7 @@ size_t pcg_ws_bytes(int64_t n, int64_t nnzL, int64_t sell_nnz, int l_dtype)
     P.n = n;
     P.nnzL = nnzL;
     P.sell_nnz = sell_nnz;
-    return carve(P, l_dtype, l_dtype == GIC_F32, nullptr).bytes;
+    return carve(P, P, l_dtype, l_dtype == GIC_F32, nullptr).bytes;
 }
 
 static unsigned vec_grid(gic_handle *h, int64_t n, int block)
@@ -1446,8 +1453,8 @@ static int precondition(gic_handle *h, const Pattern &P, SolveMode mode, const v
 }
 
 // One PCG iteration: lines 11-18 of Algorithm 1 and the stop test.
-static int pcg_iteration(gic_handle *h, const Pattern &P, SolveMode mode, const double *valA, const void *Lval,
-                         const SolveWs &W, double *x)
+static int pcg_iteration(gic_handle *h, const Pattern &P, const Pattern &PL, SolveMode mode, const double *valA,
+                         const void *Lval, const SolveWs &W, double *x)
 {
     const int64_t n = P.n;
     Prof &pr = prof_of(h);
@@ -1461,7 +1468,7 @@ static int pcg_iteration(gic_handle *h, const Pattern &P, SolveMode mode, const 
         GIC_CUDA_TRY(cudaGetLastError());
         PROF_END(GIC_PROF_VECTOR);
     } else {
-        GIC_TRY(precondition(h, P, mode, Lval, W));
+        GIC_TRY(precondition(h, PL, mode, Lval, W));
         PROF_BEGIN(GIC_PROF_VECTOR);
         ++h->launches;
         if (f32_vectors(mode))
@@ -1486,8 +1493,9 @@ static int pcg_iteration(gic_handle *h, const Pattern &P, SolveMode mode, const 
     return GIC_OK;
 }
 
-static int pcg_run(gic_handle *h, const Pattern &P, SolveMode mode, const double *valA, const void *Lval,
-                   const double *b, double *x, double rtol, int maxit, int32_t *iters, double *relres, const SolveWs &W)
+static int pcg_run(gic_handle *h, const Pattern &P, const Pattern &PL, SolveMode mode, const double *valA,
+                   const void *Lval, const double *b, double *x, double rtol, int maxit, int32_t *iters, double *relres,
+                   const SolveWs &W)
 {
     const int64_t n = P.n;
     Prof &pr = prof_of(h);
@@ -1495,7 +1503,7 @@ static int pcg_run(gic_handle *h, const Pattern &P, SolveMode mode, const double
     ++h->launches;
     k_init_scalars<<<1, 1, 0, h->stream>>>(W.sc, rtol, maxit);
     if (mode != MODE_IDENT) {
-        GIC_TRY(setup_factor(h, P, mode, Lval, W));
+        GIC_TRY(setup_factor(h, PL, mode, Lval, W));
         ++h->launches;
         if (f32_vectors(mode)) k_fill_sentinel_t<float><<<vg, 256, 0, h->stream>>>(n, W.y32, W.z32);
         else k_fill_sentinel_t<double><<<vg, 256, 0, h->stream>>>(n, W.y, W.z);
@@ -1525,7 +1533,7 @@ static int pcg_run(gic_handle *h, const Pattern &P, SolveMode mode, const double
     while (true) {
         int todo = BATCH;
         if (enq + todo > maxit) todo = maxit - enq;
-        for (int k = 0; k < todo && rc == GIC_OK; ++k) rc = pcg_iteration(h, P, mode, valA, Lval, W, x);
+        for (int k = 0; k < todo && rc == GIC_OK; ++k) rc = pcg_iteration(h, P, PL, mode, valA, Lval, W, x);
         if (rc != GIC_OK) break;
         enq += todo;
         if (pending) {
@@ -1563,7 +1571,7 @@ static int standalone_solve(gic_handle *h, const Pattern &p, const void *valL, i
                             double *out, void *ws, size_t ws_bytes, bool forward)
 {
     const SolveMode mode = solve_mode(h, p, l_dtype);
-    SolveWs W = carve(p, l_dtype, f32_vectors(mode), ws);
+    SolveWs W = carve(p, p, l_dtype, f32_vectors(mode), ws);
     if (ws_bytes < W.bytes) return GIC_ERR_WORKSPACE;
     const unsigned vg = vec_grid(h, p.n, 256);
     GIC_TRY(setup_factor(h, p, mode, valL, W));
@@ -1642,7 +1650,7 @@ int gic_workspace_size(gic_handle *h, const gic_pattern *P, int op, int l_dtype,
     GIC_TRY(check_pattern(h, P));
     if (!bytes || (l_dtype != GIC_F64 && l_dtype != GIC_F32 && l_dtype != GIC_IDENTITY)) return GIC_ERR_INVALID_ARG;
     if (op != GIC_WS_SOLVE && op != GIC_WS_PCG) return GIC_ERR_INVALID_ARG;
-    *bytes = carve(P->p, l_dtype, l_dtype == GIC_F32, nullptr).bytes;
+    *bytes = carve(P->p, P->p, l_dtype, l_dtype == GIC_F32, nullptr).bytes;
     return GIC_OK;
 }
 
@@ -1700,17 +1708,36 @@ int gic_solve_error_flags(gic_handle *h, unsigned *flags)
 int gic_pcg(gic_handle *h, const gic_pattern *P, const double *valA, const void *valL, int l_dtype, const double *b,
             double *x, double rtol, int maxit, int32_t *iters, double *relres, void *ws, size_t ws_bytes)
 {
-    GIC_TRY(check_pattern(h, P));
+    return gic_pcg_split(h, P, valA, P, valL, l_dtype, b, x, rtol, maxit, iters, relres, ws, ws_bytes);
+}
+
+int gic_workspace_size_split(gic_handle *h, const gic_pattern *PA, const gic_pattern *PL, int l_dtype, size_t *bytes)
+{
+    GIC_TRY(check_pattern(h, PA));
+    GIC_TRY(check_pattern(h, PL));
+    if (!bytes || (l_dtype != GIC_F64 && l_dtype != GIC_F32 && l_dtype != GIC_IDENTITY)) return GIC_ERR_INVALID_ARG;
+    if (PA->p.n != PL->p.n) return GIC_ERR_INVALID_ARG;
+    *bytes = carve(PA->p, PL->p, l_dtype, l_dtype == GIC_F32, nullptr).bytes;
+    return GIC_OK;
+}
+
+int gic_pcg_split(gic_handle *h, const gic_pattern *PA, const double *valA, const gic_pattern *PL, const void *valL,
+                  int l_dtype, const double *b, double *x, double rtol, int maxit, int32_t *iters, double *relres,
+                  void *ws, size_t ws_bytes)
+{
+    GIC_TRY(check_pattern(h, PA));
+    GIC_TRY(check_pattern(h, PL));
     if (!valA || !b || !x || !ws || maxit < 0 || !(rtol >= 0.0)) return GIC_ERR_INVALID_ARG;
     if (l_dtype != GIC_IDENTITY && !valL) return GIC_ERR_INVALID_ARG;
     if (l_dtype != GIC_F64 && l_dtype != GIC_F32 && l_dtype != GIC_IDENTITY) return GIC_ERR_INVALID_ARG;
-    const Pattern &p = P->p;
-    const SolveMode mode = solve_mode(h, p, l_dtype);
-    SolveWs W = carve(p, l_dtype, l_dtype == GIC_F32, ws);
+    const Pattern &p = PA->p, &pl = PL->p;
+    if (p.n != pl.n) return GIC_ERR_INVALID_ARG;
+    const SolveMode mode = solve_mode(h, pl, l_dtype);
+    SolveWs W = carve(p, pl, l_dtype, l_dtype == GIC_F32, ws);
     if (ws_bytes < W.bytes) return GIC_ERR_WORKSPACE;
     if (p.ngroups > 0 && (spmv_grid(h, p.nslices) > MAX_PARTIALS || vec_grid(h, p.n, VEC_BLOCK) > MAX_PARTIALS))
         return GIC_ERR_UNSUPPORTED;
-    return pcg_run(h, p, mode, valA, valL, b, x, rtol, maxit, iters, relres, W);
+    return pcg_run(h, p, pl, mode, valA, valL, b, x, rtol, maxit, iters, relres, W);
 }
 
 int gic_profile_enable(gic_handle *h, int on)

@@ -59,6 +59,12 @@ _SIGS = {
     "gic_ltsolve": (_int, [_vp, _vp, _vp, _int, _vp, _vp, _vp, _sz]),
     "gic_pcg": (_int, [_vp, _vp, _vp, _vp, _int, _vp, _vp, _dbl, _int, C.POINTER(_i32),
                        C.POINTER(_dbl), _vp, _sz]),
+    "gic_workspace_size_split": (_int, [_vp, _vp, _vp, _int, C.POINTER(_sz)]),
+    "gic_pcg_split": (_int, [_vp, _vp, _vp, _vp, _vp, _int, _vp, _vp, _dbl, _int, C.POINTER(_i32),
+                             C.POINTER(_dbl), _vp, _sz]),
+    "gic_dropout": (_int, [_vp, _vp, _vp, _dbl, _vp, _vp, _vp, C.POINTER(_i64), C.POINTER(_i64)]),
+    "gic_factor_deviation": (_int, [_vp, _vp, _vp, _vp, C.POINTER(_dbl)]),
+    "gic_identity_factor": (_int, [_vp, _vp, _int, _vp, _vp, _vp]),
     "gic_workspace_size": (_int, [_vp, _vp, _int, _int, C.POINTER(_sz)]),
     "gic_profile_enable": (_int, [_vp, _int]),
     "gic_profile_read": (_int, [_vp, C.POINTER(_dbl), C.POINTER(_i64)]),
@@ -296,6 +302,50 @@ def pcg(h: Handle, P: Pattern, valA, valL, b, x=None, rtol=1e-8, maxit=10000, ws
     if check and st not in (GIC_OK, GIC_ERR_NO_CONVERGENCE):
         raise GicError("gic_pcg", st)
     return dict(x=x, iters=it.value, relres=rr.value, status=st)
+
+
+def pcg_split(h: Handle, PA: Pattern, valA, PL: Pattern, valL, b, x=None, rtol=1e-8, maxit=10000, check=True):
+    """PCG with the SpMV on PA and the solves on PL's lower triangle."""
+    dt = _ldtype(valL)
+    nb = _sz()
+    _call("gic_workspace_size_split", h.h, PA.p, PL.p, dt, C.byref(nb))
+    ws = torch.empty(max(nb.value, 1), dtype=torch.uint8, device=b.device)
+    x = x if x is not None else torch.zeros_like(b)
+    it, rr = _i32(), _dbl()
+    st = lib().gic_pcg_split(h.h, PA.p, _ptr(valA), PL.p, _ptr(valL), dt, _ptr(b), _ptr(x), rtol, maxit,
+                             C.byref(it), C.byref(rr), _ptr(ws), ws.numel())
+    if check and st not in (GIC_OK, GIC_ERR_NO_CONVERGENCE):
+        raise GicError("gic_pcg_split", st)
+    return dict(x=x, iters=it.value, relres=rr.value, status=st)
+
+
+def dropout(h: Handle, P: Pattern, valL, threshold):
+    """Fill-in dropout (Eq. (10)): returns (Srowptr, Scol, Lval) -- the
+    symmetric pattern of the kept factor and its values in tril(S) order."""
+    dev = valL.device
+    Srp = torch.empty(P.n + 1, dtype=torch.int32, device=dev)
+    Sc = torch.empty(P.nnzA, dtype=torch.int32, device=dev)
+    Lv = torch.empty(P.nnzL, dtype=torch.float64, device=dev)
+    ns, nl = _i64(), _i64()
+    _call("gic_dropout", h.h, P.p, _ptr(valL), float(threshold), _ptr(Srp), _ptr(Sc), _ptr(Lv), C.byref(ns),
+          C.byref(nl))
+    return Srp, Sc[:ns.value].clone(), Lv[:nl.value].clone()
+
+
+def factor_deviation(h: Handle, P: Pattern, LIC, Lpred):
+    """(mean diag, max diag, mean off-diag, max off-diag, n diag, n off-diag)
+    of |Lpred - LIC| / |LIC|."""
+    out = (_dbl * 6)()
+    _call("gic_factor_deviation", h.h, P.p, _ptr(LIC), _ptr(Lpred), out)
+    return tuple(out)
+
+
+def identity_factor(h: Handle, P: Pattern, scale=None, ngraphs=1, want_L=True, want_hat=False):
+    dev = P.rowptr.device
+    L = torch.empty(P.nnzL, dtype=torch.float64, device=dev) if want_L else None
+    Lh = torch.empty(P.nnzL, dtype=torch.float32, device=dev) if want_hat else None
+    _call("gic_identity_factor", h.h, P.p, ngraphs, _ptr(scale), _ptr(L), _ptr(Lh))
+    return L, Lh
 
 
 def profile_enable(h: Handle, on=True):

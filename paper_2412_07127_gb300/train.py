@@ -32,9 +32,13 @@ def lr_at(t, warm, lr_max):
 
 
 class Trainer:
+    """mode "ic": the network corrects IC(0) (Eq. (2), the method); mode
+    "nic": it predicts L directly (Eq. (1), the paper's ablation), i.e. it
+    corrects the identity factor instead of L_IC."""
+
     def __init__(self, h, N=20, batch=16, probes=8, seed0=1000, sigma_lo=0.5, sigma_hi=2.0,
-                 device="cuda:0"):
-        self.h, self.N, self.B, self.m = h, N, batch, probes
+                 device="cuda:0", mode="ic"):
+        self.h, self.N, self.B, self.m, self.mode = h, N, batch, probes, mode
         self.seed0, self.lo, self.hi = seed0, sigma_lo, sigma_hi
         self.dev = torch.device(device)
         self.n = I.fem_sizes(N)[0]
@@ -69,7 +73,10 @@ class Trainer:
                 raise RuntimeError(f"IC(0) failed on batch {k} even with shifts")
             self.shifts.append(alpha)
         x9, e0, scale, Ahat = G.features(self.h, self.P, v, ngraphs=self.B, with_ahat=True)
-        LIChat = G.scale_factor(self.h, self.P, LIC, scale, ngraphs=self.B)
+        if self.mode == "nic":
+            LIChat = G.identity_factor(self.h, self.P, want_L=False, want_hat=True)[1]
+        else:
+            LIChat = G.scale_factor(self.h, self.P, LIC, scale, ngraphs=self.B)
         Z = np.concatenate([I.probes(self.m, self.n, s) for s in self._seeds(k)], axis=1)
         return x9, e0, Ahat, LIChat, torch.from_numpy(Z).to(self.dev)
 
@@ -91,8 +98,9 @@ class Trainer:
         return loss
 
 
-def validate(h, theta, N=20, seeds=range(9000, 9016), sigma=1.0, l_dtype=torch.float64):
-    """PCG iterations to 1e-8 with plain IC(0) and with the corrected factor."""
+def validate(h, theta, N=20, seeds=range(9000, 9016), sigma=1.0, l_dtype=torch.float64, mode="ic"):
+    """PCG iterations to 1e-8 with plain IC(0) and with the network's factor
+    (IC(0) corrected, or for mode "nic" the direct prediction)."""
     out = []
     dev = theta.device
     for s in seeds:
@@ -103,9 +111,12 @@ def validate(h, theta, N=20, seeds=range(9000, 9016), sigma=1.0, l_dtype=torch.f
         LIC, alpha, _ = G.ic0_auto(h, P, v)
         x9, e0, scale, _ = G.features(h, P, v)
         g = G.gnn_forward(h, P, theta, x9, e0)
-        L, ok = G.gnn_correct(h, P, LIC, g, scale)
+        base = G.identity_factor(h, P, scale)[0] if mode == "nic" else LIC
+        L, ok = G.gnn_correct(h, P, base, g, scale)
         r0 = G.pcg(h, P, v, LIC.to(l_dtype), b)
-        r1 = G.pcg(h, P, v, L.to(l_dtype), b) if ok else dict(iters=-1)
+        r1 = G.pcg(h, P, v, L.to(l_dtype), b, check=False) if ok else dict(iters=-1, status=-1)
+        if r1["status"] != 0:
+            r1 = dict(iters=-1)
         out.append(dict(seed=s, ic0=r0["iters"], gnn=r1["iters"], positive=ok, shift=alpha))
         P.close()
     return out
@@ -160,12 +171,13 @@ def main(argv=None):
     ap.add_argument("--time-limit", type=float, default=1e9, help="seconds; stop early")
     ap.add_argument("--val-every", type=int, default=0)
     ap.add_argument("--val-N", type=int, default=20)
+    ap.add_argument("--mode", default="ic", choices=["ic", "nic"])
     ap.add_argument("--out", required=True)
     ap.add_argument("--log", default=None)
     a = ap.parse_args(argv)
 
     h = G.Handle(0)
-    tr = Trainer(h, a.N, a.batch, a.probes, a.seed0)
+    tr = Trainer(h, a.N, a.batch, a.probes, a.seed0, mode=a.mode)
     dev = tr.dev
     theta = torch.from_numpy(I.gnn_init(a.init_seed, a.init_out_scale).astype(np.float32)).to(dev)
     m1, m2 = torch.zeros_like(theta), torch.zeros_like(theta)
@@ -183,7 +195,7 @@ def main(argv=None):
             log["steps"].append(rec)
             print(json.dumps(rec), flush=True)
         if a.val_every and (t + 1) % a.val_every == 0:
-            v = validate(h, theta, N=a.val_N, seeds=range(9000, 9004))
+            v = validate(h, theta, N=a.val_N, seeds=range(9000, 9004), mode=a.mode)
             log["val"].append(dict(step=t + 1, runs=v))
             print(json.dumps(dict(step=t + 1, val=v)), flush=True)
         if time.time() - t0 > a.time_limit:
@@ -194,7 +206,7 @@ def main(argv=None):
     log["ic0_shifts"] = sorted(set(tr.shifts))
     os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
     np.save(a.out, theta.cpu().numpy())
-    v = validate(h, theta, N=a.val_N)
+    v = validate(h, theta, N=a.val_N, mode=a.mode)
     log["final_val"] = v
     print(json.dumps(dict(final_val=v)), flush=True)
     with open(os.path.splitext(a.out)[0] + ".json", "w") as f:

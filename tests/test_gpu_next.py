@@ -1,0 +1,102 @@
+"""GPU parity of fill-in dropout (Supplementary 5, Eq. (10)) with PCG on the
+thinned factor, of the factor deviation diagnostic (Figure 5) and of the
+base factor of the direct prediction (Eq. (1), "NIC"), through the C-ABI."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2412_07127_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_07127_gb300 import build, gicpcg
+    build.build()
+    return gicpcg
+
+
+@pytest.fixture(scope="module")
+def h(G):
+    return G.Handle(0)
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _system(G, h, N, seed):
+    A = O.fem_hex_assemble(N, I.material_field(N, seed))
+    rp, c, v = _dev(A.rowptr), _dev(A.col), _dev(A.val)
+    return A, rp, c, v, G.Pattern(h, rp, c)
+
+
+@pytest.mark.parametrize("eps", [0.0, 0.001, 0.01, 0.02, 0.05])
+def test_dropout_matches_oracle_and_pcg(G, h, eps):
+    N = 8
+    A, rp, c, v, P = _system(G, h, N, 3)
+    L, _ = G.ic0(h, P, v)
+    _, _, scale, _ = G.features(h, P, v)
+    thr = eps * float(np.sqrt(scale.item()))
+    Srp, Sc, Lv = G.dropout(h, P, L, thr)
+    Lh = O.CSR(P.export(h)[0].cpu().numpy(), P.export(h)[1].cpu().numpy(), L.cpu().numpy())
+    Lo = O.dropout(Lh, thr)                       # same input values: exact
+    S = O.CSR(Srp.cpu().numpy(), Sc.cpu().numpy(), np.ones(Sc.numel()))
+    T = O.lower(S, with_values=False)
+    assert np.array_equal(T.rowptr, Lo.rowptr) and np.array_equal(T.col, Lo.col)
+    assert np.array_equal(Lv.cpu().numpy(), Lo.val)
+    D = np.zeros((A.n, A.n))
+    for i in range(A.n):
+        D[i, S.col[S.rowptr[i]:S.rowptr[i + 1]]] = 1
+    assert np.array_equal(D, D.T)
+    if eps == 0.0:
+        assert Lv.numel() == P.nnzL and Sc.numel() == P.nnzA
+    PS = G.Pattern(h, Srp, Sc)
+    assert PS.nnzL == Lv.numel()
+    b = I.rhs(A.n, 3)
+    r = G.pcg_split(h, P, v, PS, Lv, _dev(b), rtol=1e-8)
+    ro = O.pcg(A, b, Lo, tol=1e-8)
+    assert r["status"] == 0 and ro["status"] == 0
+    assert abs(r["iters"] - ro["iters"]) <= max(1, int(0.02 * ro["iters"])), (r["iters"], ro["iters"])
+    x = r["x"].cpu().numpy()
+    assert np.linalg.norm(x - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
+    if eps == 0.0:
+        assert r["iters"] == G.pcg(h, P, v, L, _dev(b), rtol=1e-8)["iters"]
+
+
+def test_factor_deviation_matches_oracle(G, h):
+    A, rp, c, v, P = _system(G, h, 6, 4)
+    L, _ = G.ic0(h, P, v)
+    rng = np.random.default_rng(5)
+    Lp = L * torch.from_numpy(1.0 + 0.3 * rng.standard_normal(P.nnzL)).to(DEV)
+    out = np.array(G.factor_deviation(h, P, L, Lp))
+    Lr, Lc, _, _ = P.export(h)
+    ref = O.factor_deviation(O.CSR(Lr.cpu().numpy(), Lc.cpu().numpy(), None), L.cpu().numpy(), Lp.cpu().numpy())
+    assert np.array_equal(out[4:], ref[4:])
+    assert np.allclose(out[:4], ref[:4], rtol=1e-12, atol=0)
+    assert out[4] == A.n and out[5] == P.nnzL - A.n
+
+
+def test_identity_factor_and_direct_prediction(G, h):
+    A, rp, c, v, P = _system(G, h, 4, 6)
+    x9, e0, scale, _ = G.features(h, P, v)
+    Lb, Lh = G.identity_factor(h, P, scale, want_hat=True)
+    Lr, Lc, _, _ = P.export(h)
+    Lr, Lc = Lr.cpu().numpy(), Lc.cpu().numpy()
+    rows = np.repeat(np.arange(A.n), np.diff(Lr))
+    diag = rows == Lc
+    s = scale.item()
+    assert np.array_equal(Lh.cpu().numpy(), diag.astype(np.float32))
+    assert np.allclose(Lb.cpu().numpy(), np.where(diag, np.sqrt(s), 0.0), rtol=1e-15, atol=0)
+    # the direct prediction is the correction of the identity base factor
+    th = I.gnn_init(3, out_scale=0.3)
+    g = G.gnn_forward(h, P, _dev(th.astype(np.float32)), x9, e0)
+    L, ok = G.gnn_correct(h, P, Lb, g, scale)
+    gg = g.cpu().numpy().astype(np.float64)
+    ref = np.where(diag, np.sqrt(s) * np.exp(gg / 2), np.sqrt(s) * gg)
+    assert ok and np.allclose(L.cpu().numpy(), ref, rtol=1e-6, atol=1e-12)
