@@ -304,11 +304,15 @@ int gic_adam_step(gic_handle *h, int64_t np, float *theta, const float *grad, fl
  * rows, <= 61 external columns), else 1 = staged one-warp solves (<= 3 rows,
  * <= 48 columns), else 0 = generic; a lower value caps the choice; GIC_TUNE_QDELTA = level
  * window of the dependencies the warp-specialised solves treat as "late"
- * (read by gic_analyze; default 6). */
+ * (read by gic_analyze; default 6); GIC_TUNE_GNN_BF16 = 1 (default): the
+ * inference forward (gic_gnn_forward, gic_solve_host) runs the edge MLP's
+ * first layer on the tensor cores with BF16 inputs and weights and FP32
+ * accumulation, 0: FP32 on the CUDA cores (gic_gnn_forward_train is FP32). */
 #define GIC_TUNE_SOLVE_WARPS_PER_SM 1
 #define GIC_TUNE_POLL 2
 #define GIC_TUNE_PIPELINE 3
 #define GIC_TUNE_QDELTA 4
+#define GIC_TUNE_GNN_BF16 5
 int gic_set_tuning(gic_handle *h, int key, int value);
 
 /* Failure-path self-test of the bounded device waits: one warp waits on a

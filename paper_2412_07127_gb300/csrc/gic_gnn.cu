@@ -817,14 +817,25 @@ struct FwdBufs {
     float *S[2], *M[2];
 };
 
+int edge_fwd_tc(gic_handle *h, int64_t E, const int32_t *Lrow, const int32_t *Lcol, const float *ein,
+                const float *e0, const float *x, const float *theta, int l, float *eout);
+
+// bf16: the edge MLP's first layer on the tensor cores (BF16 inputs and W1,
+// FP32 accumulation; gic_gnn_tc.cu), else FP32 on the CUDA cores
 static int gnn_forward_impl(gic_handle *h, const Pattern &p, int ngraphs, const float *theta, const float *x9,
-                            const float *e0, const FwdBufs &B, double *mu, double *sig, double *parts)
+                            const float *e0, const FwdBufs &B, double *mu, double *sig, double *parts,
+                            bool bf16 = false)
 {
     GIC_TRY(graphnorm(h, p, ngraphs, theta, x9, B.x[0], mu, sig, parts));
     const int64_t E = p.nnzL;
     for (int l = 0; l < 3; ++l) {
-        ++h->launches;
-        k_edge_fwd<<<grid1(h, E), 256, 0, h->stream>>>(E, p.Lrow, p.Lcol, B.ein[l], e0, B.x[l], theta, l, B.eout[l]);
+        if (bf16) {
+            GIC_TRY(edge_fwd_tc(h, E, p.Lrow, p.Lcol, B.ein[l], e0, B.x[l], theta, l, B.eout[l]));
+        } else {
+            ++h->launches;
+            k_edge_fwd<<<grid1(h, E), 256, 0, h->stream>>>(E, p.Lrow, p.Lcol, B.ein[l], e0, B.x[l], theta, l,
+                                                           B.eout[l]);
+        }
         if (l < 2) {
             ++h->launches;
             k_node_fwd<<<grid1(h, p.n), 256, 0, h->stream>>>(p.n, p.Lrowptr, p.Urowptr, p.tperm, B.eout[l], B.x[l],
@@ -943,7 +954,7 @@ int gic_gnn_forward(gic_handle *h, const gic_pattern *P, int ngraphs, const floa
     B.ein[0] = const_cast<float *>(e0); B.eout[0] = W.ea;
     B.ein[1] = W.ea; B.eout[1] = W.eb;
     B.ein[2] = W.eb; B.eout[2] = g;
-    return gnn_forward_impl(h, p, ngraphs, theta, x9, e0, B, W.mu, W.sig, W.parts);
+    return gnn_forward_impl(h, p, ngraphs, theta, x9, e0, B, W.mu, W.sig, W.parts, h->tune_gnn_bf16 != 0);
 }
 
 int gic_gnn_forward_train(gic_handle *h, const gic_pattern *P, int ngraphs, const float *theta, const float *x9,

@@ -365,7 +365,7 @@ def error_flags(h: Handle):
     return f.value
 
 
-GIC_TUNE_SOLVE_WARPS_PER_SM, GIC_TUNE_POLL, GIC_TUNE_PIPELINE, GIC_TUNE_QDELTA = 1, 2, 3, 4
+GIC_TUNE_SOLVE_WARPS_PER_SM, GIC_TUNE_POLL, GIC_TUNE_PIPELINE, GIC_TUNE_QDELTA, GIC_TUNE_GNN_BF16 = 1, 2, 3, 4, 5
 POLL_ONE_LANE = 1 << 16
 
 
