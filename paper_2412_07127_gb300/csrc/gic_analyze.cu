@@ -747,8 +747,9 @@ static int build_bsched(gic_handle *h, Pattern &P)
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, bad, 4, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) goto cuda_fail;
-    // the mirror of a block's rows must fit in shared memory (FP64 values)
-    if (hb == 0 && (size_t)rows_max * sizeof(double) <= 160 * 1024) {
+    // the mirror of a block's rows (FP64 values) must fit in shared memory
+    // beside the warps' staging rings (about 96 KB)
+    if (hb == 0 && (size_t)rows_max * sizeof(double) <= 120 * 1024) {
         e = cudaMalloc(&P.cb_ord_f, sizeof(int32_t) * ncb);
         if (e == cudaSuccess) e = cudaMalloc(&P.cb_ord_b, sizeof(int32_t) * ncb);
         if (e == cudaSuccess) e = cudaMemcpyAsync(P.cb_ord_f, of.data(), sizeof(int32_t) * ncb, cudaMemcpyHostToDevice, h->stream);

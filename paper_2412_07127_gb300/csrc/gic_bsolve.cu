@@ -20,9 +20,10 @@
 // the warp reduces the three sums, and lanes t < G finish
 //     y_t = -a_t - sum_{prev} K_tj y_prev_j
 // from the previous group's values held in registers. A group's static data
-// (columns, coefficients, right-hand side) is loaded one group ahead, and its
-// dependency values are read before the previous group is reduced and
-// published, so only values still missing then cost a further round trip.
+// (columns, coefficients, right-hand side) is staged in shared memory by
+// cp.async two groups ahead, and its dependency values are read before the
+// previous group is reduced and published, so only values still missing
+// then cost a further round trip.
 // Readiness is the value itself (signalling-NaN sentinel), in global and in
 // shared memory; every wait is bounded.
 #include <limits.h>
@@ -36,61 +37,54 @@ namespace gic {
 constexpr int BS_THREADS = BCHUNKS * 32;
 constexpr unsigned BFULL = 0xffffffffu;
 
+// a group's static data staged in shared memory (cp.async)
 template <typename T>
-struct GStat {
-    int32_t s, cw;      // first row, packed counts (warp-uniform)
-    int32_t c0, c1;     // dependency columns of positions lane, lane + 32 (-1: none)
-    T k0[3], k1[3];     // their coefficients for rows 0..2
-    T w0, w1;           // value of a right-hand-side position
-    T kp[3];            // lanes t < G: coefficients of the previous group's columns
-    int32_t pc[3];      // ... and those columns
-    double rdv;         // lanes t < G: r in FP64 (backward sweep with PCG)
+struct BSlot {
+    T K[3][QCOL];      // premultiplied coefficients, columns [early | late | prev]
+    T Mv[6];           // M = D^-1 packed (t, u <= t)
+    T rr[3];           // right-hand side rows
+    double rd[3];      // backward with PCG: r in FP64
+    int32_t cols[QCOL];
+    int32_t s, cw;
 };
+constexpr int BRING = 3; // slots per warp: the current group and two ahead
 
-template <typename T, bool FWD, bool PCG>
-__device__ __forceinline__ void b_load(GStat<T> &S, int32_t s, int32_t cw, int32_t b0, const int32_t *qcol,
-                                       const T *Kv, const T *rhs, const double *rd, int lane)
+template <typename T>
+__device__ __forceinline__ void b_stage(BSlot<T> &S, int32_t s, int32_t cw, int64_t b0, const int32_t *qcol,
+                                        const T *Kv, const T *rhs, const double *rd, int lane)
 {
-    const int ne = cw & 255, nl = (cw >> 8) & 255, np = (cw >> 16) & 255, G = cw >> 24;
-    const int m = ne + nl + np, mx = ne + nl;
-    S.s = s;
-    S.cw = cw;
+    const int m = (cw & 255) + ((cw >> 8) & 255) + ((cw >> 16) & 255), G = cw >> 24;
+    if (lane == 0) {
+        S.s = s;
+        S.cw = cw;
+    }
+    if (lane < m) cp_async_4(&S.cols[lane], qcol + b0 + lane);
+    if (lane + 32 < m) cp_async_4(&S.cols[lane + 32], qcol + b0 + lane + 32);
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const int p = lane + 32 * i, u = p - mx;
-        const bool dep = p < mx, own = u >= 0 && u < G;
-        const int32_t c = dep ? qcol[b0 + p] : -1;
-        T k[3];
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            T v = (T)0;
-            if (t < G) {
-                if (dep) v = Kv[b0 + (int64_t)t * m + p];
-                else if (own && (FWD ? u <= t : u >= t))
-                    v = -Kv[b0 + (int64_t)G * m + (FWD ? t * (t + 1) / 2 + u : u * (u + 1) / 2 + t)];
-            }
-            k[t] = v;
-        }
-        const T w = own ? rhs[s + u] : (T)0;
-        if (i == 0) {
-            S.c0 = c;
-            S.w0 = w;
-#pragma unroll
-            for (int t = 0; t < 3; ++t) S.k0[t] = k[t];
-        } else {
-            S.c1 = c;
-            S.w1 = w;
-#pragma unroll
-            for (int t = 0; t < 3; ++t) S.k1[t] = k[t];
+    for (int t = 0; t < 3; ++t) {
+        if (t < G) {
+            const T *row = Kv + b0 + (int64_t)t * m;
+            if (lane < m) cp_async_t(&S.K[t][lane], row + lane);
+            if (lane + 32 < m) cp_async_t(&S.K[t][lane + 32], row + lane + 32);
         }
     }
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        const bool have = lane < G && j < np;
-        S.kp[j] = have ? Kv[b0 + (int64_t)lane * m + mx + j] : (T)0;
-        S.pc[j] = have ? qcol[b0 + mx + j] : 0;
-    }
-    S.rdv = (PCG && lane < G) ? rd[s + lane] : 0.0;
+    if (lane < G * (G + 1) / 2) cp_async_t(&S.Mv[lane], Kv + b0 + (int64_t)G * m + lane);
+    if (lane < G) cp_async_t(&S.rr[lane], rhs + s + lane);
+    if (rd && lane < G) cp_async_8(&S.rd[lane], rd + s + lane);
+}
+
+// coefficient and value of position p of a staged group: p < mx a
+// dependency column (K, value loaded separately), mx <= p < mx + G the
+// group's own right-hand side (-M, rr)
+template <typename T, bool FWD>
+__device__ __forceinline__ T b_coef(const BSlot<T> &S, int t, int p, int mx, int G)
+{
+    if (t >= G) return (T)0;
+    if (p < mx) return S.K[t][p];
+    const int u = p - mx;
+    if (u >= G) return (T)0;
+    if (FWD) return (u <= t) ? -S.Mv[t * (t + 1) / 2 + u] : (T)0;
+    return (u >= t) ? -S.Mv[u * (u + 1) / 2 + t] : (T)0;
 }
 
 // bounded wait on a shared-memory word
@@ -103,10 +97,10 @@ __device__ __forceinline__ T smem_wait(const T *p, unsigned *err)
     for (long long it = 0; it < SPIN_LIMIT; ++it) {
         v = *q;
         if (!is_sentinel(v)) return v;
-        if ((it & 1023) == 1023) {
-            if (*((volatile unsigned *)err) != 0u) return qnan_of<T>();
-            __nanosleep(32);
-        }
+        // waiting warps back off so they do not take issue slots from the
+        // warps computing the values they wait for
+        if (it >= 8) __nanosleep(32);
+        if ((it & 1023) == 1023 && *((volatile unsigned *)err) != 0u) return qnan_of<T>();
     }
     atomicOr(err, ERR_TIMEOUT);
     return qnan_of<T>();
@@ -133,12 +127,12 @@ template <typename T, bool FWD, bool PCG>
 __device__ __forceinline__ void b_chunk(int32_t g0, int32_t g1, const int32_t *grp, const int32_t *rowptr,
                                         const int32_t *qcol, const int32_t *qcnt, const T *Kv, const T *rhs, T *x,
                                         T *yreset, const double *rd, T *mirror, int32_t lo, int32_t hi,
-                                        unsigned *err, int lane, double &dot)
+                                        BSlot<T> *ring, unsigned *err, int lane, double &dot)
 {
     const int cnt = g1 - g0;
     int32_t hs = 0, hc = 0, hb = 0; // headers of 32 groups, one per lane
     int wbase = -64;
-    auto header = [&](int k, int32_t &s, int32_t &cw, int32_t &b0) {
+    auto stage = [&](int k) {
         if (k - wbase >= 32) {
             wbase = k;
             const int kk = k + lane;
@@ -149,68 +143,74 @@ __device__ __forceinline__ void b_chunk(int32_t g0, int32_t g1, const int32_t *g
                 hb = rowptr[hs];
             }
         }
-        s = __shfl_sync(BFULL, hs, k - wbase);
-        cw = __shfl_sync(BFULL, hc, k - wbase);
-        b0 = __shfl_sync(BFULL, hb, k - wbase);
+        const int32_t s = __shfl_sync(BFULL, hs, k - wbase), cw = __shfl_sync(BFULL, hc, k - wbase);
+        const int32_t b0 = __shfl_sync(BFULL, hb, k - wbase);
+        b_stage<T>(ring[k % BRING], s, cw, b0, qcol, Kv, rhs, rd, lane);
     };
-    GStat<T> cur, nxt;
-    {
-        int32_t s, cw, b0;
-        header(0, s, cw, b0);
-        b_load<T, FWD, PCG>(cur, s, cw, b0, qcol, Kv, rhs, rd, lane);
-    }
-    // dependency values of the current group, loaded before the previous
-    // group is published (may still be the sentinel: re-polled when used)
-    T v0 = (cur.c0 >= 0) ? b_peek<T>(cur.c0, x, mirror, lo, hi) : cur.w0;
-    T v1 = (cur.c1 >= 0) ? b_peek<T>(cur.c1, x, mirror, lo, hi) : cur.w1;
+    // dependency values of a staged group (positions lane, lane + 32; the
+    // previous group's columns excluded), read before the group before it is
+    // published: may still be the sentinel, re-polled when used
+    auto peek = [&](const BSlot<T> &S, T &v0, T &v1) {
+        const int mx = (S.cw & 255) + ((S.cw >> 8) & 255);
+        v0 = (lane < mx) ? b_peek<T>(S.cols[lane], x, mirror, lo, hi) : (T)0;
+        v1 = (lane + 32 < mx) ? b_peek<T>(S.cols[lane + 32], x, mirror, lo, hi) : (T)0;
+    };
+    stage(0);
+    cp_async_commit();
+    if (cnt > 1) stage(1);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncwarp();
+    T v0, v1;
+    peek(ring[0], v0, v1);
     T p0 = 0, p1 = 0, p2 = 0; // the previous group's values
     int32_t prev_s = 0;
     for (int k = 0; k < cnt; ++k) {
-        if (k + 1 < cnt) {
-            int32_t s, cw, b0;
-            header(k + 1, s, cw, b0);
-            b_load<T, FWD, PCG>(nxt, s, cw, b0, qcol, Kv, rhs, rd, lane);
-        }
-        const int ne = cur.cw & 255, nl = (cur.cw >> 8) & 255, np = (cur.cw >> 16) & 255, G = cur.cw >> 24;
+        if (k + 2 < cnt) stage(k + 2);
+        cp_async_commit();
+        const BSlot<T> &S = ring[k % BRING];
+        const int ne = S.cw & 255, nl = (S.cw >> 8) & 255, np = (S.cw >> 16) & 255, G = S.cw >> 24;
         const int mx = ne + nl;
-        const bool two = mx + G > 32; // uniform
-        if (cur.c0 >= 0 && is_sentinel(v0)) v0 = b_fetch<T>(cur.c0, x, mirror, lo, hi, err);
-        if (two && cur.c1 >= 0 && is_sentinel(v1)) v1 = b_fetch<T>(cur.c1, x, mirror, lo, hi, err);
+        if (lane < mx && is_sentinel(v0)) v0 = b_fetch<T>(S.cols[lane], x, mirror, lo, hi, err);
+        if (lane + 32 < mx && is_sentinel(v1)) v1 = b_fetch<T>(S.cols[lane + 32], x, mirror, lo, hi, err);
+        const T w0 = (lane < mx) ? v0 : ((lane - mx < G) ? S.rr[lane - mx] : (T)0);
+        const T w1 = (lane + 32 < mx) ? v1 : ((lane + 32 - mx < G) ? S.rr[lane + 32 - mx] : (T)0);
         T a[3];
-        if (two) {
+        if (mx + G > 32) { // uniform
 #pragma unroll
-            for (int t = 0; t < 3; ++t) a[t] = fma(cur.k1[t], v1, cur.k0[t] * v0);
+            for (int t = 0; t < 3; ++t)
+                a[t] = fma(b_coef<T, FWD>(S, t, lane + 32, mx, G), w1, b_coef<T, FWD>(S, t, lane, mx, G) * w0);
         } else {
 #pragma unroll
-            for (int t = 0; t < 3; ++t) a[t] = cur.k0[t] * v0;
+            for (int t = 0; t < 3; ++t) a[t] = b_coef<T, FWD>(S, t, lane, mx, G) * w0;
         }
-        // the next group's dependencies other than this group: in flight
-        // while this group is reduced and published
-        if (k + 1 < cnt) {
-            v0 = (nxt.c0 >= 0) ? b_peek<T>(nxt.c0, x, mirror, lo, hi) : nxt.w0;
-            v1 = (nxt.c1 >= 0) ? b_peek<T>(nxt.c1, x, mirror, lo, hi) : nxt.w1;
+        if (k + 1 < cnt) { // the next group's data are in; its dependencies start loading
+            cp_async_wait<1>();
+            __syncwarp();
+            peek(ring[(k + 1) % BRING], v0, v1);
         }
         warp_sum_n<T, 3>(a, lane);
         T yv = 0;
         if (lane < G) {
             yv = -pick3<T>(lane, a[0], a[1], a[2]);
-#pragma unroll
-            for (int j = 0; j < 3; ++j)
-                if (j < np) yv = fma(-cur.kp[j], pick3<T>(cur.pc[j] - prev_s, p0, p1, p2), yv);
-            const int32_t row = cur.s + lane;
+            for (int j = 0; j < np; ++j)
+                yv = fma(-S.K[lane][mx + j], pick3<T>(S.cols[mx + j] - prev_s, p0, p1, p2), yv);
+            const int32_t row = S.s + lane;
             st_relaxed(x + row, yv);
             ((volatile T *)mirror)[row - lo] = yv;
             if (PCG) {
                 yreset[row] = sentinel_of<T>();
-                dot = fma(cur.rdv, (double)yv, dot);
+                dot = fma(S.rd[lane], (double)yv, dot);
             }
         }
         p0 = __shfl_sync(BFULL, yv, 0);
         p1 = __shfl_sync(BFULL, yv, 1);
         p2 = __shfl_sync(BFULL, yv, 2);
-        prev_s = cur.s;
-        cur = nxt;
+        prev_s = S.s;
+        __syncwarp(); // slot k is refilled two iterations later
     }
+    cp_async_wait<0>();
+    __syncwarp();
 }
 
 // FWD: L y = r (x = y, rhs = r). Backward: L^T z = y (x = z, rhs = y); with
@@ -229,7 +229,8 @@ __global__ void __launch_bounds__(BS_THREADS, 1) k_bsolve(int32_t nchunks, int32
 {
     if (sc && sc->done) return;
     extern __shared__ __align__(16) unsigned char b_raw[];
-    T *mirror = reinterpret_cast<T *>(b_raw);
+    BSlot<T> *ring = reinterpret_cast<BSlot<T> *>(b_raw) + (threadIdx.x >> 5) * BRING;
+    T *mirror = reinterpret_cast<T *>(b_raw + sizeof(BSlot<T>) * BRING * BCHUNKS);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     double dot = 0.0;
     for (int32_t bi = blockIdx.x; bi < ncb; bi += gridDim.x) {
@@ -241,7 +242,7 @@ __global__ void __launch_bounds__(BS_THREADS, 1) k_bsolve(int32_t nchunks, int32
         const int32_t c = c0 + w;
         if (c < c1)
             b_chunk<T, FWD, PCG>(chunk_grp[c], chunk_grp[c + 1], grp, rowptr, qcol, qcnt, Kv, rhs, x, yreset,
-                                 PCG ? rd : nullptr, mirror, lo, hi, err, lane, dot);
+                                 PCG ? rd : nullptr, mirror, lo, hi, ring, err, lane, dot);
         __syncthreads();
     }
     if (PCG) {
@@ -284,7 +285,7 @@ static int b_launch(gic_handle *h, const Pattern &P, const T *Kv, const T *rhs, 
     const int32_t *qc = FWD ? P.qf_col : P.qb_col, *qn = FWD ? P.qf_cnt : P.qb_cnt;
     unsigned *er = h->dev_err;
     void *args[] = {&nc, &ncb, &ord, &cg, &g, &rp, &qc, &qn, &Kv, &rhs, &x, &yreset, &rd, &partials, &er, &sc};
-    const size_t smem = sizeof(T) * (size_t)(P.mirror_rows > 0 ? P.mirror_rows : 1);
+    const size_t smem = sizeof(BSlot<T>) * BRING * BCHUNKS + sizeof(T) * (size_t)(P.mirror_rows > 0 ? P.mirror_rows : 1);
     static size_t ad[64] = {};
     if (ad[h->device & 63] < smem) {
         GIC_CUDA_TRY(cudaFuncSetAttribute(k_bsolve<T, FWD, PCG>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -36,6 +36,7 @@ namespace gic {
 constexpr int QR = 4;                    // ring slots per warp pair
 constexpr int QD = 2;                    // groups staged ahead by the producer
 constexpr int QPAIRS = SOLVE_BLOCK / 64; // warp pairs per block
+constexpr int QPAIRS_PER_SM = 4;         // default cap on resident pairs per SM
 constexpr unsigned FULL = 0xffffffffu;
 
 template <typename T>
@@ -218,7 +219,7 @@ __device__ __forceinline__ bool q_produce(QPair<T> &Q, int seq, int32_t g0, int3
 // Finisher of one chunk: lanes t < G own row t of the group.
 template <typename T, bool PCG>
 __device__ __forceinline__ bool q_finish(QPair<T> &Q, int seq, int cnt, T *x, T *yreset, unsigned *err, int lane,
-                                         double &dot)
+                                         double &dot, unsigned sleep_ns)
 {
     T yp = 0;          // lane t: row t of the previous group of the chunk
     int32_t prev_s = 0;
@@ -244,7 +245,7 @@ __device__ __forceinline__ bool q_finish(QPair<T> &Q, int seq, int cnt, T *x, T 
             for (int j = 0; j < QLATE; ++j) {
                 if (j < nl) {
                     T v = lv[j];
-                    if (is_sentinel(v)) v = wait_word(x + S.cols[ne + j], err, 0);
+                    if (is_sentinel(v)) v = wait_word(x + S.cols[ne + j], err, sleep_ns);
                     if (j & 1) acc2 = fma(-S.K[t][ne + j], v, acc2);
                     else acc = fma(-S.K[t][ne + j], v, acc);
                 }
@@ -303,7 +304,7 @@ __global__ void __launch_bounds__(SOLVE_BLOCK, 2) k_qsolve(int32_t nchunks, cons
             ok = q_produce<T, FWD>(Q, seq, g0, g1, grp, rowptr, qcol, qcnt, Kv, rhs, x, PCG ? rd : nullptr, err, poll,
                                    lane);
         else
-            ok = q_finish<T, PCG>(Q, seq, g1 - g0, x, yreset, err, lane, dot);
+            ok = q_finish<T, PCG>(Q, seq, g1 - g0, x, yreset, err, lane, dot, (unsigned)(poll & 0xffff));
         seq += g1 - g0;
     }
     if (PCG) {
@@ -415,11 +416,12 @@ static int q_launch(gic_handle *h, const Pattern &P, const T *Kv, const T *rhs, 
     unsigned *er = h->dev_err;
     int poll = h->tune_poll;
     void *args[] = {&nc, &ord, &cg, &g, &rp, &qc, &qn, &Kv, &rhs, &x, &yreset, &rd, &partials, &er, &poll, &sc};
-    int64_t need = 2 * (int64_t)nc; // warps: one pair per chunk
-    if (h->tune_solve_warps_per_sm > 0) {
-        const int64_t cap = 2 * (int64_t)h->tune_solve_warps_per_sm * h->num_sms;
-        if (need > cap) need = cap;
-    }
+    // warps: one pair per chunk, at most QPAIRS_PER_SM pairs per SM unless
+    // tuned (fewer co-resident pairs contend less for the FP64 pipe and issue
+    // slots; 4 measured best for the 40^3 hex system in FP64 and FP32)
+    int64_t need = 2 * (int64_t)nc;
+    const int per_sm = h->tune_solve_warps_per_sm > 0 ? h->tune_solve_warps_per_sm : QPAIRS_PER_SM;
+    if (need > 2 * (int64_t)per_sm * h->num_sms) need = 2 * (int64_t)per_sm * h->num_sms;
     if (PCG && need > MAX_PARTIALS) need = MAX_PARTIALS; // grid warps <= partial slots
     const size_t smem = sizeof(QPair<T>) * QPAIRS;
     static bool ad[64] = {};
