@@ -297,12 +297,14 @@ int gic_adam_step(gic_handle *h, int64_t np, float *theta, const float *grad, fl
  * solve warps (warp pairs for the warp-specialised solves) per SM (0 = no
  * cap); GIC_TUNE_POLL = polling: low 16 bits = nanoseconds slept between
  * polls, bit 16 set = one polling lane per warp (default 1<<16);
- * GIC_TUNE_PIPELINE = triangular-solve kernels: 3 = SM-local solves (blocks
- * of 16 neighbouring chunks per CTA, intra-block dependencies in shared
- * memory) where the pattern's block order allows, else 2 (default) =
- * warp-specialised solves on premultiplied row-group blocks (groups of <= 3
- * rows, <= 61 external columns), else 1 = staged one-warp solves (<= 3 rows,
- * <= 48 columns), else 0 = generic; a lower value caps the choice; GIC_TUNE_QDELTA = level
+ * GIC_TUNE_PIPELINE = triangular-solve kernels: 4 (default) = automatic
+ * (warp-specialised for an FP64 factor, staged one-warp for an FP32 factor),
+ * 3 = SM-local solves (blocks of 16 neighbouring chunks per CTA,
+ * intra-block dependencies in shared memory) where the pattern's block order
+ * allows, else 2 = warp-specialised solves on premultiplied row-group blocks
+ * (groups of <= 3 rows, <= 61 external columns), else 1 = staged one-warp
+ * solves (<= 3 rows, <= 48 columns), else 0 = generic; a lower value caps the
+ * choice; GIC_TUNE_QDELTA = level
  * window of the dependencies the warp-specialised solves treat as "late"
  * (read by gic_analyze; default 6); GIC_TUNE_GNN_BF16 = 1 (default): the
  * inference forward (gic_gnn_forward, gic_solve_host) runs the edge MLP's

@@ -322,7 +322,7 @@ struct gic_handle {
     long long launches = 0;        // kernels this handle has launched
     int tune_solve_warps_per_sm = 0; // cap on resident solve warps per SM (0: none)
     int tune_poll = gic::POLL_ONE_LANE; // polling configuration of the sync-free kernels
-    int tune_pipeline = 2;              // 3: SM-local, 2: warp-specialised, 1: staged, 0: generic solves
+    int tune_pipeline = 4;              // 4: automatic, 3: SM-local, 2: warp-specialised, 1: staged, 0: generic
     int tune_qdelta = 6;                // level window of the "late" columns (pattern analysis)
     int tune_gnn_bf16 = 1;              // GNN inference: edge MLP on the tensor cores in BF16 (0: FP32)
 };

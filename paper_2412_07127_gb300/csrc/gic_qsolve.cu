@@ -416,12 +416,14 @@ static int q_launch(gic_handle *h, const Pattern &P, const T *Kv, const T *rhs, 
     unsigned *er = h->dev_err;
     int poll = h->tune_poll;
     void *args[] = {&nc, &ord, &cg, &g, &rp, &qc, &qn, &Kv, &rhs, &x, &yreset, &rd, &partials, &er, &poll, &sc};
-    // warps: one pair per chunk, at most QPAIRS_PER_SM pairs per SM unless
-    // tuned (fewer co-resident pairs contend less for the FP64 pipe and issue
-    // slots; 4 measured best for the 40^3 hex system in FP64 and FP32)
+    // warps: one pair per chunk. With few chunks per SM (the 40^3 hex system:
+    // ~11) at most QPAIRS_PER_SM pairs per SM (fewer co-resident pairs contend
+    // less for the FP64 pipe and issue slots); with many (69^3: ~32, 148^3:
+    // ~145) as many as fit, since then the chunks queue for pairs.
     int64_t need = 2 * (int64_t)nc;
-    const int per_sm = h->tune_solve_warps_per_sm > 0 ? h->tune_solve_warps_per_sm : QPAIRS_PER_SM;
-    if (need > 2 * (int64_t)per_sm * h->num_sms) need = 2 * (int64_t)per_sm * h->num_sms;
+    int per_sm = h->tune_solve_warps_per_sm;
+    if (per_sm == 0 && (int64_t)nc < 16 * (int64_t)h->num_sms) per_sm = QPAIRS_PER_SM;
+    if (per_sm > 0 && need > 2 * (int64_t)per_sm * h->num_sms) need = 2 * (int64_t)per_sm * h->num_sms;
     if (PCG && need > MAX_PARTIALS) need = MAX_PARTIALS; // grid warps <= partial slots
     const size_t smem = sizeof(QPair<T>) * QPAIRS;
     static bool ad[64] = {};

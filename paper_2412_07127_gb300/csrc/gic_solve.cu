@@ -1155,9 +1155,15 @@ static bool pipelined_fits(const Pattern &P)
 static SolveMode solve_mode(const gic_handle *h, const Pattern &P, int l_dtype)
 {
     if (l_dtype == GIC_IDENTITY) return MODE_IDENT;
-    if (h->tune_pipeline >= 3 && P.bready) return (l_dtype == GIC_F32) ? MODE_B32 : MODE_B64;
-    if (h->tune_pipeline >= 2 && P.qready) return (l_dtype == GIC_F32) ? MODE_Q32 : MODE_Q64;
-    const bool pipe = h->tune_pipeline && pipelined_fits(P);
+    // automatic choice (measured on the hex systems from 40^3 to 148^3): the
+    // warp-specialised kernels take the FP64 work off the dependency chain,
+    // which pays for an FP64 factor; with an FP32 factor the staged one-warp
+    // kernels keep more chunks in flight and are faster
+    int pipeline = h->tune_pipeline;
+    if (pipeline >= 4) pipeline = (l_dtype == GIC_F32) ? 1 : 2;
+    if (pipeline >= 3 && P.bready) return (l_dtype == GIC_F32) ? MODE_B32 : MODE_B64;
+    if (pipeline >= 2 && P.qready) return (l_dtype == GIC_F32) ? MODE_Q32 : MODE_Q64;
+    const bool pipe = pipeline && pipelined_fits(P);
     if (l_dtype == GIC_F32) return pipe ? MODE_P32 : MODE_GEN32;
     return pipe ? MODE_P64 : MODE_GEN64;
 }

@@ -235,7 +235,7 @@ def test_spmv_matches_oracle(G, h):
     assert abs(_np(d)[0] - x @ yo) <= 1e-12 * abs(x @ yo)
 
 
-@pytest.mark.parametrize("pipeline", [3, 2, 1, 0])
+@pytest.mark.parametrize("pipeline", [4, 3, 2, 1, 0])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("case", ["fem8", "fem5", "random", "tridiag"])
 def test_triangular_solves_match_oracle(G, h, dtype, case, pipeline):
@@ -269,7 +269,7 @@ def test_triangular_solves_match_oracle(G, h, dtype, case, pipeline):
         nrel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
         assert nrel(_np(y), yo) <= 1e-5 and nrel(_np(z), zo) <= 1e-5
     assert G.error_flags(h) == 0
-    G.set_tuning(h, G.GIC_TUNE_PIPELINE, 2)
+    G.set_tuning(h, G.GIC_TUNE_PIPELINE, 4)
 
 
 @pytest.mark.parametrize("pipeline", [3, 2])
@@ -291,7 +291,7 @@ def test_solve_late_window_variants(G, h, qdelta, pipeline):
     assert _rel(_np(y), yo) <= 1e-11
     assert _rel(_np(z), O.ltsolve(Lo, yo)) <= 1e-11
     assert G.error_flags(h) == 0
-    G.set_tuning(h, G.GIC_TUNE_PIPELINE, 2)
+    G.set_tuning(h, G.GIC_TUNE_PIPELINE, 4)
 
 
 # ---------------------------------------------------------------- A7 PCG
@@ -340,7 +340,7 @@ def test_pcg_f32_factor(G, h, pipeline):
     P = G.Pattern(h, rp, c)
     Lg, _ = G.ic0(h, P, v)
     res = G.pcg(h, P, v, G.to_f32(h, Lg), _dev(b), rtol=1e-8)
-    G.set_tuning(h, G.GIC_TUNE_PIPELINE, 2)
+    G.set_tuning(h, G.GIC_TUNE_PIPELINE, 4)
     ro = O.pcg(A, b, L32, tol=1e-8)
     assert _iters_ok(res["iters"], ro["iters"]), (res["iters"], ro["iters"])
     x = _np(res["x"])
