@@ -13,7 +13,7 @@
 //    N = 32, K = 16 each, BF16 x BF16 -> FP32) into a 32-column TMEM
 //    accumulator and commits them to an mbarrier;
 //  * every thread reads its edge's 32 accumulators back with tcgen05.ld and
-//    finishes b1, tanh, W2 and b2 in FP32 on the CUDA cores.
+//    finishes b1, tanh (the hardware approximation), W2 and b2 in FP32.
 // W1 is rounded to BF16 once per CTA; b1, W2, b2 and the accumulation stay
 // FP32. The bounded mbarrier wait sets the error flag and skips the tile on
 // timeout; the TMEM columns are always released before the CTA exits.
@@ -58,6 +58,15 @@ constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(T
 __device__ __forceinline__ uint16_t tc_bf16(float v)
 {
     return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+
+// hardware tanh (PTX tanh.approx.f32, relative error about 2^-11): finer
+// than the BF16 rounding of the layer's inputs (2^-8)
+__device__ __forceinline__ float tc_tanh(float v)
+{
+    float r;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
 }
 
 __device__ __forceinline__ uint32_t tc_pack(float a, float b)
@@ -177,7 +186,7 @@ __global__ void __launch_bounds__(TC_M) k_edge_fwd_tc(int64_t E, const int32_t *
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         float out = b2s;
 #pragma unroll
-        for (int u = 0; u < TC_N; ++u) out = fmaf(W2[u], tanhf(__uint_as_float(r[u]) + b1[u]), out);
+        for (int u = 0; u < TC_N; ++u) out = fmaf(W2[u], tc_tanh(__uint_as_float(r[u]) + b1[u]), out);
         if (valid) eout[p] = out;
         // every thread's TMEM reads finish before the next tile's MMA
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -194,7 +203,10 @@ __global__ void __launch_bounds__(TC_M) k_edge_fwd_tc(int64_t E, const int32_t *
 int edge_fwd_tc(gic_handle *h, int64_t E, const int32_t *Lrow, const int32_t *Lcol, const float *ein,
                 const float *e0, const float *x, const float *theta, int l, float *eout)
 {
-    int64_t tiles = (E + TC_M - 1) / TC_M, cap = (int64_t)h->num_sms * 4;
+    // up to 8 CTAs per SM (registers allow 8 of 128 threads; 8 x 32 TMEM
+    // columns of the SM's 512): the tile loop has no internal overlap, so
+    // co-resident CTAs hide each other's gathers
+    int64_t tiles = (E + TC_M - 1) / TC_M, cap = (int64_t)h->num_sms * 8;
     if (tiles > cap) tiles = cap;
     if (tiles < 1) tiles = 1;
     ++h->launches;
