@@ -298,7 +298,8 @@ int gic_adam_step(gic_handle *h, int64_t np, float *theta, const float *grad, fl
  * cap); GIC_TUNE_POLL = polling: low 16 bits = nanoseconds slept between
  * polls, bit 16 set = one polling lane per warp (default 1<<16);
  * GIC_TUNE_PIPELINE = triangular-solve kernels: 4 (default) = automatic
- * (warp-specialised for an FP64 factor, staged one-warp for an FP32 factor),
+ * (warp-specialised unless the pattern has more than 64 chunks per SM, then
+ * staged one-warp),
  * 3 = SM-local solves (blocks of 16 neighbouring chunks per CTA,
  * intra-block dependencies in shared memory) where the pattern's block order
  * allows, else 2 = warp-specialised solves on premultiplied row-group blocks

@@ -46,6 +46,14 @@ __device__ __forceinline__ bool is_sentinel(double v)
     return (unsigned long long)__double_as_longlong(v) == SENTINEL_BITS;
 }
 
+// Relaxed load of a value that is its own ready flag (no other data is read
+// on the strength of it; code that reads other data after a wait puts a
+// fence in between). The FP64 flavour keeps a "memory" clobber, the FP32 one
+// does not: without it the compiler may move shared-memory reads ahead of the
+// load (a volatile asm is still never merged, hoisted out of a polling loop
+// or reordered with another volatile asm). Measured on the triangular
+// solves: the FP32 sweeps are 10-25% faster without the clobber, the FP64
+// ones 4-16% slower (their FMA chains are scheduled worse).
 __device__ __forceinline__ double ld_relaxed(const double *p)
 {
     double v;
@@ -112,7 +120,7 @@ __device__ __forceinline__ bool is_sentinel(float v) { return __float_as_uint(v)
 __device__ __forceinline__ float ld_relaxed(const float *p)
 {
     float v;
-    asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
     return v;
 }
 __device__ __forceinline__ void st_relaxed(float *p, float v)

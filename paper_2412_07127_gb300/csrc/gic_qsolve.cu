@@ -233,21 +233,62 @@ __device__ __forceinline__ bool q_finish(QPair<T> &Q, int seq, int cnt, T *x, T 
         T yv = 0;
         if (lane < G) {
             const int t = lane;
+            // the late loads go out first; the previous group's part (values
+            // in registers) is computed while they are in flight
             T lv[QLATE];
-#pragma unroll
-            for (int j = 0; j < QLATE; ++j) lv[j] = (j < nl) ? ld_relaxed(x + S.cols[ne + j]) : (T)0;
             T acc = S.base[t], acc2 = 0;
-            for (int j = 0; j < np; ++j) {
-                const int32_t cc = S.cols[ne + nl + j];
-                acc = fma(-S.K[t][ne + nl + j], pick3<T>(cc - prev_s, p0, p1, p2), acc);
-            }
+            if constexpr (sizeof(T) == 4) {
+                // FP32: every shared-memory operand into registers, all late
+                // loads in flight, one check, then an FMA pass in four chains
+                // (FP32 FMAs are cheap; the loads are the latency)
+                T kl[QLATE];
+                int32_t cl[QLATE];
 #pragma unroll
-            for (int j = 0; j < QLATE; ++j) {
-                if (j < nl) {
-                    T v = lv[j];
-                    if (is_sentinel(v)) v = wait_word(x + S.cols[ne + j], err, sleep_ns);
-                    if (j & 1) acc2 = fma(-S.K[t][ne + j], v, acc2);
-                    else acc = fma(-S.K[t][ne + j], v, acc);
+                for (int j = 0; j < QLATE; ++j) {
+                    cl[j] = (j < nl) ? S.cols[ne + j] : -1;
+                    kl[j] = (j < nl) ? S.K[t][ne + j] : (T)0;
+                }
+#pragma unroll
+                for (int j = 0; j < QLATE; ++j) lv[j] = (cl[j] >= 0) ? ld_relaxed(x + cl[j]) : (T)0;
+                for (int j = 0; j < np; ++j)
+                    acc = fma(-S.K[t][ne + nl + j], pick3<T>(S.cols[ne + nl + j] - prev_s, p0, p1, p2), acc);
+                bool missing = false;
+#pragma unroll
+                for (int j = 0; j < QLATE; ++j) missing |= (cl[j] >= 0) && is_sentinel(lv[j]);
+                if (missing) { // rare: wait for what was not there yet
+#pragma unroll
+                    for (int j = 0; j < QLATE; ++j)
+                        if (cl[j] >= 0 && is_sentinel(lv[j])) lv[j] = wait_word(x + cl[j], err, sleep_ns);
+                }
+                T acc1 = 0, acc3 = 0;
+#pragma unroll
+                for (int j = 0; j < QLATE; j += 4) {
+                    if (j < nl) {
+                        acc = fma(-kl[j], lv[j], acc);
+                        acc1 = fma(-kl[j + 1], lv[j + 1], acc1);
+                        acc2 = fma(-kl[j + 2], lv[j + 2], acc2);
+                        acc3 = fma(-kl[j + 3], lv[j + 3], acc3);
+                    }
+                }
+                acc += acc1;
+                acc2 += acc3;
+            } else {
+                // FP64: each value consumed as it arrives, exactly nl FMAs in
+                // two chains (a dependent FP64 FMA is ~65-360 cycles and every
+                // FP64 instruction costs SM pipe time, so the chain must
+                // overlap the loads)
+#pragma unroll
+                for (int j = 0; j < QLATE; ++j) lv[j] = (j < nl) ? ld_relaxed(x + S.cols[ne + j]) : (T)0;
+                for (int j = 0; j < np; ++j)
+                    acc = fma(-S.K[t][ne + nl + j], pick3<T>(S.cols[ne + nl + j] - prev_s, p0, p1, p2), acc);
+#pragma unroll
+                for (int j = 0; j < QLATE; ++j) {
+                    if (j < nl) {
+                        T v = lv[j];
+                        if (is_sentinel(v)) v = wait_word(x + S.cols[ne + j], err, sleep_ns);
+                        if (j & 1) acc2 = fma(-S.K[t][ne + j], v, acc2);
+                        else acc = fma(-S.K[t][ne + j], v, acc);
+                    }
                 }
             }
             yv = acc + acc2;

@@ -1156,11 +1156,12 @@ static SolveMode solve_mode(const gic_handle *h, const Pattern &P, int l_dtype)
 {
     if (l_dtype == GIC_IDENTITY) return MODE_IDENT;
     // automatic choice (measured on the hex systems from 40^3 to 148^3): the
-    // warp-specialised kernels take the FP64 work off the dependency chain,
-    // which pays for an FP64 factor; with an FP32 factor the staged one-warp
-    // kernels keep more chunks in flight and are faster
+    // warp-specialised kernels (two warps per chunk, FP64 work off the
+    // dependency chain) win while the chunks fit the resident warp pairs; with
+    // many more chunks than that the staged one-warp kernels win
     int pipeline = h->tune_pipeline;
-    if (pipeline >= 4) pipeline = (l_dtype == GIC_F32) ? 1 : 2;
+    if (pipeline >= 4) // many chunks per SM (the 148^3 system): the one-warp kernels keep more of them in flight
+        pipeline = ((int64_t)P.nchunks > 64 * (int64_t)h->num_sms) ? 1 : 2;
     if (pipeline >= 3 && P.bready) return (l_dtype == GIC_F32) ? MODE_B32 : MODE_B64;
     if (pipeline >= 2 && P.qready) return (l_dtype == GIC_F32) ? MODE_Q32 : MODE_Q64;
     const bool pipe = pipeline && pipelined_fits(P);
