@@ -183,6 +183,14 @@ int gic_pcg_split(gic_handle *h, const gic_pattern *PA, const double *valA, cons
  * of tril(S). Host outputs: *nnzS, *nnzL_out. */
 int gic_dropout(gic_handle *h, const gic_pattern *P, const double *valL, double threshold,
                 int32_t *Srowptr, int32_t *Scol, double *Lval_out, int64_t *nnzS, int64_t *nnzL_out);
+/* Node-granular variant (no counterpart in the paper; it keeps the row-group
+ * structure the fast solve kernels need): within each row group of P (rows
+ * with identical patterns, a hex node's three dofs) an external column is
+ * dropped from all the group's rows only when every one of their entries in
+ * it is at most threshold; the group's own lower block always stays.
+ * Arguments and outputs as gic_dropout. */
+int gic_dropout_grouped(gic_handle *h, const gic_pattern *P, const double *valL, double threshold,
+                        int32_t *Srowptr, int32_t *Scol, double *Lval_out, int64_t *nnzS, int64_t *nnzL_out);
 /* Deviation of a factor from the IC(0) factor (the diagnostic of the paper's
  * Figure 5): |Lpred_ij - LIC_ij| / |LIC_ij| over entries with LIC_ij != 0.
  * LIC, Lpred: device float64 on P. out (host, 6 values): mean and maximum on

@@ -65,6 +65,10 @@ def lib():
         L.or_dropout.argtypes = [_i64, _i32p, _i32p, _f64p, _dbl, _i32p, _i32p, _f64p]
         L.or_dropout.restype = _i64
         L.or_factor_deviation.argtypes = [_i64, _i32p, _i32p, _f64p, _f64p, _f64p]
+        L.or_row_groups.argtypes = [_i64, _i32p, _i32p, C.c_int, _i32p]
+        L.or_row_groups.restype = _i64
+        L.or_dropout_grouped.argtypes = [_i64, _i32p, _i32p, _f64p, _dbl, _i64, _i32p, _i32p, _i32p, _f64p]
+        L.or_dropout_grouped.restype = _i64
         L.or_lr_at.argtypes = [C.c_int, C.c_int, _dbl]
         L.or_lr_at.restype = _dbl
         _lib = L
@@ -308,3 +312,22 @@ def factor_deviation(L: CSR, LIC_val, Lpred_val):
     lib().or_factor_deviation(L.n, L.rowptr, L.col, np.ascontiguousarray(LIC_val, np.float64),
                               np.ascontiguousarray(Lpred_val, np.float64), out)
     return out
+
+
+def row_groups(A: CSR, gmax=8):
+    """Start rows of the runs of identical-pattern rows (cut every gmax), n last."""
+    st = np.zeros(A.n + 1, np.int32)
+    ng = lib().or_row_groups(A.n, A.rowptr, A.col, gmax, st)
+    return st[:ng + 1].copy()
+
+
+def dropout_grouped(L: CSR, thr, starts):
+    """Node-granular dropout: an external column leaves a row group only if all
+    the group's entries in it are <= thr."""
+    rp = np.zeros(L.n + 1, np.int32)
+    col = np.zeros(len(L.col), np.int32)
+    val = np.zeros(len(L.col))
+    st = np.ascontiguousarray(starts, np.int32)
+    k = lib().or_dropout_grouped(L.n, L.rowptr, L.col, np.ascontiguousarray(L.val, np.float64), thr,
+                                 len(st) - 1, st, rp, col, val)
+    return CSR(rp, col[:k].copy(), val[:k].copy())

@@ -36,6 +36,9 @@
  *   or_dropout                pinned: eps = 0 keeps L, a huge eps keeps the
  *                             diagonal only, hand-built 3x3 case
  *   or_factor_deviation       pinned: zero for equal factors, hand-built case
+ *   or_row_groups             pinned: hex nodes (groups of 3), hand-built runs
+ *   or_dropout_grouped        pinned: eps = 0 keeps L, reduces to or_dropout
+ *                             on single-row groups, hand-built 2-row group
  */
 #include <math.h>
 #include <stdint.h>
@@ -998,4 +1001,59 @@ void or_factor_deviation(int64_t n, const int32_t *Lrowptr, const int32_t *Lcol,
     out[3] = mo;
     out[4] = cd;
     out[5] = co;
+}
+
+/* Row groups: runs of consecutive rows with identical column sets in A, cut
+ * every gmax rows (a hex node's three dofs form one group). Writes the start
+ * rows and n at the end; returns the group count. */
+int64_t or_row_groups(int64_t n, const int32_t *rowptr, const int32_t *col, int gmax, int32_t *starts)
+{
+    int64_t ng = 0;
+    int64_t run = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int same = 0;
+        if (i > 0 && rowptr[i] - rowptr[i - 1] == rowptr[i + 1] - rowptr[i]) {
+            same = 1;
+            for (int32_t k = 0; k < rowptr[i + 1] - rowptr[i]; ++k)
+                if (col[rowptr[i - 1] + k] != col[rowptr[i] + k]) { same = 0; break; }
+        }
+        if (!same) run = i;
+        if ((i - run) % gmax == 0) starts[ng++] = (int32_t)i;
+    }
+    starts[ng] = (int32_t)n;
+    return ng;
+}
+
+/* Node-granular fill-in dropout: in every row group an external column of
+ * the factor is removed from all the group's rows only when every one of its
+ * entries there is at most thr in absolute value; the group's own lower
+ * block (in-group entries and diagonals) always stays. Output as or_dropout. */
+int64_t or_dropout_grouped(int64_t n, const int32_t *Lrowptr, const int32_t *Lcol, const double *Lval,
+                           double thr, int64_t ngroups, const int32_t *starts, int32_t *out_rowptr,
+                           int32_t *out_col, double *out_val)
+{
+    int64_t k = 0;
+    out_rowptr[0] = 0;
+    for (int64_t g = 0; g < ngroups; ++g) {
+        int32_t s = starts[g], e = starts[g + 1];
+        for (int32_t i = s; i < e; ++i) {
+            for (int32_t p = Lrowptr[i]; p < Lrowptr[i + 1]; ++p) {
+                int32_t c = Lcol[p];
+                int keep = 1;
+                if (c < s) { /* external column: position p - Lrowptr[i] is the same in every row */
+                    int32_t pos = p - Lrowptr[i];
+                    keep = 0;
+                    for (int32_t r = s; r < e; ++r)
+                        if (fabs(Lval[Lrowptr[r] + pos]) > thr) keep = 1;
+                }
+                if (keep) {
+                    out_col[k] = c;
+                    out_val[k] = Lval[p];
+                    ++k;
+                }
+            }
+            out_rowptr[i + 1] = (int32_t)k;
+        }
+    }
+    return k;
 }

@@ -32,6 +32,30 @@ __global__ void k_drop_keep(int64_t n, const int32_t *Lrowptr, const int32_t *Lc
     }
 }
 
+// Node-granular variant: in every row group an external column stays for all
+// the group's rows if any of their entries in it exceeds thr (the group's own
+// lower block always stays), so the kept rows of a group keep identical
+// patterns and the thinned factor still runs the row-group solve kernels.
+__global__ void k_drop_keep_grouped(int32_t ngroups, const int32_t *grp, const int32_t *Lrowptr, const double *Lval,
+                                    double thr, unsigned char *keep, int32_t *lcnt)
+{
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = grp[g], e = grp[g + 1];
+        const int32_t m = Lrowptr[s + 1] - Lrowptr[s] - 1; // external columns, shared by the group's rows
+        int32_t kept = 0;
+        for (int32_t k = 0; k < m; ++k) {
+            bool any = false;
+            for (int32_t r = s; r < e; ++r) any = any || (fabs(Lval[Lrowptr[r] + k]) > thr);
+            for (int32_t r = s; r < e; ++r) keep[Lrowptr[r] + k] = any ? 1 : 0;
+            kept += any ? 1 : 0;
+        }
+        for (int32_t r = s; r < e; ++r) {
+            for (int32_t p = Lrowptr[r] + m; p < Lrowptr[r + 1]; ++p) keep[p] = 1;
+            lcnt[r] = kept + (Lrowptr[r + 1] - Lrowptr[r] - m);
+        }
+    }
+}
+
 // Per row of A: which entries stay in S = L' + L'^T. Lower entries map to L
 // positions in order; upper entries of row i are the off-diagonal entries of
 // U row i (the transpose of L) in the same order, whose L positions tperm
@@ -146,8 +170,8 @@ using namespace gic;
 
 extern "C" {
 
-int gic_dropout(gic_handle *h, const gic_pattern *P, const double *valL, double threshold, int32_t *Srowptr,
-                int32_t *Scol, double *Lval_out, int64_t *nnzS, int64_t *nnzL_out)
+static int dropout_impl(gic_handle *h, const gic_pattern *P, const double *valL, double threshold, bool grouped,
+                        int32_t *Srowptr, int32_t *Scol, double *Lval_out, int64_t *nnzS, int64_t *nnzL_out)
 {
     GIC_TRY(check_handle(h));
     if (!P || P->p.device != h->device || !valL || !Srowptr || !Scol || !Lval_out || !(threshold >= 0.0))
@@ -168,7 +192,11 @@ int gic_dropout(gic_handle *h, const gic_pattern *P, const double *valL, double 
     int rc = GIC_OK;
     const unsigned g = x_grid(h, n);
     ++h->launches;
-    k_drop_keep<<<g, X_BLOCK, 0, h->stream>>>(n, p.Lrowptr, p.Lcol, valL, threshold, keep, lcnt);
+    if (grouped)
+        k_drop_keep_grouped<<<x_grid(h, p.ngroups), X_BLOCK, 0, h->stream>>>(p.ngroups, p.grp, p.Lrowptr, valL,
+                                                                            threshold, keep, lcnt);
+    else
+        k_drop_keep<<<g, X_BLOCK, 0, h->stream>>>(n, p.Lrowptr, p.Lcol, valL, threshold, keep, lcnt);
     e = cudaGetLastError();
     if (e == cudaSuccess) rc = scan_excl_i32(h, lcnt, n, lptr, &tl);
     if (e == cudaSuccess && rc == GIC_OK) {
@@ -194,6 +222,18 @@ int gic_dropout(gic_handle *h, const gic_pattern *P, const double *valL, double 
     if (nnzS) *nnzS = ts;
     if (nnzL_out) *nnzL_out = tl;
     return GIC_OK;
+}
+
+int gic_dropout(gic_handle *h, const gic_pattern *P, const double *valL, double threshold, int32_t *Srowptr,
+                int32_t *Scol, double *Lval_out, int64_t *nnzS, int64_t *nnzL_out)
+{
+    return dropout_impl(h, P, valL, threshold, false, Srowptr, Scol, Lval_out, nnzS, nnzL_out);
+}
+
+int gic_dropout_grouped(gic_handle *h, const gic_pattern *P, const double *valL, double threshold, int32_t *Srowptr,
+                        int32_t *Scol, double *Lval_out, int64_t *nnzS, int64_t *nnzL_out)
+{
+    return dropout_impl(h, P, valL, threshold, true, Srowptr, Scol, Lval_out, nnzS, nnzL_out);
 }
 
 int gic_factor_deviation(gic_handle *h, const gic_pattern *P, const double *LIC, const double *Lpred, double *out)

@@ -4,7 +4,8 @@ sequences calls and times them with CUDA events):
 
   dropout    fill-in dropout (Supplementary 5, Eq. (10), Table 3): for each
              epsilon, nnz of the thinned factor, PCG iterations, setup and CG
-             time, mean triangular-solve time.
+             time, mean triangular-solve time. --grouped thins per row
+             group (a node's rows) instead of per entry.
   deviation  the factor deviation of the paper's Figure 5: mean and maximum
              |L - L_IC| / |L_IC| on and off the diagonal for the shipped
              network (correcting IC(0)) and for a direct prediction.
@@ -45,13 +46,13 @@ def _timed(fn):
     return out, e0.elapsed_time(e1) / 1e3
 
 
-def dropout(h, N, seed, eps_list, f32):
+def dropout(h, N, seed, eps_list, f32, grouped=False):
     rp, c, v, P, b = _system(h, N, seed)
     L, _ = G.ic0(h, P, v)
     _, _, scale, _ = G.features(h, P, v)
     sq = float(np.sqrt(scale.item()))
     for eps in eps_list:
-        (Srp, Sc, Lv), t_drop = _timed(lambda: G.dropout(h, P, L, eps * sq))
+        (Srp, Sc, Lv), t_drop = _timed(lambda: G.dropout(h, P, L, eps * sq, grouped=grouped))
         PS, t_an = _timed(lambda: G.Pattern(h, Srp, Sc))
         Lr = G.to_f32(h, Lv) if f32 else Lv
         G.pcg_split(h, P, v, PS, Lr, b, maxit=3)  # warm
@@ -63,7 +64,9 @@ def dropout(h, N, seed, eps_list, f32):
         print(json.dumps({"experiment": "dropout", "N": N, "n": P.n, "eps": eps, "nnzL": int(Lv.numel()),
                           "nnzL_fraction": Lv.numel() / P.nnzL, "iters": r["iters"], "relres": r["relres"],
                           "setup_s": t_drop + t_an, "cg_s": t_cg, "trisolve_pair_s": tri,
-                          "l_dtype": "f32" if f32 else "f64"}), flush=True)
+                          "l_dtype": "f32" if f32 else "f64", "granularity": "node" if grouped else "entry",
+                          "solve_kernels": "warp-specialised" if PS.warp_specialised else "staged"}),
+              flush=True)
         PS.close()
 
 
@@ -108,11 +111,13 @@ def main(argv=None):
     ap.add_argument("--seeds", default="9000,9001,9002,9003")
     ap.add_argument("--eps", default="0,0.001,0.01,0.02")
     ap.add_argument("--f32", action="store_true", help="apply the thinned factor in FP32")
+    ap.add_argument("--grouped", action="store_true",
+                    help="node-granular dropout: a column leaves all rows of a row group or none")
     ap.add_argument("--weights", default=WEIGHTS)
     a = ap.parse_args(argv)
     h = G.Handle(0)
     if a.experiment == "dropout":
-        dropout(h, a.N, a.seed, [float(x) for x in a.eps.split(",")], a.f32)
+        dropout(h, a.N, a.seed, [float(x) for x in a.eps.split(",")], a.f32, a.grouped)
     elif a.experiment == "deviation":
         deviation(h, a.N, a.seed, a.weights)
     else:

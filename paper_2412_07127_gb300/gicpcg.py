@@ -63,6 +63,7 @@ _SIGS = {
     "gic_pcg_split": (_int, [_vp, _vp, _vp, _vp, _vp, _int, _vp, _vp, _dbl, _int, C.POINTER(_i32),
                              C.POINTER(_dbl), _vp, _sz]),
     "gic_dropout": (_int, [_vp, _vp, _vp, _dbl, _vp, _vp, _vp, C.POINTER(_i64), C.POINTER(_i64)]),
+    "gic_dropout_grouped": (_int, [_vp, _vp, _vp, _dbl, _vp, _vp, _vp, C.POINTER(_i64), C.POINTER(_i64)]),
     "gic_factor_deviation": (_int, [_vp, _vp, _vp, _vp, C.POINTER(_dbl)]),
     "gic_identity_factor": (_int, [_vp, _vp, _int, _vp, _vp, _vp]),
     "gic_workspace_size": (_int, [_vp, _vp, _int, _int, C.POINTER(_sz)]),
@@ -319,16 +320,17 @@ def pcg_split(h: Handle, PA: Pattern, valA, PL: Pattern, valL, b, x=None, rtol=1
     return dict(x=x, iters=it.value, relres=rr.value, status=st)
 
 
-def dropout(h: Handle, P: Pattern, valL, threshold):
+def dropout(h: Handle, P: Pattern, valL, threshold, grouped=False):
     """Fill-in dropout (Eq. (10)): returns (Srowptr, Scol, Lval) -- the
-    symmetric pattern of the kept factor and its values in tril(S) order."""
+    symmetric pattern of the kept factor and its values in tril(S) order.
+    grouped: the node-granular variant (gic_dropout_grouped)."""
     dev = valL.device
     Srp = torch.empty(P.n + 1, dtype=torch.int32, device=dev)
     Sc = torch.empty(P.nnzA, dtype=torch.int32, device=dev)
     Lv = torch.empty(P.nnzL, dtype=torch.float64, device=dev)
     ns, nl = _i64(), _i64()
-    _call("gic_dropout", h.h, P.p, _ptr(valL), float(threshold), _ptr(Srp), _ptr(Sc), _ptr(Lv), C.byref(ns),
-          C.byref(nl))
+    _call("gic_dropout_grouped" if grouped else "gic_dropout", h.h, P.p, _ptr(valL), float(threshold), _ptr(Srp),
+          _ptr(Sc), _ptr(Lv), C.byref(ns), C.byref(nl))
     return Srp, Sc[:ns.value].clone(), Lv[:nl.value].clone()
 
 

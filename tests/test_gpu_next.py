@@ -69,6 +69,33 @@ def test_dropout_matches_oracle_and_pcg(G, h, eps):
         assert r["iters"] == G.pcg(h, P, v, L, _dev(b), rtol=1e-8)["iters"]
 
 
+
+@pytest.mark.parametrize("eps", [0.0, 0.01, 0.05])
+def test_dropout_grouped_matches_oracle(G, h, eps):
+    N = 8
+    A, rp, c, v, P = _system(G, h, N, 5)
+    L, _ = G.ic0(h, P, v)
+    _, _, scale, _ = G.features(h, P, v)
+    thr = eps * float(np.sqrt(scale.item()))
+    Srp, Sc, Lv = G.dropout(h, P, L, thr, grouped=True)
+    Lh = O.CSR(P.export(h)[0].cpu().numpy(), P.export(h)[1].cpu().numpy(), L.cpu().numpy())
+    Lo = O.dropout_grouped(Lh, thr, O.row_groups(A))
+    S = O.CSR(Srp.cpu().numpy(), Sc.cpu().numpy(), np.ones(Sc.numel()))
+    T = O.lower(S, with_values=False)
+    assert np.array_equal(T.rowptr, Lo.rowptr) and np.array_equal(T.col, Lo.col)
+    assert np.array_equal(Lv.cpu().numpy(), Lo.val)
+    assert Lv.numel() >= G.dropout(h, P, L, thr)[2].numel()
+    PS = G.Pattern(h, Srp, Sc)
+    assert PS.warp_specialised == 1                 # node groups survive the thinning
+    b = I.rhs(A.n, 5)
+    r = G.pcg_split(h, P, v, PS, Lv, _dev(b), rtol=1e-8)
+    ro = O.pcg(A, b, Lo, tol=1e-8)
+    assert r["status"] == 0 and ro["status"] == 0
+    assert abs(r["iters"] - ro["iters"]) <= max(1, int(0.02 * ro["iters"])), (r["iters"], ro["iters"])
+    x = r["x"].cpu().numpy()
+    assert np.linalg.norm(x - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
+    PS.close()
+
 def test_factor_deviation_matches_oracle(G, h):
     A, rp, c, v, P = _system(G, h, 6, 4)
     L, _ = G.ic0(h, P, v)

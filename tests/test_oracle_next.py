@@ -51,3 +51,44 @@ def test_factor_deviation_hand_case():
     out = O.factor_deviation(L, LIC, Lp)
     assert np.allclose(out, [0.05, 0.1, 1.0, 1.0, 2.0, 1.0], rtol=0, atol=1e-15)
     assert np.array_equal(O.factor_deviation(L, LIC, LIC), [0, 0, 0, 0, 2, 1])
+
+
+def test_row_groups():
+    A = O.fem_hex_assemble(3, I.material_field(3, 1))
+    assert np.array_equal(O.row_groups(A), np.arange(0, A.n + 1, 3))      # a node's three dofs
+    D = np.eye(6) * 4
+    D[2, 0] = D[0, 2] = D[3, 0] = D[0, 3] = D[3, 1] = D[1, 3] = -1       # rows 2 and 3 differ
+    st = O.row_groups(O.csr_from_dense(D), gmax=2)
+    assert list(st) == [0, 1, 2, 3, 4, 5, 6]
+    E = 4 * np.eye(5) + np.ones((5, 5))                                   # dense: one run
+    assert list(O.row_groups(O.csr_from_dense(E), gmax=2)) == [0, 2, 4, 5]
+
+
+def test_dropout_grouped():
+    A = O.fem_hex_assemble(3, I.material_field(3, 2))
+    L, _ = O.ic0(A)
+    st = O.row_groups(A)
+    same = O.dropout_grouped(L, 0.0, st)
+    assert np.array_equal(same.col, L.col) and np.array_equal(same.val, L.val)
+    # with one row per group it is the entry-wise dropout
+    single = np.arange(L.n + 1, dtype=np.int32)
+    thr = 0.05 * np.abs(L.val).max()
+    a, b = O.dropout_grouped(L, thr, single), O.dropout(L, thr)
+    assert np.array_equal(a.rowptr, b.rowptr) and np.array_equal(a.col, b.col) and np.array_equal(a.val, b.val)
+    # grouped keeps a superset of the entries, and the groups' rows stay alike
+    g = O.dropout_grouped(L, thr, st)
+    assert len(g.col) >= len(b.col)
+    for k in range(len(st) - 1):
+        s, e = st[k], st[k + 1]
+        ext = [set(c for c in g.col[g.rowptr[r]:g.rowptr[r + 1]] if c < s) for r in range(s, e)]
+        assert all(x == ext[0] for x in ext)
+
+
+def test_dropout_grouped_hand_case():
+    # rows 1 and 2 form a group (identical columns {0, 1, 2}); column 0 is kept
+    # for both because row 2's entry is large, although row 1's is small
+    D = np.array([[4.0, 0.005, -0.5], [0.005, 2.0, 0.1], [-0.5, 0.1, 3.0]])
+    L = O.lower(O.csr_from_dense(D))
+    Lv = O.CSR(L.rowptr, L.col, np.array([2.0, 0.005, 1.0, -0.5, 0.1, 3.0]))
+    g = O.dropout_grouped(Lv, 0.01, np.array([0, 1, 3], np.int32))
+    assert list(g.col) == [0, 0, 1, 0, 1, 2]
