@@ -405,7 +405,7 @@ def run_ours(args, rank, world, local):
            "gnn_kept": bool(recs[-1][3]), "ic0_shift": recs[-1][4], "gnn_policy": gnn_policy(),
            "kernels": kern, "roofline": roof, "spmv_roofline": spmv_roof, "clocks": clk,
            "gpu_launches": launches,
-           "schedule": {"chunks": P.nchunks, "multi_group_chunks": bool(P.chunked), "sell_padding":
+           "schedule": {"chunks": P.nchunks, "multi_group_chunks": bool(P.chunked), "chunk_order": P.chunked, "sell_padding":
                         P.sell_nnz / P.nnzA - 1.0},
            "f32_apply": other}
 

@@ -99,8 +99,11 @@ int gic_pattern_destroy(gic_pattern *P);
 int gic_pattern_info(const gic_pattern *P, int64_t *n, int64_t *nnzA, int64_t *nnzL,
                      int32_t *nlevels, int32_t *ngroups);
 /* Schedule of the sync-free kernels (host outputs, any may be NULL): number
- * of chunks (runs of row groups one warp processes in order), whether they
- * are multi-group runs (1) or single groups in level order (0), and the
+ * of chunks (runs of row groups one warp processes in order), how they are
+ * ordered -- 0: single groups in level order; 1: multi-group runs in order of
+ * their first (forward) or last (backward) level; 2: multi-group runs in a
+ * topological order of their dependencies, taken when the level order would
+ * start a run before one it reads (as thinning a factor can make) -- and the
  * padded entry count of the SELL-32 copy of A used by the PCG SpMV. */
 int gic_pattern_schedule(const gic_pattern *P, int32_t *nchunks, int32_t *chunked, int64_t *sell_nnz);
 /* Which triangular-solve kernels the pattern admits (host outputs, any may be

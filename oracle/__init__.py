@@ -322,8 +322,8 @@ def row_groups(A: CSR, gmax=8):
 
 
 def dropout_grouped(L: CSR, thr, starts):
-    """Node-granular dropout: an external column leaves a row group only if all
-    the group's entries in it are <= thr."""
+    """Node-granular dropout: the external block of row group g against an
+    earlier group h leaves the factor only if all its entries are <= thr."""
     rp = np.zeros(L.n + 1, np.int32)
     col = np.zeros(len(L.col), np.int32)
     val = np.zeros(len(L.col))

@@ -36,9 +36,11 @@
  *   or_dropout                pinned: eps = 0 keeps L, a huge eps keeps the
  *                             diagonal only, hand-built 3x3 case
  *   or_factor_deviation       pinned: zero for equal factors, hand-built case
- *   or_row_groups             pinned: hex nodes (groups of 3), hand-built runs
+ *   or_row_groups             pinned: hex nodes (groups of 3), hand-built runs,
+ *                             runs cut at their common length
  *   or_dropout_grouped        pinned: eps = 0 keeps L, reduces to or_dropout
- *                             on single-row groups, hand-built 2-row group
+ *                             on single-row groups, hand-built 2x2 blocks,
+ *                             node blocks kept whole (hex)
  */
 #include <math.h>
 #include <stdint.h>
@@ -1004,34 +1006,57 @@ void or_factor_deviation(int64_t n, const int32_t *Lrowptr, const int32_t *Lcol,
 }
 
 /* Row groups: runs of consecutive rows with identical column sets in A, cut
- * every gmax rows (a hex node's three dofs form one group). Writes the start
- * rows and n at the end; returns the group count. */
+ * every c rows, c being the greatest common divisor of the run lengths when
+ * it lies in 2..gmax and gmax otherwise (a hex node's three dofs form one
+ * group even where two nodes have identical rows). Writes the start rows and
+ * n at the end; returns the group count. */
+static int same_row(const int32_t *rowptr, const int32_t *col, int64_t a, int64_t b)
+{
+    if (rowptr[a + 1] - rowptr[a] != rowptr[b + 1] - rowptr[b]) return 0;
+    for (int32_t k = 0; k < rowptr[a + 1] - rowptr[a]; ++k)
+        if (col[rowptr[a] + k] != col[rowptr[b] + k]) return 0;
+    return 1;
+}
+
 int64_t or_row_groups(int64_t n, const int32_t *rowptr, const int32_t *col, int gmax, int32_t *starts)
 {
-    int64_t ng = 0;
-    int64_t run = 0;
-    for (int64_t i = 0; i < n; ++i) {
-        int same = 0;
-        if (i > 0 && rowptr[i] - rowptr[i - 1] == rowptr[i + 1] - rowptr[i]) {
-            same = 1;
-            for (int32_t k = 0; k < rowptr[i + 1] - rowptr[i]; ++k)
-                if (col[rowptr[i - 1] + k] != col[rowptr[i] + k]) { same = 0; break; }
+    int64_t g = 0, run = 0;
+    for (int64_t i = 1; i <= n; ++i) {
+        if (i == n || !same_row(rowptr, col, i - 1, i)) {
+            int64_t a = g, b = i - run;
+            while (b) {
+                int64_t t = a % b;
+                a = b;
+                b = t;
+            }
+            g = a;
+            run = i;
         }
-        if (!same) run = i;
-        if ((i - run) % gmax == 0) starts[ng++] = (int32_t)i;
+    }
+    int64_t cut = (g >= 2 && g <= gmax) ? g : gmax;
+    int64_t ng = 0;
+    run = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (i > 0 && !same_row(rowptr, col, i - 1, i)) run = i;
+        if ((i - run) % cut == 0) starts[ng++] = (int32_t)i;
     }
     starts[ng] = (int32_t)n;
     return ng;
 }
 
-/* Node-granular fill-in dropout: in every row group an external column of
- * the factor is removed from all the group's rows only when every one of its
- * entries there is at most thr in absolute value; the group's own lower
- * block (in-group entries and diagonals) always stays. Output as or_dropout. */
+/* Node-granular fill-in dropout: the factor is cut into blocks by the row
+ * groups (rows of one group against the columns of one group); an external
+ * block -- rows of group g, columns of an earlier group h -- is removed as a
+ * whole when every one of its entries is at most thr in absolute value, and
+ * group g's own lower block (in-group entries and diagonals) always stays.
+ * Output as or_dropout. */
 int64_t or_dropout_grouped(int64_t n, const int32_t *Lrowptr, const int32_t *Lcol, const double *Lval,
                            double thr, int64_t ngroups, const int32_t *starts, int32_t *out_rowptr,
                            int32_t *out_col, double *out_val)
 {
+    int64_t *gof = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t g = 0; g < ngroups; ++g)
+        for (int32_t i = starts[g]; i < starts[g + 1]; ++i) gof[i] = g;
     int64_t k = 0;
     out_rowptr[0] = 0;
     for (int64_t g = 0; g < ngroups; ++g) {
@@ -1040,11 +1065,12 @@ int64_t or_dropout_grouped(int64_t n, const int32_t *Lrowptr, const int32_t *Lco
             for (int32_t p = Lrowptr[i]; p < Lrowptr[i + 1]; ++p) {
                 int32_t c = Lcol[p];
                 int keep = 1;
-                if (c < s) { /* external column: position p - Lrowptr[i] is the same in every row */
-                    int32_t pos = p - Lrowptr[i];
+                if (c < s) { /* external column, in group h */
+                    int64_t h = gof[c];
                     keep = 0;
                     for (int32_t r = s; r < e; ++r)
-                        if (fabs(Lval[Lrowptr[r] + pos]) > thr) keep = 1;
+                        for (int32_t q = Lrowptr[r]; q < Lrowptr[r + 1] && Lcol[q] < s; ++q)
+                            if (gof[Lcol[q]] == h && fabs(Lval[q]) > thr) keep = 1;
                 }
                 if (keep) {
                     out_col[k] = c;
@@ -1055,5 +1081,6 @@ int64_t or_dropout_grouped(int64_t n, const int32_t *Lrowptr, const int32_t *Lco
             out_rowptr[i + 1] = (int32_t)k;
         }
     }
+    free(gof);
     return k;
 }

@@ -241,11 +241,45 @@ __global__ void k_run_keys(int64_t n, const int32_t *same, int32_t *key)
         key[i] = same[i] ? -1 : (int32_t)i;
 }
 
-// group starts: run start, or every GMAX rows inside a run
-__global__ void k_group_flags(int64_t n, const int32_t *runstart, int32_t *gflag)
+// Greatest common divisor of the run lengths (a run ends where the next row
+// differs): the pattern's natural block size, e.g. 3 for a hex node's dofs.
+__device__ __forceinline__ int32_t gcd_i32(int32_t a, int32_t b)
+{
+    while (b) {
+        const int32_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+__global__ void k_run_gcd(int64_t n, const int32_t *same, const int32_t *runstart, int32_t *out)
+{
+    int32_t g = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (i == n - 1 || !same[i + 1]) g = gcd_i32(g, (int32_t)(i + 1 - runstart[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) g = gcd_i32(g, __shfl_xor_sync(0xffffffffu, g, o));
+    if ((threadIdx.x & 31) == 0 && g > 0) {
+        int32_t old = *((volatile int32_t *)out);
+        for (;;) {
+            const int32_t nv = gcd_i32(old, g);
+            if (nv == old) break;
+            const int32_t prev = atomicCAS(out, old, nv);
+            if (prev == old) break;
+            old = prev;
+        }
+    }
+}
+
+// group starts: run start, or every gcut rows inside a run, gcut being the
+// natural block size when it is 2 .. GMAX, else GMAX. Cutting runs at the
+// block size keeps one group per block where blocks of a thinned pattern
+// happen to have identical rows.
+__global__ void k_group_flags(int64_t n, const int32_t *runstart, int32_t gcut, int32_t *gflag)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        gflag[i] = ((i - runstart[i]) % GMAX) == 0;
+        gflag[i] = ((i - runstart[i]) % gcut) == 0;
 }
 
 __global__ void k_group_starts(int64_t n, const int32_t *gflag, const int32_t *gid, int32_t *grp, int32_t ngroups)
@@ -347,6 +381,55 @@ __global__ void k_row_chunk(int32_t nchunks, const int32_t *chunk_grp, const int
 {
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks; c += (int64_t)gridDim.x * blockDim.x)
         for (int32_t i = grp[chunk_grp[c]]; i < grp[chunk_grp[c + 1]]; ++i) rowchunk[i] = (int32_t)c;
+}
+
+// Topological sweep keys of the chunks, used when ordering the chunks by
+// their first (forward) or last (backward) row level would put a chunk before
+// one it reads, which thinning a factor can do. Forward:
+// key[c] = max(lv_s[c], key[c'] + 1 over every other chunk c' that chunk c's
+// groups read); backward: key[c] = max(maxlev - lv_e[c], key[c'] + 1 over the
+// chunks that read chunk c). A sweep that takes the chunks in ascending key
+// order then finds every input finished, and where the level order was
+// already valid the keys mostly repeat it. One warp per chunk, sync-free as
+// k_levels: key[] starts at -1, the inputs of a chunk have lower (forward) or
+// higher (backward) chunk indices, and chunks are taken round-robin in that
+// order by a co-resident grid, so the first unfinished chunk always
+// progresses; every wait is bounded.
+template <bool BACKWARD>
+__global__ void k_chunk_keys(int32_t nchunks, const int32_t *chunk_grp, const int32_t *grp, const int32_t *Xrowptr,
+                             const int32_t *Xcol, const int32_t *rowchunk, const int32_t *lv, int32_t maxlev,
+                             int32_t *key, unsigned *err)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = w; t < nchunks; t += nw) {
+        const int32_t c = BACKWARD ? (int32_t)(nchunks - 1 - t) : (int32_t)t;
+        int mx = (BACKWARD ? maxlev - lv[c] : lv[c]) - 1;
+        for (int32_t g = chunk_grp[c]; g < chunk_grp[c + 1]; ++g) {
+            // forward: the first row's lower columns other than the diagonal;
+            // backward: the last row's upper columns other than the diagonal
+            const int32_t r = BACKWARD ? grp[g + 1] - 1 : grp[g];
+            const int32_t b0 = Xrowptr[r] + (BACKWARD ? 1 : 0), m = Xrowptr[r + 1] - Xrowptr[r] - 1;
+            for (int32_t k = lane; k < m; k += 32) {
+                const int32_t cj = rowchunk[Xcol[b0 + k]];
+                if (cj == c) continue;
+                int v = ld_acquire_i32(key + cj);
+                long long it = 0;
+                while (v < 0 && it < SPIN_LIMIT) {
+                    if (it > 32) __nanosleep(64);
+                    v = ld_acquire_i32(key + cj);
+                    ++it;
+                    if ((it & 1023) == 0 && *((volatile unsigned *)err) != 0u) break;
+                }
+                if (v < 0) { atomicOr(err, ERR_TIMEOUT); v = 0; }
+                mx = max(mx, v);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) st_release_i32(key + c, mx + 1);
+    }
 }
 
 __global__ void k_check_order(int32_t ngroups, const int32_t *grp, const int32_t *Lrowptr, const int32_t *Lcol,
@@ -568,6 +651,10 @@ static void free_pattern(Pattern &p)
 }
 
 // Chunks, their sweep orders and the dependency check (see Pattern).
+// Attempt 0: level-monotone runs of groups, swept in order of their first
+// (forward) and last (backward) level. Attempt 1: the same runs in the order
+// of their topological keys (k_chunk_keys). Attempt 2: one group per chunk in
+// level order, which is always valid.
 static int build_schedule(gic_handle *h, Pattern &P, int32_t *cflag, int32_t *cid, int32_t *lv_s, int32_t *lv_e)
 {
     const int32_t ng = P.ngroups;
@@ -578,61 +665,100 @@ static int build_schedule(gic_handle *h, Pattern &P, int32_t *cflag, int32_t *ci
     GIC_CUDA_TRY(cudaGetLastError());
     GIC_TRY(scan_i32<false>(h, cflag, ng, cid, &tot));
     int32_t nc = (int32_t)tot;
-    int32_t *rowchunk = nullptr, *pos = nullptr;
+    int32_t *rowchunk = nullptr, *pos = nullptr, *keys = nullptr;
     unsigned *bad = (unsigned *)((char *)h->dev_small + 62000);
     std::vector<int32_t> hs, he, of, ob;
-    for (int attempt = 0; attempt < 2; ++attempt) {
-        // attempt 0: level-monotone runs; attempt 1: one group per chunk
-        cudaFree(P.chunk_grp); cudaFree(P.ord_f); cudaFree(P.ord_b);
-        P.chunk_grp = P.ord_f = P.ord_b = nullptr;
-        if (attempt == 1) nc = ng;
-        GIC_CUDA_TRY(cudaMalloc(&P.chunk_grp, sizeof(int32_t) * (size_t)(nc + 1)));
-        GIC_CUDA_TRY(cudaMalloc(&P.ord_f, sizeof(int32_t) * (size_t)nc));
-        GIC_CUDA_TRY(cudaMalloc(&P.ord_b, sizeof(int32_t) * (size_t)nc));
-        if (attempt == 0) {
+    int rc = GIC_OK;
+    cudaError_t e = cudaMalloc(&rowchunk, sizeof(int32_t) * (size_t)P.n);
+    for (int attempt = 0; attempt < 3 && e == cudaSuccess && rc == GIC_OK; ++attempt) {
+        if (attempt != 1) {
+            cudaFree(P.chunk_grp); cudaFree(P.ord_f); cudaFree(P.ord_b);
+            cudaFree(pos); cudaFree(keys);
+            P.chunk_grp = P.ord_f = P.ord_b = pos = keys = nullptr;
+            if (attempt == 2) nc = ng;
+            if ((e = cudaMalloc(&P.chunk_grp, sizeof(int32_t) * (size_t)(nc + 1))) != cudaSuccess) break;
+            if ((e = cudaMalloc(&P.ord_f, sizeof(int32_t) * (size_t)nc)) != cudaSuccess) break;
+            if ((e = cudaMalloc(&P.ord_b, sizeof(int32_t) * (size_t)nc)) != cudaSuccess) break;
+            if ((e = cudaMalloc(&pos, sizeof(int32_t) * 2 * (size_t)nc)) != cudaSuccess) break;
+            if ((e = cudaMalloc(&keys, sizeof(int32_t) * 2 * (size_t)nc)) != cudaSuccess) break;
+            if (attempt == 0) {
+                ++h->launches;
+                k_chunk_starts<<<gr, T_ROWS, 0, h->stream>>>(ng, cflag, cid, P.chunk_grp, nc);
+            } else {
+                std::vector<int32_t> id(nc + 1);
+                for (int32_t k = 0; k <= nc; ++k) id[k] = k;
+                if ((e = cudaMemcpyAsync(P.chunk_grp, id.data(), sizeof(int32_t) * (size_t)(nc + 1),
+                                         cudaMemcpyHostToDevice, h->stream)) != cudaSuccess) break;
+            }
             ++h->launches;
-            k_chunk_starts<<<gr, T_ROWS, 0, h->stream>>>(ng, cflag, cid, P.chunk_grp, nc);
-        } else {
-            std::vector<int32_t> id(nc + 1);
-            for (int32_t k = 0; k <= nc; ++k) id[k] = k;
-            GIC_CUDA_TRY(cudaMemcpyAsync(P.chunk_grp, id.data(), sizeof(int32_t) * (size_t)(nc + 1),
-                                         cudaMemcpyHostToDevice, h->stream));
+            k_chunk_levels<<<grid_rows(h, nc), T_ROWS, 0, h->stream>>>(nc, P.chunk_grp, P.grp, P.level, lv_s, lv_e);
+            ++h->launches;
+            k_row_chunk<<<grid_rows(h, nc), T_ROWS, 0, h->stream>>>(nc, P.chunk_grp, P.grp, rowchunk);
+            if ((e = cudaGetLastError()) != cudaSuccess) break;
         }
-        ++h->launches;
-        k_chunk_levels<<<grid_rows(h, nc), T_ROWS, 0, h->stream>>>(nc, P.chunk_grp, P.grp, P.level, lv_s, lv_e);
-        GIC_CUDA_TRY(cudaGetLastError());
+        const int32_t *ks = lv_s, *ke = lv_e;
+        if (attempt == 1) {
+            if ((e = cudaMemsetAsync(keys, 0xff, sizeof(int32_t) * 2 * (size_t)nc, h->stream)) != cudaSuccess) break;
+            int32_t nc_ = nc, ml = P.nlevels - 1;
+            const int32_t *cg = P.chunk_grp, *g_ = P.grp, *rc_ = rowchunk, *lr = P.Lrowptr, *lc = P.Lcol,
+                          *ur = P.Urowptr, *uc = P.Ucol;
+            int32_t *kf = keys, *kb = keys + nc;
+            unsigned *er = h->dev_err;
+            void *af[] = {&nc_, &cg, &g_, &lr, &lc, &rc_, &ks, &ml, &kf, &er};
+            if ((rc = launch_persistent(h, (const void *)k_chunk_keys<false>, 256, 0, nc, af)) != GIC_OK) break;
+            void *ab[] = {&nc_, &cg, &g_, &ur, &uc, &rc_, &ke, &ml, &kb, &er};
+            if ((rc = launch_persistent(h, (const void *)k_chunk_keys<true>, 256, 0, nc, ab)) != GIC_OK) break;
+            unsigned flags = 0;
+            if ((rc = read_and_clear_dev_err(h, &flags)) != GIC_OK) break;
+            if (flags) continue; // a key wait gave up: one group per chunk
+            ks = kf;
+            ke = kb;
+        }
         hs.resize(nc); he.resize(nc); of.resize(nc); ob.resize(nc);
-        GIC_CUDA_TRY(cudaMemcpyAsync(hs.data(), lv_s, sizeof(int32_t) * (size_t)nc, cudaMemcpyDeviceToHost, h->stream));
-        GIC_CUDA_TRY(cudaMemcpyAsync(he.data(), lv_e, sizeof(int32_t) * (size_t)nc, cudaMemcpyDeviceToHost, h->stream));
-        GIC_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        if ((e = cudaMemcpyAsync(hs.data(), ks, sizeof(int32_t) * (size_t)nc, cudaMemcpyDeviceToHost, h->stream)) !=
+            cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(he.data(), ke, sizeof(int32_t) * (size_t)nc, cudaMemcpyDeviceToHost, h->stream)) !=
+            cudaSuccess) break;
+        if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) break;
         for (int32_t k = 0; k < nc; ++k) of[k] = ob[k] = k;
         std::stable_sort(of.begin(), of.end(), [&](int32_t a, int32_t b) { return hs[a] < hs[b]; });
-        std::stable_sort(ob.begin(), ob.end(), [&](int32_t a, int32_t b) { return he[a] > he[b]; });
-        GIC_CUDA_TRY(cudaMemcpyAsync(P.ord_f, of.data(), sizeof(int32_t) * (size_t)nc, cudaMemcpyHostToDevice, h->stream));
-        GIC_CUDA_TRY(cudaMemcpyAsync(P.ord_b, ob.data(), sizeof(int32_t) * (size_t)nc, cudaMemcpyHostToDevice, h->stream));
-        if (attempt == 1) break; // level order per group is always valid
-        GIC_CUDA_TRY(cudaMalloc(&rowchunk, sizeof(int32_t) * (size_t)P.n));
-        GIC_CUDA_TRY(cudaMalloc(&pos, sizeof(int32_t) * 2 * (size_t)nc));
-        ++h->launches;
-        k_row_chunk<<<grid_rows(h, nc), T_ROWS, 0, h->stream>>>(nc, P.chunk_grp, P.grp, rowchunk);
+        if (attempt == 1) // backward keys ascend along the sweep
+            std::stable_sort(ob.begin(), ob.end(), [&](int32_t a, int32_t b) { return he[a] < he[b]; });
+        else
+            std::stable_sort(ob.begin(), ob.end(), [&](int32_t a, int32_t b) { return he[a] > he[b]; });
+        if ((e = cudaMemcpyAsync(P.ord_f, of.data(), sizeof(int32_t) * (size_t)nc, cudaMemcpyHostToDevice,
+                                 h->stream)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(P.ord_b, ob.data(), sizeof(int32_t) * (size_t)nc, cudaMemcpyHostToDevice,
+                                 h->stream)) != cudaSuccess) break;
+        if (attempt == 2) { // level order per group is always valid
+            P.chunked = 0;
+            break;
+        }
         ++h->launches;
         k_inverse_perm<<<grid_rows(h, nc), T_ROWS, 0, h->stream>>>(nc, P.ord_f, pos);
         ++h->launches;
         k_inverse_perm<<<grid_rows(h, nc), T_ROWS, 0, h->stream>>>(nc, P.ord_b, pos + nc);
-        GIC_CUDA_TRY(cudaMemsetAsync(bad, 0, 4, h->stream));
+        if ((e = cudaMemsetAsync(bad, 0, 4, h->stream)) != cudaSuccess) break;
         ++h->launches;
         k_check_order<<<gr, T_ROWS, 0, h->stream>>>(ng, P.grp, P.Lrowptr, P.Lcol, P.Urowptr, P.Ucol, rowchunk, pos,
                                                     pos + nc, bad);
         unsigned hb = 1;
-        GIC_CUDA_TRY(cudaMemcpyAsync(&hb, bad, 4, cudaMemcpyDeviceToHost, h->stream));
-        GIC_CUDA_TRY(cudaStreamSynchronize(h->stream));
-        cudaFree(rowchunk);
-        cudaFree(pos);
-        rowchunk = pos = nullptr;
-        if (hb == 0) break;
+        if ((e = cudaMemcpyAsync(&hb, bad, 4, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess) break;
+        if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) break;
+        if (hb == 0) {
+            P.chunked = (nc < ng) ? 1 + attempt : 0;
+            break;
+        }
     }
+    cudaFree(rowchunk);
+    cudaFree(pos);
+    cudaFree(keys);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e, "gic_pattern_create", __FILE__, __LINE__);
+        return GIC_ERR_CUDA;
+    }
+    if (rc != GIC_OK) return rc;
     P.nchunks = nc;
-    P.chunked = (nc < ng) ? 1 : 0;
     return GIC_OK;
 }
 
@@ -824,8 +950,17 @@ static int analyze_impl(gic_handle *h, int64_t n, int64_t nnz, const int32_t *ro
 
     k_run_keys<<<gr, T_ROWS, 0, h->stream>>>(n, same, key);
     STEP(scan_i32<true>(h, key, n, runstart, nullptr));
+    {
+        int32_t *bs = stats + 4, hb = 0;
+        ++h->launches;
+        k_run_gcd<<<gr, T_ROWS, 0, h->stream>>>(n, same, runstart, bs);
+        CUDA_STEP(cudaGetLastError());
+        CUDA_STEP(cudaMemcpyAsync(&hb, bs, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+        CUDA_STEP(cudaStreamSynchronize(h->stream));
+        P.block_rows = (hb >= 2 && hb <= GMAX) ? hb : GMAX;
+    }
     ++h->launches;
-    k_group_flags<<<gr, T_ROWS, 0, h->stream>>>(n, runstart, gflag);
+    k_group_flags<<<gr, T_ROWS, 0, h->stream>>>(n, runstart, P.block_rows, gflag);
     STEP(scan_i32<false>(h, gflag, n, gid, &tot));
     P.ngroups = (int32_t)tot;
     CUDA_STEP(cudaMalloc(&P.grp, sizeof(int32_t) * (size_t)(P.ngroups + 1)));

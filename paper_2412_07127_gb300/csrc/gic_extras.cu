@@ -32,22 +32,39 @@ __global__ void k_drop_keep(int64_t n, const int32_t *Lrowptr, const int32_t *Lc
     }
 }
 
-// Node-granular variant: in every row group an external column stays for all
-// the group's rows if any of their entries in it exceeds thr (the group's own
-// lower block always stays), so the kept rows of a group keep identical
-// patterns and the thinned factor still runs the row-group solve kernels.
-__global__ void k_drop_keep_grouped(int32_t ngroups, const int32_t *grp, const int32_t *Lrowptr, const double *Lval,
-                                    double thr, unsigned char *keep, int32_t *lcnt)
+// Node-granular variant: the factor is cut into blocks by the row groups. An
+// external block (rows of group g, columns of an earlier group h) stays whole
+// if any of its entries exceeds thr and leaves whole otherwise; g's own lower
+// block always stays. The rows of a group keep identical lower patterns and,
+// through the transpose, identical upper ones, so the thinned factor keeps
+// the row groups and the solve kernels built on them. One thread per group;
+// a column's group is found by binary search over the group starts.
+__global__ void k_drop_keep_grouped(int32_t ngroups, const int32_t *grp, const int32_t *Lrowptr, const int32_t *Lcol,
+                                    const double *Lval, double thr, unsigned char *keep, int32_t *lcnt)
 {
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += (int64_t)gridDim.x * blockDim.x) {
         const int32_t s = grp[g], e = grp[g + 1];
-        const int32_t m = Lrowptr[s + 1] - Lrowptr[s] - 1; // external columns, shared by the group's rows
+        const int32_t b0 = Lrowptr[s];
+        const int32_t m = Lrowptr[s + 1] - b0 - 1; // external columns, shared by the group's rows
         int32_t kept = 0;
-        for (int32_t k = 0; k < m; ++k) {
+        for (int32_t k = 0; k < m;) {
+            const int32_t c = Lcol[b0 + k];
+            int32_t lo = 0, hi = (int32_t)g; // the group h with grp[h] <= c < grp[h + 1]
+            while (hi - lo > 1) {
+                const int32_t mid = (lo + hi) >> 1;
+                if (grp[mid] <= c) lo = mid;
+                else hi = mid;
+            }
+            const int32_t hend = grp[lo + 1];
+            int32_t kend = k + 1;
+            while (kend < m && Lcol[b0 + kend] < hend) ++kend;
             bool any = false;
-            for (int32_t r = s; r < e; ++r) any = any || (fabs(Lval[Lrowptr[r] + k]) > thr);
-            for (int32_t r = s; r < e; ++r) keep[Lrowptr[r] + k] = any ? 1 : 0;
-            kept += any ? 1 : 0;
+            for (int32_t r = s; r < e; ++r)
+                for (int32_t q = k; q < kend; ++q) any = any || (fabs(Lval[Lrowptr[r] + q]) > thr);
+            for (int32_t r = s; r < e; ++r)
+                for (int32_t q = k; q < kend; ++q) keep[Lrowptr[r] + q] = any ? 1 : 0;
+            kept += any ? kend - k : 0;
+            k = kend;
         }
         for (int32_t r = s; r < e; ++r) {
             for (int32_t p = Lrowptr[r] + m; p < Lrowptr[r + 1]; ++p) keep[p] = 1;
@@ -193,8 +210,8 @@ static int dropout_impl(gic_handle *h, const gic_pattern *P, const double *valL,
     const unsigned g = x_grid(h, n);
     ++h->launches;
     if (grouped)
-        k_drop_keep_grouped<<<x_grid(h, p.ngroups), X_BLOCK, 0, h->stream>>>(p.ngroups, p.grp, p.Lrowptr, valL,
-                                                                            threshold, keep, lcnt);
+        k_drop_keep_grouped<<<x_grid(h, p.ngroups), X_BLOCK, 0, h->stream>>>(p.ngroups, p.grp, p.Lrowptr, p.Lcol,
+                                                                            valL, threshold, keep, lcnt);
     else
         k_drop_keep<<<g, X_BLOCK, 0, h->stream>>>(n, p.Lrowptr, p.Lcol, valL, threshold, keep, lcnt);
     e = cudaGetLastError();

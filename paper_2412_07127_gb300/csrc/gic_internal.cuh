@@ -256,6 +256,7 @@ __device__ __forceinline__ T warp_sum(T v)
 struct Pattern {
     int64_t n = 0, nnzA = 0, nnzL = 0;
     int32_t ngroups = 0, nlevels = 0;
+    int32_t block_rows = 8; // rows at which runs of identical rows are cut into groups
     int32_t max_ext_lower = 0, max_ext_upper = 0, max_group = 0;
     // A (borrowed, caller owned; must outlive the pattern)
     const int32_t *rowptr = nullptr, *col = nullptr;
@@ -273,7 +274,7 @@ struct Pattern {
     // Every cross-chunk dependency points to an earlier chunk in that order
     // (checked; otherwise every group is its own chunk, in level order).
     int32_t nchunks = 0;
-    int chunked = 0;
+    int chunked = 0; // 0 single groups, 1 runs in level order, 2 runs in key order
     int32_t *chunk_grp = nullptr;     // nchunks+1 start groups
     int32_t *ord_f = nullptr, *ord_b = nullptr;
     // SELL-32 layout of A's pattern for SpMV: slices of 32 rows, column-major

@@ -104,14 +104,9 @@ def test_analysis_fem(G, h, N):
 
 
 def _expected_groups(A):
-    """Runs of rows with identical column sets, cut every 8 rows."""
-    starts, run = [], 0
-    for i in range(A.n):
-        if i == 0 or not np.array_equal(A.col[A.rowptr[i - 1]:A.rowptr[i]], A.col[A.rowptr[i]:A.rowptr[i + 1]]):
-            run = i
-        if (i - run) % 8 == 0:
-            starts.append(i)
-    return np.array(starts + [A.n])
+    """Runs of rows with identical column sets, cut at the runs' common
+    length (8 when that is 1 or above 8): the oracle's row groups."""
+    return O.row_groups(A)
 
 
 @pytest.mark.parametrize("case", ["random", "banded", "tridiag", "diag"])

@@ -62,6 +62,16 @@ def test_row_groups():
     assert list(st) == [0, 1, 2, 3, 4, 5, 6]
     E = 4 * np.eye(5) + np.ones((5, 5))                                   # dense: one run
     assert list(O.row_groups(O.csr_from_dense(E), gmax=2)) == [0, 2, 4, 5]
+    # runs of 6 and 3 rows: cut at their common length 3
+    F = 4 * np.eye(9)
+    F[:6, :6] += 1
+    F[6:, 6:] += 1
+    assert list(O.row_groups(O.csr_from_dense(F))) == [0, 3, 6, 9]
+    # runs of 6 and 4 rows: common length 2
+    F = 4 * np.eye(10)
+    F[:6, :6] += 1
+    F[6:, 6:] += 1
+    assert list(O.row_groups(O.csr_from_dense(F))) == [0, 2, 4, 6, 8, 10]
 
 
 def test_dropout_grouped():
@@ -92,3 +102,42 @@ def test_dropout_grouped_hand_case():
     Lv = O.CSR(L.rowptr, L.col, np.array([2.0, 0.005, 1.0, -0.5, 0.1, 3.0]))
     g = O.dropout_grouped(Lv, 0.01, np.array([0, 1, 3], np.int32))
     assert list(g.col) == [0, 0, 1, 0, 1, 2]
+
+
+def test_dropout_grouped_blocks():
+    # groups {0, 1} and {2, 3}: the external block rows 2-3 x columns 0-1
+    # stays whole when one of its four entries is large, and leaves whole
+    # when none is; in-group entries (1,0) and (3,2) always stay
+    L = O.lower(O.csr_from_dense(np.ones((4, 4)) + 4 * np.eye(4)))
+    st = np.array([0, 2, 4], np.int32)
+    small = np.array([2.0, 0.001, 2.0, 0.002, 0.003, 2.0, 0.004, 0.005, 0.006, 2.0])
+    big = small.copy()
+    big[7] = 0.5                                       # entry (3, 1)
+    kb = O.dropout_grouped(O.CSR(L.rowptr, L.col, big), 0.01, st)
+    assert list(kb.rowptr) == [0, 1, 3, 6, 10] and np.array_equal(kb.val, big)
+    ks = O.dropout_grouped(O.CSR(L.rowptr, L.col, small), 0.01, st)
+    assert list(ks.rowptr) == [0, 1, 3, 4, 6]
+    assert list(ks.col) == [0, 0, 1, 2, 2, 3]
+    assert np.array_equal(ks.val, small[[0, 1, 2, 5, 8, 9]])
+
+
+def test_dropout_grouped_keeps_node_blocks():
+    # hex elasticity: every external node block is kept with all 9 entries or
+    # none, so S = L' + L'^T keeps A's row groups (one per node)
+    N = 3
+    A = O.fem_hex_assemble(N, I.material_field(N, 4))
+    L, _ = O.ic0(A)
+    st = O.row_groups(A)
+    thr = 0.05 * np.abs(L.val).max()
+    g = O.dropout_grouped(L, thr, st)
+    assert len(g.col) < len(L.col)
+    gof = np.repeat(np.arange(len(st) - 1), np.diff(st))
+    rows = np.repeat(np.arange(g.n), np.diff(g.rowptr))
+    blocks = {}
+    for r, c in zip(rows, g.col):
+        blocks[(gof[r], gof[c])] = blocks.get((gof[r], gof[c]), 0) + 1
+    assert all(v == 9 or (a == b and v == 6) for (a, b), v in blocks.items())
+    D = np.zeros((g.n, g.n))
+    D[rows, g.col] = 1
+    S = O.csr_from_dense(D + D.T + np.eye(g.n))
+    assert np.array_equal(O.row_groups(S), st)
