@@ -16,10 +16,10 @@
 //    (cp.async, QD groups ahead, a ring of QR slots), loads the "early"
 //    dependencies (finished well before the group), reduces their part of
 //    the dot products across lanes and leaves base = M r_g - K_early y_early;
-//  * the finisher (lanes 0..G-1, one row each) adds the contribution of the
-//    previous group of the chunk from registers and of the few "late"
-//    dependencies (within a level window of the group), waiting only for
-//    those, and publishes y.
+//  * the finisher (four lanes per row, one accumulation chain each) adds the
+//    contribution of the previous group of the chunk from registers and of
+//    the few "late" dependencies (within a level window of the group),
+//    waiting only for those, and publishes y.
 // The producer's lane-parallel work runs while the finisher waits, so the
 // chain from one group to the next is a handful of FMAs plus the latency of
 // the dependencies themselves. Readiness is the solution word itself (a
@@ -36,7 +36,8 @@ namespace gic {
 constexpr int QR = 4;                    // ring slots per warp pair
 constexpr int QD = 2;                    // groups staged ahead by the producer
 constexpr int QPAIRS = SOLVE_BLOCK / 64; // warp pairs per block
-constexpr int QPAIRS_PER_SM = 4;         // default cap on resident pairs per SM
+constexpr int QPAIRS_PER_SM = 4;         // cap on resident pairs per SM, few chunks
+constexpr int QPAIRS_PER_SM_MANY = 8;    // cap on resident pairs per SM, many chunks
 constexpr unsigned FULL = 0xffffffffu;
 
 template <typename T>
@@ -216,12 +217,18 @@ __device__ __forceinline__ bool q_produce(QPair<T> &Q, int seq, int32_t g0, int3
     return ok;
 }
 
-// Finisher of one chunk: lanes t < G own row t of the group.
+// Finisher of one chunk: lane 4t + c (t < G, c < 4) accumulates chain c of
+// row t and two shuffle levels add the chains. Against one lane per row this
+// issues a quarter of the arithmetic and load instructions (an FP64 warp
+// instruction occupies the SM's FP64 pipe as long with 3 active lanes as with
+// 32) and makes the dependent chain a quarter as deep: ~25% faster sweeps in
+// FP64 and ~20% in FP32 on the hex systems.
 template <typename T, bool PCG>
 __device__ __forceinline__ bool q_finish(QPair<T> &Q, int seq, int cnt, T *x, T *yreset, unsigned *err, int lane,
                                          double &dot, unsigned sleep_ns)
 {
-    T yp = 0;          // lane t: row t of the previous group of the chunk
+    const int t = lane >> 2, c = lane & 3;
+    T yp = 0;          // the previous group of the chunk: row t in lanes 4t .. 4t + 3
     int32_t prev_s = 0;
     for (int k = 0; k < cnt; ++k) {
         const int q = seq + k;
@@ -229,76 +236,42 @@ __device__ __forceinline__ bool q_finish(QPair<T> &Q, int seq, int cnt, T *x, T 
         const QSlot<T> &S = Q.slot[q % QR];
         const int32_t cw = S.cw, s = S.s;
         const int ne = cw & 255, nl = (cw >> 8) & 255, np = (cw >> 16) & 255, G = cw >> 24;
-        const T p0 = __shfl_sync(FULL, yp, 0), p1 = __shfl_sync(FULL, yp, 1), p2 = __shfl_sync(FULL, yp, 2);
-        T yv = 0;
-        if (lane < G) {
-            const int t = lane;
-            // the late loads go out first; the previous group's part (values
-            // in registers) is computed while they are in flight
-            T lv[QLATE];
-            T acc = S.base[t], acc2 = 0;
-            if constexpr (sizeof(T) == 4) {
-                // FP32: every shared-memory operand into registers, all late
-                // loads in flight, one check, then an FMA pass in four chains
-                // (FP32 FMAs are cheap; the loads are the latency)
-                T kl[QLATE];
-                int32_t cl[QLATE];
+        const T p0 = __shfl_sync(FULL, yp, 0), p1 = __shfl_sync(FULL, yp, 4), p2 = __shfl_sync(FULL, yp, 8);
+        T acc = 0;
+        if (t < G) {
+            // chain c takes late values j = c, c + 4, ... (the schedule orders
+            // them farthest level first, so the one most likely to arrive
+            // last is consumed last) and previous-group columns j = c, c + 4,
+            // ...; chain 0 starts from the producer's base
+            T lv[QLATE / 4];
 #pragma unroll
-                for (int j = 0; j < QLATE; ++j) {
-                    cl[j] = (j < nl) ? S.cols[ne + j] : -1;
-                    kl[j] = (j < nl) ? S.K[t][ne + j] : (T)0;
-                }
-#pragma unroll
-                for (int j = 0; j < QLATE; ++j) lv[j] = (cl[j] >= 0) ? ld_relaxed(x + cl[j]) : (T)0;
-                for (int j = 0; j < np; ++j)
-                    acc = fma(-S.K[t][ne + nl + j], pick3<T>(S.cols[ne + nl + j] - prev_s, p0, p1, p2), acc);
-                bool missing = false;
-#pragma unroll
-                for (int j = 0; j < QLATE; ++j) missing |= (cl[j] >= 0) && is_sentinel(lv[j]);
-                if (missing) { // rare: wait for what was not there yet
-#pragma unroll
-                    for (int j = 0; j < QLATE; ++j)
-                        if (cl[j] >= 0 && is_sentinel(lv[j])) lv[j] = wait_word(x + cl[j], err, sleep_ns);
-                }
-                T acc1 = 0, acc3 = 0;
-#pragma unroll
-                for (int j = 0; j < QLATE; j += 4) {
-                    if (j < nl) {
-                        acc = fma(-kl[j], lv[j], acc);
-                        acc1 = fma(-kl[j + 1], lv[j + 1], acc1);
-                        acc2 = fma(-kl[j + 2], lv[j + 2], acc2);
-                        acc3 = fma(-kl[j + 3], lv[j + 3], acc3);
-                    }
-                }
-                acc += acc1;
-                acc2 += acc3;
-            } else {
-                // FP64: each value consumed as it arrives, exactly nl FMAs in
-                // two chains (a dependent FP64 FMA is ~65-360 cycles and every
-                // FP64 instruction costs SM pipe time, so the chain must
-                // overlap the loads)
-#pragma unroll
-                for (int j = 0; j < QLATE; ++j) lv[j] = (j < nl) ? ld_relaxed(x + S.cols[ne + j]) : (T)0;
-                for (int j = 0; j < np; ++j)
-                    acc = fma(-S.K[t][ne + nl + j], pick3<T>(S.cols[ne + nl + j] - prev_s, p0, p1, p2), acc);
-#pragma unroll
-                for (int j = 0; j < QLATE; ++j) {
-                    if (j < nl) {
-                        T v = lv[j];
-                        if (is_sentinel(v)) v = wait_word(x + S.cols[ne + j], err, sleep_ns);
-                        if (j & 1) acc2 = fma(-S.K[t][ne + j], v, acc2);
-                        else acc = fma(-S.K[t][ne + j], v, acc);
-                    }
-                }
+            for (int i = 0; i < QLATE / 4; ++i) {
+                const int j = c + 4 * i;
+                lv[i] = (j < nl) ? ld_relaxed(x + S.cols[ne + j]) : (T)0;
             }
-            yv = acc + acc2;
-            st_relaxed(x + s + t, yv);
-            if (PCG) {
-                yreset[s + t] = sentinel_of<T>();
-                dot = fma(S.rd[t], (double)yv, dot);
+            if (c == 0) acc = S.base[t];
+            for (int j = c; j < np; j += 4)
+                acc = fma(-S.K[t][ne + nl + j], pick3<T>(S.cols[ne + nl + j] - prev_s, p0, p1, p2), acc);
+#pragma unroll
+            for (int i = 0; i < QLATE / 4; ++i) {
+                const int j = c + 4 * i;
+                if (j < nl) {
+                    T v = lv[i];
+                    if (is_sentinel(v)) v = wait_word(x + S.cols[ne + j], err, sleep_ns);
+                    acc = fma(-S.K[t][ne + j], v, acc);
+                }
             }
         }
-        yp = yv;
+        acc += __shfl_xor_sync(FULL, acc, 1);
+        acc += __shfl_xor_sync(FULL, acc, 2); // row t's value in lanes 4t .. 4t + 3
+        if (c == 0 && t < G) {
+            st_relaxed(x + s + t, acc);
+            if (PCG) {
+                yreset[s + t] = sentinel_of<T>();
+                dot = fma(S.rd[t], (double)acc, dot);
+            }
+        }
+        yp = acc;
         __threadfence_block();
         __syncwarp();
         if (lane == 0) mbar_arrive(&Q.freed[q % QR]);
@@ -457,13 +430,14 @@ static int q_launch(gic_handle *h, const Pattern &P, const T *Kv, const T *rhs, 
     unsigned *er = h->dev_err;
     int poll = h->tune_poll;
     void *args[] = {&nc, &ord, &cg, &g, &rp, &qc, &qn, &Kv, &rhs, &x, &yreset, &rd, &partials, &er, &poll, &sc};
-    // warps: one pair per chunk. With few chunks per SM (the 40^3 hex system:
-    // ~11) at most QPAIRS_PER_SM pairs per SM (fewer co-resident pairs contend
-    // less for the FP64 pipe and issue slots); with many (69^3: ~32, 148^3:
-    // ~145) as many as fit, since then the chunks queue for pairs.
+    // warps: one pair per chunk, at most QPAIRS_PER_SM pairs per SM with few
+    // chunks per SM (the 40^3 hex system: ~11) and QPAIRS_PER_SM_MANY with
+    // many (69^3: ~32), since then the chunks queue for pairs; co-resident
+    // pairs beyond that contend for the FP64 pipe and issue slots and slow
+    // the chain more than the extra chunks in flight gain.
     int64_t need = 2 * (int64_t)nc;
     int per_sm = h->tune_solve_warps_per_sm;
-    if (per_sm == 0 && (int64_t)nc < 16 * (int64_t)h->num_sms) per_sm = QPAIRS_PER_SM;
+    if (per_sm == 0) per_sm = ((int64_t)nc < 16 * (int64_t)h->num_sms) ? QPAIRS_PER_SM : QPAIRS_PER_SM_MANY;
     if (per_sm > 0 && need > 2 * (int64_t)per_sm * h->num_sms) need = 2 * (int64_t)per_sm * h->num_sms;
     if (PCG && need > MAX_PARTIALS) need = MAX_PARTIALS; // grid warps <= partial slots
     const size_t smem = sizeof(QPair<T>) * QPAIRS;
