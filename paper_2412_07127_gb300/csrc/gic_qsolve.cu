@@ -36,8 +36,9 @@ namespace gic {
 constexpr int QR = 4;                    // ring slots per warp pair
 constexpr int QD = 2;                    // groups staged ahead by the producer
 constexpr int QPAIRS = SOLVE_BLOCK / 64; // warp pairs per block
-constexpr int QPAIRS_PER_SM = 4;         // cap on resident pairs per SM, few chunks
-constexpr int QPAIRS_PER_SM_MANY = 8;    // cap on resident pairs per SM, many chunks
+constexpr int QPAIRS_PER_SM = 4;         // cap on resident pairs per SM: < 16 chunks per SM,
+constexpr int QPAIRS_PER_SM_MANY = 8;    // < 64 chunks per SM,
+constexpr int QPAIRS_PER_SM_QUEUED = 16; // more
 constexpr unsigned FULL = 0xffffffffu;
 
 template <typename T>
@@ -430,14 +431,15 @@ static int q_launch(gic_handle *h, const Pattern &P, const T *Kv, const T *rhs, 
     unsigned *er = h->dev_err;
     int poll = h->tune_poll;
     void *args[] = {&nc, &ord, &cg, &g, &rp, &qc, &qn, &Kv, &rhs, &x, &yreset, &rd, &partials, &er, &poll, &sc};
-    // warps: one pair per chunk, at most QPAIRS_PER_SM pairs per SM with few
-    // chunks per SM (the 40^3 hex system: ~11) and QPAIRS_PER_SM_MANY with
-    // many (69^3: ~32), since then the chunks queue for pairs; co-resident
-    // pairs beyond that contend for the FP64 pipe and issue slots and slow
-    // the chain more than the extra chunks in flight gain.
+    // warps: one pair per chunk, capped per SM by the chunks per SM (40^3
+    // hex system: ~11 -> 4 pairs, 69^3: ~32 -> 8, 148^3: ~145 -> 16): extra
+    // co-resident pairs contend for the FP64 pipe and issue slots and slow
+    // the chain, which pays only once the chunks queue for pairs.
     int64_t need = 2 * (int64_t)nc;
     int per_sm = h->tune_solve_warps_per_sm;
-    if (per_sm == 0) per_sm = ((int64_t)nc < 16 * (int64_t)h->num_sms) ? QPAIRS_PER_SM : QPAIRS_PER_SM_MANY;
+    const int64_t nsm = h->num_sms;
+    if (per_sm == 0)
+        per_sm = (nc < 16 * nsm) ? QPAIRS_PER_SM : (nc < 64 * nsm) ? QPAIRS_PER_SM_MANY : QPAIRS_PER_SM_QUEUED;
     if (per_sm > 0 && need > 2 * (int64_t)per_sm * h->num_sms) need = 2 * (int64_t)per_sm * h->num_sms;
     if (PCG && need > MAX_PARTIALS) need = MAX_PARTIALS; // grid warps <= partial slots
     const size_t smem = sizeof(QPair<T>) * QPAIRS;
