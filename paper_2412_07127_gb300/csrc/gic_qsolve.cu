@@ -15,11 +15,12 @@
 //  * the producer stages a group's columns and coefficients in shared memory
 //    (cp.async, QD groups ahead, a ring of QR slots), loads the "early"
 //    dependencies (finished well before the group), reduces their part of
-//    the dot products across lanes and leaves base = M r_g - K_early y_early;
+//    the dot products across lanes and leaves base = -K_early y_early;
 //  * the finisher (four lanes per row, one accumulation chain each) adds the
-//    contribution of the previous group of the chunk from registers and of
-//    the few "late" dependencies (within a level window of the group),
-//    waiting only for those, and publishes y.
+//    group's own right-hand side M r_g, the contribution of the previous
+//    group of the chunk from registers and of the few "late" dependencies
+//    (within a level window of the group), waiting only for those, and
+//    publishes y.
 // The producer's lane-parallel work runs while the finisher waits, so the
 // chain from one group to the next is a handful of FMAs plus the latency of
 // the dependencies themselves. Readiness is the solution word itself (a
@@ -122,14 +123,23 @@ __device__ __forceinline__ void q_stage(QSlot<T> &S, int32_t s, int32_t cw, int6
     if (rd && lane < G) cp_async_8(&S.rd[lane], rd + s + lane);
 }
 
-// -M coefficient of right-hand-side entry u in row t of the group (forward:
-// y_t gets sum_{u<=t} M_tu r_u; backward: z_t gets sum_{u>=t} M_ut y_u)
-template <typename T, bool FWD>
-__device__ __forceinline__ T q_mcoef(const QSlot<T> &S, int t, int u, int G)
+// Transposed warp sum of three values (the first two butterfly levels
+// exchange halves so each lane adds 2, then 1 value): 6 adds; row t's total
+// ends in lanes 8t .. 8t + 7.
+template <typename T>
+__device__ __forceinline__ T warp_sum_3_rows(const T (&a)[3], int lane)
 {
-    if (u < 0 || u >= G) return (T)0;
-    if (FWD) return (u <= t) ? -S.Mv[t * (t + 1) / 2 + u] : (T)0;
-    return (u >= t) ? -S.Mv[u * (u + 1) / 2 + t] : (T)0;
+    const bool hi16 = lane & 16;
+    T k0 = hi16 ? a[2] : a[0], k1 = hi16 ? (T)0 : a[1];
+    const T s0 = hi16 ? a[0] : a[2], s1 = hi16 ? a[1] : (T)0;
+    k0 += __shfl_xor_sync(FULL, s0, 16);
+    k1 += __shfl_xor_sync(FULL, s1, 16);
+    const bool b8 = lane & 8;
+    T kk = b8 ? k1 : k0;
+    kk += __shfl_xor_sync(FULL, b8 ? k0 : k1, 8);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) kk += __shfl_xor_sync(FULL, kk, o);
+    return kk;
 }
 
 // Producer of one chunk (groups in sweep order k = 0..cnt-1).
@@ -189,27 +199,26 @@ __device__ __forceinline__ bool q_produce(QPair<T> &Q, int seq, int32_t g0, int3
         QSlot<T> &S = Q.slot[(seq + k) % QR];
         const int ne = S.cw & 255, G = S.cw >> 24;
         wait_pair<FWD, T>(x, j0, j1, v0, v1, err, poll);
-        // positions p < ne: early columns (K, y); ne <= p < ne + G: the
-        // group's own right-hand side (-M, rr), so a = K y_early - M rr
-        const int u0 = lane - ne, u1 = lane + 32 - ne;
-        const T w0 = (j0 >= 0) ? v0 : ((u0 >= 0 && u0 < G) ? S.rr[u0] : (T)0);
-        const T w1 = (j1 >= 0) ? v1 : ((u1 >= 0 && u1 < G) ? S.rr[u1] : (T)0);
-        const bool two = ne + G > 32; // uniform over the warp
+        // a = K_early y_early over the early columns p < ne (v is 0 past
+        // them); the group's own right-hand side part M rr is the
+        // finisher's
+        const bool two = ne > 32; // uniform over the warp
         T a[3];
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
-            const T c0 = (t < G) ? ((j0 >= 0) ? S.K[t][lane] : q_mcoef<T, FWD>(S, t, u0, G)) : (T)0;
+            const T c0 = (t < G && j0 >= 0) ? S.K[t][lane] : (T)0;
             if (two) {
-                const T c1 = (t < G) ? ((j1 >= 0) ? S.K[t][lane + 32] : q_mcoef<T, FWD>(S, t, u1, G)) : (T)0;
-                a[t] = fma(c1, w1, c0 * w0);
+                const T c1 = (t < G && j1 >= 0) ? S.K[t][lane + 32] : (T)0;
+                a[t] = fma(c1, v1, c0 * v0);
             } else {
-                a[t] = c0 * w0;
+                a[t] = c0 * v0;
             }
         }
         if (k + 1 < cnt) load_early(k + 1);
-        warp_sum_n<T, 3>(a, lane);
-        if (lane < G) S.base[lane] = -pick3<T>(lane, a[0], a[1], a[2]);
-        __threadfence_block();
+        const T tot = warp_sum_3_rows<T>(a, lane); // row t's total in lanes 8t .. 8t + 7
+        if ((lane & 7) == 0 && (lane >> 3) < G) S.base[lane >> 3] = -tot;
+        // __syncwarp orders the lanes' base stores before lane 0's arrive,
+        // whose release makes them visible to the finisher's acquiring wait
         __syncwarp();
         if (lane == 0) mbar_arrive(&Q.full[(seq + k) % QR]);
     }
@@ -224,7 +233,7 @@ __device__ __forceinline__ bool q_produce(QPair<T> &Q, int seq, int32_t g0, int3
 // instruction occupies the SM's FP64 pipe as long with 3 active lanes as with
 // 32) and makes the dependent chain a quarter as deep: ~25% faster sweeps in
 // FP64 and ~20% in FP32 on the hex systems.
-template <typename T, bool PCG>
+template <typename T, bool FWD, bool PCG>
 __device__ __forceinline__ bool q_finish(QPair<T> &Q, int seq, int cnt, T *x, T *yreset, unsigned *err, int lane,
                                          double &dot, unsigned sleep_ns)
 {
@@ -251,6 +260,10 @@ __device__ __forceinline__ bool q_finish(QPair<T> &Q, int seq, int cnt, T *x, T 
                 lv[i] = (j < nl) ? ld_relaxed(x + S.cols[ne + j]) : (T)0;
             }
             if (c == 0) acc = S.base[t];
+            // the group's own right-hand side: forward y_t gets M_tu r_u
+            // (u <= t), backward z_t gets M_ut y_u (u >= t); chain c takes u = c
+            if (c < G && (FWD ? c <= t : c >= t))
+                acc = fma(FWD ? S.Mv[t * (t + 1) / 2 + c] : S.Mv[c * (c + 1) / 2 + t], S.rr[c], acc);
             for (int j = c; j < np; j += 4)
                 acc = fma(-S.K[t][ne + nl + j], pick3<T>(S.cols[ne + nl + j] - prev_s, p0, p1, p2), acc);
 #pragma unroll
@@ -273,8 +286,7 @@ __device__ __forceinline__ bool q_finish(QPair<T> &Q, int seq, int cnt, T *x, T 
             }
         }
         yp = acc;
-        __threadfence_block();
-        __syncwarp();
+        __syncwarp(); // the lanes' slot reads precede lane 0's releasing arrive
         if (lane == 0) mbar_arrive(&Q.freed[q % QR]);
         prev_s = s;
     }
@@ -319,7 +331,7 @@ __global__ void __launch_bounds__(SOLVE_BLOCK, 2) k_qsolve(int32_t nchunks, cons
             ok = q_produce<T, FWD>(Q, seq, g0, g1, grp, rowptr, qcol, qcnt, Kv, rhs, x, PCG ? rd : nullptr, err, poll,
                                    lane);
         else
-            ok = q_finish<T, PCG>(Q, seq, g1 - g0, x, yreset, err, lane, dot, (unsigned)(poll & 0xffff));
+            ok = q_finish<T, FWD, PCG>(Q, seq, g1 - g0, x, yreset, err, lane, dot, (unsigned)(poll & 0xffff));
         seq += g1 - g0;
     }
     if (PCG) {

@@ -1157,13 +1157,10 @@ static SolveMode solve_mode(const gic_handle *h, const Pattern &P, int l_dtype)
     if (l_dtype == GIC_IDENTITY) return MODE_IDENT;
     // automatic choice (measured on the hex systems from 40^3 to 148^3): the
     // warp-specialised kernels (two warps per chunk, most arithmetic off the
-    // dependency chain) win everywhere in FP64 (1.7x at 148^3) and in FP32
-    // while the chunks fit the resident warp pairs; an FP32 factor with many
-    // chunks per SM (148^3) runs as fast on the staged one-warp kernels,
-    // which keep twice as many chunks in flight
+    // dependency chain) where the pattern admits them, else the staged
+    // one-warp kernels
     int pipeline = h->tune_pipeline;
-    if (pipeline >= 4)
-        pipeline = (l_dtype == GIC_F32 && (int64_t)P.nchunks > 64 * (int64_t)h->num_sms) ? 1 : 2;
+    if (pipeline >= 4) pipeline = 2;
     if (pipeline >= 3 && P.bready) return (l_dtype == GIC_F32) ? MODE_B32 : MODE_B64;
     if (pipeline >= 2 && P.qready) return (l_dtype == GIC_F32) ? MODE_Q32 : MODE_Q64;
     const bool pipe = pipeline && pipelined_fits(P);
