@@ -11,19 +11,22 @@
 // product: no in-group substitution chain is left on the critical path.
 // Backward (L^T z = y) uses z_g = M^T y_g - (M^T U_ext) z_ext on U = L^T.
 //
-// Two warps share one chunk (a run of groups solved in order):
-//  * the producer stages a group's columns and coefficients in shared memory
-//    (cp.async, QD groups ahead, a ring of QR slots), loads the "early"
-//    dependencies (finished well before the group), reduces their part of
-//    the dot products across lanes and leaves base = -K_early y_early;
+// A team of three warps shares one chunk (a run of groups solved in order):
+//  * two producers, one for the even and one for the odd groups of the
+//    chunk, stage a group's columns and coefficients in shared memory
+//    (cp.async, a ring of QR slots), load the "early" dependencies (finished
+//    well before the group), reduce their part of the dot products across
+//    lanes and leave base = -K_early y_early;
 //  * the finisher (four lanes per row, one accumulation chain each) adds the
 //    group's own right-hand side M r_g, the contribution of the previous
 //    group of the chunk from registers and of the few "late" dependencies
 //    (within a level window of the group), waiting only for those, and
 //    publishes y.
-// The producer's lane-parallel work runs while the finisher waits, so the
+// The producers' lane-parallel work runs while the finisher waits, so the
 // chain from one group to the next is a handful of FMAs plus the latency of
-// the dependencies themselves. Readiness is the solution word itself (a
+// the dependencies themselves; with two producers their per-group cycle
+// (staging, reduction, hand-off: ~1.3 us on GB300) no longer sets the
+// chunk's pace. Readiness is the solution word itself (a
 // signalling-NaN sentinel until written), every wait is bounded, and the
 // chunk order guarantees that the earliest unfinished chunk can always run.
 #include <limits.h>
@@ -34,12 +37,13 @@
 
 namespace gic {
 
-constexpr int QR = 4;                    // ring slots per warp pair
-constexpr int QD = 2;                    // groups staged ahead by the producer
-constexpr int QPAIRS = SOLVE_BLOCK / 64; // warp pairs per block
-constexpr int QPAIRS_PER_SM = 4;         // cap on resident pairs per SM: < 16 chunks per SM,
-constexpr int QPAIRS_PER_SM_MANY = 8;    // < 64 chunks per SM,
-constexpr int QPAIRS_PER_SM_QUEUED = 16; // more
+constexpr int QR = 8;                    // ring slots per chunk team
+constexpr int QDO = 2;                   // own groups a producer stages ahead
+constexpr int QBLOCK = 192;              // threads per block: two teams of three warps
+constexpr int QTEAMS = QBLOCK / 96;      // teams per block
+constexpr int QTEAMS_PER_SM = 4;         // cap on resident teams per SM: < 16 chunks per SM,
+constexpr int QTEAMS_PER_SM_MANY = 8;    // < 64 chunks per SM,
+constexpr int QTEAMS_PER_SM_QUEUED = 16; // more
 constexpr unsigned FULL = 0xffffffffu;
 
 template <typename T>
@@ -59,7 +63,7 @@ struct QSlot {
 // slot may be refilled). Waiting threads are suspended by the hardware
 // (mbarrier try_wait) instead of spinning on shared memory.
 template <typename T>
-struct QPair {
+struct QRing {
     QSlot<T> slot[QR];
     unsigned long long full[QR], freed[QR];
 };
@@ -142,9 +146,10 @@ __device__ __forceinline__ T warp_sum_3_rows(const T (&a)[3], int lane)
     return kk;
 }
 
-// Producer of one chunk (groups in sweep order k = 0..cnt-1).
+// Producer of the groups k = parity, parity + 2, ... of one chunk (groups in
+// sweep order k = 0..cnt-1); the team's other producer takes the others.
 template <typename T, bool FWD>
-__device__ __forceinline__ bool q_produce(QPair<T> &Q, int seq, int32_t g0, int32_t g1, const int32_t *grp,
+__device__ __forceinline__ bool q_produce(QRing<T> &Q, int seq, int32_t g0, int32_t g1, int parity, const int32_t *grp,
                                           const int32_t *rowptr, const int32_t *qcol, const int32_t *qcnt,
                                           const T *Kv, const T *rhs, const T *x, const double *rd, unsigned *err,
                                           int poll, int lane)
@@ -174,16 +179,16 @@ __device__ __forceinline__ bool q_produce(QPair<T> &Q, int seq, int32_t g0, int3
         q_stage<T>(Q.slot[(seq + k) % QR], s, cw, b0, qcol, Kv, rhs, rd, lane);
     };
 #pragma unroll
-    for (int d = 0; d < QD; ++d) {
-        if (d < cnt && ok) stage(d);
+    for (int d = 0; d < QDO; ++d) {
+        if (parity + 2 * d < cnt && ok) stage(parity + 2 * d);
         cp_async_commit();
     }
     // early dependency values of the group about to be reduced (loaded one
-    // group ahead so their latency overlaps the previous reduction)
+    // own group ahead so their latency overlaps the previous reduction)
     T v0 = 0, v1 = 0;
     int32_t j0 = -1, j1 = -1;
     auto load_early = [&](int k) {
-        cp_async_wait<QD - 1>();
+        cp_async_wait<QDO - 1>();
         __syncwarp();
         const QSlot<T> &S = Q.slot[(seq + k) % QR];
         const int ne = S.cw & 255;
@@ -192,9 +197,9 @@ __device__ __forceinline__ bool q_produce(QPair<T> &Q, int seq, int32_t g0, int3
         v0 = (j0 >= 0) ? ld_relaxed(x + j0) : (T)0;
         v1 = (j1 >= 0) ? ld_relaxed(x + j1) : (T)0;
     };
-    if (cnt > 0 && ok) load_early(0);
-    for (int k = 0; k < cnt && ok; ++k) {
-        if (k + QD < cnt) stage(k + QD);
+    if (parity < cnt && ok) load_early(parity);
+    for (int k = parity; k < cnt && ok; k += 2) {
+        if (k + 2 * QDO < cnt) stage(k + 2 * QDO);
         cp_async_commit();
         QSlot<T> &S = Q.slot[(seq + k) % QR];
         const int ne = S.cw & 255, G = S.cw >> 24;
@@ -214,7 +219,7 @@ __device__ __forceinline__ bool q_produce(QPair<T> &Q, int seq, int32_t g0, int3
                 a[t] = c0 * v0;
             }
         }
-        if (k + 1 < cnt) load_early(k + 1);
+        if (k + 2 < cnt) load_early(k + 2);
         const T tot = warp_sum_3_rows<T>(a, lane); // row t's total in lanes 8t .. 8t + 7
         if ((lane & 7) == 0 && (lane >> 3) < G) S.base[lane >> 3] = -tot;
         // __syncwarp orders the lanes' base stores before lane 0's arrive,
@@ -234,7 +239,7 @@ __device__ __forceinline__ bool q_produce(QPair<T> &Q, int seq, int32_t g0, int3
 // 32) and makes the dependent chain a quarter as deep: ~25% faster sweeps in
 // FP64 and ~20% in FP32 on the hex systems.
 template <typename T, bool FWD, bool PCG>
-__device__ __forceinline__ bool q_finish(QPair<T> &Q, int seq, int cnt, T *x, T *yreset, unsigned *err, int lane,
+__device__ __forceinline__ bool q_finish(QRing<T> &Q, int seq, int cnt, T *x, T *yreset, unsigned *err, int lane,
                                          double &dot, unsigned sleep_ns)
 {
     const int t = lane >> 2, c = lane & 3;
@@ -298,7 +303,7 @@ __device__ __forceinline__ bool q_finish(QPair<T> &Q, int seq, int cnt, T *x, T 
 // r^T z in FP64, then beta = r_k^T z_k / r_{k-1}^T z_{k-1} (Algorithm 1) in
 // the last warp to finish. x must hold the sentinel.
 template <typename T, bool FWD, bool PCG>
-__global__ void __launch_bounds__(SOLVE_BLOCK, 2) k_qsolve(int32_t nchunks, const int32_t *__restrict__ ord,
+__global__ void __launch_bounds__(QBLOCK, 4) k_qsolve(int32_t nchunks, const int32_t *__restrict__ ord,
                                                         const int32_t *__restrict__ chunk_grp,
                                                         const int32_t *__restrict__ grp,
                                                         const int32_t *__restrict__ rowptr,
@@ -309,27 +314,27 @@ __global__ void __launch_bounds__(SOLVE_BLOCK, 2) k_qsolve(int32_t nchunks, cons
 {
     if (sc && sc->done) return;
     extern __shared__ __align__(16) unsigned char q_raw[];
-    QPair<T> *pairs = reinterpret_cast<QPair<T> *>(q_raw);
+    QRing<T> *rings = reinterpret_cast<QRing<T> *>(q_raw);
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const bool producer = (wib & 1) == 0;
-    QPair<T> &Q = pairs[wib >> 1];
-    if (producer && lane < QR) {
+    const int role = wib % 3; // 0, 1: producers of the even / odd groups; 2: finisher
+    QRing<T> &Q = rings[wib / 3];
+    if (role == 0 && lane < QR) {
         mbar_init(&Q.full[lane], 1);
         mbar_init(&Q.freed[lane], 1);
     }
     __syncthreads();
-    const int64_t gpair = (int64_t)blockIdx.x * QPAIRS + (wib >> 1);
-    const int64_t npair = (int64_t)gridDim.x * QPAIRS;
+    const int64_t gteam = (int64_t)blockIdx.x * QTEAMS + wib / 3;
+    const int64_t nteam = (int64_t)gridDim.x * QTEAMS;
     int seq = 0;
     double dot = 0.0;
     bool ok = true;
-    for (int64_t pos = gpair; pos < nchunks && ok; pos += npair) {
+    for (int64_t pos = gteam; pos < nchunks && ok; pos += nteam) {
         const int32_t c = ord[pos];
         const int32_t g0 = chunk_grp[c], g1 = chunk_grp[c + 1];
-        if (producer)
-            ok = q_produce<T, FWD>(Q, seq, g0, g1, grp, rowptr, qcol, qcnt, Kv, rhs, x, PCG ? rd : nullptr, err, poll,
-                                   lane);
+        if (role < 2)
+            ok = q_produce<T, FWD>(Q, seq, g0, g1, role, grp, rowptr, qcol, qcnt, Kv, rhs, x, PCG ? rd : nullptr, err,
+                                   poll, lane);
         else
             ok = q_finish<T, FWD, PCG>(Q, seq, g1 - g0, x, yreset, err, lane, dot, (unsigned)(poll & 0xffff));
         seq += g1 - g0;
@@ -443,25 +448,25 @@ static int q_launch(gic_handle *h, const Pattern &P, const T *Kv, const T *rhs, 
     unsigned *er = h->dev_err;
     int poll = h->tune_poll;
     void *args[] = {&nc, &ord, &cg, &g, &rp, &qc, &qn, &Kv, &rhs, &x, &yreset, &rd, &partials, &er, &poll, &sc};
-    // warps: one pair per chunk, capped per SM by the chunks per SM (40^3
-    // hex system: ~11 -> 4 pairs, 69^3: ~32 -> 8, 148^3: ~145 -> 16): extra
-    // co-resident pairs contend for the FP64 pipe and issue slots and slow
-    // the chain, which pays only once the chunks queue for pairs.
-    int64_t need = 2 * (int64_t)nc;
+    // warps: one team of three per chunk, teams capped per SM by the chunks
+    // per SM (40^3 hex system: ~11 -> 4 teams, 69^3: ~32 -> 8, 148^3: ~145
+    // -> 16): extra co-resident teams contend for the FP64 pipe and issue
+    // slots and slow the chain, which pays only once the chunks queue.
+    int64_t need = 3 * (int64_t)nc;
     int per_sm = h->tune_solve_warps_per_sm;
     const int64_t nsm = h->num_sms;
     if (per_sm == 0)
-        per_sm = (nc < 16 * nsm) ? QPAIRS_PER_SM : (nc < 64 * nsm) ? QPAIRS_PER_SM_MANY : QPAIRS_PER_SM_QUEUED;
-    if (per_sm > 0 && need > 2 * (int64_t)per_sm * h->num_sms) need = 2 * (int64_t)per_sm * h->num_sms;
+        per_sm = (nc < 16 * nsm) ? QTEAMS_PER_SM : (nc < 64 * nsm) ? QTEAMS_PER_SM_MANY : QTEAMS_PER_SM_QUEUED;
+    if (per_sm > 0 && need > 3 * (int64_t)per_sm * h->num_sms) need = 3 * (int64_t)per_sm * h->num_sms;
     if (PCG && need > MAX_PARTIALS) need = MAX_PARTIALS; // grid warps <= partial slots
-    const size_t smem = sizeof(QPair<T>) * QPAIRS;
+    const size_t smem = sizeof(QRing<T>) * QTEAMS;
     static bool ad[64] = {};
     if (!ad[h->device & 63]) {
         GIC_CUDA_TRY(cudaFuncSetAttribute(k_qsolve<T, FWD, PCG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
         ad[h->device & 63] = true;
     }
-    return launch_persistent(h, (const void *)k_qsolve<T, FWD, PCG>, SOLVE_BLOCK, smem, need, args);
+    return launch_persistent(h, (const void *)k_qsolve<T, FWD, PCG>, QBLOCK, smem, need, args);
 }
 
 int q_lsolve(gic_handle *h, const Pattern &P, bool f32, const void *Kf, const void *r, void *y, const Scalars *sc)
