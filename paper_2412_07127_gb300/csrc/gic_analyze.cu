@@ -290,6 +290,13 @@ __global__ void k_group_starts(int64_t n, const int32_t *gflag, const int32_t *g
 }
 
 // Per-group maxima: external lower / upper counts and group size.
+// first row of every row's group
+__global__ void k_row_group(int32_t ngroups, const int32_t *grp, int32_t *rowgrp)
+{
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += (int64_t)gridDim.x * blockDim.x)
+        for (int32_t i = grp[g]; i < grp[g + 1]; ++i) rowgrp[i] = grp[g];
+}
+
 __global__ void k_group_stats(int32_t ngroups, const int32_t *grp, const int32_t *Lrowptr, const int32_t *Urowptr,
                               int32_t *stats)
 {
@@ -631,6 +638,7 @@ static void free_pattern(Pattern &p)
     cudaFree(p.Ucol);
     cudaFree(p.tperm);
     cudaFree(p.grp);
+    cudaFree(p.rowgrp);
     cudaFree(p.level);
     cudaFree(p.Lrow);
     cudaFree(p.chunk_grp);
@@ -966,6 +974,9 @@ static int analyze_impl(gic_handle *h, int64_t n, int64_t nnz, const int32_t *ro
     CUDA_STEP(cudaMalloc(&P.grp, sizeof(int32_t) * (size_t)(P.ngroups + 1)));
     ++h->launches;
     k_group_starts<<<gr, T_ROWS, 0, h->stream>>>(n, gflag, gid, P.grp, P.ngroups);
+    CUDA_STEP(cudaMalloc(&P.rowgrp, sizeof(int32_t) * (size_t)(n > 0 ? n : 1)));
+    ++h->launches;
+    k_row_group<<<grid_rows(h, P.ngroups), T_ROWS, 0, h->stream>>>(P.ngroups, P.grp, P.rowgrp);
     ++h->launches;
     k_group_stats<<<grid_rows(h, P.ngroups), T_ROWS, 0, h->stream>>>(P.ngroups, P.grp, P.Lrowptr, P.Urowptr, stats);
     CUDA_STEP(cudaGetLastError());

@@ -12,11 +12,13 @@
 //
 // Per group (rows s..s+G-1, shared external columns J[0..m)):
 //   1. wait for the rows J[u], then gather M[u][v] = L_{J[u],J[v]} (v <= u)
-//      into shared memory;
+//      into shared memory, row group by row group (the rows of a group share
+//      their external columns, so each is looked up once);
 //   2. the external part of every group row solves the same lower-triangular
 //      system M l = a_J, so all G rows are swept together, column by column
 //      in ascending order (the order of the sum above);
-//   3. the in-group columns and the diagonal of each row follow in order.
+//   3. the in-group columns and the diagonal of each row follow in order;
+//      the group's rows are published together (one fence).
 // A pivot <= 0 or non-finite records the smallest such row (atomicMin), and
 // the row publishes NaN so its dependants finish instead of waiting.
 #include <limits.h>
@@ -29,13 +31,22 @@ namespace gic {
 constexpr int IC_WARPS = 4;
 
 struct IcWarpSmem {
-    double M[MAXDIM * MAXDIM];   // row-major, lower triangle of the external block
+    double M[MAXDIM * MAXDIM];   // column-major (M[v * MAXDIM + u]), lower triangle of the external block:
+                                 // the sweep reads a column across lanes, conflict-free
     double invd[MAXDIM];         // 1 / M[v][v]
     double lg[GMAX][MAXDIM];     // external part of each group row
     double lin[GMAX][GMAX + 1];  // in-group part (and diagonal) of each group row
     int32_t J[MAXDIM];
     int32_t rs[MAXDIM];          // start of row J[u] in L
-    int32_t off[MAXDIM + 1];     // prefix of the gathered rows' lengths
+    int32_t len[MAXDIM];         // length of row J[u] in L (its diagonal included)
+    // J holds whole row groups (rows of a group are identical in A, which is
+    // symmetric), and a group's rows share their external columns: blocks
+    int32_t bu0[MAXDIM];         // first u of block b
+    int32_t bG[MAXDIM];          // rows of block b
+    int32_t boff[MAXDIM + 1];    // prefix of the blocks' external lengths
+    int nb;
+    double dd[6];                // the group's dot products l_t . l_q, q <= t (G <= 3)
+    double ain[6];               // the group's in-group entries of A, (t, q <= t) at t(t+1)/2 + q (G <= 3)
 };
 
 __device__ __forceinline__ int find_in(const int32_t *J, int lo, int hi, int32_t key)
@@ -53,6 +64,7 @@ __device__ __forceinline__ int find_in(const int32_t *J, int lo, int hi, int32_t
 __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t nchunks, const int32_t *__restrict__ ord,
                                                        const int32_t *__restrict__ chunk_grp,
                                                        const int32_t *__restrict__ grp,
+                                                       const int32_t *__restrict__ rowgrp,
                                                        const int32_t *__restrict__ Arowptr,
                                                        const double *__restrict__ valA,
                                                        const int32_t *__restrict__ Lrowptr,
@@ -77,17 +89,28 @@ __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t nchunks, const in
         const int m = Lrowptr[s + 1] - b0 - 1; // external columns (host checked m <= MAXDIM)
 
         // 1. external columns, their readiness (relaxed polling, one fence
-        // after the last wait), their row starts and lengths
+        // after the last wait), their row starts and lengths, and the blocks
+        // (row groups) they form
         int32_t dp0 = -1, dp1 = -1;
+        bool st0 = false, st1 = false;
         for (int u = lane; u < m; u += 32) {
             int32_t j = Lcol[b0 + u];
             S.J[u] = j;
             const int32_t rs = Lrowptr[j];
             const int32_t dpos = Lrowptr[j + 1] - 1;
             S.rs[u] = rs;
-            S.off[u + 1] = dpos + 1 - rs; // length of row j (its diagonal included)
-            if (u < 32) dp0 = dpos; else if (u < 64) dp1 = dpos;
+            S.len[u] = dpos + 1 - rs;
+            const bool st = (u == 0) || (rowgrp[j] == j);
+            if (u < 32) { dp0 = dpos; st0 = st; } else { dp1 = dpos; st1 = st; }
         }
+        if (G <= 3 && lane < G * (G + 1) / 2) { // read now, used after the sweep
+            int tt = 0;
+            while ((tt + 1) * (tt + 2) / 2 <= lane) ++tt;
+            const int qq = lane - tt * (tt + 1) / 2;
+            S.ain[lane] = valA[(int64_t)Arowptr[s + tt] + m + qq];
+        }
+        const unsigned long long bits =
+            (unsigned long long)__ballot_sync(0xffffffffu, st0) | ((unsigned long long)__ballot_sync(0xffffffffu, st1) << 32);
         {   // one lane at a time polls the diagonal written last
             double d0 = (dp0 >= 0) ? ld_relaxed(Lval + dp0) : 0.0;
             double d1 = (dp1 >= 0) ? ld_relaxed(Lval + dp1) : 0.0;
@@ -95,47 +118,78 @@ __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t nchunks, const in
         }
         __syncwarp();
         fence_acq_rel(); // pairs with the producers' release of each diagonal
+        for (int u = lane; u < m; u += 32) {
+            if ((bits >> u) & 1ull) {
+                const int b = __popcll(bits & ((1ull << u) - 1ull));
+                const unsigned long long rest = (u + 1 < 64) ? (bits >> (u + 1)) : 0ull;
+                const int u1 = rest ? u + __ffsll((long long)rest) : m;
+                S.bu0[b] = u;
+                S.bG[b] = u1 - u;
+                S.boff[b + 1] = S.len[u] - 1; // the block's first row: every entry but the diagonal is external
+            }
+        }
+        __syncwarp();
         if (lane == 0) {
-            S.off[0] = 0;
-            for (int u = 0; u < m; ++u) S.off[u + 1] += S.off[u];
+            const int nb = __popcll(bits);
+            S.nb = nb;
+            S.boff[0] = 0;
+            for (int b = 0; b < nb; ++b) S.boff[b + 1] += S.boff[b];
         }
         for (int idx = lane; idx < m * m; idx += 32) S.M[(idx / m) * MAXDIM + (idx % m)] = 0.0;
         __syncwarp();
 
-        // gather M[u][v] = L_{J[u],J[v]} for the entries of row J[u] inside J,
-        // four independent (column, value) loads in flight per lane
-        const int P = S.off[m];
-        int u = 0;
-        for (int base = lane; base < P; base += 128) {
-            int32_t q[4], uu[4];
+        // gather M[u][v] = L_{J[u],J[v]} (v <= u) block by block: a block's
+        // external column is looked up in J once for all its rows; four
+        // (column, values) reads in flight per lane
+        const int nb = S.nb, PT = S.boff[nb];
+        int bcur = 0;
+        for (int base = lane; base < PT; base += 128) {
+            int bb[4], pp[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const int idx = base + 32 * k;
-                if (idx < P) {
-                    while (S.off[u + 1] <= idx) ++u;
-                    uu[k] = u;
-                    q[k] = S.rs[u] + (idx - S.off[u]);
+                if (idx < PT) {
+                    while (S.boff[bcur + 1] <= idx) ++bcur;
+                    bb[k] = bcur;
+                    pp[k] = idx - S.boff[bcur];
                 } else {
-                    uu[k] = -1;
-                    q[k] = 0;
+                    bb[k] = -1;
+                    pp[k] = 0;
                 }
             }
             int32_t cc[4];
-            double vv[4];
+            double vv[4][3];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                cc[k] = (uu[k] >= 0) ? Lcol[q[k]] : -1;
-                vv[k] = (uu[k] >= 0) ? Lval[q[k]] : 0.0;
-            }
+                cc[k] = -1;
+                if (bb[k] >= 0) {
+                    const int u0 = S.bu0[bb[k]], gb = S.bG[bb[k]];
+                    cc[k] = Lcol[S.rs[u0] + pp[k]];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (uu[k] < 0) continue;
-                const int v = find_in(S.J, 0, uu[k] + 1, cc[k]);
-                if (v >= 0) {
-                    S.M[uu[k] * MAXDIM + v] = vv[k];
-                    if (v == uu[k]) S.invd[v] = 1.0 / vv[k];
+                    for (int r = 0; r < 3; ++r) vv[k][r] = (r < gb) ? Lval[S.rs[u0 + r] + pp[k]] : 0.0;
                 }
             }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (bb[k] < 0) continue;
+                const int u0 = S.bu0[bb[k]], gb = S.bG[bb[k]];
+                const int v = find_in(S.J, 0, u0, cc[k]);
+                if (v < 0) continue;
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+                    if (r < gb) S.M[v * MAXDIM + u0 + r] = vv[k][r];
+                for (int r = 3; r < gb; ++r) S.M[v * MAXDIM + u0 + r] = Lval[S.rs[u0 + r] + pp[k]];
+            }
+        }
+        // the blocks' own lower triangles (in-group entries and diagonals)
+        for (int b = lane; b < nb; b += 32) {
+            const int u0 = S.bu0[b], gb = S.bG[b], me = S.boff[b + 1] - S.boff[b];
+            for (int r = 0; r < gb; ++r)
+                for (int q2 = 0; q2 <= r; ++q2) {
+                    const double val = Lval[S.rs[u0 + r] + me + q2];
+                    S.M[(u0 + q2) * MAXDIM + u0 + r] = val;
+                    if (q2 == r) S.invd[u0 + r] = 1.0 / val;
+                }
         }
         __syncwarp();
 
@@ -155,8 +209,8 @@ __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t nchunks, const in
         for (int v = 0; v < m; ++v) {
             const int owner = v & 31;
             const double iv = S.invd[v];
-            const double mu0 = (lane > v && lane < m) ? S.M[lane * MAXDIM + v] : 0.0;
-            const double mu1 = (lane + 32 > v && lane + 32 < m) ? S.M[(lane + 32) * MAXDIM + v] : 0.0;
+            const double mu0 = (lane > v && lane < m) ? S.M[v * MAXDIM + lane] : 0.0;
+            const double mu1 = (lane + 32 > v && lane + 32 < m) ? S.M[v * MAXDIM + lane + 32] : 0.0;
 #pragma unroll
             for (int t = 0; t < GMAX; ++t) {
                 if (t < G) {
@@ -170,49 +224,90 @@ __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t nchunks, const in
         }
         __syncwarp();
 
-        // 3. in-group columns and diagonals, row by row
-        for (int t = 0; t < G; ++t) {
-            const int32_t i = s + t;
-            const int64_t ab = Arowptr[i];
-            // in-group column s+q (q < t): (a_{i,s+q} - l_t . l_q - sum_{q'<q}) / L_{s+q,s+q}
-            for (int q = 0; q < t; ++q) {
+        // 3. in-group columns and diagonals: the group's dot products
+        // l_t . l_q (q <= t) first (for G <= 3 all six at once, so their
+        // warp reductions overlap), then the small dense Cholesky in lane 0
+        if (G <= 3) {
+            double d[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}; // (t, q): 00, 10, 11, 20, 21, 22
+            for (int v = lane; v < m; v += 32) {
+                const double l0 = S.lg[0][v], l1 = (G > 1) ? S.lg[1][v] : 0.0, l2 = (G > 2) ? S.lg[2][v] : 0.0;
+                d[0] = fma(l0, l0, d[0]);
+                d[1] = fma(l1, l0, d[1]);
+                d[2] = fma(l1, l1, d[2]);
+                d[3] = fma(l2, l0, d[3]);
+                d[4] = fma(l2, l1, d[4]);
+                d[5] = fma(l2, l2, d[5]);
+            }
+#pragma unroll
+            for (int k = 0; k < 6; ++k) d[k] = warp_sum(d[k]);
+            if (lane == 0) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) S.dd[k] = d[k];
+                for (int t = 0; t < G; ++t) {
+                    for (int q = 0; q < t; ++q) {
+                        double x = S.ain[t * (t + 1) / 2 + q] - S.dd[t * (t + 1) / 2 + q];
+                        for (int q2 = 0; q2 < q; ++q2) x = fma(-S.lin[t][q2], S.lin[q][q2], x);
+                        S.lin[t][q] = x / S.lin[q][q];
+                    }
+                    const double a = S.ain[t * (t + 1) / 2 + t];
+                    double x = __dadd_rn(a, __dmul_rn(alpha, a)) - S.dd[t * (t + 1) / 2 + t];
+                    for (int q = 0; q < t; ++q) x = fma(-S.lin[t][q], S.lin[t][q], x);
+                    double piv;
+                    if (!(x > 0.0) || !isfinite(x)) {
+                        atomicMin(bad_row, (unsigned long long)(s + t));
+                        piv = qnan;
+                    } else {
+                        piv = sqrt(x);
+                    }
+                    S.lin[t][t] = piv;
+                }
+            }
+        } else {
+            for (int t = 0; t < G; ++t) {
+                const int64_t ab = Arowptr[s + t];
+                // in-group column s+q (q < t): (a_{i,s+q} - l_t . l_q - sum_{q'<q}) / L_{s+q,s+q}
+                for (int q = 0; q < t; ++q) {
+                    double d = 0.0;
+                    for (int v = lane; v < m; v += 32) d = fma(S.lg[t][v], S.lg[q][v], d);
+                    d = warp_sum(d);
+                    if (lane == 0) {
+                        double x = valA[ab + m + q] - d;
+                        for (int q2 = 0; q2 < q; ++q2) x = fma(-S.lin[t][q2], S.lin[q][q2], x);
+                        S.lin[t][q] = x / S.lin[q][q];
+                    }
+                    __syncwarp();
+                }
                 double d = 0.0;
-                for (int v = lane; v < m; v += 32) d = fma(S.lg[t][v], S.lg[q][v], d);
+                for (int v = lane; v < m; v += 32) d = fma(S.lg[t][v], S.lg[t][v], d);
                 d = warp_sum(d);
                 if (lane == 0) {
-                    double x = valA[ab + m + q] - d;
-                    for (int q2 = 0; q2 < q; ++q2) x = fma(-S.lin[t][q2], S.lin[q][q2], x);
-                    S.lin[t][q] = x / S.lin[q][q];
+                    const double a = valA[ab + m + t];
+                    double x = __dadd_rn(a, __dmul_rn(alpha, a)) - d;
+                    for (int q = 0; q < t; ++q) x = fma(-S.lin[t][q], S.lin[t][q], x);
+                    double piv;
+                    if (!(x > 0.0) || !isfinite(x)) {
+                        atomicMin(bad_row, (unsigned long long)(s + t));
+                        piv = qnan;
+                    } else {
+                        piv = sqrt(x);
+                    }
+                    S.lin[t][t] = piv;
                 }
                 __syncwarp();
             }
-            // diagonal
-            double d = 0.0;
-            for (int v = lane; v < m; v += 32) d = fma(S.lg[t][v], S.lg[t][v], d);
-            d = warp_sum(d);
-            double piv = 0.0;
-            if (lane == 0) {
-                const double a = valA[ab + m + t];
-                double x = __dadd_rn(a, __dmul_rn(alpha, a)) - d;
-                for (int q = 0; q < t; ++q) x = fma(-S.lin[t][q], S.lin[t][q], x);
-                if (!(x > 0.0) || !isfinite(x)) {
-                    atomicMin(bad_row, (unsigned long long)i);
-                    piv = qnan;
-                } else {
-                    piv = sqrt(x);
-                }
-                S.lin[t][t] = piv;
-            }
-            // publish row i: off-diagonals, then the diagonal with release
-            const int64_t lb = Lrowptr[i];
-            for (int v = lane; v < m; v += 32) Lval[lb + v] = S.lg[t][v];
-            __syncwarp();
-            if (lane < t) Lval[lb + m + lane] = S.lin[t][lane];
-            __threadfence();
-            __syncwarp();
-            if (lane == 0) st_release(Lval + lb + m + t, piv);
-            __syncwarp();
         }
+        __syncwarp();
+        // publish the group: every off-diagonal entry, one fence, then each
+        // row's diagonal with release (the readiness word)
+        for (int t = 0; t < G; ++t) {
+            const int64_t lb = Lrowptr[s + t];
+            for (int v = lane; v < m; v += 32) Lval[lb + v] = S.lg[t][v];
+            if (lane < t) Lval[lb + m + lane] = S.lin[t][lane];
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane < G) st_release(Lval + Lrowptr[s + lane] + m + lane, S.lin[lane][lane]);
+        __syncwarp();
       }
     }
 }
@@ -242,10 +337,11 @@ static int ic0_once(gic_handle *h, const Pattern &P, const double *valA, double 
         attr_set[h->device & 63] = 1;
     }
     int32_t nc = P.nchunks;
-    const int32_t *ord = P.ord_f, *cg = P.chunk_grp, *g = P.grp, *ar = P.rowptr, *lr = P.Lrowptr, *lc = P.Lcol;
+    const int32_t *ord = P.ord_f, *cg = P.chunk_grp, *g = P.grp, *rg = P.rowgrp, *ar = P.rowptr, *lr = P.Lrowptr,
+                  *lc = P.Lcol;
     unsigned *er = h->dev_err;
     int poll = h->tune_poll;
-    void *args[] = {&nc, &ord, &cg, &g, &ar, &valA, &lr, &lc, &valL, &alpha, &bad_dev, &er, &poll};
+    void *args[] = {&nc, &ord, &cg, &g, &rg, &ar, &valA, &lr, &lc, &valL, &alpha, &bad_dev, &er, &poll};
     GIC_TRY(launch_persistent(h, (const void *)k_ic0, IC_WARPS * 32, smem, nc, args));
     unsigned long long *hb = (unsigned long long *)((char *)h->host_pinned + 2048);
     GIC_CUDA_TRY(cudaMemcpyAsync(hb, bad_dev, sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));

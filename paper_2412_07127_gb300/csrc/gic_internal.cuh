@@ -266,6 +266,7 @@ struct Pattern {
     int32_t *Urowptr = nullptr, *Ucol = nullptr, *tperm = nullptr;
     // groups of consecutive rows with identical A patterns (<= GMAX rows)
     int32_t *grp = nullptr;   // ngroups+1 start rows
+    int32_t *rowgrp = nullptr; // n: the first row of each row's group
     int32_t *level = nullptr; // n row levels
     int32_t *Lrow = nullptr;  // nnzL: row of every L entry (edge -> its row node)
     // Solve schedule: chunks = runs of consecutive groups with increasing
