@@ -206,20 +206,30 @@ __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t nchunks, const in
                 if (lane + 32 < m) acc1[t] = valA[ab + lane + 32];
             }
         }
+        // Column v's accumulator is final once the sweep reaches it, so each
+        // step broadcasts it unscaled and the lanes fold 1 / M[v][v] into
+        // their coefficient (independent of the chain, issued ahead): the
+        // dependent chain per step is one shuffle and one FMA; the values
+        // l = acc / M[v][v] are formed once at the end.
         for (int v = 0; v < m; ++v) {
             const int owner = v & 31;
             const double iv = S.invd[v];
-            const double mu0 = (lane > v && lane < m) ? S.M[v * MAXDIM + lane] : 0.0;
-            const double mu1 = (lane + 32 > v && lane + 32 < m) ? S.M[v * MAXDIM + lane + 32] : 0.0;
+            const double mu0 = (lane > v && lane < m) ? S.M[v * MAXDIM + lane] * iv : 0.0;
+            const double mu1 = (lane + 32 > v && lane + 32 < m) ? S.M[v * MAXDIM + lane + 32] * iv : 0.0;
 #pragma unroll
             for (int t = 0; t < GMAX; ++t) {
                 if (t < G) {
-                    double mine = (v < 32) ? acc0[t] : acc1[t];
-                    double lv = __shfl_sync(0xffffffffu, mine * iv, owner);
-                    if (lane == owner) S.lg[t][v] = lv;
-                    acc0[t] = fma(-mu0, lv, acc0[t]);
-                    acc1[t] = fma(-mu1, lv, acc1[t]);
+                    const double a = __shfl_sync(0xffffffffu, (v < 32) ? acc0[t] : acc1[t], owner);
+                    acc0[t] = fma(-mu0, a, acc0[t]);
+                    acc1[t] = fma(-mu1, a, acc1[t]);
                 }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < GMAX; ++t) {
+            if (t < G) {
+                if (lane < m) S.lg[t][lane] = acc0[t] * S.invd[lane];
+                if (lane + 32 < m) S.lg[t][lane + 32] = acc1[t] * S.invd[lane + 32];
             }
         }
         __syncwarp();
