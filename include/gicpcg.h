@@ -85,7 +85,8 @@ int gic_fem_hex_assemble(gic_handle *h, int N, double nu, int nb, const double *
 /* ------------------------------------------------- A2: pattern analysis
  * Builds, on the device, the pattern of L = tril(A) (IC(0) keeps A's lower
  * pattern: Introduction; Model Architecture), its transpose, groups of
- * consecutive rows with identical patterns (solved together by one warp) and
+ * consecutive rows with identical patterns (solved together; runs of such
+ * rows are cut at their common length when it is 2..8, else every 8 rows) and
  * the level of every row (level 0: no strictly-lower entry; else 1 + the
  * largest level among its strictly-lower columns). rowptr/col (device) are
  * borrowed and must stay valid and unchanged while *P lives. The pattern is
@@ -187,11 +188,13 @@ int gic_pcg_split(gic_handle *h, const gic_pattern *PA, const double *valA, cons
 int gic_dropout(gic_handle *h, const gic_pattern *P, const double *valL, double threshold,
                 int32_t *Srowptr, int32_t *Scol, double *Lval_out, int64_t *nnzS, int64_t *nnzL_out);
 /* Node-granular variant (no counterpart in the paper; it keeps the row-group
- * structure the fast solve kernels need): within each row group of P (rows
- * with identical patterns, a hex node's three dofs) an external column is
- * dropped from all the group's rows only when every one of their entries in
- * it is at most threshold; the group's own lower block always stays.
- * Arguments and outputs as gic_dropout. */
+ * structure the fast solve kernels need): the factor is cut into blocks by
+ * the row groups of P (rows with identical patterns, a hex node's three
+ * dofs); an external block (rows of group g, columns of an earlier group h)
+ * is dropped whole when every entry in it is at most threshold and kept
+ * whole otherwise; each group's own lower block always stays. The rows of a
+ * group then keep identical patterns in S, so gic_analyze of S finds the
+ * same groups. Arguments and outputs as gic_dropout. */
 int gic_dropout_grouped(gic_handle *h, const gic_pattern *P, const double *valL, double threshold,
                         int32_t *Srowptr, int32_t *Scol, double *Lval_out, int64_t *nnzS, int64_t *nnzL_out);
 /* Deviation of a factor from the IC(0) factor (the diagnostic of the paper's
@@ -305,12 +308,12 @@ int gic_adam_step(gic_handle *h, int64_t np, float *theta, const float *grad, fl
 
 /* Tuning of the sync-free kernels (IC(0), triangular solves); results agree
  * to round-off across settings: GIC_TUNE_SOLVE_WARPS_PER_SM = cap on resident
- * solve warps (warp pairs for the warp-specialised solves) per SM (0 = no
- * cap); GIC_TUNE_POLL = polling: low 16 bits = nanoseconds slept between
- * polls, bit 16 set = one polling lane per warp (default 1<<16);
+ * solve warps (teams of three warps for the warp-specialised solves) per SM
+ * (0 = automatic: 4, 8 or 16 teams by chunks per SM); GIC_TUNE_POLL =
+ * polling: low 16 bits = nanoseconds slept between polls, bit 16 set = one
+ * polling lane per warp (default 1<<16);
  * GIC_TUNE_PIPELINE = triangular-solve kernels: 4 (default) = automatic
- * (warp-specialised unless the pattern has more than 64 chunks per SM, then
- * staged one-warp),
+ * (warp-specialised where the pattern admits them, else staged one-warp),
  * 3 = SM-local solves (blocks of 16 neighbouring chunks per CTA,
  * intra-block dependencies in shared memory) where the pattern's block order
  * allows, else 2 = warp-specialised solves on premultiplied row-group blocks
