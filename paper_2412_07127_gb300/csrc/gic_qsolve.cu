@@ -251,7 +251,11 @@ __device__ __forceinline__ bool q_finish(QRing<T> &Q, int seq, int cnt, T *x, T 
         const QSlot<T> &S = Q.slot[q % QR];
         const int32_t cw = S.cw, s = S.s;
         const int ne = cw & 255, nl = (cw >> 8) & 255, np = (cw >> 16) & 255, G = cw >> 24;
-        const T p0 = __shfl_sync(FULL, yp, 0), p1 = __shfl_sync(FULL, yp, 4), p2 = __shfl_sync(FULL, yp, 8);
+        // the previous group's columns (its rows: np <= 3, the analysis admits
+        // groups of at most 3 rows) go to chains c < np, so lane (t, c) needs
+        // one value: previous-group row jr, held by lanes 4 jr .. 4 jr + 3
+        const int jr = (c < np) ? S.cols[ne + nl + c] - prev_s : 0;
+        const T pv = __shfl_sync(FULL, yp, 4 * jr);
         T acc = 0;
         if (t < G) {
             // chain c takes late values j = c, c + 4, ... (the schedule orders
@@ -269,8 +273,7 @@ __device__ __forceinline__ bool q_finish(QRing<T> &Q, int seq, int cnt, T *x, T 
             // (u <= t), backward z_t gets M_ut y_u (u >= t); chain c takes u = c
             if (c < G && (FWD ? c <= t : c >= t))
                 acc = fma(FWD ? S.Mv[t * (t + 1) / 2 + c] : S.Mv[c * (c + 1) / 2 + t], S.rr[c], acc);
-            for (int j = c; j < np; j += 4)
-                acc = fma(-S.K[t][ne + nl + j], pick3<T>(S.cols[ne + nl + j] - prev_s, p0, p1, p2), acc);
+            if (c < np) acc = fma(-S.K[t][ne + nl + c], pv, acc);
 #pragma unroll
             for (int i = 0; i < QLATE / 4; ++i) {
                 const int j = c + 4 * i;
