@@ -159,6 +159,10 @@ def test_analysis_rejects_bad_patterns(G, h):
     with pytest.raises(G.GicError) as e:
         G.Pattern(h, _dev(np.array(rp, np.int32)), _dev(np.array(cl, np.int32)))
     assert e.value.status == G.GIC_ERR_INVALID_ARG
+    # empty input: no rows
+    with pytest.raises(G.GicError) as e:
+        G.Pattern(h, _dev(np.zeros(1, np.int32)), _dev(np.zeros(0, np.int32)))
+    assert e.value.status == G.GIC_ERR_INVALID_ARG
 
 
 # ---------------------------------------------------------------- A3
