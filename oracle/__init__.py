@@ -34,6 +34,12 @@ def lib():
         L.or_hex_element_stiffness.argtypes = [_dbl, _dbl, _f64p]
         L.or_fem_hex_sizes.argtypes = [C.c_int, C.c_int, C.POINTER(_i64), C.POINTER(_i64)]
         L.or_fem_hex_assemble.argtypes = [C.c_int, C.c_int, _dbl, _f64p, _i32p, _i32p, _f64p]
+        L.or_fem_box_sizes.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(_i64), C.POINTER(_i64)]
+        L.or_fem_box_assemble.argtypes = [C.c_int, C.c_int, C.c_int, _dbl, C.c_int, _dbl, _f64p, _i32p, _i32p,
+                                          _f64p]
+        L.or_spmv_threads.argtypes = [_i64, _i32p, _i32p, _f64p, _f64p, _f64p]
+        L.or_spmv_threads.restype = None
+        L.or_threads.restype = C.c_int
         L.or_lower_nnz.argtypes = [_i64, _i32p, _i32p]
         L.or_lower_nnz.restype = _i64
         L.or_lower_pattern.argtypes = [_i64, _i32p, _i32p, C.c_void_p, _i32p, _i32p, C.c_void_p]
@@ -55,6 +61,9 @@ def lib():
         L.or_round_bf16.argtypes = [_dbl]
         L.or_round_bf16.restype = _dbl
         L.or_gnn_forward.argtypes = [_i64, _i32p, _i32p, _f64p, _f64p, _f64p, C.c_int, _f64p]
+        L.or_gnn_forward_parts.argtypes = [_i64, _i32p, _i32p, _f64p, _f64p, _f64p, C.c_int, _f64p, _f64p,
+                                           _f64p, _f64p, _f64p]
+        L.or_gnn_forward_parts.restype = None
         L.or_correct.argtypes = [_i64, _i32p, _i32p, _f64p, _f64p, _f64p]
         L.or_correct_backward.argtypes = [_i64, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p]
         L.or_gnn_backward.argtypes = [_i64, _i32p, _i32p, _f64p, _f64p, _f64p, C.c_int, _f64p, _f64p]
@@ -147,6 +156,37 @@ def fem_hex_assemble(N, E, nu=0.3, clamp=True):
     if rc != 0:
         raise RuntimeError(f"or_fem_hex_assemble failed: {rc}")
     return CSR(rowptr, col, val)
+
+
+def fem_box_assemble(Nx, Ny, Nz, h, E, nu=0.3, clamp=True):
+    """A = sum_e E_e K_e on a box of Nx x Ny x Nz hex elements of side h
+    (element id ex + Nx (ey + Ny ez)); E has Nx Ny Nz entries. The first z
+    layers of the N^3 cube (h = 1/N) give the cube's rows of the nodes they
+    hold, except on the box's top node plane."""
+    E = _c64(E)
+    assert E.size == Nx * Ny * Nz
+    n, nnz = _i64(), _i64()
+    if lib().or_fem_box_sizes(Nx, Ny, Nz, 1 if clamp else 0, C.byref(n), C.byref(nnz)) != 0:
+        raise ValueError("bad box")
+    rowptr = np.zeros(n.value + 1, np.int32)
+    col = np.zeros(nnz.value, np.int32)
+    val = np.zeros(nnz.value)
+    rc = lib().or_fem_box_assemble(Nx, Ny, Nz, h, 1 if clamp else 0, nu, E, rowptr, col, val)
+    if rc != 0:
+        raise RuntimeError(f"or_fem_box_assemble failed: {rc}")
+    return CSR(rowptr, col, val)
+
+
+def spmv_threads(A: CSR, x):
+    """or_spmv with its rows split over the host's cores (same result)."""
+    y = np.zeros(A.n)
+    lib().or_spmv_threads(A.n, A.rowptr, A.col, A.val, _c64(x), y)
+    return y
+
+
+def threads():
+    """Threads or_spmv_threads uses (OpenMP's default: the host's cores)."""
+    return int(lib().or_threads())
 
 
 # ---------------------------------------------------------------- A2
@@ -257,6 +297,18 @@ def gnn_forward(T: CSR, x9, e0, theta, bf16=False):
     lib().or_gnn_forward(T.n, T.rowptr, T.col, _c64(x9).ravel(), _c64(e0), _c64(theta),
                          1 if bf16 else 0, g)
     return g
+
+
+def gnn_forward_parts(T: CSR, x9, e0, theta, bf16=False):
+    """(g, x0, S0, M0, x1): the output and the intermediates tests pin:
+    GraphNorm output, block 0's node sums and means, block 0's node update."""
+    n = T.n
+    g = np.zeros(T.nnz)
+    x0, x1 = np.zeros(9 * n), np.zeros(9 * n)
+    S0, M0 = np.zeros(n), np.zeros(n)
+    lib().or_gnn_forward_parts(T.n, T.rowptr, T.col, _c64(x9).ravel(), _c64(e0), _c64(theta),
+                               1 if bf16 else 0, g, x0, S0, M0, x1)
+    return g, x0.reshape(n, 9), S0, M0, x1.reshape(n, 9)
 
 
 def correct(T: CSR, LIC_val, g):

@@ -16,6 +16,10 @@
  *   or_hex_element_stiffness  pinned: symmetry, 6 rigid-body null vectors,
  *                             uniform-strain patch test (closed form forces)
  *   or_fem_hex_assemble       pinned: closed-form nnz, symmetry, rigid modes
+ *   or_fem_box_assemble       pinned: equals the cube for Nx = Ny = Nz = N;
+ *                             the rows of its first m node planes equal the
+ *                             cube's (a z-slab of the cube's elements)
+ *   or_spmv_threads           pinned: identical to or_spmv
  *   or_lower_pattern/levels   pinned: closed-form level formula x+2y+4(z-1)
  *   or_ic0                    pinned: dense Cholesky on no-fill patterns,
  *                             (LL^T)_ij == a_ij on the pattern, dense masked
@@ -24,10 +28,15 @@
  *   or_pcg                    pinned: <= n steps, 1 step with exact Cholesky,
  *                             Eq.(6) bound, dense solve
  *   or_features               pinned: hand-computed 4x4 cases
- *   or_gnn_forward            pinned: g = 0 => L = L_IC; independent dense
- *                             restatement. Against the paper itself the
- *                             architecture is parity unpinned (Figure 1 is
- *                             missing from the text; the layout is a reading).
+ *   or_gnn_forward            pinned: g = 0 => L = L_IC; GraphNorm output
+ *                             moments in closed form; block-0 node sums =
+ *                             full-row counts / row sums of A (each edge to
+ *                             both endpoints, a self-loop once), means = sums
+ *                             / incident-edge count; a hand-worked 2-node
+ *                             graph; an independent dense restatement. The
+ *                             layout itself is a reading (Figure 1 is missing
+ *                             from the text): parity unpinned against the
+ *                             paper for the architecture, not its arithmetic.
  *   or_correct(+backward)     pinned: g = 0 => L_IC; finite differences
  *   or_probe_loss(+grad)      pinned: unbiased vs dense ||LL^T-A||_F^2,
  *                             central finite differences
@@ -42,6 +51,9 @@
  *                             on single-row groups, hand-built 2x2 blocks,
  *                             node blocks kept whole (hex)
  */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -106,11 +118,18 @@ void or_hex_element_stiffness(double nu, double h, double *Ke)
     }
 }
 
-/* Free nodes are those with z >= z0 (z0 = 1 when the z = 0 face is clamped
+/* A box of Nx x Ny x Nz hexahedral elements of side h (the unit cube of N^3
+ * elements is Nx = Ny = Nz = N, h = 1/N). Nodes (x, y, z), 0 <= x <= Nx,
+ * 0 <= y <= Ny, 0 <= z <= Nz, are numbered x fastest, then y, then z.
+ * Free nodes are those with z >= z0 (z0 = 1 when the z = 0 face is clamped
  * and its dofs eliminated, z0 = 0 for the free-floating body). */
-static int64_t node_id(int N, int z0, int x, int y, int z)
+typedef struct {
+    int nx, ny, nz, z0;
+} Box;
+
+static int64_t node_id(const Box *B, int x, int y, int z)
 {
-    return (int64_t)x + (int64_t)(N + 1) * ((int64_t)y + (int64_t)(N + 1) * (z - z0));
+    return (int64_t)x + (int64_t)(B->nx + 1) * ((int64_t)y + (int64_t)(B->ny + 1) * (z - B->z0));
 }
 
 static int cmp_i64(const void *a, const void *b)
@@ -121,18 +140,18 @@ static int cmp_i64(const void *a, const void *b)
 
 /* Neighbour free nodes of free node (x,y,z): the free nodes of every element
  * that contains it, sorted and deduplicated. Returns the count (<= 27). */
-static int node_neighbours(int N, int z0, int x, int y, int z, int64_t *out)
+static int node_neighbours(const Box *B, int x, int y, int z, int64_t *out)
 {
     int64_t tmp[64];
     int cnt = 0;
     for (int ez = z - 1; ez <= z; ++ez)
         for (int ey = y - 1; ey <= y; ++ey)
             for (int ex = x - 1; ex <= x; ++ex) {
-                if (ex < 0 || ey < 0 || ez < 0 || ex >= N || ey >= N || ez >= N) continue;
+                if (ex < 0 || ey < 0 || ez < 0 || ex >= B->nx || ey >= B->ny || ez >= B->nz) continue;
                 for (int a = 0; a < 8; ++a) {
                     int nx = ex + (a & 1), ny = ey + ((a >> 1) & 1), nz = ez + ((a >> 2) & 1);
-                    if (nz < z0) continue;
-                    tmp[cnt++] = node_id(N, z0, nx, ny, nz);
+                    if (nz < B->z0) continue;
+                    tmp[cnt++] = node_id(B, nx, ny, nz);
                 }
             }
     qsort(tmp, (size_t)cnt, sizeof(int64_t), cmp_i64);
@@ -142,43 +161,47 @@ static int node_neighbours(int N, int z0, int x, int y, int z, int64_t *out)
     return m;
 }
 
-/* Sizes of the assembled system: n = 3 * #free nodes, nnz of the CSR. */
-int or_fem_hex_sizes(int N, int clamp, int64_t *n, int64_t *nnz)
+/* Sizes of the assembled box system: n = 3 * #free nodes, nnz of the CSR. */
+int or_fem_box_sizes(int Nx, int Ny, int Nz, int clamp, int64_t *n, int64_t *nnz)
 {
-    if (N < 1) return -1;
-    int z0 = clamp ? 1 : 0;
-    int64_t nn = 0, nz = 0;
+    if (Nx < 1 || Ny < 1 || Nz < 1) return -1;
+    Box B = {Nx, Ny, Nz, clamp ? 1 : 0};
+    int64_t nn = 0, nzc = 0;
     int64_t nb[27];
-    for (int z = z0; z <= N; ++z)
-        for (int y = 0; y <= N; ++y)
-            for (int x = 0; x <= N; ++x) {
+    for (int z = B.z0; z <= Nz; ++z)
+        for (int y = 0; y <= Ny; ++y)
+            for (int x = 0; x <= Nx; ++x) {
                 nn += 1;
-                nz += 9 * (int64_t)node_neighbours(N, z0, x, y, z, nb);
+                nzc += 9 * (int64_t)node_neighbours(&B, x, y, z, nb);
             }
     *n = 3 * nn;
-    *nnz = nz;
+    *nnz = nzc;
     return 0;
 }
 
-/* Assemble A = sum_e E_e K_e over the N^3 elements (element id
- * ex + N*(ey + N*ez)), keeping only free dofs (dof = 3*node + component).
- * Columns are sorted in each row. The value of every entry is accumulated
- * element by element in ascending element order. */
-int or_fem_hex_assemble(int N, int clamp, double nu, const double *E,
+int or_fem_hex_sizes(int N, int clamp, int64_t *n, int64_t *nnz)
+{
+    return or_fem_box_sizes(N, N, N, clamp, n, nnz);
+}
+
+/* Assemble A = sum_e E_e K_e over the box's elements (element id
+ * ex + Nx*(ey + Ny*ez)), element side h, keeping only free dofs (dof =
+ * 3*node + component). Columns are sorted in each row. The value of every
+ * entry is accumulated element by element in ascending element order. */
+int or_fem_box_assemble(int Nx, int Ny, int Nz, double h, int clamp, double nu, const double *E,
                         int32_t *rowptr, int32_t *col, double *val)
 {
-    if (N < 1) return -1;
-    int z0 = clamp ? 1 : 0;
-    double h = 1.0 / N;
+    if (Nx < 1 || Ny < 1 || Nz < 1 || !(h > 0.0)) return -1;
+    Box B = {Nx, Ny, Nz, clamp ? 1 : 0};
     double Ke[576];
     or_hex_element_stiffness(nu, h, Ke);
     int64_t nb[27];
     int64_t pos = 0;
     rowptr[0] = 0;
-    for (int z = z0; z <= N; ++z)
-        for (int y = 0; y <= N; ++y)
-            for (int x = 0; x <= N; ++x) {
-                int m = node_neighbours(N, z0, x, y, z, nb);
+    for (int z = B.z0; z <= Nz; ++z)
+        for (int y = 0; y <= Ny; ++y)
+            for (int x = 0; x <= Nx; ++x) {
+                int m = node_neighbours(&B, x, y, z, nb);
                 for (int c = 0; c < 3; ++c) {
                     for (int k = 0; k < m; ++k)
                         for (int d = 0; d < 3; ++d) {
@@ -186,22 +209,22 @@ int or_fem_hex_assemble(int N, int clamp, double nu, const double *E,
                             val[pos] = 0.0;
                             pos++;
                         }
-                    int64_t row = 3 * node_id(N, z0, x, y, z) + c;
+                    int64_t row = 3 * node_id(&B, x, y, z) + c;
                     rowptr[row + 1] = (int32_t)pos;
                 }
             }
-    for (int ez = 0; ez < N; ++ez)
-        for (int ey = 0; ey < N; ++ey)
-            for (int ex = 0; ex < N; ++ex) {
-                double Ee = E[(int64_t)ex + (int64_t)N * (ey + (int64_t)N * ez)];
+    for (int ez = 0; ez < Nz; ++ez)
+        for (int ey = 0; ey < Ny; ++ey)
+            for (int ex = 0; ex < Nx; ++ex) {
+                double Ee = E[(int64_t)ex + (int64_t)Nx * (ey + (int64_t)Ny * ez)];
                 for (int a = 0; a < 8; ++a) {
                     int az = ez + ((a >> 2) & 1);
-                    if (az < z0) continue;
-                    int64_t pa = node_id(N, z0, ex + (a & 1), ey + ((a >> 1) & 1), az);
+                    if (az < B.z0) continue;
+                    int64_t pa = node_id(&B, ex + (a & 1), ey + ((a >> 1) & 1), az);
                     for (int b = 0; b < 8; ++b) {
                         int bz = ez + ((b >> 2) & 1);
-                        if (bz < z0) continue;
-                        int64_t pb = node_id(N, z0, ex + (b & 1), ey + ((b >> 1) & 1), bz);
+                        if (bz < B.z0) continue;
+                        int64_t pb = node_id(&B, ex + (b & 1), ey + ((b >> 1) & 1), bz);
                         for (int c = 0; c < 3; ++c) {
                             int64_t i = 3 * pa + c;
                             for (int d = 0; d < 3; ++d) {
@@ -219,6 +242,14 @@ int or_fem_hex_assemble(int N, int clamp, double nu, const double *E,
                 }
             }
     return 0;
+}
+
+/* The unit cube of N^3 elements (element id ex + N*(ey + N*ez)). */
+int or_fem_hex_assemble(int N, int clamp, double nu, const double *E,
+                        int32_t *rowptr, int32_t *col, double *val)
+{
+    if (N < 1) return -1;
+    return or_fem_box_assemble(N, N, N, 1.0 / N, clamp, nu, E, rowptr, col, val);
 }
 
 /* ======================================================================
@@ -347,6 +378,30 @@ void or_spmv(int64_t n, const int32_t *rowptr, const int32_t *col, const double 
         for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) s = s + val[p] * x[col[p]];
         y[i] = s;
     }
+}
+
+/* The same product with the rows split over the host's cores (OpenMP), for
+ * the all-core CPU timing; every row is summed exactly as in or_spmv, so the
+ * result is identical. The triangular solves have no such variant: they are
+ * sequential by definition. */
+void or_spmv_threads(int64_t n, const int32_t *rowptr, const int32_t *col, const double *val,
+                     const double *x, double *y)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) s = s + val[p] * x[col[p]];
+        y[i] = s;
+    }
+}
+
+int or_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /* Forward substitution L y = r (Supplementary 5, Eq.(11) read as
@@ -719,6 +774,23 @@ void or_gnn_forward(int64_t n, const int32_t *Lrowptr, const int32_t *Lcol, cons
     or_gnn_tape t;
     tape_alloc(&t, n, Lrowptr[n]);
     gnn_forward_tape(n, Lrowptr, Lcol, x9, e0, theta, bf16, g, &t);
+    tape_free(&t);
+}
+
+/* The same forward, also returning intermediates that tests pin to closed
+ * forms: x0 (n x 9, the GraphNorm output), block 0's node sums S0 and means
+ * M0 (n each) and its node update x1 (n x 9). */
+void or_gnn_forward_parts(int64_t n, const int32_t *Lrowptr, const int32_t *Lcol, const double *x9,
+                          const double *e0, const double *theta, int bf16, double *g, double *x0,
+                          double *S0, double *M0, double *x1)
+{
+    or_gnn_tape t;
+    tape_alloc(&t, n, Lrowptr[n]);
+    gnn_forward_tape(n, Lrowptr, Lcol, x9, e0, theta, bf16, g, &t);
+    memcpy(x0, t.x[0], sizeof(double) * (size_t)(9 * n));
+    memcpy(S0, t.S[0], sizeof(double) * (size_t)n);
+    memcpy(M0, t.M[0], sizeof(double) * (size_t)n);
+    memcpy(x1, t.x[1], sizeof(double) * (size_t)(9 * n));
     tape_free(&t);
 }
 

@@ -153,3 +153,41 @@ def test_lower_pattern_matches_dense_tril():
     D = A.to_dense()
     assert T.nnz == (A.nnz + A.n) // 2
     assert np.array_equal(T.to_dense(), np.tril(D))
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (2, 3, 4), (5, 2, 1), (4, 4, 2)])
+def test_box_sizes_closed_form(dims):
+    """Per direction, summing a node's 1-D neighbour count over the nodes of
+    a line of k elements gives 3k + 1 (free) or 3k - 2 (z, clamped at 0), so
+    nnz = 9 (3Nx+1)(3Ny+1)(3Nz-2) and n = 3 (Nx+1)(Ny+1)Nz."""
+    Nx, Ny, Nz = dims
+    A = O.fem_box_assemble(Nx, Ny, Nz, 0.5, np.ones(Nx * Ny * Nz))
+    assert A.n == 3 * (Nx + 1) * (Ny + 1) * Nz
+    assert A.nnz == 9 * (3 * Nx + 1) * (3 * Ny + 1) * (3 * Nz - 2)
+    D = A.to_dense()
+    assert np.allclose(D, D.T, rtol=0, atol=1e-14 * np.abs(D).max())
+
+
+def test_box_of_the_cube_is_the_cube():
+    N = 6
+    E = I.material_field(N, 3)
+    A = O.fem_hex_assemble(N, E)
+    B = O.fem_box_assemble(N, N, N, 1.0 / N, E)
+    assert np.array_equal(A.rowptr, B.rowptr) and np.array_equal(A.col, B.col)
+    assert np.array_equal(A.val, B.val)
+
+
+@pytest.mark.parametrize("m", [1, 2, 4])
+def test_slab_rows_equal_the_cube_rows(m):
+    """The elements of the cube's first m + 1 layers hold every element that
+    touches a node of the first m free planes, so the slab's rows of those
+    nodes are the cube's rows, columns and values alike (node numbering is
+    the same up to plane m + 1)."""
+    N = 7
+    E = I.material_field(N, 4)
+    A = O.fem_hex_assemble(N, E)
+    S = O.fem_box_assemble(N, N, m + 1, 1.0 / N, E[: N * N * (m + 1)])
+    k = 3 * (N + 1) ** 2 * m
+    assert np.array_equal(A.rowptr[: k + 1], S.rowptr[: k + 1])
+    e = A.rowptr[k]
+    assert np.array_equal(A.col[:e], S.col[:e]) and np.array_equal(A.val[:e], S.val[:e])

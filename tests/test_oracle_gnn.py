@@ -215,3 +215,95 @@ def test_adam_constant_gradient_steps():
         O.adam_step(theta, g, m1, m2, t, 0.005)
         assert np.allclose(theta, t0 - t * 0.005 * g / (np.abs(g) + 1e-8), rtol=1e-12)
     assert O.lr_at(0, 10) == 0.0 and O.lr_at(5, 10) == 0.0025 and O.lr_at(50, 10) == 0.005
+
+
+# ---------------------------------------------------------------- closed forms of the forward
+def _set(theta, name, index, value):
+    """theta[name][index] = value (index a tuple into the parameter's shape)."""
+    off, shape = I.param_slices()[name]
+    theta[off + int(np.ravel_multi_index(index, shape))] = value
+
+
+def _graph(n, seed):
+    """A random symmetric pattern with a stored diagonal (diagonally dominant)."""
+    rng = np.random.default_rng(seed)
+    M = (rng.random((n, n)) < 0.15) * rng.standard_normal((n, n))
+    S = M + M.T
+    A = O.csr_from_dense(S + np.diag(np.abs(S).sum(1) + 1.0))
+    return A, O.lower(A)
+
+
+def test_graphnorm_output_moments_closed_form():
+    """GraphNorm: out = gamma (x - alpha mu) / sqrt(m2 + 1e-5) + beta with m2
+    the mean square of x - alpha mu, so per feature mean(out) = gamma (1 -
+    alpha) mu / sqrt(m2 + 1e-5) + beta and mean((out - beta)^2) = gamma^2 m2
+    / (m2 + 1e-5), m2 = var(x) + ((1 - alpha) mu)^2."""
+    A, T = _graph(40, 3)
+    rng = np.random.default_rng(4)
+    x9 = rng.standard_normal((A.n, 9)) * 2.0 + 0.7
+    e0 = rng.standard_normal(T.nnz)
+    th = np.zeros(I.N_PARAMS)
+    gam, bet, alp = rng.uniform(0.5, 2, 9), rng.standard_normal(9), rng.uniform(0, 1, 9)
+    for f in range(9):
+        _set(th, "gn_gamma", (f,), gam[f])
+        _set(th, "gn_beta", (f,), bet[f])
+        _set(th, "gn_alpha", (f,), alp[f])
+    _, x0, _, _, _ = O.gnn_forward_parts(T, x9, e0, th)
+    mu, var = x9.mean(0), x9.var(0)
+    m2 = var + ((1 - alp) * mu) ** 2
+    assert np.allclose(x0.mean(0), gam * (1 - alp) * mu / np.sqrt(m2 + 1e-5) + bet, rtol=1e-12, atol=1e-12)
+    assert np.allclose(((x0 - bet) ** 2).mean(0), gam ** 2 * m2 / (m2 + 1e-5), rtol=1e-12)
+
+
+def test_aggregation_counts_each_edge_at_both_ends_and_a_self_loop_once():
+    """Block 0's edge outputs all 1 (W2 = 0, b2 = 1): a node's sum is its
+    incident-edge count, which on a symmetric pattern with a stored diagonal
+    is the full row count of A; its mean is 1."""
+    A, T = _graph(50, 5)
+    rng = np.random.default_rng(6)
+    th = np.zeros(I.N_PARAMS)
+    _set(th, "b2_0", (0,), 1.0)
+    _, _, S0, M0, _ = O.gnn_forward_parts(T, rng.standard_normal((A.n, 9)), rng.standard_normal(T.nnz), th)
+    assert np.array_equal(S0, np.diff(A.rowptr).astype(float))
+    assert np.array_equal(M0, np.ones(A.n))
+
+
+def test_aggregation_sums_edge_values_over_the_full_row():
+    """Block 0's edge output ~ e0 (one hidden unit in its linear range: tanh(eps
+    e0) / eps = e0 + O(eps^2)): with e0 = tril(A) / s, a node's sum is its full
+    row sum of A over s (the lower entries of its row plus, through the
+    transposed edges, those of its column) and its mean that over the row
+    count."""
+    A, T = _graph(50, 7)
+    x9, e0, s = O.features(A)
+    eps = 1e-5
+    th = np.zeros(I.N_PARAMS)
+    _set(th, "W1_0", (0, 1), eps)
+    _set(th, "W2_0", (0,), 1.0 / eps)
+    _, _, S0, M0, _ = O.gnn_forward_parts(T, x9, e0, th)
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    rowsum = np.bincount(rows, weights=A.val, minlength=A.n) / s
+    cnt = np.diff(A.rowptr).astype(float)
+    tol = 1e-9 * np.abs(A.val).max() / s * cnt.max()
+    assert np.max(np.abs(S0 - rowsum)) <= tol
+    assert np.max(np.abs(M0 - rowsum / cnt)) <= tol
+
+
+def test_gnn_forward_hand_worked_two_nodes():
+    gold = json.load(open(os.path.join(GOLD, "gnn_2node.json")))
+    A = O.csr_from_dense(np.array([[4.0, -1.0], [-1.0, 3.0]]))
+    T = O.lower(A)
+    th = np.zeros(I.N_PARAMS)
+    for key, val in gold["weights"].items():
+        if isinstance(val, list):
+            for f, v in enumerate(val):
+                _set(th, key, (f,), v)
+            continue
+        name, idx = (key.split("[", 1) + [""])[:2]
+        index = tuple(int(k) for k in idx.replace("]", " ").replace("[", " ").split()) or (0,)
+        _set(th, name, index, val)
+    g, x0, S0, M0, x1 = O.gnn_forward_parts(T, np.array(gold["x9"]), np.array(gold["e0"]), th)
+    assert np.allclose(S0, gold["S0"], rtol=1e-14, atol=1e-15)
+    assert np.allclose(M0, gold["M0"], rtol=1e-14, atol=1e-15)
+    assert np.allclose(x1[:, :2], gold["x1_f0_f1"], rtol=1e-14, atol=1e-15)
+    assert np.allclose(g, gold["g"], rtol=1e-14, atol=1e-15)
