@@ -108,10 +108,10 @@ int gic_pattern_info(const gic_pattern *P, int64_t *n, int64_t *nnzA, int64_t *n
  * padded entry count of the SELL-32 copy of A used by the PCG SpMV. */
 int gic_pattern_schedule(const gic_pattern *P, int32_t *nchunks, int32_t *chunked, int64_t *sell_nnz);
 /* Which triangular-solve kernels the pattern admits (host outputs, any may be
- * NULL): warp-specialised (1/0), SM-local blocks (1/0) and the rows the
- * largest block mirrors in shared memory. */
-int gic_pattern_solve_kernels(const gic_pattern *P, int32_t *warp_specialised, int32_t *sm_local,
-                              int32_t *mirror_rows);
+ * NULL): warp-specialised (1/0), level-sliced (1/0; one lane per row, slices
+ * of whole row groups of one level) and the forward sweep's slice count. */
+int gic_pattern_solve_kernels(const gic_pattern *P, int32_t *warp_specialised, int32_t *level_sliced,
+                              int32_t *slices);
 /* Copies of the analysis (device outputs, any may be NULL): Lrowptr (n+1),
  * Lcol (nnzL), level (n), group start rows (ngroups+1). */
 int gic_pattern_export(gic_handle *h, const gic_pattern *P, int32_t *Lrowptr, int32_t *Lcol,
@@ -309,16 +309,18 @@ int gic_adam_step(gic_handle *h, int64_t np, float *theta, const float *grad, fl
 /* Tuning of the sync-free kernels (IC(0), triangular solves); results agree
  * to round-off across settings: GIC_TUNE_SOLVE_WARPS_PER_SM = cap on resident
  * solve warps (teams of three warps for the warp-specialised solves) per SM
- * (0 = automatic: 4, 8 or 16 teams by chunks per SM); GIC_TUNE_POLL =
+ * (0 = automatic: 4, 8 or 16 teams by chunks per SM; 32 warps for the
+ * level-sliced solves); GIC_TUNE_POLL =
  * polling: low 16 bits = nanoseconds slept between polls, bit 16 set = one
  * polling lane per warp (default 1<<16);
  * GIC_TUNE_PIPELINE = triangular-solve kernels: 4 (default) = automatic
- * (warp-specialised where the pattern admits them, else staged one-warp),
- * 3 = SM-local solves (blocks of 16 neighbouring chunks per CTA,
- * intra-block dependencies in shared memory) where the pattern's block order
- * allows, else 2 = warp-specialised solves on premultiplied row-group blocks
- * (groups of <= 3 rows, <= 61 external columns), else 1 = staged one-warp
- * solves (<= 3 rows, <= 48 columns), else 0 = generic; a lower value caps the
+ * (level-sliced from 48 chunks per SM, else warp-specialised, where the
+ * pattern admits them, else staged one-warp), 3 = level-sliced solves (one
+ * lane per row; slices of whole row groups of one level, premultiplied
+ * blocks) where the pattern admits them, else 2 = warp-specialised solves on
+ * premultiplied row-group blocks (groups of <= 3 rows, <= 61 external
+ * columns), else 1 = staged one-warp solves (<= 3 rows, <= 48 columns),
+ * else 0 = generic; a lower value caps the
  * choice; GIC_TUNE_QDELTA = level
  * window of the dependencies the warp-specialised solves treat as "late"
  * (read by gic_analyze; default 6); GIC_TUNE_GNN_BF16 = 1 (default): the
@@ -344,8 +346,11 @@ int gic_selftest_wait_timeout(gic_handle *h, int64_t polls);
  * arithmetic as gic_spmv, but it needs no handle, no pattern and no
  * workspace, and allocates nothing. Its scratch (partial sums and a
  * counter) is a file-scope device array of about 8 MiB that every GPU
- * loading this library holds until exit; the first call on a device looks up
- * that array's device address, so make it before any stream capture.
+ * loading this library holds until exit. The first call in a CUDA context
+ * (a device's primary context, another driver context, or the primary context
+ * again after cudaDeviceReset) looks up that array's device address in that
+ * context, so make it before any stream capture: a first call whose stream
+ * is being captured returns GIC_ERR_UNSUPPORTED.
  * Calls share the scratch: calls that overlap on the GPU (other streams)
  * race; calls in one stream are ordered. rowptr (n+1), col, val, x, y,
  * xdoty: device memory of the current device; stream: a cudaStream_t

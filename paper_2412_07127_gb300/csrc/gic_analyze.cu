@@ -567,26 +567,6 @@ __global__ void k_qsched(int32_t ngroups, const int32_t *grp, const int32_t *Lro
     }
 }
 
-// every dependency of a group on another chunk block must sit in a block
-// that comes earlier in the sweep's block order
-__global__ void k_check_block_order(int32_t ngroups, const int32_t *grp, const int32_t *Lrowptr, const int32_t *Lcol,
-                                    const int32_t *Urowptr, const int32_t *Ucol, const int32_t *rowchunk, int bw,
-                                    const int32_t *pos_f, const int32_t *pos_b, unsigned *bad)
-{
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t s = grp[g], e = grp[g + 1] - 1;
-        const int32_t b = rowchunk[s] / bw;
-        for (int32_t p = Lrowptr[s]; p < Lrowptr[s + 1] - 1; ++p) {
-            const int32_t bj = rowchunk[Lcol[p]] / bw;
-            if (bj != b && pos_f[bj] >= pos_f[b]) atomicOr(bad, 1u);
-        }
-        for (int32_t q = Urowptr[e] + 1; q < Urowptr[e + 1]; ++q) {
-            const int32_t bj = rowchunk[Ucol[q]] / bw;
-            if (bj != b && pos_b[bj] >= pos_b[b]) atomicOr(bad, 2u);
-        }
-    }
-}
-
 static const int T_ROWS = 256;
 
 static unsigned grid_rows(gic_handle *h, int64_t n)
@@ -653,8 +633,8 @@ static void free_pattern(Pattern &p)
     cudaFree(p.qb_pos);
     cudaFree(p.qf_cnt);
     cudaFree(p.qb_cnt);
-    cudaFree(p.cb_ord_f);
-    cudaFree(p.cb_ord_b);
+    free_ssched(p.sf);
+    free_ssched(p.sb);
     p = Pattern();
 }
 
@@ -831,76 +811,6 @@ static int build_qsched(gic_handle *h, Pattern &P)
     return GIC_OK;
 }
 
-// Block schedule of the SM-local solves (needs the warp-specialised
-// schedule's premultiplied layout).
-static int build_bsched(gic_handle *h, Pattern &P)
-{
-    P.bready = 0;
-    if (!P.qready || P.nchunks == 0) return GIC_OK;
-    const int32_t nc = P.nchunks, ng = P.ngroups, bw = BCHUNKS;
-    const int32_t ncb = (nc + bw - 1) / bw;
-    std::vector<int32_t> hcg(nc + 1), hgrp(ng + 1);
-    int32_t *tmp = nullptr;
-    GIC_CUDA_TRY(cudaMalloc(&tmp, sizeof(int32_t) * (2 * (size_t)ncb + (size_t)P.n + 1)));
-    int32_t *pos = tmp, *rowchunk = pos + 2 * ncb;
-    unsigned *bad = (unsigned *)((char *)h->dev_small + 61000);
-    std::vector<int32_t> of(ncb), ob(ncb), pf(ncb), pb(ncb);
-    int32_t rows_max = 0;
-    unsigned hb = 1;
-    cudaError_t e = cudaMemcpyAsync(hcg.data(), P.chunk_grp, sizeof(int32_t) * (nc + 1), cudaMemcpyDeviceToHost,
-                                    h->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(hgrp.data(), P.grp, sizeof(int32_t) * (ng + 1), cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) goto cuda_fail;
-    // Blocks run in index order forward and in reverse index order backward:
-    // dependencies point to smaller (larger) rows, hence to blocks at or
-    // before the block in that order. (Level order is no valid block order:
-    // a block that straddles two planes of pencils starts early but depends
-    // on the block before it.)
-    for (int32_t b = 0; b < ncb; ++b) {
-        const int32_t c0 = b * bw, c1 = std::min(c0 + bw, nc);
-        rows_max = std::max(rows_max, hgrp[hcg[c1]] - hgrp[hcg[c0]]);
-        of[b] = b;
-        ob[b] = ncb - 1 - b;
-    }
-    for (int32_t k = 0; k < ncb; ++k) {
-        pf[of[k]] = k;
-        pb[ob[k]] = k;
-    }
-    e = cudaMemcpyAsync(pos, pf.data(), sizeof(int32_t) * ncb, cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(pos + ncb, pb.data(), sizeof(int32_t) * ncb, cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, 4, h->stream);
-    if (e != cudaSuccess) goto cuda_fail;
-    ++h->launches;
-    k_row_chunk<<<grid_rows(h, nc), T_ROWS, 0, h->stream>>>(nc, P.chunk_grp, P.grp, rowchunk);
-    ++h->launches;
-    k_check_block_order<<<grid_rows(h, ng), T_ROWS, 0, h->stream>>>(ng, P.grp, P.Lrowptr, P.Lcol, P.Urowptr, P.Ucol,
-                                                                    rowchunk, bw, pos, pos + ncb, bad);
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, bad, 4, cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) goto cuda_fail;
-    // the mirror of a block's rows (FP64 values) must fit in shared memory
-    // beside the warps' staging rings (about 96 KB)
-    if (hb == 0 && (size_t)rows_max * sizeof(double) <= 120 * 1024) {
-        e = cudaMalloc(&P.cb_ord_f, sizeof(int32_t) * ncb);
-        if (e == cudaSuccess) e = cudaMalloc(&P.cb_ord_b, sizeof(int32_t) * ncb);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(P.cb_ord_f, of.data(), sizeof(int32_t) * ncb, cudaMemcpyHostToDevice, h->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(P.cb_ord_b, ob.data(), sizeof(int32_t) * ncb, cudaMemcpyHostToDevice, h->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-        if (e != cudaSuccess) goto cuda_fail;
-        P.ncb = ncb;
-        P.mirror_rows = rows_max;
-        P.bready = 1;
-    }
-    cudaFree(tmp);
-    return GIC_OK;
-cuda_fail:
-    set_last_cuda_error(e, "build_bsched", __FILE__, __LINE__);
-    cudaFree(tmp);
-    return GIC_ERR_CUDA;
-}
 
 static int analyze_impl(gic_handle *h, int64_t n, int64_t nnz, const int32_t *rowptr, const int32_t *col, Pattern &P)
 {
@@ -1005,7 +915,7 @@ static int analyze_impl(gic_handle *h, int64_t n, int64_t nnz, const int32_t *ro
     STEP(build_schedule(h, P, gflag, gid, tmp2_a, tmp2_b));
     STEP(build_sell(h, P));
     STEP(build_qsched(h, P));
-    STEP(build_bsched(h, P));
+    STEP(build_ssched(h, P));
 out:
 #undef STEP
 #undef CUDA_STEP
@@ -1053,13 +963,13 @@ int gic_pattern_info(const gic_pattern *P, int64_t *n, int64_t *nnzA, int64_t *n
     return GIC_OK;
 }
 
-int gic_pattern_solve_kernels(const gic_pattern *P, int32_t *warp_specialised, int32_t *sm_local,
-                              int32_t *mirror_rows)
+int gic_pattern_solve_kernels(const gic_pattern *P, int32_t *warp_specialised, int32_t *level_sliced,
+                              int32_t *slices)
 {
     if (!P) return GIC_ERR_INVALID_ARG;
     if (warp_specialised) *warp_specialised = P->p.qready;
-    if (sm_local) *sm_local = P->p.bready;
-    if (mirror_rows) *mirror_rows = P->p.mirror_rows;
+    if (level_sliced) *level_sliced = P->p.sready;
+    if (slices) *slices = P->p.sf.nsl;
     return GIC_OK;
 }
 

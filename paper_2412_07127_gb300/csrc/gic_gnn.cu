@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(TB) k_edge_bwd(int64_t E, const int32_t *__res
                                                  const float *__restrict__ e0, const float *__restrict__ x,
                                                  const float *__restrict__ theta, int l, const float *__restrict__ de,
                                                  float *__restrict__ dh, float *__restrict__ dec,
-                                                 float *__restrict__ partials)
+                                                 double *__restrict__ partials)
 {
     __shared__ float W1[H * 20], b1[H], W2[H];
     __shared__ float s_dz[TB][H + 1];
@@ -438,9 +438,9 @@ __global__ void __launch_bounds__(TB) k_edge_bwd(int64_t E, const int32_t *__res
     }
     __syncthreads();
     // outputs owned by this thread: o = threadIdx.x + k*TB, k < 6 (705 total)
-    float acc[6];
+    double acc[6]; // across tiles in FP64 (one add per tile and output)
 #pragma unroll
-    for (int k = 0; k < 6; ++k) acc[k] = 0.f;
+    for (int k = 0; k < 6; ++k) acc[k] = 0.0;
     const int64_t ntiles = (E + TB - 1) / TB;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t p = tile * TB + threadIdx.x;
@@ -501,7 +501,7 @@ __global__ void __launch_bounds__(TB) k_edge_bwd(int64_t E, const int32_t *__res
             } else { // db2
                 for (int t = 0; t < TB; ++t) s += s_h[t][20];
             }
-            acc[k] += s;
+            acc[k] += (double)s;
         }
         __syncthreads();
     }
@@ -518,7 +518,7 @@ __global__ void __launch_bounds__(TB) k_node_bwd(int64_t n, const float *__restr
                                                  const float *__restrict__ M, const float *__restrict__ theta, int l,
                                                  const float *__restrict__ dxo, float *__restrict__ dxd,
                                                  float *__restrict__ dS, float *__restrict__ dM,
-                                                 float *__restrict__ partials)
+                                                 double *__restrict__ partials)
 {
     __shared__ float W3[H * 11], b3[H], W4[9 * H];
     __shared__ float s_dz[TB][H + 1];
@@ -530,9 +530,9 @@ __global__ void __launch_bounds__(TB) k_node_bwd(int64_t n, const float *__restr
     for (int t = threadIdx.x; t < 9 * H; t += blockDim.x) W4[t] = P[H * 11 + H + t];
     if (threadIdx.x < H) b3[threadIdx.x] = P[H * 11 + threadIdx.x];
     __syncthreads();
-    float acc[6];
+    double acc[6]; // across tiles in FP64 (one add per tile and output)
 #pragma unroll
-    for (int k = 0; k < 6; ++k) acc[k] = 0.f;
+    for (int k = 0; k < 6; ++k) acc[k] = 0.0;
     const int64_t ntiles = (n + TB - 1) / TB;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t v = tile * TB + threadIdx.x;
@@ -598,7 +598,7 @@ __global__ void __launch_bounds__(TB) k_node_bwd(int64_t n, const float *__restr
                 const int f = o - H * 12 - 9 * H;
                 for (int t = 0; t < TB; ++t) s += s_dx[t][f];
             }
-            acc[k] += s;
+            acc[k] += (double)s;
         }
         __syncthreads();
     }
@@ -718,7 +718,7 @@ __global__ void k_gn_bwd_finish(int pass, int ngraphs, const double *partials, i
 }
 
 // out[k] = sum over blocks b of partials[b][k], in block order
-__global__ void k_reduce_partials(const float *partials, int nblocks, int count, float *out)
+__global__ void k_reduce_partials(const double *partials, int nblocks, int count, float *out)
 {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
         double s = 0.0;
@@ -851,7 +851,7 @@ struct TrainWs {
     double *mu, *sig, *parts, *sdsig;
     float *x[3], *eout[3], *S[2], *M[2];
     float *de, *dec, *dh, *dxa, *dxb, *dxd, *dS, *dM;
-    float *pe, *pn; // weight-gradient partials
+    double *pe, *pn; // weight-gradient partials
     size_t bytes;
 };
 
@@ -878,8 +878,8 @@ static TrainWs carve_train(int64_t n, int64_t E, int ngraphs, int gE, int gN, vo
     o.dxd = (float *)(c + off); off += al(4 * 9 * (size_t)n);
     o.dS = (float *)(c + off); off += al(4 * (size_t)n);
     o.dM = (float *)(c + off); off += al(4 * (size_t)n);
-    o.pe = (float *)(c + off); off += al(4 * (size_t)gE * NP_EDGE);
-    o.pn = (float *)(c + off); off += al(4 * (size_t)gN * NP_NODE);
+    o.pe = (double *)(c + off); off += al(8 * (size_t)gE * NP_EDGE);
+    o.pn = (double *)(c + off); off += al(8 * (size_t)gN * NP_NODE);
     o.bytes = off;
     return o;
 }

@@ -253,6 +253,23 @@ __device__ __forceinline__ T warp_sum(T v)
 
 // ---------------------------------------------------------------- pattern
 // Analysis of one symmetric CSR pattern (device arrays, library owned).
+// One sweep's level-sliced schedule: per slice its width w (column steps),
+// the early part's width we (steps [0, we): early columns; [we, w): late and
+// previous-group ones, each part front-padded per group), its group count
+// ng, the offset of its first step in the coefficient arrays (kv, in steps
+// of 32 values) and in the column array (kc); per slice 32 lane descriptors
+// (row or -1, slot | t << 8 | G << 16 | ne << 24: the group's slot in the
+// slice, the row's index in its group, the group's size, its early column
+// count); the columns of slot i at step k at col[kc + k ng + i] (-1: padding).
+struct SliceSched {
+    int32_t nsl = 0;
+    int64_t steps = 0, ncol = 0;
+    int32_t *w = nullptr, *we = nullptr, *ng = nullptr;
+    int64_t *kv = nullptr, *kc = nullptr;
+    int2 *lane = nullptr;
+    int32_t *col = nullptr;
+};
+
 struct Pattern {
     int64_t n = 0, nnzA = 0, nnzL = 0;
     int32_t ngroups = 0, nlevels = 0;
@@ -297,18 +314,15 @@ struct Pattern {
     int32_t *qf_col = nullptr, *qb_col = nullptr;
     uint8_t *qf_pos = nullptr, *qb_pos = nullptr;
     int32_t *qf_cnt = nullptr, *qb_cnt = nullptr;
-    // Block schedule of the SM-local solves: chunk blocks = runs of BCHUNKS
-    // consecutive chunks (one CTA each, one warp per chunk, a shared-memory
-    // mirror of the block's rows), in index order (forward) and reverse
-    // index order (backward); every dependency on another chunk block points
-    // to an earlier one in that order (checked).
-    int bready = 0;
-    int32_t ncb = 0, mirror_rows = 0;
-    int32_t *cb_ord_f = nullptr, *cb_ord_b = nullptr;
+    // Level-sliced schedule (one lane per row, gic_ssolve.cu), per sweep:
+    // the groups sorted by level (forward: first row's, ascending; backward:
+    // last row's, descending), then by external column count and index, cut
+    // into slices of whole groups with at most 32 rows that never span two
+    // levels. Needs the warp-specialised schedule (its column orders).
+    int sready = 0;
+    SliceSched sf, sb;
     int device = 0;
 };
-
-constexpr int BCHUNKS = 16; // chunks (warps) per block of the SM-local solves
 
 constexpr int QCOL = 64;   // external columns of a group in the warp-specialised solves
 constexpr int QLATE = 16;  // at most this many late columns per group
@@ -316,6 +330,12 @@ constexpr int QLATE = 16;  // at most this many late columns per group
 constexpr int GMAX = 8;    // rows per group
 constexpr int MAXDIM = 48; // max lower entries of a row handled by IC(0)
 
+}  // namespace gic
+
+namespace gic {
+// level-sliced schedule of a pattern (gic_ssolve.cu)
+int build_ssched(gic_handle *h, Pattern &P);
+void free_ssched(SliceSched &S);
 }  // namespace gic
 
 struct gic_pattern {

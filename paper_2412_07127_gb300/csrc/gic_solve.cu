@@ -21,6 +21,10 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <mutex>
+
+#include <cuda.h>
+
 #include "gic_internal.cuh"
 #include "gic_solve.cuh"
 
@@ -1130,14 +1134,16 @@ static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 // and sums in FP32 too.
 // SM-local (gic_bsolve.cu) on the same blocks where the pattern's chunk
 // blocks allow it.
-enum SolveMode { MODE_GEN64, MODE_GEN32, MODE_P64, MODE_P32, MODE_Q64, MODE_Q32, MODE_B64, MODE_B32, MODE_IDENT };
+enum SolveMode { MODE_GEN64, MODE_GEN32, MODE_P64, MODE_P32, MODE_Q64, MODE_Q32, MODE_S64, MODE_S32, MODE_IDENT };
 
-static bool f32_vectors(SolveMode m) { return m == MODE_P32 || m == MODE_Q32 || m == MODE_B32; }
-static bool premultiplied(SolveMode m) { return m == MODE_Q64 || m == MODE_Q32 || m == MODE_B64 || m == MODE_B32; }
+static bool f32_vectors(SolveMode m) { return m == MODE_P32 || m == MODE_Q32 || m == MODE_S32; }
+static bool premultiplied(SolveMode m) { return m == MODE_Q64 || m == MODE_Q32; }
+static bool sliced(SolveMode m) { return m == MODE_S64 || m == MODE_S32; }
 
 struct SolveWs {
-    void *Uval;                   // U values (generic, pipelined) or backward blocks (warp-specialised)
-    void *Qf;                     // forward premultiplied blocks (warp-specialised)
+    void *Uval;                   // U values (generic, pipelined), backward blocks (warp-specialised) or
+                                  // backward slice coefficients (level-sliced)
+    void *Qf;                     // forward premultiplied blocks or forward slice coefficients
     double *invd;                 // generic modes and P64
     float *invd32, *r32, *y32, *z32; // P32
     double *r, *y, *z, *p, *w;
@@ -1156,12 +1162,13 @@ static SolveMode solve_mode(const gic_handle *h, const Pattern &P, int l_dtype)
 {
     if (l_dtype == GIC_IDENTITY) return MODE_IDENT;
     // automatic choice (measured on the hex systems from 40^3 to 148^3): the
-    // warp-specialised kernels (two warps per chunk, most arithmetic off the
-    // dependency chain) where the pattern admits them, else the staged
-    // one-warp kernels
+    // level-sliced kernels (one lane per row) where many independent groups
+    // are ready at once, i.e. many chunks per SM; else the warp-specialised
+    // kernels (three warps per chunk, most arithmetic off the dependency
+    // chain) where the pattern admits them, else the staged one-warp kernels
     int pipeline = h->tune_pipeline;
-    if (pipeline >= 4) pipeline = 2;
-    if (pipeline >= 3 && P.bready) return (l_dtype == GIC_F32) ? MODE_B32 : MODE_B64;
+    if (pipeline >= 4) pipeline = (P.nchunks >= (int64_t)SLICED_CHUNKS_PER_SM * h->num_sms) ? 3 : 2;
+    if (pipeline >= 3 && P.sready) return (l_dtype == GIC_F32) ? MODE_S32 : MODE_S64;
     if (pipeline >= 2 && P.qready) return (l_dtype == GIC_F32) ? MODE_Q32 : MODE_Q64;
     const bool pipe = pipeline && pipelined_fits(P);
     if (l_dtype == GIC_F32) return pipe ? MODE_P32 : MODE_GEN32;
@@ -1171,20 +1178,23 @@ static SolveMode solve_mode(const gic_handle *h, const Pattern &P, int l_dtype)
 // Workspace layout for a PCG whose SpMV runs on pattern PA and whose solves
 // run on the factor pattern PL (the same object unless the factor's pattern
 // was thinned, e.g. by fill-in dropout).
-static SolveWs carve(const Pattern &PA, const Pattern &PL, int l_dtype, bool p32, void *ws)
+static SolveWs carve(const Pattern &PA, const Pattern &PL, int l_dtype, SolveMode mode, void *ws)
 {
     Pattern P;
     P.n = PA.n;
     P.nnzL = PL.nnzL;
     P.sell_nnz = PA.sell_nnz;
+    const bool p32 = f32_vectors(mode);
     SolveWs o = {};
     char *c = (char *)ws;
     size_t off = 0;
     size_t es = (l_dtype == GIC_F32) ? 4 : 8;
+    const size_t fb = sliced(mode) ? s_values_bytes(PL.sf, es) : es * (size_t)P.nnzL;
+    const size_t bb = sliced(mode) ? s_values_bytes(PL.sb, es) : es * (size_t)P.nnzL;
     o.sc = (Scalars *)(c + off); off += align_up(sizeof(Scalars));
     o.partials = (double *)(c + off); off += align_up(sizeof(double) * 2 * MAX_PARTIALS);
-    o.Uval = c + off; off += (l_dtype == GIC_IDENTITY) ? 0 : align_up(es * (size_t)P.nnzL);
-    o.Qf = c + off; off += (l_dtype == GIC_IDENTITY) ? 0 : align_up(es * (size_t)P.nnzL);
+    o.Uval = c + off; off += (l_dtype == GIC_IDENTITY) ? 0 : align_up(bb);
+    o.Qf = c + off; off += (l_dtype == GIC_IDENTITY) ? 0 : align_up(fb);
     o.invd = (double *)(c + off); off += (l_dtype == GIC_IDENTITY) ? 0 : align_up(8 * (size_t)P.n);
     if (p32) {
         float **fv[4] = {&o.invd32, &o.r32, &o.y32, &o.z32};
@@ -1197,13 +1207,19 @@ static SolveWs carve(const Pattern &PA, const Pattern &PL, int l_dtype, bool p32
     return o;
 }
 
+// Workspace bound for a PCG on a pattern not analysed yet (the end-to-end
+// call): the warp-specialised layout plus room for the level-sliced one on
+// patterns like the hex systems' (one slice per 10 groups of 3 rows, a few
+// padded steps); a pattern that needs more runs the warp-specialised solves.
 size_t pcg_ws_bytes(int64_t n, int64_t nnzL, int64_t sell_nnz, int l_dtype)
 {
     Pattern P;
     P.n = n;
     P.nnzL = nnzL;
     P.sell_nnz = sell_nnz;
-    return carve(P, P, l_dtype, l_dtype == GIC_F32, nullptr).bytes;
+    const size_t es = (l_dtype == GIC_F32) ? 4 : 8;
+    const SolveMode m = (l_dtype == GIC_F32) ? MODE_Q32 : MODE_Q64;
+    return carve(P, P, l_dtype, m, nullptr).bytes + 2 * es * (size_t)(nnzL / 8 + 8 * n) + 4096;
 }
 
 static unsigned vec_grid(gic_handle *h, int64_t n, int block)
@@ -1352,6 +1368,7 @@ static int launch_ltsolve_p(gic_handle *h, const Pattern &P, const T *Uval, cons
 static int setup_factor(gic_handle *h, const Pattern &P, SolveMode mode, const void *Lval, const SolveWs &W)
 {
     if (premultiplied(mode)) return q_setup(h, P, f32_vectors(mode), Lval, W.Qf, W.Uval);
+    if (sliced(mode)) return s_setup(h, P, f32_vectors(mode), Lval, W.Qf, W.Uval);
     int64_t cnt = P.nnzL > P.n ? P.nnzL : P.n;
     unsigned gr = vec_grid(h, cnt, 256);
     ++h->launches;
@@ -1428,8 +1445,8 @@ static int precondition(gic_handle *h, const Pattern &P, SolveMode mode, const v
     case MODE_P32: GIC_TRY(launch_lsolve_p<float>(h, P, (const float *)Lval, W.invd32, W.r32, W.y32, W.sc)); break;
     case MODE_Q64: GIC_TRY(q_lsolve(h, P, false, W.Qf, W.r, W.y, W.sc)); break;
     case MODE_Q32: GIC_TRY(q_lsolve(h, P, true, W.Qf, W.r32, W.y32, W.sc)); break;
-    case MODE_B64: GIC_TRY(b_lsolve(h, P, false, W.Qf, W.r, W.y, W.sc)); break;
-    case MODE_B32: GIC_TRY(b_lsolve(h, P, true, W.Qf, W.r32, W.y32, W.sc)); break;
+    case MODE_S64: GIC_TRY(s_lsolve(h, P, false, W.Qf, W.r, W.y, W.sc)); break;
+    case MODE_S32: GIC_TRY(s_lsolve(h, P, true, W.Qf, W.r32, W.y32, W.sc)); break;
     default: break;
     }
     PROF_END(GIC_PROF_LSOLVE);
@@ -1450,8 +1467,8 @@ static int precondition(gic_handle *h, const Pattern &P, SolveMode mode, const v
         break;
     case MODE_Q64: GIC_TRY(q_ltsolve(h, P, false, true, W.Uval, W.y, W.z, W.r, W.partials, W.sc)); break;
     case MODE_Q32: GIC_TRY(q_ltsolve(h, P, true, true, W.Uval, W.y32, W.z32, W.r, W.partials, W.sc)); break;
-    case MODE_B64: GIC_TRY(b_ltsolve(h, P, false, true, W.Uval, W.y, W.z, W.r, W.partials, W.sc)); break;
-    case MODE_B32: GIC_TRY(b_ltsolve(h, P, true, true, W.Uval, W.y32, W.z32, W.r, W.partials, W.sc)); break;
+    case MODE_S64: GIC_TRY(s_ltsolve(h, P, false, true, W.Uval, W.y, W.z, W.r, W.partials, W.sc)); break;
+    case MODE_S32: GIC_TRY(s_ltsolve(h, P, true, true, W.Uval, W.y32, W.z32, W.r, W.partials, W.sc)); break;
     default: break;
     }
     PROF_END(GIC_PROF_LTSOLVE);
@@ -1577,7 +1594,7 @@ static int standalone_solve(gic_handle *h, const Pattern &p, const void *valL, i
                             double *out, void *ws, size_t ws_bytes, bool forward)
 {
     const SolveMode mode = solve_mode(h, p, l_dtype);
-    SolveWs W = carve(p, p, l_dtype, f32_vectors(mode), ws);
+    SolveWs W = carve(p, p, l_dtype, mode, ws);
     if (ws_bytes < W.bytes) return GIC_ERR_WORKSPACE;
     const unsigned vg = vec_grid(h, p.n, 256);
     GIC_TRY(setup_factor(h, p, mode, valL, W));
@@ -1600,8 +1617,8 @@ static int standalone_solve(gic_handle *h, const Pattern &p, const void *valL, i
         case MODE_P32: GIC_TRY(launch_lsolve_p<float>(h, p, (const float *)valL, W.invd32, W.r32, W.y32, nullptr)); break;
         case MODE_Q64: GIC_TRY(q_lsolve(h, p, false, W.Qf, in, out, nullptr)); break;
         case MODE_Q32: GIC_TRY(q_lsolve(h, p, true, W.Qf, W.r32, W.y32, nullptr)); break;
-        case MODE_B64: GIC_TRY(b_lsolve(h, p, false, W.Qf, in, out, nullptr)); break;
-        case MODE_B32: GIC_TRY(b_lsolve(h, p, true, W.Qf, W.r32, W.y32, nullptr)); break;
+        case MODE_S64: GIC_TRY(s_lsolve(h, p, false, W.Qf, in, out, nullptr)); break;
+        case MODE_S32: GIC_TRY(s_lsolve(h, p, true, W.Qf, W.r32, W.y32, nullptr)); break;
         default: break;
         }
         PROF_END(GIC_PROF_LSOLVE);
@@ -1624,8 +1641,8 @@ static int standalone_solve(gic_handle *h, const Pattern &p, const void *valL, i
             break;
         case MODE_Q64: GIC_TRY(q_ltsolve(h, p, false, false, W.Uval, yy, out, nullptr, nullptr, nullptr)); break;
         case MODE_Q32: GIC_TRY(q_ltsolve(h, p, true, false, W.Uval, W.r32, W.y32, nullptr, nullptr, nullptr)); break;
-        case MODE_B64: GIC_TRY(b_ltsolve(h, p, false, false, W.Uval, yy, out, nullptr, nullptr, nullptr)); break;
-        case MODE_B32: GIC_TRY(b_ltsolve(h, p, true, false, W.Uval, W.r32, W.y32, nullptr, nullptr, nullptr)); break;
+        case MODE_S64: GIC_TRY(s_ltsolve(h, p, false, false, W.Uval, yy, out, nullptr, nullptr, nullptr)); break;
+        case MODE_S32: GIC_TRY(s_ltsolve(h, p, true, false, W.Uval, W.r32, W.y32, nullptr, nullptr, nullptr)); break;
         default: break;
         }
         PROF_END(GIC_PROF_LTSOLVE);
@@ -1656,7 +1673,7 @@ int gic_workspace_size(gic_handle *h, const gic_pattern *P, int op, int l_dtype,
     GIC_TRY(check_pattern(h, P));
     if (!bytes || (l_dtype != GIC_F64 && l_dtype != GIC_F32 && l_dtype != GIC_IDENTITY)) return GIC_ERR_INVALID_ARG;
     if (op != GIC_WS_SOLVE && op != GIC_WS_PCG) return GIC_ERR_INVALID_ARG;
-    *bytes = carve(P->p, P->p, l_dtype, l_dtype == GIC_F32, nullptr).bytes;
+    *bytes = carve(P->p, P->p, l_dtype, solve_mode(h, P->p, l_dtype), nullptr).bytes;
     return GIC_OK;
 }
 
@@ -1723,7 +1740,7 @@ int gic_workspace_size_split(gic_handle *h, const gic_pattern *PA, const gic_pat
     GIC_TRY(check_pattern(h, PL));
     if (!bytes || (l_dtype != GIC_F64 && l_dtype != GIC_F32 && l_dtype != GIC_IDENTITY)) return GIC_ERR_INVALID_ARG;
     if (PA->p.n != PL->p.n) return GIC_ERR_INVALID_ARG;
-    *bytes = carve(PA->p, PL->p, l_dtype, l_dtype == GIC_F32, nullptr).bytes;
+    *bytes = carve(PA->p, PL->p, l_dtype, solve_mode(h, PL->p, l_dtype), nullptr).bytes;
     return GIC_OK;
 }
 
@@ -1738,8 +1755,12 @@ int gic_pcg_split(gic_handle *h, const gic_pattern *PA, const double *valA, cons
     if (l_dtype != GIC_F64 && l_dtype != GIC_F32 && l_dtype != GIC_IDENTITY) return GIC_ERR_INVALID_ARG;
     const Pattern &p = PA->p, &pl = PL->p;
     if (p.n != pl.n) return GIC_ERR_INVALID_ARG;
-    const SolveMode mode = solve_mode(h, pl, l_dtype);
-    SolveWs W = carve(p, pl, l_dtype, l_dtype == GIC_F32, ws);
+    SolveMode mode = solve_mode(h, pl, l_dtype);
+    SolveWs W = carve(p, pl, l_dtype, mode, ws);
+    if (ws_bytes < W.bytes && sliced(mode)) { // a workspace sized before the analysis
+        mode = (l_dtype == GIC_F32) ? MODE_Q32 : MODE_Q64;
+        W = carve(p, pl, l_dtype, mode, ws);
+    }
     if (ws_bytes < W.bytes) return GIC_ERR_WORKSPACE;
     if (p.ngroups > 0 && (spmv_grid(h, p.nslices) > MAX_PARTIALS || vec_grid(h, p.n, VEC_BLOCK) > MAX_PARTIALS))
         return GIC_ERR_UNSUPPORTED;
@@ -1815,8 +1836,9 @@ int gic_launch_count(gic_handle *h, int64_t *count)
 // library holds until the process exits (about 8 MiB).
 namespace gic {
 
-constexpr int64_t NOALLOC_SLOTS = 1 << 20;               // one partial per block of 8 rows
-constexpr int64_t NOALLOC_MAX_ROWS = 8 * NOALLOC_SLOTS;   // 8,388,608 rows
+// one partial per block; the launch uses at most min(8 per SM, this many)
+constexpr int64_t NOALLOC_SLOTS = 1 << 20;
+constexpr int64_t NOALLOC_MAX_ROWS = 8 * NOALLOC_SLOTS; // the stated row limit: 8,388,608 rows
 
 struct NoallocScratch {
     Scalars sc; // only its last-block counter is used; zeroed by every call
@@ -1824,24 +1846,80 @@ struct NoallocScratch {
 };
 static __device__ __align__(256) NoallocScratch g_noalloc_scratch;
 
-// Device address of the scratch, looked up once per device with that device
-// current. (In host code the symbol only names a host-side stand-in; a kernel
-// given it would fault or read the wrong memory.)
-static NoallocScratch *g_noalloc_addr[64];
+// Device address of the scratch in the calling thread's current context. In
+// host code the symbol only names a host-side stand-in; a kernel given it
+// would fault or read the wrong memory. The address belongs to one context
+// (a device's primary context, another driver context on the same device,
+// or the primary context again after cudaDeviceReset each load their own
+// copy of the module), so it is cached per context ID, which the driver never
+// reuses within a process; the cache is filled under a mutex.
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext *);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long *);
 
-static int noalloc_address(int device, NoallocScratch **out)
+struct NoallocCacheEntry {
+    unsigned long long ctx_id;
+    NoallocScratch *addr;
+};
+constexpr int NOALLOC_CACHE = 16;
+static std::mutex g_noalloc_mu;
+static NoallocCacheEntry g_noalloc_cache[NOALLOC_CACHE];
+static int g_noalloc_next = 0;
+static PfnCtxGetCurrent g_ctx_get_current = nullptr;
+static PfnCtxGetId g_ctx_get_id = nullptr;
+static bool g_noalloc_pfn_ok = false, g_noalloc_pfn_tried = false;
+
+// current context's ID; 0 if no context is current
+static int noalloc_ctx_id(unsigned long long *id)
 {
-    if (device < 0 || device >= 64) return GIC_ERR_UNSUPPORTED;
-    if (!g_noalloc_addr[device]) {
-        void *ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess) {
-            set_last_cuda_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
-            return GIC_ERR_CUDA;
+    *id = 0;
+    CUcontext ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS) return GIC_ERR_CUDA;
+    if (!ctx) return GIC_OK;
+    if (g_ctx_get_id(ctx, id) != CUDA_SUCCESS) return GIC_ERR_CUDA;
+    return GIC_OK;
+}
+
+static int noalloc_address(cudaStream_t s, NoallocScratch **out)
+{
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_pfn_tried) {
+        g_noalloc_pfn_tried = true;
+        cudaDriverEntryPointQueryResult q1, q2;
+        void *f1 = nullptr, *f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess && f1 && f2) {
+            g_ctx_get_current = (PfnCtxGetCurrent)f1;
+            g_ctx_get_id = (PfnCtxGetId)f2;
+            g_noalloc_pfn_ok = true;
         }
-        g_noalloc_addr[device] = (NoallocScratch *)ptr;
     }
-    *out = g_noalloc_addr[device];
+    if (!g_noalloc_pfn_ok) return GIC_ERR_UNSUPPORTED;
+    unsigned long long id = 0;
+    GIC_TRY(noalloc_ctx_id(&id));
+    if (id != 0) {
+        for (int k = 0; k < NOALLOC_CACHE; ++k)
+            if (g_noalloc_cache[k].ctx_id == id) {
+                *out = g_noalloc_cache[k].addr;
+                return GIC_OK;
+            }
+    }
+    // first call in this context: the look-up is not made while the stream
+    // is being captured
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    GIC_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return GIC_ERR_UNSUPPORTED;
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
+        return GIC_ERR_CUDA;
+    }
+    if (id == 0) GIC_TRY(noalloc_ctx_id(&id)); // the runtime made its context current just now
+    if (id == 0) return GIC_ERR_CUDA;
+    g_noalloc_cache[g_noalloc_next] = {id, (NoallocScratch *)ptr};
+    g_noalloc_next = (g_noalloc_next + 1) % NOALLOC_CACHE;
+    *out = (NoallocScratch *)ptr;
     return GIC_OK;
 }
 
@@ -1852,14 +1930,21 @@ extern "C" int gic_spmv_dot_noalloc(int64_t n, const int32_t *rowptr, const int3
 {
     if (n < 1 || !rowptr || !col || !val || !x || !y || !xdoty) return GIC_ERR_INVALID_ARG;
     if (n > gic::NOALLOC_MAX_ROWS) return GIC_ERR_TOO_LARGE;
-    int device = 0;
-    GIC_CUDA_TRY(cudaGetDevice(&device));
-    gic::NoallocScratch *scr = nullptr;
-    GIC_TRY(gic::noalloc_address(device, &scr));
     cudaStream_t s = (cudaStream_t)stream;
+    gic::NoallocScratch *scr = nullptr;
+    GIC_TRY(gic::noalloc_address(s, &scr));
+    int device = 0, sms = 0;
+    GIC_CUDA_TRY(cudaGetDevice(&device));
+    GIC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
     // the reduction counter must start at zero, whatever an earlier call left
     GIC_CUDA_TRY(cudaMemsetAsync(&scr->sc, 0, sizeof(gic::Scalars), s));
-    const int64_t blocks = (n + 7) / 8; // 8 warps per block, one row per warp
+    // 8 warps per block, one row per warp per pass; the grid strides over the
+    // rows, so it is capped at 8 blocks per SM (that also keeps the last
+    // block's sum over the per-block partials short)
+    int64_t blocks = (n + 7) / 8;
+    const int64_t cap = 8 * (int64_t)(sms > 0 ? sms : 1);
+    if (blocks > cap) blocks = cap;
+    if (blocks > gic::NOALLOC_SLOTS) blocks = gic::NOALLOC_SLOTS;
     gic::k_spmv<0><<<(unsigned)blocks, gic::SPMV_BLOCK, 0, s>>>(n, rowptr, col, val, x, y, nullptr, scr->partials,
                                                                 xdoty, &scr->sc);
     GIC_CUDA_TRY(cudaGetLastError());

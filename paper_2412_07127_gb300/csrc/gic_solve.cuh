@@ -73,9 +73,16 @@ int q_lsolve(gic_handle *h, const Pattern &P, bool f32, const void *Kf, const vo
 int q_ltsolve(gic_handle *h, const Pattern &P, bool f32, bool pcg, const void *Kb, void *y, void *z,
               const double *rd, double *partials, Scalars *sc);
 
-// SM-local solves (gic_bsolve.cu) on the same premultiplied blocks.
-int b_lsolve(gic_handle *h, const Pattern &P, bool f32, const void *Kf, const void *r, void *y, const Scalars *sc);
-int b_ltsolve(gic_handle *h, const Pattern &P, bool f32, bool pcg, const void *Kb, void *y, void *z,
+// Level-sliced solves (gic_ssolve.cu): s_setup writes a factor's
+// coefficients in the slice layout into Sf (forward) and Sb (backward),
+// s_values_bytes(sched, element size) bytes each.
+size_t s_values_bytes(const SliceSched &S, size_t es);
+int s_setup(gic_handle *h, const Pattern &P, bool f32, const void *Lval, void *Sf, void *Sb);
+int s_lsolve(gic_handle *h, const Pattern &P, bool f32, const void *Sf, const void *r, void *y, const Scalars *sc);
+int s_ltsolve(gic_handle *h, const Pattern &P, bool f32, bool pcg, const void *Sb, void *y, void *z,
               const double *rd, double *partials, Scalars *sc);
+
+// automatic solve choice: level-sliced kernels from this many chunks per SM
+constexpr int SLICED_CHUNKS_PER_SM = 48;
 
 }  // namespace gic

@@ -191,7 +191,7 @@ class Pattern:
         self.nchunks, self.chunked, self.sell_nnz = nc.value, ch.value, sn.value
         q, b, mr = _i32(), _i32(), _i32()
         _call("gic_pattern_solve_kernels", p, C.byref(q), C.byref(b), C.byref(mr))
-        self.warp_specialised, self.sm_local, self.mirror_rows = q.value, b.value, mr.value
+        self.warp_specialised, self.level_sliced, self.slices = q.value, b.value, mr.value
 
     def export(self, h: Handle):
         dev = self.rowptr.device

@@ -55,7 +55,7 @@ def test_full_size_solver_properties(G, N):
     assert c.numel() == nnz == 9 * (3 * N + 1) ** 2 * (3 * N - 2)
     P = G.Pattern(h, rp, c)
     assert P.nnzL == nnzL and P.nlevels == nlev == 21 * N - 9
-    assert P.sm_local == 1 or P.warp_specialised == 1
+    assert P.level_sliced == 1 and P.warp_specialised == 1
     Lr, Lc, lev, _ = P.export(h)
     assert np.array_equal(lev.cpu().numpy(), _levels_closed_form(N))
 

@@ -100,7 +100,7 @@ def test_analysis_fem(G, h, N):
     if N >= 2:  # then every group is the 3 dofs of one node
         assert P.ngroups == A.n // 3 and np.array_equal(grp, np.arange(0, A.n + 1, 3))
         # the hex systems admit the fastest solve kernels (so the tests run them)
-        assert P.warp_specialised == 1 and P.sm_local == 1
+        assert P.warp_specialised == 1 and P.level_sliced == 1 and P.slices > 0
 
 
 def _expected_groups(A):
@@ -238,7 +238,7 @@ def test_spmv_matches_oracle(G, h):
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("case", ["fem8", "fem5", "random", "tridiag"])
 def test_triangular_solves_match_oracle(G, h, dtype, case, pipeline):
-    """Every solve path (SM-local, warp-specialised and pipelined where the
+    """Every solve path (level-sliced, warp-specialised and pipelined where the
     pattern allows, generic) against the oracle on the same factor."""
     G.set_tuning(h, G.GIC_TUNE_PIPELINE, pipeline)
     if case == "fem8":
@@ -294,8 +294,10 @@ def test_solve_late_window_variants(G, h, qdelta, pipeline):
 
 
 # ---------------------------------------------------------------- A7 PCG
+@pytest.mark.parametrize("pipeline", [4, 3])
 @pytest.mark.parametrize("N", [2, 4, 8, 12])
-def test_pcg_matches_oracle(G, h, N):
+def test_pcg_matches_oracle(G, h, N, pipeline):
+    G.set_tuning(h, G.GIC_TUNE_PIPELINE, pipeline)
     E = I.material_field(N, 7)
     A = O.fem_hex_assemble(N, E)
     b = I.rhs(A.n, 7)
@@ -303,6 +305,7 @@ def test_pcg_matches_oracle(G, h, N):
     P = G.Pattern(h, rp, c)
     Lg, bad = G.ic0(h, P, v)
     res = G.pcg(h, P, v, Lg, _dev(b), rtol=1e-8)
+    G.set_tuning(h, G.GIC_TUNE_PIPELINE, 4)
     Lo, _ = O.ic0(A)
     ro = O.pcg(A, b, Lo, tol=1e-8)
     assert res["status"] == 0 and ro["status"] == 0
