@@ -107,6 +107,12 @@ int gic_pattern_info(const gic_pattern *P, int64_t *n, int64_t *nnzA, int64_t *n
  * start a run before one it reads (as thinning a factor can make) -- and the
  * padded entry count of the SELL-32 copy of A used by the PCG SpMV. */
 int gic_pattern_schedule(const gic_pattern *P, int32_t *nchunks, int32_t *chunked, int64_t *sell_nnz);
+/* SpMV layout the PCG uses for this pattern (host outputs, any may be NULL):
+ * node_blocks = 1 if A is made of 3x3 node blocks (runs of 3 rows from a
+ * multiple of 3 with identical columns in aligned triples: the hex systems),
+ * which then run the block SpMV, else 0 (SELL-32 CSR); entries = values in
+ * that layout, padding included. */
+int gic_pattern_spmv_layout(const gic_pattern *P, int32_t *node_blocks, int64_t *entries);
 /* Which triangular-solve kernels the pattern admits (host outputs, any may be
  * NULL): warp-specialised (1/0), level-sliced (1/0; one lane per row, slices
  * of whole row groups of one level) and the forward sweep's slice count. */

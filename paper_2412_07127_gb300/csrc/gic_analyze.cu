@@ -635,6 +635,7 @@ static void free_pattern(Pattern &p)
     cudaFree(p.qb_cnt);
     free_ssched(p.sf);
     free_ssched(p.sb);
+    free_bsr(p);
     p = Pattern();
 }
 
@@ -914,6 +915,7 @@ static int analyze_impl(gic_handle *h, int64_t n, int64_t nnz, const int32_t *ro
     if (flags & ERR_TIMEOUT) { rc = GIC_ERR_TIMEOUT; goto out; }
     STEP(build_schedule(h, P, gflag, gid, tmp2_a, tmp2_b));
     STEP(build_sell(h, P));
+    STEP(build_bsr(h, P));
     STEP(build_qsched(h, P));
     STEP(build_ssched(h, P));
 out:

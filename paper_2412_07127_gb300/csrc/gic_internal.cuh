@@ -301,6 +301,13 @@ struct Pattern {
     int64_t *sell_ptr = nullptr;      // nslices+1 entry offsets
     int32_t *sell_w = nullptr;        // nslices widths
     int32_t *sell_col = nullptr;      // sell_nnz column indices
+    // 3x3 node-block copy of A's pattern for the PCG SpMV (gic_bsr.cu), where
+    // A is made of them: slices of 32 nodes, bsr_ptr[s] = first block step
+    // of slice s, bsr_w[s] = its width, bsr_col = node column per (step, lane)
+    int bsr_ready = 0;
+    int64_t bsr_nsl = 0, bsr_steps = 0;
+    int64_t *bsr_ptr = nullptr;
+    int32_t *bsr_w = nullptr, *bsr_col = nullptr;
     // Schedule of the warp-specialised solves (groups of <= 3 rows with at
     // most QCOL - 3 external columns): every group's external columns in the
     // order [early | late | prev] -- prev: rows of the group solved just
@@ -336,6 +343,9 @@ namespace gic {
 // level-sliced schedule of a pattern (gic_ssolve.cu)
 int build_ssched(gic_handle *h, Pattern &P);
 void free_ssched(SliceSched &S);
+// 3x3 node-block SpMV layout of a pattern (gic_bsr.cu)
+int build_bsr(gic_handle *h, Pattern &P);
+void free_bsr(Pattern &P);
 }  // namespace gic
 
 struct gic_pattern {

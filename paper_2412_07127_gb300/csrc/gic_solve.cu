@@ -33,30 +33,6 @@ namespace gic {
 constexpr int SPMV_BLOCK = 256;
 constexpr int VEC_BLOCK = 256;
 
-// ------------------------------------------------------------ helpers
-__device__ __forceinline__ double block_sum(double v, double *sh)
-{
-    v = warp_sum(v);
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sh[k];
-    __syncthreads();
-    return s; // valid in thread 0
-}
-
-// Called by thread 0 of every block after writing partials[blockIdx.x]
-// (count = gridDim.x). Returns true in the one block that arrives last.
-__device__ __forceinline__ bool last_block(unsigned *counter, unsigned count)
-{
-    __threadfence();
-    unsigned t = atomicAdd(counter, 1u);
-    return t == count - 1;
-}
-
-
 // ------------------------------------------------------------ SpTRSV
 // Schedule: the pattern's chunks (runs of consecutive row groups with
 // increasing levels; for hex elasticity the x-pencils) are dealt round-robin
@@ -1200,7 +1176,7 @@ static SolveWs carve(const Pattern &PA, const Pattern &PL, int l_dtype, SolveMod
         float **fv[4] = {&o.invd32, &o.r32, &o.y32, &o.z32};
         for (int k = 0; k < 4; ++k) { *fv[k] = (float *)(c + off); off += align_up(4 * (size_t)P.n); }
     }
-    o.sval = (double *)(c + off); off += align_up(8 * (size_t)P.sell_nnz);
+    o.sval = (double *)(c + off); off += align_up(8 * (size_t)(PA.bsr_ready ? 288 * PA.bsr_steps : P.sell_nnz));
     double **vecs[5] = {&o.r, &o.y, &o.z, &o.p, &o.w};
     for (int k = 0; k < 5; ++k) { *vecs[k] = (double *)(c + off); off += align_up(8 * (size_t)P.n); }
     o.bytes = off;
@@ -1502,10 +1478,14 @@ static int pcg_iteration(gic_handle *h, const Pattern &P, const Pattern &PL, Sol
         PROF_END(GIC_PROF_VECTOR);
     }
     PROF_BEGIN(GIC_PROF_SPMV);
-    ++h->launches;
-    k_spmv_sell<1><<<spmv_grid(h, P.nslices), SPMV_BLOCK, 0, h->stream>>>(
-        n, P.nslices, P.sell_ptr, P.sell_w, P.sell_col, W.sval, W.p, W.w, nullptr, W.partials, W.sc);
-    GIC_CUDA_TRY(cudaGetLastError());
+    if (P.bsr_ready) {
+        GIC_TRY(bsr_spmv(h, P, 1, W.sval, W.p, W.w, nullptr, W.partials, W.sc));
+    } else {
+        ++h->launches;
+        k_spmv_sell<1><<<spmv_grid(h, P.nslices), SPMV_BLOCK, 0, h->stream>>>(
+            n, P.nslices, P.sell_ptr, P.sell_w, P.sell_col, W.sval, W.p, W.w, nullptr, W.partials, W.sc);
+        GIC_CUDA_TRY(cudaGetLastError());
+    }
     PROF_END(GIC_PROF_SPMV);
     PROF_BEGIN(GIC_PROF_VECTOR);
     ++h->launches;
@@ -1531,14 +1511,22 @@ static int pcg_run(gic_handle *h, const Pattern &P, const Pattern &PL, SolveMode
         if (f32_vectors(mode)) k_fill_sentinel_t<float><<<vg, 256, 0, h->stream>>>(n, W.y32, W.z32);
         else k_fill_sentinel_t<double><<<vg, 256, 0, h->stream>>>(n, W.y, W.z);
     }
-    ++h->launches;
-    k_sell_vals<<<vec_grid(h, P.nslices * 32, 256), 256, 0, h->stream>>>(n, P.nslices, P.rowptr, valA, P.sell_ptr,
-                                                                          P.sell_w, W.sval);
+    if (P.bsr_ready) {
+        GIC_TRY(bsr_values(h, P, valA, W.sval));
+    } else {
+        ++h->launches;
+        k_sell_vals<<<vec_grid(h, P.nslices * 32, 256), 256, 0, h->stream>>>(n, P.nslices, P.rowptr, valA,
+                                                                              P.sell_ptr, P.sell_w, W.sval);
+    }
     PROF_BEGIN(GIC_PROF_SPMV);
-    ++h->launches;
-    k_spmv_sell<2><<<spmv_grid(h, P.nslices), SPMV_BLOCK, 0, h->stream>>>(
-        n, P.nslices, P.sell_ptr, P.sell_w, P.sell_col, W.sval, x, W.r, b, W.partials, W.sc);
-    GIC_CUDA_TRY(cudaGetLastError());
+    if (P.bsr_ready) {
+        GIC_TRY(bsr_spmv(h, P, 2, W.sval, x, W.r, b, W.partials, W.sc));
+    } else {
+        ++h->launches;
+        k_spmv_sell<2><<<spmv_grid(h, P.nslices), SPMV_BLOCK, 0, h->stream>>>(
+            n, P.nslices, P.sell_ptr, P.sell_w, P.sell_col, W.sval, x, W.r, b, W.partials, W.sc);
+        GIC_CUDA_TRY(cudaGetLastError());
+    }
     PROF_END(GIC_PROF_SPMV);
     if (f32_vectors(mode)) {
         ++h->launches;
@@ -1805,6 +1793,14 @@ int gic_set_tuning(gic_handle *h, int key, int value)
     case GIC_TUNE_GNN_BF16: h->tune_gnn_bf16 = value; return GIC_OK;
     default: return GIC_ERR_INVALID_ARG;
     }
+}
+
+int gic_pattern_spmv_layout(const gic_pattern *P, int32_t *node_blocks, int64_t *entries)
+{
+    if (!P) return GIC_ERR_INVALID_ARG;
+    if (node_blocks) *node_blocks = P->p.bsr_ready;
+    if (entries) *entries = P->p.bsr_ready ? 9 * 32 * P->p.bsr_steps : P->p.sell_nnz;
+    return GIC_OK;
 }
 
 int gic_pattern_schedule(const gic_pattern *P, int32_t *nchunks, int32_t *chunked, int64_t *sell_nnz)

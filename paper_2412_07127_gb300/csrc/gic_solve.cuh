@@ -17,6 +17,30 @@ struct Scalars {
     unsigned pad;
 };
 
+// Block sum of one double per thread (warp sums, then thread 0 adds the
+// warps' in order); the result is valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+    v = warp_sum(v);
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sh[k];
+    __syncthreads();
+    return s;
+}
+
+// Called by thread 0 of every block after writing partials[blockIdx.x]
+// (count = gridDim.x). Returns true in the one block that arrives last.
+__device__ __forceinline__ bool last_block(unsigned *counter, unsigned count)
+{
+    __threadfence();
+    unsigned t = atomicAdd(counter, 1u);
+    return t == count - 1;
+}
+
 constexpr int SOLVE_BLOCK = 256;
 constexpr int MAX_PARTIALS = 1 << 16;
 
@@ -81,6 +105,13 @@ int s_setup(gic_handle *h, const Pattern &P, bool f32, const void *Lval, void *S
 int s_lsolve(gic_handle *h, const Pattern &P, bool f32, const void *Sf, const void *r, void *y, const Scalars *sc);
 int s_ltsolve(gic_handle *h, const Pattern &P, bool f32, bool pcg, const void *Sb, void *y, void *z,
               const double *rd, double *partials, Scalars *sc);
+
+// 3x3 node-block SpMV (gic_bsr.cu): A's values in the block layout
+// (9 * 32 * P.bsr_steps doubles), and y = A x with the PCG's fused
+// reductions (mode 1: p^T w and alpha; mode 2: r = b - A x, ||r||, ||b||).
+int bsr_values(gic_handle *h, const Pattern &P, const double *valA, double *bval);
+int bsr_spmv(gic_handle *h, const Pattern &P, int mode, const double *bval, const double *x, double *y,
+             const double *b, double *partials, Scalars *sc);
 
 // automatic solve choice: level-sliced kernels from this many chunks per SM
 constexpr int SLICED_CHUNKS_PER_SM = 48;

@@ -182,6 +182,10 @@ __global__ void __launch_bounds__(SBLOCK, 2) k_ssolve(SliceView S, const T *__re
                 kv[b] = kn[b];
             }
         }
+        // the group's own right-hand side M r (zero where unused), off the
+        // chain that follows the late values
+#pragma unroll
+        for (int u = 0; u < 3; ++u) acc1 = fma(mv[u], rv[u], acc1);
         // late section (the nearest levels and the previous group of the
         // chunk): every value is requested at once, then summed in two waves,
         // the last SNEAR steps (for hex elasticity: the level just before)
@@ -224,8 +228,6 @@ __global__ void __launch_bounds__(SBLOCK, 2) k_ssolve(SliceView S, const T *__re
                 }
             }
         }
-#pragma unroll
-        for (int u = 0; u < 3; ++u) acc1 = fma(mv[u], rv[u], acc1); // M r (zero where unused)
         const T y = (acc0 + acc1) + (acc2 + acc3);
         // the rows of a group (its own slice, this warp) read their right-hand
         // side before any lane resets it; the warp enters the next slice together

@@ -9,8 +9,13 @@ sequences calls and times them with CUDA events):
   deviation  the factor deviation of the paper's Figure 5: mean and maximum
              |L - L_IC| / |L_IC| on and off the diagonal for the shipped
              network (correcting IC(0)) and for a direct prediction.
-  sweep      PCG iterations of IC(0) and of the corrected factor over seeds
-             and sizes (Figures 2-4).
+  sweep      PCG iterations of IC(0), of the corrected factor and (with
+             --nic-weights) of the direct prediction over seeds and sizes
+             (Figures 2-4).
+  table      IC(0) / NIC (direct prediction, Eq. (1)) / GNN-IC (Eq. (2)) per
+             size, as Table 1 lays them out: iterations, P-time (factor
+             construction), CG-time, and the Figure 5 deviation of each
+             learned factor from L_IC; times by CUDA events.
 
 Usage: python -m paper_2412_07127_gb300.experiments dropout --N 69
 Each line printed is one JSON record.
@@ -26,6 +31,7 @@ from . import gicpcg as G
 from . import inputs as I
 
 WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "gnn_theta.npy")
+NIC_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "nic_theta.npy")
 
 
 def _system(h, N, seed, sigma=1.0):
@@ -84,27 +90,72 @@ def deviation(h, N, seed, weights):
                       "positive": ok}), flush=True)
 
 
-def sweep(h, Ns, seeds, weights):
+def _learned_factor(h, P, v, L, theta, nic):
+    """The network's factor: IC(0) corrected (Eq. 2) or, for NIC, the
+    identity base corrected, i.e. the direct prediction (Eq. 1)."""
+    x9, e0, scale, _ = G.features(h, P, v)
+    g = G.gnn_forward(h, P, theta, x9, e0)
+    base = G.identity_factor(h, P, scale)[0] if nic else L
+    return G.gnn_correct(h, P, base, g, scale)
+
+
+def sweep(h, Ns, seeds, weights, nic_weights=None):
     from .train import load_weights
-    th, _ = load_weights(weights)
-    theta = torch.from_numpy(th).cuda()
+    theta = torch.from_numpy(load_weights(weights)[0]).cuda()
+    tnic = torch.from_numpy(load_weights(nic_weights)[0]).cuda() if nic_weights else None
     for N in Ns:
         for seed in seeds:
             rp, c, v, P, b = _system(h, N, seed)
             L, alpha, _ = G.ic0_auto(h, P, v)
-            x9, e0, scale, _ = G.features(h, P, v)
-            g = G.gnn_forward(h, P, theta, x9, e0)
-            Lc, ok = G.gnn_correct(h, P, L, g, scale)
+            Lc, ok = _learned_factor(h, P, v, L, theta, False)
             r0 = G.pcg(h, P, v, L, b)
-            r1 = G.pcg(h, P, v, Lc, b, check=False) if ok else {"iters": -1}
-            print(json.dumps({"experiment": "sweep", "N": N, "n": P.n, "seed": seed, "ic0": r0["iters"],
-                              "gnn": r1["iters"], "shift": alpha}), flush=True)
+            r1 = G.pcg(h, P, v, Lc, b, check=False) if ok else {"iters": -1, "status": -1}
+            rec = {"experiment": "sweep", "N": N, "n": P.n, "seed": seed, "ic0": r0["iters"],
+                   "gnn": r1["iters"] if r1["status"] == 0 else -1, "shift": alpha}
+            if tnic is not None:
+                Ln, okn = _learned_factor(h, P, v, L, tnic, True)
+                r2 = G.pcg(h, P, v, Ln, b, check=False) if okn else {"iters": -1, "status": -1}
+                rec["nic"] = r2["iters"] if r2["status"] == 0 else -1
+            print(json.dumps(rec), flush=True)
+            P.close()
+
+
+def table(h, Ns, seeds, weights, nic_weights, reps=2):
+    from .train import load_weights
+    theta = torch.from_numpy(load_weights(weights)[0]).cuda()
+    tnic = torch.from_numpy(load_weights(nic_weights)[0]).cuda()
+    for N in Ns:
+        for seed in seeds:
+            rp, c, v, P, b = _system(h, N, seed)
+            rows = {}
+            for name in ("ic0", "nic", "gnn_ic"):
+                best = None
+                for _ in range(reps):   # the first run includes one-time costs (workspaces, module load)
+                    def build():
+                        L, _, _ = G.ic0_auto(h, P, v)
+                        if name == "ic0":
+                            return L, L, True
+                        Lf, ok = _learned_factor(h, P, v, L, tnic if name == "nic" else theta, name == "nic")
+                        return L, Lf, ok
+                    (L, Lf, ok), tp = _timed(build)
+                    if name == "nic":   # the direct prediction needs no IC(0): time it without
+                        (_, ok), tp = _timed(lambda: _learned_factor(h, P, v, None, tnic, True))
+                    r, tc = _timed(lambda: G.pcg(h, P, v, Lf, b, check=False) if ok else {"iters": -1, "status": -1})
+                    if best is None or tp + tc < best["p_time_s"] + best["cg_time_s"]:
+                        best = {"iters": r["iters"] if r["status"] == 0 else -1, "p_time_s": tp, "cg_time_s": tc,
+                                "positive": ok}
+                        if name != "ic0":
+                            d = G.factor_deviation(h, P, L, Lf)
+                            best.update(dev_diag_mean=d[0], dev_off_mean=d[2])
+                rows[name] = best
+            print(json.dumps({"experiment": "table", "N": N, "n": P.n, "nnz": P.nnzA, "seed": seed, **rows}),
+                  flush=True)
             P.close()
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("experiment", choices=["dropout", "deviation", "sweep"])
+    ap.add_argument("experiment", choices=["dropout", "deviation", "sweep", "table"])
     ap.add_argument("--N", type=int, default=69)
     ap.add_argument("--Ns", default="8,12,20,40")
     ap.add_argument("--seed", type=int, default=0)
@@ -114,14 +165,19 @@ def main(argv=None):
     ap.add_argument("--grouped", action="store_true",
                     help="node-granular dropout: a column leaves all rows of a row group or none")
     ap.add_argument("--weights", default=WEIGHTS)
+    ap.add_argument("--nic-weights", default=None, help=f"NIC weights (table: default {NIC_WEIGHTS})")
     a = ap.parse_args(argv)
     h = G.Handle(0)
     if a.experiment == "dropout":
         dropout(h, a.N, a.seed, [float(x) for x in a.eps.split(",")], a.f32, a.grouped)
     elif a.experiment == "deviation":
         deviation(h, a.N, a.seed, a.weights)
+    elif a.experiment == "table":
+        table(h, [int(x) for x in a.Ns.split(",")], [int(x) for x in a.seeds.split(",")], a.weights,
+              a.nic_weights or NIC_WEIGHTS)
     else:
-        sweep(h, [int(x) for x in a.Ns.split(",")], [int(x) for x in a.seeds.split(",")], a.weights)
+        sweep(h, [int(x) for x in a.Ns.split(",")], [int(x) for x in a.seeds.split(",")], a.weights,
+              a.nic_weights)
 
 
 if __name__ == "__main__":

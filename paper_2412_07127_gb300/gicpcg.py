@@ -51,6 +51,7 @@ _SIGS = {
     "gic_pattern_export": (_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "gic_pattern_schedule": (_int, [_vp, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i64)]),
     "gic_pattern_solve_kernels": (_int, [_vp, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i32)]),
+    "gic_pattern_spmv_layout": (_int, [_vp, C.POINTER(_i32), C.POINTER(_i64)]),
     "gic_ic0": (_int, [_vp, _vp, _vp, _vp, _dbl, C.POINTER(_i64)]),
     "gic_ic0_auto": (_int, [_vp, _vp, _vp, _vp, _int, C.POINTER(_dbl), C.POINTER(_i64)]),
     "gic_convert_f64_f32": (_int, [_vp, _i64, _vp, _vp]),
@@ -192,6 +193,9 @@ class Pattern:
         q, b, mr = _i32(), _i32(), _i32()
         _call("gic_pattern_solve_kernels", p, C.byref(q), C.byref(b), C.byref(mr))
         self.warp_specialised, self.level_sliced, self.slices = q.value, b.value, mr.value
+        nbk, ent = _i32(), _i64()
+        _call("gic_pattern_spmv_layout", p, C.byref(nbk), C.byref(ent))
+        self.node_blocks, self.spmv_entries = nbk.value, ent.value
 
     def export(self, h: Handle):
         dev = self.rowptr.device

@@ -10,7 +10,14 @@ One step on a batch of B independent N^3 systems (one block-diagonal pattern):
   backward -> GNN backward -> Adam.
 The batch's pattern is the same at every step, so it is analysed once.
 
-Usage: python -m paper_2412_07127_gb300.train --steps 2000 --out theta.npy
+Training runs a fixed set of generated systems for a number of epochs,
+validates every epoch (PCG iterations on held-out systems) and keeps the
+weights of the validation with the fewest iterations (Section "Training and
+Inference"); --checkpoint / --resume save and restore the whole state. The
+gradient comes from loss.backward() through the torch.autograd Functions of
+paper_2412_07127_gb300.autograd.
+
+Usage: python -m paper_2412_07127_gb300.train --epochs 50 --out theta.npy
 """
 import argparse
 import json
@@ -61,8 +68,9 @@ class Trainer:
         E = torch.from_numpy(np.concatenate(Es)).to(self.dev)
         return G.fem_hex_assemble(self.h, self.N, E, nb=self.B)
 
-    def batch(self, k):
-        """Device inputs of batch k: (x9, e0, A_hat, L_IC_hat, Z)."""
+    def batch(self, k, probe_epoch=0):
+        """Device inputs of batch k: (x9, e0, A_hat, L_IC_hat, Z); the probes
+        of a later epoch are drawn afresh."""
         _, _, v = self._assemble(k)
         LIC = torch.empty(self.P.nnzL, dtype=torch.float64, device=self.dev)
         nL = self.P1.nnzL
@@ -77,7 +85,7 @@ class Trainer:
             LIChat = G.identity_factor(self.h, self.P, want_L=False, want_hat=True)[1]
         else:
             LIChat = G.scale_factor(self.h, self.P, LIC, scale, ngraphs=self.B)
-        Z = np.concatenate([I.probes(self.m, self.n, s) for s in self._seeds(k)], axis=1)
+        Z = np.concatenate([I.probes(self.m, self.n, s + 1_000_003 * probe_epoch) for s in self._seeds(k)], axis=1)
         return x9, e0, Ahat, LIChat, torch.from_numpy(Z).to(self.dev)
 
     def loss_grad(self, theta, data, grad=True):
@@ -138,14 +146,18 @@ def weights_meta(log):
                                 f"per system, seeds {a['seed0']}+",
                      "probes": f"{a['probes']} Gaussian per system", "steps_done": log["steps_done"],
                      "seconds": round(log["train_seconds"], 1), "lr": a["lr"], "warmup_frac": a["warmup_frac"],
+                     "epochs": a.get("epochs"), "train_systems": a.get("train_systems"), "mode": a.get("mode"),
+                     "kept_step": log.get("best_step"),
+                     "validation_means": [[r["step"], r["mean"]] for r in log["val"]],
                      "ic0_shifts_seen": log["ic0_shifts"],
                      "loss_ratio_to_ic0_first": round(st[0]["ratio"], 4),
                      "loss_ratio_to_ic0_last": round(st[-1]["ratio"], 4)},
         "validation": {"systems": f"{a['val_N']}^3-element hex elasticity, sigma = 1, seeds 9000-9015, "
                                   f"PCG to 1e-8, FP64", "iters_ic0_mean": ic0, "iters_gnn_mean": gnn, "runs": v},
         "use_gnn": bool(gnn < ic0),
-        "policy": "the corrected factor is used only when its validation iteration count is below plain "
-                  "IC(0)'s; otherwise plain IC(0) is the fallback",
+        "policy": "the weights kept are those of the validation with the fewest iterations (the starting "
+                  "point included); the corrected factor is used only when that count is below plain IC(0)'s, "
+                  "otherwise plain IC(0) is the fallback",
     }
 
 
@@ -157,9 +169,19 @@ def load_weights(path):
     return th, meta
 
 
+def save_checkpoint(path, theta, m1, m2, step, log):
+    """Everything a run needs to resume: parameters, Adam moments, the next
+    step and the log so far (the inputs are regenerated from their seeds)."""
+    tmp = path + ".tmp"
+    torch.save({"theta": theta.detach().cpu(), "m1": m1.cpu(), "m2": m2.cpu(), "step": step, "log": log}, tmp)
+    os.replace(tmp, path)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--epochs", type=int, default=50, help="passes over the training set")
+    ap.add_argument("--train-systems", type=int, default=400, help="systems in the training set")
+    ap.add_argument("--steps", type=int, default=0, help="if > 0: stop after this many steps")
     ap.add_argument("--N", type=int, default=20)
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--probes", type=int, default=8)
@@ -169,46 +191,77 @@ def main(argv=None):
     ap.add_argument("--init-out-scale", type=float, default=0.02)
     ap.add_argument("--seed0", type=int, default=1000)
     ap.add_argument("--time-limit", type=float, default=1e9, help="seconds; stop early")
-    ap.add_argument("--val-every", type=int, default=0)
+    ap.add_argument("--val-every", type=int, default=0, help="steps between validations (0: once per epoch)")
     ap.add_argument("--val-N", type=int, default=20)
     ap.add_argument("--mode", default="ic", choices=["ic", "nic"])
+    ap.add_argument("--checkpoint", default=None, help="resumable state, written at every validation")
+    ap.add_argument("--resume", action="store_true", help="continue from --checkpoint")
     ap.add_argument("--out", required=True)
     ap.add_argument("--log", default=None)
     a = ap.parse_args(argv)
+    from .autograd import training_loss
 
     h = G.Handle(0)
     tr = Trainer(h, a.N, a.batch, a.probes, a.seed0, mode=a.mode)
     dev = tr.dev
+    nb = max(1, a.train_systems // a.batch)        # batches per epoch (a fixed training set)
+    total = nb * a.epochs if a.steps <= 0 else a.steps
+    val_every = a.val_every if a.val_every > 0 else nb
+    warm = int(a.warmup_frac * total)
     theta = torch.from_numpy(I.gnn_init(a.init_seed, a.init_out_scale).astype(np.float32)).to(dev)
     m1, m2 = torch.zeros_like(theta), torch.zeros_like(theta)
-    warm = int(a.warmup_frac * a.steps)
-    log = dict(args=vars(a), steps=[], val=[])
+    log = dict(args=vars(a), steps=[], val=[], train_seconds_before=0.0)
+    t_start = 0
+    if a.resume and a.checkpoint and os.path.exists(a.checkpoint):
+        ck = torch.load(a.checkpoint)
+        theta, m1, m2 = ck["theta"].to(dev), ck["m1"].to(dev), ck["m2"].to(dev)
+        t_start, log = ck["step"], ck["log"]
+    # validation baseline: plain IC(0) iterations on the held-out systems, and
+    # the starting point itself, which the best-by-iterations rule may keep
+    if not log["val"]:
+        v0 = validate(h, theta, N=a.val_N, mode=a.mode)
+        log["val"].append(dict(step=0, runs=v0, mean=float(np.mean([r["gnn"] if r["gnn"] >= 0 else np.inf
+                                                                      for r in v0]))))
+        print(json.dumps(dict(step=0, val_mean=log["val"][-1]["mean"])), flush=True)
     t0 = time.time()
-    for t in range(a.steps):
-        data = tr.batch(t)
-        loss, grad = tr.loss_grad(theta, data)
+    t = t_start
+    for t in range(t_start, total):
+        # batch t mod nb of the training set; fresh Gaussian probes each epoch
+        data = tr.batch(t % nb, probe_epoch=t // nb)
+        x9, e0, Ahat, LIChat, Z = data
+        th = theta.clone().requires_grad_(True)
+        loss = training_loss(th, h, tr.P, x9, e0, LIChat, Ahat, Z, ngraphs=a.batch, gnn_ws=tr.ws, probe_ws=tr.pws)
+        loss.backward()
+        grad = th.grad
         G.adam_step(h, theta, grad, m1, m2, t + 1, lr_at(t, warm, a.lr))
-        if t % 20 == 0 or t == a.steps - 1:
+        if t % 20 == 0 or t == total - 1:
             l_ic = float(tr.ic0_loss(data)[a.batch])
-            rec = dict(step=t, loss=float(loss[a.batch]), loss_ic0=l_ic, ratio=float(loss[a.batch]) / l_ic,
-                       gnorm=float(grad.norm()), wall=time.time() - t0)
+            rec = dict(step=t, loss=float(loss), loss_ic0=l_ic, ratio=float(loss) / l_ic,
+                       gnorm=float(grad.norm()), wall=log["train_seconds_before"] + time.time() - t0)
             log["steps"].append(rec)
             print(json.dumps(rec), flush=True)
-        if a.val_every and (t + 1) % a.val_every == 0:
-            v = validate(h, theta, N=a.val_N, seeds=range(9000, 9004), mode=a.mode)
-            log["val"].append(dict(step=t + 1, runs=v))
-            print(json.dumps(dict(step=t + 1, val=v)), flush=True)
+        if (t + 1) % val_every == 0 or t == total - 1:
+            v = validate(h, theta, N=a.val_N, mode=a.mode)
+            mean = float(np.mean([r["gnn"] if r["gnn"] >= 0 else np.inf for r in v]))
+            log["val"].append(dict(step=t + 1, runs=v, mean=mean))
+            print(json.dumps(dict(step=t + 1, val_mean=mean)), flush=True)
+            best = min(log["val"], key=lambda r: (r["mean"], r["step"]))
+            if best["step"] == t + 1:   # the paper keeps the step with the fewest validation iterations
+                np.save(a.out, theta.cpu().numpy())
+            if a.checkpoint:
+                save_checkpoint(a.checkpoint, theta, m1, m2, t + 1,
+                                dict(log, train_seconds_before=log["train_seconds_before"] + time.time() - t0))
         if time.time() - t0 > a.time_limit:
             break
     torch.cuda.synchronize()
-    log["train_seconds"] = time.time() - t0
+    log["train_seconds"] = log["train_seconds_before"] + time.time() - t0
     log["steps_done"] = t + 1
     log["ic0_shifts"] = sorted(set(tr.shifts))
-    os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
-    np.save(a.out, theta.cpu().numpy())
-    v = validate(h, theta, N=a.val_N, mode=a.mode)
-    log["final_val"] = v
-    print(json.dumps(dict(final_val=v)), flush=True)
+    best = min(log["val"], key=lambda r: (r["mean"], r["step"]))
+    if best["step"] == 0:   # nothing beat the starting point
+        np.save(a.out, I.gnn_init(a.init_seed, a.init_out_scale).astype(np.float32))
+    log["best_step"] = best["step"]
+    log["final_val"] = best["runs"]
     with open(os.path.splitext(a.out)[0] + ".json", "w") as f:
         json.dump(weights_meta(log), f, indent=1)
     if a.log:

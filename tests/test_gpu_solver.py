@@ -101,6 +101,7 @@ def test_analysis_fem(G, h, N):
         assert P.ngroups == A.n // 3 and np.array_equal(grp, np.arange(0, A.n + 1, 3))
         # the hex systems admit the fastest solve kernels (so the tests run them)
         assert P.warp_specialised == 1 and P.level_sliced == 1 and P.slices > 0
+        assert P.node_blocks == 1  # 3x3 node blocks: the PCG runs the block SpMV
 
 
 def _expected_groups(A):
@@ -128,6 +129,38 @@ def test_analysis_generic(G, h, case):
     assert np.array_equal(Lr, T.rowptr) and np.array_equal(Lc, T.col)
     assert np.array_equal(lev, olev) and P.nlevels == onl
     assert np.array_equal(grp, _expected_groups(A))
+    assert P.node_blocks == 0  # none of these is made of 3x3 node blocks
+
+
+def _node_block_spd(nodes, density, seed):
+    """A random SPD matrix made of dense 3x3 node blocks (not a mesh)."""
+    rng = np.random.default_rng(seed)
+    mask = rng.random((nodes, nodes)) < density
+    mask = mask | mask.T | np.eye(nodes, dtype=bool)
+    M = np.kron(mask, np.ones((3, 3))) * rng.standard_normal((3 * nodes, 3 * nodes))
+    S = M + M.T
+    return S + np.diag(np.abs(S).sum(1) + 1.0)
+
+
+@pytest.mark.parametrize("nodes,density", [(7, 0.3), (100, 0.05), (333, 0.012)])
+def test_pcg_node_block_pattern_matches_oracle(G, h, nodes, density):
+    """The block SpMV path of the PCG on a non-mesh node-block matrix
+    (slices of 32 nodes with ragged widths and a partial last slice; rows
+    within the IC(0) kernel's 48 lower entries)."""
+    A = O.csr_from_dense(_node_block_spd(nodes, density, nodes))
+    rp, c, v = _upload(A)
+    P = G.Pattern(h, rp, c)
+    assert P.node_blocks == 1
+    b = np.random.default_rng(nodes).uniform(-1, 1, A.n)
+    Lg, bad = G.ic0(h, P, v)
+    assert bad == -1
+    res = G.pcg(h, P, v, Lg, _dev(b), rtol=1e-10)
+    Lo, _ = O.ic0(A)
+    ro = O.pcg(A, b, Lo, tol=1e-10)
+    assert res["status"] == 0 and _iters_ok(res["iters"], ro["iters"]), (res["iters"], ro["iters"])
+    x = _np(res["x"])
+    assert np.linalg.norm(x - ro["x"]) <= 1e-8 * np.linalg.norm(ro["x"])
+    assert np.linalg.norm(b - O.spmv(A, x)) <= 1e-9 * np.linalg.norm(b)
 
 
 def test_analysis_rejects_bad_patterns(G, h):
