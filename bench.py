@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--no-f32", action="store_true", help="skip the FP32-apply comparison")
     ap.add_argument("--side-steps", type=int, default=2,
                     help="steps of each comparison run after the timed region")
+    ap.add_argument("--pipeline", type=int, default=4,
+                    help="triangular-solve kernels (GIC_TUNE_PIPELINE): 4 automatic, 3 level-sliced, "
+                         "2 warp-specialised, 1 staged, 0 generic")
     return ap.parse_args()
 
 
@@ -375,6 +378,7 @@ def run_ours(args, rank, world, local):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     stream = torch.cuda.current_stream()
     h = G.Handle(local, stream)
+    G.set_tuning(h, G.GIC_TUNE_PIPELINE, args.pipeline)
     N = args.N
     seed = rank_seed(args.seed, rank)
     theta_np, theta_src = load_theta(I.N_PARAMS)
@@ -516,7 +520,9 @@ def run_ours(args, rank, world, local):
            "roofline": roof, "spmv_roofline": spmv_roof, "clocks": clk,
            "gpu_launches": launches,
            "schedule": {"chunks": P.nchunks, "level_sliced": bool(P.level_sliced), "slices": P.slices,
-                        "sell_padding": P.sell_nnz / P.nnzA - 1.0},
+                        "solve_kernels": G.solve_kernels_chosen(h, P, ldt),
+                        "spmv": "3x3 node blocks" if P.node_blocks else "SELL-32",
+                        "spmv_padding": P.spmv_entries / P.nnzA - 1.0},
            "f32_apply": other}
 
     if not args.no_e2e:

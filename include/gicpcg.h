@@ -113,6 +113,11 @@ int gic_pattern_schedule(const gic_pattern *P, int32_t *nchunks, int32_t *chunke
  * which then run the block SpMV, else 0 (SELL-32 CSR); entries = values in
  * that layout, padding included. */
 int gic_pattern_spmv_layout(const gic_pattern *P, int32_t *node_blocks, int64_t *entries);
+/* The triangular-solve kernels gic_pcg / gic_lsolve / gic_ltsolve will run on
+ * this pattern for a factor of l_dtype (GIC_F64 or GIC_F32) under the
+ * handle's current tuning (host output): 3 level-sliced, 2 warp-specialised,
+ * 1 staged one-warp, 0 generic. */
+int gic_solve_kernels_chosen(gic_handle *h, const gic_pattern *P, int l_dtype, int32_t *pipeline);
 /* Which triangular-solve kernels the pattern admits (host outputs, any may be
  * NULL): warp-specialised (1/0), level-sliced (1/0; one lane per row, slices
  * of whole row groups of one level) and the forward sweep's slice count. */

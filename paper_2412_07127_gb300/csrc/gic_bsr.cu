@@ -87,7 +87,11 @@ __global__ void k_bsr_vals(int64_t nodes, int64_t nsl, const int32_t *__restrict
 
 // MODE 1: w = A p, p^T w, alpha = r^T z / p^T w (Algorithm 1);
 // MODE 2: r = b - A x, ||r||^2, ||b||^2 and the stop test (its first line).
-template <int MODE>
+// LPN lanes per node: 1 = a warp per slice of 32 nodes; 2 = a warp per half
+// slice, the two lanes of a node taking the even and the odd block steps
+// (twice the warps and half the chain per lane, for systems whose slices are
+// too few to fill the SMs), their sums added by one shuffle.
+template <int MODE, int LPN>
 __global__ void __launch_bounds__(BSR_BLOCK) k_spmv_bsr(int64_t n, int64_t nsl, const int64_t *__restrict__ bptr,
                                                         const int32_t *__restrict__ bw,
                                                         const int32_t *__restrict__ bcol,
@@ -102,21 +106,25 @@ __global__ void __launch_bounds__(BSR_BLOCK) k_spmv_bsr(int64_t n, int64_t nsl, 
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nodes = n / 3;
+    const int col_lane = (LPN == 1) ? lane : (lane >> 1);  // the node's column in the slice (per half)
+    const int kpar = (LPN == 1) ? 0 : (lane & 1);
     double d1 = 0.0, d2 = 0.0;
-    for (int64_t sl = w; sl < nsl; sl += nw) {
-        const int64_t node = sl * 32 + lane;
+    for (int64_t item = w; item < nsl * LPN; item += nw) {
+        const int64_t sl = item / LPN;
+        const int sub = (LPN == 1) ? col_lane : (int)(item % LPN) * 16 + col_lane; // lane column in the slice
+        const int64_t node = sl * 32 + sub;
         const int32_t width = (node < nodes) ? bw[sl] : 0; // lanes past the last node load nothing
         const int64_t o = bptr[sl];
-        // two accumulators per row (even and odd blocks)
+        // two accumulators per row (alternate block steps of this lane)
         double a0 = 0.0, a1 = 0.0, a2 = 0.0, c0 = 0.0, c1 = 0.0, c2 = 0.0;
-        int32_t k = 0;
-        for (; k + 2 <= width; k += 2) {
-            const int32_t j0 = __ldg(bcol + (o + k) * 32 + lane), j1 = __ldg(bcol + (o + k + 1) * 32 + lane);
+        int32_t k = kpar;
+        for (; k + LPN < width; k += 2 * LPN) {
+            const int32_t j0 = __ldg(bcol + (o + k) * 32 + sub), j1 = __ldg(bcol + (o + k + LPN) * 32 + sub);
             double v0[9], v1[9];
 #pragma unroll
             for (int e = 0; e < 9; ++e) {
-                v0[e] = __ldg(bval + ((o + k) * 9 + e) * 32 + lane);
-                v1[e] = __ldg(bval + ((o + k + 1) * 9 + e) * 32 + lane);
+                v0[e] = __ldg(bval + ((o + k) * 9 + e) * 32 + sub);
+                v1[e] = __ldg(bval + ((o + k + LPN) * 9 + e) * 32 + sub);
             }
             const double x00 = __ldg(x + 3 * (int64_t)j0), x01 = __ldg(x + 3 * (int64_t)j0 + 1),
                          x02 = __ldg(x + 3 * (int64_t)j0 + 2);
@@ -130,18 +138,22 @@ __global__ void __launch_bounds__(BSR_BLOCK) k_spmv_bsr(int64_t n, int64_t nsl, 
             c0 = fma(v1[2], x12, c0); c1 = fma(v1[5], x12, c1); c2 = fma(v1[8], x12, c2);
         }
         if (k < width) {
-            const int32_t j0 = __ldg(bcol + (o + k) * 32 + lane);
+            const int32_t j0 = __ldg(bcol + (o + k) * 32 + sub);
             double v0[9];
 #pragma unroll
-            for (int e = 0; e < 9; ++e) v0[e] = __ldg(bval + ((o + k) * 9 + e) * 32 + lane);
+            for (int e = 0; e < 9; ++e) v0[e] = __ldg(bval + ((o + k) * 9 + e) * 32 + sub);
             const double x00 = __ldg(x + 3 * (int64_t)j0), x01 = __ldg(x + 3 * (int64_t)j0 + 1),
                          x02 = __ldg(x + 3 * (int64_t)j0 + 2);
             a0 = fma(v0[0], x00, a0); a1 = fma(v0[3], x00, a1); a2 = fma(v0[6], x00, a2);
             a0 = fma(v0[1], x01, a0); a1 = fma(v0[4], x01, a1); a2 = fma(v0[7], x01, a2);
             a0 = fma(v0[2], x02, a0); a1 = fma(v0[5], x02, a1); a2 = fma(v0[8], x02, a2);
         }
-        if (node < nodes) {
-            const double s[3] = {a0 + c0, a1 + c1, a2 + c2};
+        double s[3] = {a0 + c0, a1 + c1, a2 + c2};
+        if (LPN == 2) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) s[r] += __shfl_xor_sync(0xffffffffu, s[r], 1);
+        }
+        if (node < nodes && kpar == 0) {
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
                 const int64_t i = 3 * node + r;
@@ -278,14 +290,26 @@ int bsr_spmv(gic_handle *h, const Pattern &P, int mode, const double *bval, cons
              const double *b, double *partials, Scalars *sc)
 {
     ++h->launches;
-    // one warp per slice of 32 nodes, the grid striding over the slices
-    const unsigned grid = bgrid(h, P.bsr_nsl * 32, 8);
-    if (mode == 1)
-        k_spmv_bsr<1><<<grid, BSR_BLOCK, 0, h->stream>>>(P.n, P.bsr_nsl, P.bsr_ptr, P.bsr_w, P.bsr_col, bval, x, y,
-                                                          nullptr, partials, sc);
-    else
-        k_spmv_bsr<2><<<grid, BSR_BLOCK, 0, h->stream>>>(P.n, P.bsr_nsl, P.bsr_ptr, P.bsr_w, P.bsr_col, bval, x, y,
-                                                          b, partials, sc);
+    // a warp per slice of 32 nodes, the grid striding over the slices; with
+    // fewer slices than 24 warps per SM, a warp per half slice
+    const bool split = P.bsr_nsl < 24 * (int64_t)h->num_sms;
+    const unsigned grid = bgrid(h, P.bsr_nsl * 32 * (split ? 2 : 1), 8);
+    const int64_t n = P.n, ns = P.bsr_nsl;
+    if (mode == 1) {
+        if (split)
+            k_spmv_bsr<1, 2><<<grid, BSR_BLOCK, 0, h->stream>>>(n, ns, P.bsr_ptr, P.bsr_w, P.bsr_col, bval, x, y,
+                                                                 nullptr, partials, sc);
+        else
+            k_spmv_bsr<1, 1><<<grid, BSR_BLOCK, 0, h->stream>>>(n, ns, P.bsr_ptr, P.bsr_w, P.bsr_col, bval, x, y,
+                                                                 nullptr, partials, sc);
+    } else {
+        if (split)
+            k_spmv_bsr<2, 2><<<grid, BSR_BLOCK, 0, h->stream>>>(n, ns, P.bsr_ptr, P.bsr_w, P.bsr_col, bval, x, y, b,
+                                                                 partials, sc);
+        else
+            k_spmv_bsr<2, 1><<<grid, BSR_BLOCK, 0, h->stream>>>(n, ns, P.bsr_ptr, P.bsr_w, P.bsr_col, bval, x, y, b,
+                                                                 partials, sc);
+    }
     GIC_CUDA_TRY(cudaGetLastError());
     return GIC_OK;
 }

@@ -1795,6 +1795,19 @@ int gic_set_tuning(gic_handle *h, int key, int value)
     }
 }
 
+int gic_solve_kernels_chosen(gic_handle *h, const gic_pattern *P, int l_dtype, int32_t *pipeline)
+{
+    GIC_TRY(check_pattern(h, P));
+    if (!pipeline || (l_dtype != GIC_F64 && l_dtype != GIC_F32)) return GIC_ERR_INVALID_ARG;
+    switch (solve_mode(h, P->p, l_dtype)) {
+    case MODE_S64: case MODE_S32: *pipeline = 3; break;
+    case MODE_Q64: case MODE_Q32: *pipeline = 2; break;
+    case MODE_P64: case MODE_P32: *pipeline = 1; break;
+    default: *pipeline = 0; break;
+    }
+    return GIC_OK;
+}
+
 int gic_pattern_spmv_layout(const gic_pattern *P, int32_t *node_blocks, int64_t *entries)
 {
     if (!P) return GIC_ERR_INVALID_ARG;

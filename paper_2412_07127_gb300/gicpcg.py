@@ -52,6 +52,7 @@ _SIGS = {
     "gic_pattern_schedule": (_int, [_vp, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i64)]),
     "gic_pattern_solve_kernels": (_int, [_vp, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i32)]),
     "gic_pattern_spmv_layout": (_int, [_vp, C.POINTER(_i32), C.POINTER(_i64)]),
+    "gic_solve_kernels_chosen": (_int, [_vp, _vp, _int, C.POINTER(_i32)]),
     "gic_ic0": (_int, [_vp, _vp, _vp, _vp, _dbl, C.POINTER(_i64)]),
     "gic_ic0_auto": (_int, [_vp, _vp, _vp, _vp, _int, C.POINTER(_dbl), C.POINTER(_i64)]),
     "gic_convert_f64_f32": (_int, [_vp, _i64, _vp, _vp]),
@@ -389,6 +390,16 @@ def spmv_dot_noalloc(rowptr, col, val, x, y, xdoty, stream=None):
 def selftest_wait_timeout(h: Handle, polls=4096):
     """Status of a deliberately unsatisfiable bounded wait (GIC_ERR_TIMEOUT expected)."""
     return lib().gic_selftest_wait_timeout(h.h, polls)
+
+
+SOLVE_KERNELS = {3: "level-sliced", 2: "warp-specialised", 1: "staged one-warp", 0: "generic"}
+
+
+def solve_kernels_chosen(h: Handle, P: Pattern, l_dtype=GIC_F64):
+    """Name of the triangular-solve kernels the PCG will run on P."""
+    k = _i32()
+    _call("gic_solve_kernels_chosen", h.h, P.p, l_dtype, C.byref(k))
+    return SOLVE_KERNELS[k.value]
 
 
 def launch_count(h: Handle):
