@@ -115,29 +115,41 @@ __global__ void __launch_bounds__(BSR_BLOCK) k_spmv_bsr(int64_t n, int64_t nsl, 
         const int64_t node = sl * 32 + sub;
         const int32_t width = (node < nodes) ? bw[sl] : 0; // lanes past the last node load nothing
         const int64_t o = bptr[sl];
-        // two accumulators per row (alternate block steps of this lane)
+        // two accumulators per row (alternate block steps of this lane); U
+        // block steps per iteration, their loads in flight together (more for
+        // the half-slice variant, whose warps are few per SM)
+        constexpr int U = (LPN == 1) ? 2 : 4;
         double a0 = 0.0, a1 = 0.0, a2 = 0.0, c0 = 0.0, c1 = 0.0, c2 = 0.0;
         int32_t k = kpar;
-        for (; k + LPN < width; k += 2 * LPN) {
-            const int32_t j0 = __ldg(bcol + (o + k) * 32 + sub), j1 = __ldg(bcol + (o + k + LPN) * 32 + sub);
-            double v0[9], v1[9];
+        for (; k + (U - 1) * LPN < width; k += U * LPN) {
+            int32_t j[U];
+            double v[U][9], xv[U][3];
 #pragma unroll
-            for (int e = 0; e < 9; ++e) {
-                v0[e] = __ldg(bval + ((o + k) * 9 + e) * 32 + sub);
-                v1[e] = __ldg(bval + ((o + k + LPN) * 9 + e) * 32 + sub);
-            }
-            const double x00 = __ldg(x + 3 * (int64_t)j0), x01 = __ldg(x + 3 * (int64_t)j0 + 1),
-                         x02 = __ldg(x + 3 * (int64_t)j0 + 2);
-            const double x10 = __ldg(x + 3 * (int64_t)j1), x11 = __ldg(x + 3 * (int64_t)j1 + 1),
-                         x12 = __ldg(x + 3 * (int64_t)j1 + 2);
-            a0 = fma(v0[0], x00, a0); a1 = fma(v0[3], x00, a1); a2 = fma(v0[6], x00, a2);
-            c0 = fma(v1[0], x10, c0); c1 = fma(v1[3], x10, c1); c2 = fma(v1[6], x10, c2);
-            a0 = fma(v0[1], x01, a0); a1 = fma(v0[4], x01, a1); a2 = fma(v0[7], x01, a2);
-            c0 = fma(v1[1], x11, c0); c1 = fma(v1[4], x11, c1); c2 = fma(v1[7], x11, c2);
-            a0 = fma(v0[2], x02, a0); a1 = fma(v0[5], x02, a1); a2 = fma(v0[8], x02, a2);
-            c0 = fma(v1[2], x12, c0); c1 = fma(v1[5], x12, c1); c2 = fma(v1[8], x12, c2);
+            for (int u = 0; u < U; ++u) j[u] = __ldg(bcol + (o + k + u * LPN) * 32 + sub);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int e = 0; e < 9; ++e) v[u][e] = __ldg(bval + ((o + k + u * LPN) * 9 + e) * 32 + sub);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) xv[u][c] = __ldg(x + 3 * (int64_t)j[u] + c);
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (u & 1) {
+                        c0 = fma(v[u][c], xv[u][c], c0);
+                        c1 = fma(v[u][3 + c], xv[u][c], c1);
+                        c2 = fma(v[u][6 + c], xv[u][c], c2);
+                    } else {
+                        a0 = fma(v[u][c], xv[u][c], a0);
+                        a1 = fma(v[u][3 + c], xv[u][c], a1);
+                        a2 = fma(v[u][6 + c], xv[u][c], a2);
+                    }
+                }
         }
-        if (k < width) {
+        for (; k < width; k += LPN) {
             const int32_t j0 = __ldg(bcol + (o + k) * 32 + sub);
             double v0[9];
 #pragma unroll

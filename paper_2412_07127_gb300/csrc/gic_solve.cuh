@@ -44,12 +44,16 @@ __device__ __forceinline__ bool last_block(unsigned *counter, unsigned count)
 constexpr int SOLVE_BLOCK = 256;
 constexpr int MAX_PARTIALS = 1 << 16;
 
-// deterministic sum of partials[0..count) by one warp (lane-strided, then tree)
+// deterministic sum of partials[0..count) by one warp (lane-strided in index
+// order, then tree). The caller has fenced after seeing every producer's
+// ticket; the loads bypass L1 (__ldcg) and are not volatile, so up to eight
+// of a lane's loads are in flight at once instead of one after another.
 __device__ __forceinline__ double warp_sum_partials(const double *partials, int count)
 {
     int lane = threadIdx.x & 31;
     double s = 0.0;
-    for (int k = lane; k < count; k += 32) s += ((volatile const double *)partials)[k];
+#pragma unroll 8
+    for (int k = lane; k < count; k += 32) s += __ldcg(partials + k);
     return warp_sum(s);
 }
 

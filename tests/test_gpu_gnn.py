@@ -12,8 +12,10 @@ from paper_2412_07127_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda:0")
 # BF16 inputs and W1 carry 8 significant bits (relative rounding <= 2^-9 =
-# 2e-3 each); through three tanh layers the output moves by a few of them
-BF16_VS_FP64 = 1e-2
+# 2e-3 each), and through three blocks the output moves by several of them:
+# measured 0.7-2.5e-2 relative (norm-wise) against the plain FP64 oracle at
+# 4^3-12^3, against <= 3e-4 when the oracle rounds the same operands
+BF16_VS_FP64 = 5e-2
 
 
 @pytest.fixture(scope="module")
