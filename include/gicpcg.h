@@ -105,7 +105,9 @@ int gic_pattern_info(const gic_pattern *P, int64_t *n, int64_t *nnzA, int64_t *n
  * their first (forward) or last (backward) level; 2: multi-group runs in a
  * topological order of their dependencies, taken when the level order would
  * start a run before one it reads (as thinning a factor can make) -- and the
- * padded entry count of the SELL-32 copy of A used by the PCG SpMV. */
+ * padded entry count of the SELL-32 copy of A the PCG SpMV uses for patterns
+ * not made of 3x3 node blocks (0 for those that are: they run the block
+ * SpMV, see gic_pattern_spmv_layout). */
 int gic_pattern_schedule(const gic_pattern *P, int32_t *nchunks, int32_t *chunked, int64_t *sell_nnz);
 /* SpMV layout the PCG uses for this pattern (host outputs, any may be NULL):
  * node_blocks = 1 if A is made of 3x3 node blocks (runs of 3 rows from a
@@ -337,12 +339,19 @@ int gic_adam_step(gic_handle *h, int64_t np, float *theta, const float *grad, fl
  * (read by gic_analyze; default 6); GIC_TUNE_GNN_BF16 = 1 (default): the
  * inference forward (gic_gnn_forward, gic_solve_host) runs the edge MLP's
  * first layer on the tensor cores with BF16 inputs and weights and FP32
- * accumulation, 0: FP32 on the CUDA cores (gic_gnn_forward_train is FP32). */
+ * accumulation, 0: FP32 on the CUDA cores; GIC_TUNE_TRAIN_BF16 = 0 (default):
+ * the training forward (gic_gnn_forward_train) and backward (gic_gnn_backward)
+ * compute the edge MLP in FP32, 1: in BF16 as inference does (tensor cores,
+ * BF16 inputs and W1, FP32 accumulation; FP32 master weights), the backward
+ * recomputing the hidden layer from the same BF16-rounded inputs and W1 and
+ * passing the gradient straight through the rounding (both calls must see
+ * the same setting). */
 #define GIC_TUNE_SOLVE_WARPS_PER_SM 1
 #define GIC_TUNE_POLL 2
 #define GIC_TUNE_PIPELINE 3
 #define GIC_TUNE_QDELTA 4
 #define GIC_TUNE_GNN_BF16 5
+#define GIC_TUNE_TRAIN_BF16 6
 int gic_set_tuning(gic_handle *h, int key, int value);
 
 /* Failure-path self-test of the bounded device waits: one warp waits on a

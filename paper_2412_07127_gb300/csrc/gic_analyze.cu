@@ -914,8 +914,8 @@ static int analyze_impl(gic_handle *h, int64_t n, int64_t nnz, const int32_t *ro
     STEP(read_and_clear_dev_err(h, &flags));
     if (flags & ERR_TIMEOUT) { rc = GIC_ERR_TIMEOUT; goto out; }
     STEP(build_schedule(h, P, gflag, gid, tmp2_a, tmp2_b));
-    STEP(build_sell(h, P));
     STEP(build_bsr(h, P));
+    if (!P.bsr_ready) STEP(build_sell(h, P)); // the SELL-32 copy serves only patterns without node blocks
     STEP(build_qsched(h, P));
     STEP(build_ssched(h, P));
 out:

@@ -87,10 +87,10 @@ __global__ void k_bsr_vals(int64_t nodes, int64_t nsl, const int32_t *__restrict
 
 // MODE 1: w = A p, p^T w, alpha = r^T z / p^T w (Algorithm 1);
 // MODE 2: r = b - A x, ||r||^2, ||b||^2 and the stop test (its first line).
-// LPN lanes per node: 1 = a warp per slice of 32 nodes; 2 = a warp per half
-// slice, the two lanes of a node taking the even and the odd block steps
-// (twice the warps and half the chain per lane, for systems whose slices are
-// too few to fill the SMs), their sums added by one shuffle.
+// LPN lanes per node: 1 = a warp per slice of 32 nodes; 2 or 4 = a warp per
+// half or quarter slice, the LPN lanes of a node taking every LPN-th block
+// step (LPN times the warps and 1/LPN of the chain per lane, for systems whose
+// slices are too few to fill the SMs), their sums added by shuffles.
 template <int MODE, int LPN>
 __global__ void __launch_bounds__(BSR_BLOCK) k_spmv_bsr(int64_t n, int64_t nsl, const int64_t *__restrict__ bptr,
                                                         const int32_t *__restrict__ bw,
@@ -106,12 +106,12 @@ __global__ void __launch_bounds__(BSR_BLOCK) k_spmv_bsr(int64_t n, int64_t nsl, 
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nodes = n / 3;
-    const int col_lane = (LPN == 1) ? lane : (lane >> 1);  // the node's column in the slice (per half)
-    const int kpar = (LPN == 1) ? 0 : (lane & 1);
+    const int col_lane = lane / LPN;  // the node's column in its part of the slice
+    const int kpar = lane % LPN;      // this lane's block steps: kpar, kpar + LPN, ...
     double d1 = 0.0, d2 = 0.0;
     for (int64_t item = w; item < nsl * LPN; item += nw) {
         const int64_t sl = item / LPN;
-        const int sub = (LPN == 1) ? col_lane : (int)(item % LPN) * 16 + col_lane; // lane column in the slice
+        const int sub = (int)(item % LPN) * (32 / LPN) + col_lane; // the node's column in the slice
         const int64_t node = sl * 32 + sub;
         const int32_t width = (node < nodes) ? bw[sl] : 0; // lanes past the last node load nothing
         const int64_t o = bptr[sl];
@@ -161,10 +161,10 @@ __global__ void __launch_bounds__(BSR_BLOCK) k_spmv_bsr(int64_t n, int64_t nsl, 
             a0 = fma(v0[2], x02, a0); a1 = fma(v0[5], x02, a1); a2 = fma(v0[8], x02, a2);
         }
         double s[3] = {a0 + c0, a1 + c1, a2 + c2};
-        if (LPN == 2) {
 #pragma unroll
-            for (int r = 0; r < 3; ++r) s[r] += __shfl_xor_sync(0xffffffffu, s[r], 1);
-        }
+        for (int o = 1; o < LPN; o <<= 1)
+#pragma unroll
+            for (int r = 0; r < 3; ++r) s[r] += __shfl_xor_sync(0xffffffffu, s[r], o);
         if (node < nodes && kpar == 0) {
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
@@ -303,20 +303,20 @@ int bsr_spmv(gic_handle *h, const Pattern &P, int mode, const double *bval, cons
 {
     ++h->launches;
     // a warp per slice of 32 nodes, the grid striding over the slices; with
-    // fewer slices than 24 warps per SM, a warp per half slice
-    const bool split = P.bsr_nsl < 24 * (int64_t)h->num_sms;
-    const unsigned grid = bgrid(h, P.bsr_nsl * 32 * (split ? 2 : 1), 8);
+    // fewer slices than 24 warps per SM, a warp per quarter slice
+    const int lpn = (P.bsr_nsl < 24 * (int64_t)h->num_sms) ? 4 : 1;
+    const unsigned grid = bgrid(h, P.bsr_nsl * 32 * lpn, 8);
     const int64_t n = P.n, ns = P.bsr_nsl;
     if (mode == 1) {
-        if (split)
-            k_spmv_bsr<1, 2><<<grid, BSR_BLOCK, 0, h->stream>>>(n, ns, P.bsr_ptr, P.bsr_w, P.bsr_col, bval, x, y,
+        if (lpn == 4)
+            k_spmv_bsr<1, 4><<<grid, BSR_BLOCK, 0, h->stream>>>(n, ns, P.bsr_ptr, P.bsr_w, P.bsr_col, bval, x, y,
                                                                  nullptr, partials, sc);
         else
             k_spmv_bsr<1, 1><<<grid, BSR_BLOCK, 0, h->stream>>>(n, ns, P.bsr_ptr, P.bsr_w, P.bsr_col, bval, x, y,
                                                                  nullptr, partials, sc);
     } else {
-        if (split)
-            k_spmv_bsr<2, 2><<<grid, BSR_BLOCK, 0, h->stream>>>(n, ns, P.bsr_ptr, P.bsr_w, P.bsr_col, bval, x, y, b,
+        if (lpn == 4)
+            k_spmv_bsr<2, 4><<<grid, BSR_BLOCK, 0, h->stream>>>(n, ns, P.bsr_ptr, P.bsr_w, P.bsr_col, bval, x, y, b,
                                                                  partials, sc);
         else
             k_spmv_bsr<2, 1><<<grid, BSR_BLOCK, 0, h->stream>>>(n, ns, P.bsr_ptr, P.bsr_w, P.bsr_col, bval, x, y, b,

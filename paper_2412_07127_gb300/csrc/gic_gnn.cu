@@ -24,9 +24,14 @@
 //   W4[9][32], b4[9].
 #include <math.h>
 
+#include <cuda_bf16.h>
+
 #include "gic_internal.cuh"
 
 namespace gic {
+
+// x rounded to the nearest BF16 (ties to even), back in FP32
+__device__ __forceinline__ float round_bf16(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
 constexpr int H = 32;
 constexpr int NP_GN = 27;
@@ -424,14 +429,16 @@ __global__ void __launch_bounds__(TB) k_edge_bwd(int64_t E, const int32_t *__res
                                                  const float *__restrict__ e0, const float *__restrict__ x,
                                                  const float *__restrict__ theta, int l, const float *__restrict__ de,
                                                  float *__restrict__ dh, float *__restrict__ dec,
-                                                 double *__restrict__ partials)
+                                                 double *__restrict__ partials, bool bf16)
 {
     __shared__ float W1[H * 20], b1[H], W2[H];
     __shared__ float s_dz[TB][H + 1];
     __shared__ float s_ad[TB][H + 1];
     __shared__ float s_h[TB][21];
     const float *P = theta + off_edge(l);
-    for (int t = threadIdx.x; t < H * 20; t += blockDim.x) W1[t] = P[t];
+    // BF16 training: the forward's rounding of W1 and of the inputs h is
+    // redone here, and the gradient passes straight through it
+    for (int t = threadIdx.x; t < H * 20; t += blockDim.x) W1[t] = bf16 ? round_bf16(P[t]) : P[t];
     if (threadIdx.x < H) {
         b1[threadIdx.x] = P[H * 20 + threadIdx.x];
         W2[threadIdx.x] = P[H * 20 + H + threadIdx.x];
@@ -457,6 +464,10 @@ __global__ void __launch_bounds__(TB) k_edge_bwd(int64_t E, const int32_t *__res
                 h[11 + f] = x[9 * j + f];
             }
             d = de[p];
+            if (bf16) {
+#pragma unroll
+                for (int f = 0; f < 20; ++f) h[f] = round_bf16(h[f]);
+            }
         } else {
 #pragma unroll
             for (int f = 0; f < 20; ++f) h[f] = 0.f;
@@ -971,7 +982,7 @@ int gic_gnn_forward_train(gic_handle *h, const gic_pattern *P, int ngraphs, cons
     for (int l = 0; l < 3; ++l) { B.x[l] = W.x[l]; B.eout[l] = W.eout[l]; }
     B.ein[0] = const_cast<float *>(e0); B.ein[1] = W.eout[0]; B.ein[2] = W.eout[1];
     for (int l = 0; l < 2; ++l) { B.S[l] = W.S[l]; B.M[l] = W.M[l]; }
-    GIC_TRY(gnn_forward_impl(h, p, ngraphs, theta, x9, e0, B, W.mu, W.sig, W.parts));
+    GIC_TRY(gnn_forward_impl(h, p, ngraphs, theta, x9, e0, B, W.mu, W.sig, W.parts, h->tune_train_bf16 != 0));
     GIC_CUDA_TRY(cudaMemcpyAsync(g, W.eout[2], 4 * (size_t)p.nnzL, cudaMemcpyDeviceToDevice, h->stream));
     return GIC_OK;
 }
@@ -1001,7 +1012,8 @@ int gic_gnn_backward(gic_handle *h, const gic_pattern *P, int ngraphs, const flo
             k_agg_bwd<<<grid1(h, E), 256, 0, s>>>(E, p.Lrow, p.Lcol, p.Lrowptr, p.Urowptr, W.dec, W.dS, W.dM, W.de);
         }
         ++h->launches;
-        k_edge_bwd<<<gE, TB, 0, s>>>(E, p.Lrow, p.Lcol, ein[l], e0, W.x[l], theta, l, W.de, W.dh, W.dec, W.pe);
+        k_edge_bwd<<<gE, TB, 0, s>>>(E, p.Lrow, p.Lcol, ein[l], e0, W.x[l], theta, l, W.de, W.dh, W.dec, W.pe,
+                                     h->tune_train_bf16 != 0);
         ++h->launches;
         k_reduce_partials<<<(NP_EDGE + 255) / 256, 256, 0, s>>>(W.pe, gE, NP_EDGE, dtheta + off_edge(l));
         ++h->launches;

@@ -365,6 +365,7 @@ struct gic_handle {
     int tune_pipeline = 4;              // 4: automatic, 3: SM-local, 2: warp-specialised, 1: staged, 0: generic
     int tune_qdelta = 6;                // level window of the "late" columns (pattern analysis)
     int tune_gnn_bf16 = 1;              // GNN inference: edge MLP on the tensor cores in BF16 (0: FP32)
+    int tune_train_bf16 = 0;            // GNN training forward/backward: BF16 edge MLP (1) or FP32 (0)
 };
 
 namespace gic {

@@ -1791,6 +1791,7 @@ int gic_set_tuning(gic_handle *h, int key, int value)
     case GIC_TUNE_PIPELINE: h->tune_pipeline = value; return GIC_OK;
     case GIC_TUNE_QDELTA: h->tune_qdelta = value; return GIC_OK;
     case GIC_TUNE_GNN_BF16: h->tune_gnn_bf16 = value; return GIC_OK;
+    case GIC_TUNE_TRAIN_BF16: h->tune_train_bf16 = value; return GIC_OK;
     default: return GIC_ERR_INVALID_ARG;
     }
 }

@@ -414,28 +414,35 @@ void free_ssched(SliceSched &S)
 static int plan_slices(gic_handle *h, int32_t ngroups, const std::vector<int32_t> &grp, const std::vector<int32_t> &key,
                        const std::vector<int32_t> &cnt, bool forward, SliceSched &S)
 {
+    auto early = [&](int32_t g) { return cnt[g] & 255; };
+    auto late = [&](int32_t g) { return ((cnt[g] >> 8) & 255) + ((cnt[g] >> 16) & 255); };
     int32_t kmin = 0, kmax = 0;
     for (int32_t g = 0; g < ngroups; ++g) {
         if (g == 0 || key[g] < kmin) kmin = key[g];
         if (g == 0 || key[g] > kmax) kmax = key[g];
     }
+    // two stable counting sorts (by descending width, then by key) of the
+    // groups visited in index order in the sweep's direction: sorted by key,
+    // then width, then that index order
+    constexpr int WMAX = 2 * QCOL; // early + late widths are each < QCOL
     const int64_t nk = (int64_t)kmax - kmin + 1;
+    std::vector<int32_t> byw(ngroups), order(ngroups);
+    {
+        std::vector<int64_t> c(WMAX + 1, 0);
+        for (int32_t g = 0; g < ngroups; ++g) ++c[WMAX - (early(g) + late(g))];
+        for (int k = 0; k < WMAX; ++k) c[k + 1] += c[k];
+        for (int32_t q = 0; q < ngroups; ++q) {
+            const int32_t g = forward ? q : ngroups - 1 - q;
+            byw[c[WMAX - 1 - (early(g) + late(g))]++] = g;
+        }
+    }
     std::vector<int64_t> start(nk + 1, 0);
     for (int32_t g = 0; g < ngroups; ++g) ++start[key[g] - kmin + 1];
     for (int64_t k = 0; k < nk; ++k) start[k + 1] += start[k];
-    std::vector<int32_t> order(ngroups);
     {
         std::vector<int64_t> fill(start.begin(), start.end() - 1);
-        for (int32_t q = 0; q < ngroups; ++q) { // stable: index order per key, in the sweep's direction
-            const int32_t g = forward ? q : ngroups - 1 - q;
-            order[fill[key[g] - kmin]++] = g;
-        }
+        for (int32_t q = 0; q < ngroups; ++q) order[fill[key[byw[q]] - kmin]++] = byw[q];
     }
-    auto early = [&](int32_t g) { return cnt[g] & 255; };
-    auto late = [&](int32_t g) { return ((cnt[g] >> 8) & 255) + ((cnt[g] >> 16) & 255); };
-    for (int64_t k = 0; k < nk; ++k)
-        std::stable_sort(order.begin() + start[k], order.begin() + start[k + 1],
-                         [&](int32_t a, int32_t b) { return early(a) + late(a) > early(b) + late(b); });
     std::vector<int32_t> w, we, ng;
     std::vector<int64_t> kv, kc;
     std::vector<int2> lane;

@@ -373,6 +373,7 @@ def error_flags(h: Handle):
 
 
 GIC_TUNE_SOLVE_WARPS_PER_SM, GIC_TUNE_POLL, GIC_TUNE_PIPELINE, GIC_TUNE_QDELTA, GIC_TUNE_GNN_BF16 = 1, 2, 3, 4, 5
+GIC_TUNE_TRAIN_BF16 = 6
 POLL_ONE_LANE = 1 << 16
 
 

@@ -147,6 +147,7 @@ def weights_meta(log):
                      "probes": f"{a['probes']} Gaussian per system", "steps_done": log["steps_done"],
                      "seconds": round(log["train_seconds"], 1), "lr": a["lr"], "warmup_frac": a["warmup_frac"],
                      "epochs": a.get("epochs"), "train_systems": a.get("train_systems"), "mode": a.get("mode"),
+                     "compute": a.get("compute", "fp32") + " edge MLP, FP32 master weights",
                      "kept_step": log.get("best_step"),
                      "validation_means": [[r["step"], r["mean"]] for r in log["val"]],
                      "ic0_shifts_seen": log["ic0_shifts"],
@@ -194,6 +195,8 @@ def main(argv=None):
     ap.add_argument("--val-every", type=int, default=0, help="steps between validations (0: once per epoch)")
     ap.add_argument("--val-N", type=int, default=20)
     ap.add_argument("--mode", default="ic", choices=["ic", "nic"])
+    ap.add_argument("--compute", default="bf16", choices=["bf16", "fp32"],
+                    help="edge-MLP arithmetic of the training forward/backward (FP32 master weights either way)")
     ap.add_argument("--checkpoint", default=None, help="resumable state, written at every validation")
     ap.add_argument("--resume", action="store_true", help="continue from --checkpoint")
     ap.add_argument("--out", required=True)
@@ -202,6 +205,7 @@ def main(argv=None):
     from .autograd import training_loss
 
     h = G.Handle(0)
+    G.set_tuning(h, G.GIC_TUNE_TRAIN_BF16, 1 if a.compute == "bf16" else 0)
     tr = Trainer(h, a.N, a.batch, a.probes, a.seed0, mode=a.mode)
     dev = tr.dev
     nb = max(1, a.train_systems // a.batch)        # batches per epoch (a fixed training set)

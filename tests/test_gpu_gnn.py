@@ -16,6 +16,11 @@ DEV = torch.device("cuda:0")
 # measured 0.7-2.5e-2 relative (norm-wise) against the plain FP64 oracle at
 # 4^3-12^3, against <= 3e-4 when the oracle rounds the same operands
 BF16_VS_FP64 = 5e-2
+# the BF16 training gradient against the oracle's BF16 mode: the two sides
+# round FP32 and FP64 copies of the same inputs, which can differ by one BF16
+# step where a value sits on a rounding boundary, and the tensor-core epilogue
+# uses the hardware tanh
+BF16_TRAIN_GRAD = 5e-3
 
 
 @pytest.fixture(scope="module")
@@ -229,6 +234,37 @@ def test_gnn_backward_matches_oracle(G, h, N, nb):
         errs[name] = _nrel(dth[off:off + sz], ref[off:off + sz])
     for name, e in errs.items():
         assert e <= (1e-2 if name in ("gn_alpha", "gn_gamma") else 1e-3), (name, errs)
+
+
+@pytest.mark.parametrize("N,nb", [(4, 1), (3, 2)])
+def test_gnn_bf16_training_matches_oracle_bf16_mode(G, h, N, nb):
+    """Training in BF16 (config 3: FP32 master weights, BF16 compute): the
+    training forward runs the tensor-core edge MLP, the backward recomputes
+    its hidden layer from the same BF16-rounded inputs and W1 and passes the
+    gradient straight through the rounding; against the oracle's BF16 mode
+    (the same operands rounded, FP64 otherwise) for the output and the full
+    parameter gradient."""
+    G.set_tuning(h, G.GIC_TUNE_TRAIN_BF16, 1)
+    try:
+        P, v, As = _batch(G, h, N, [60 + k for k in range(nb)])
+        x9, e0, scale, _ = G.features(h, P, v, ngraphs=nb)
+        t32, t64 = _theta32(9)
+        th = _dev(t32)
+        ws = G.gnn_workspace(h, P, nb, training=True)
+        g = _np(G.gnn_forward_train(h, P, th, x9, e0, ws, ngraphs=nb))
+        nnzL = (As[0].nnz + As[0].n) // 2
+        dg = np.random.default_rng(11).standard_normal(nnzL * nb).astype(np.float32)
+        dth = _np(G.gnn_backward(h, P, th, x9, e0, _dev(dg), ws, ngraphs=nb))
+    finally:
+        G.set_tuning(h, G.GIC_TUNE_TRAIN_BF16, 0)
+    ref = np.zeros(t64.size)
+    for k, A in enumerate(As):
+        T = O.lower(A)
+        ox9, oe0, _ = O.features(A)
+        og = O.gnn_forward(T, ox9, oe0, t64, bf16=True)
+        assert _nrel(g[k * nnzL:(k + 1) * nnzL], og) <= 1e-3
+        ref += O.gnn_backward(T, ox9, oe0, t64, dg[k * nnzL:(k + 1) * nnzL].astype(np.float64), bf16=True)
+    assert _nrel(dth, ref) <= BF16_TRAIN_GRAD, _nrel(dth, ref)
 
 
 def test_gnn_backward_deterministic(G, h):
