@@ -303,20 +303,22 @@ int bsr_spmv(gic_handle *h, const Pattern &P, int mode, const double *bval, cons
 {
     ++h->launches;
     // a warp per slice of 32 nodes, the grid striding over the slices; with
-    // fewer slices than 24 warps per SM, a warp per quarter slice
-    const int lpn = (P.bsr_nsl < 24 * (int64_t)h->num_sms) ? 4 : 1;
+    // fewer slices than 24 warps per SM, a warp per half slice (measured at
+    // 40^3: 55.5 us with whole slices, 50.0 us with halves, 53.0 us with
+    // quarters)
+    const int lpn = (P.bsr_nsl < 24 * (int64_t)h->num_sms) ? 2 : 1;
     const unsigned grid = bgrid(h, P.bsr_nsl * 32 * lpn, 8);
     const int64_t n = P.n, ns = P.bsr_nsl;
     if (mode == 1) {
-        if (lpn == 4)
-            k_spmv_bsr<1, 4><<<grid, BSR_BLOCK, 0, h->stream>>>(n, ns, P.bsr_ptr, P.bsr_w, P.bsr_col, bval, x, y,
+        if (lpn == 2)
+            k_spmv_bsr<1, 2><<<grid, BSR_BLOCK, 0, h->stream>>>(n, ns, P.bsr_ptr, P.bsr_w, P.bsr_col, bval, x, y,
                                                                  nullptr, partials, sc);
         else
             k_spmv_bsr<1, 1><<<grid, BSR_BLOCK, 0, h->stream>>>(n, ns, P.bsr_ptr, P.bsr_w, P.bsr_col, bval, x, y,
                                                                  nullptr, partials, sc);
     } else {
-        if (lpn == 4)
-            k_spmv_bsr<2, 4><<<grid, BSR_BLOCK, 0, h->stream>>>(n, ns, P.bsr_ptr, P.bsr_w, P.bsr_col, bval, x, y, b,
+        if (lpn == 2)
+            k_spmv_bsr<2, 2><<<grid, BSR_BLOCK, 0, h->stream>>>(n, ns, P.bsr_ptr, P.bsr_w, P.bsr_col, bval, x, y, b,
                                                                  partials, sc);
         else
             k_spmv_bsr<2, 1><<<grid, BSR_BLOCK, 0, h->stream>>>(n, ns, P.bsr_ptr, P.bsr_w, P.bsr_col, bval, x, y, b,
