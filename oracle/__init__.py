@@ -292,10 +292,16 @@ def round_bf16(v):
     return np.array([f(float(t)) for t in np.ravel(v)]).reshape(np.shape(v))
 
 
+def _bf16_bits(bf16):
+    """bf16: False / True (the edge MLP's first layer) or the oracle's bit set
+    (1 edge MLP, 2 node MLP, 3 both: the tensor-core inference path)."""
+    return int(bf16)
+
+
 def gnn_forward(T: CSR, x9, e0, theta, bf16=False):
     g = np.zeros(T.nnz)
     lib().or_gnn_forward(T.n, T.rowptr, T.col, _c64(x9).ravel(), _c64(e0), _c64(theta),
-                         1 if bf16 else 0, g)
+                         _bf16_bits(bf16), g)
     return g
 
 
@@ -307,7 +313,7 @@ def gnn_forward_parts(T: CSR, x9, e0, theta, bf16=False):
     x0, x1 = np.zeros(9 * n), np.zeros(9 * n)
     S0, M0 = np.zeros(n), np.zeros(n)
     lib().or_gnn_forward_parts(T.n, T.rowptr, T.col, _c64(x9).ravel(), _c64(e0), _c64(theta),
-                               1 if bf16 else 0, g, x0, S0, M0, x1)
+                               _bf16_bits(bf16), g, x0, S0, M0, x1)
     return g, x0.reshape(n, 9), S0, M0, x1.reshape(n, 9)
 
 
@@ -326,7 +332,7 @@ def correct_backward(T: CSR, LIC_val, g, dLout):
 def gnn_backward(T: CSR, x9, e0, theta, dg, bf16=False):
     d = np.zeros(gnn_param_count())
     lib().or_gnn_backward(T.n, T.rowptr, T.col, _c64(x9).ravel(), _c64(e0), _c64(theta),
-                          1 if bf16 else 0, _c64(dg), d)
+                          _bf16_bits(bf16), _c64(dg), d)
     return d
 
 

@@ -597,9 +597,12 @@ void or_features(int64_t n, const int32_t *rowptr, const int32_t *col, const dou
  * Correction  (in units scaled by s): off-diagonal Lhat_ij = LhatIC_ij + g_ij,
  *             diagonal Lhat_ii = LhatIC_ii * exp(g_ii / 2), i.e. the exp then
  *             sqrt positivity map applied multiplicatively to L_IC.
- * With bf16 != 0 the inputs of the first edge-MLP layer (W1 and h) are
- * rounded to bfloat16 (round to nearest even) before an exact FP64 product,
- * which is what BF16 weights with FP32 accumulation compute.
+ * bf16 is a bit set of the operands rounded to bfloat16 (round to nearest
+ * even) before an exact FP64 product, which is what BF16 weights with FP32
+ * accumulation compute: bit 0 (value 1) the edge MLP's first layer (W1 and
+ * its input h); bit 1 (value 2) both layers of the node MLP (W3 and its input
+ * [x, S, M]; W4 and the tanh output). The backward pass honours bit 0 only
+ * (the node-MLP rounding is an inference mode).
  * ====================================================================== */
 #define GH 32
 #define GPAR_GN 27
@@ -714,13 +717,13 @@ static void gnn_forward_tape(int64_t n, const int32_t *Lrowptr, const int32_t *L
                 h[1] = e0[p];
                 for (int f = 0; f < 9; ++f) h[2 + f] = xl[9 * i + f];
                 for (int f = 0; f < 9; ++f) h[11 + f] = xl[9 * (int64_t)j + f];
-                if (bf16)
+                if (bf16 & 1)
                     for (int f = 0; f < 20; ++f) h[f] = or_round_bf16(h[f]);
                 double out = b2[0];
                 for (int u = 0; u < GH; ++u) {
                     double z = b1[u];
                     for (int f = 0; f < 20; ++f) {
-                        double w = bf16 ? or_round_bf16(W1[u * 20 + f]) : W1[u * 20 + f];
+                        double w = (bf16 & 1) ? or_round_bf16(W1[u * 20 + f]) : W1[u * 20 + f];
                         z += w * h[f];
                     }
                     double a = tanh(z);
@@ -750,14 +753,18 @@ static void gnn_forward_tape(int64_t n, const int32_t *Lrowptr, const int32_t *L
             u_in[9] = S[v];
             u_in[10] = M[v];
             double *a3 = t->a3[l] + v * GH;
+            const int rn = (bf16 & 2) != 0;
+            if (rn)
+                for (int f = 0; f < 11; ++f) u_in[f] = or_round_bf16(u_in[f]);
             for (int u = 0; u < GH; ++u) {
                 double z = b3[u];
-                for (int f = 0; f < 11; ++f) z += W3[u * 11 + f] * u_in[f];
+                for (int f = 0; f < 11; ++f) z += (rn ? or_round_bf16(W3[u * 11 + f]) : W3[u * 11 + f]) * u_in[f];
                 a3[u] = tanh(z);
             }
             for (int f = 0; f < 9; ++f) {
                 double o = b4[f];
-                for (int u = 0; u < GH; ++u) o += W4[f * GH + u] * a3[u];
+                for (int u = 0; u < GH; ++u)
+                    o += rn ? or_round_bf16(W4[f * GH + u]) * or_round_bf16(a3[u]) : W4[f * GH + u] * a3[u];
                 t->x[l + 1][9 * v + f] = o;
             }
         }
@@ -824,6 +831,7 @@ void or_gnn_backward(int64_t n, const int32_t *Lrowptr, const int32_t *Lcol, con
     or_gnn_tape t;
     tape_alloc(&t, n, E);
     double *g = (double *)malloc(sizeof(double) * (size_t)(E > 0 ? E : 1));
+    bf16 &= 1; /* the node-MLP rounding is an inference mode */
     gnn_forward_tape(n, Lrowptr, Lcol, x9, e0, theta, bf16, g, &t);
     free(g);
     memset(dtheta, 0, sizeof(double) * GPAR_TOTAL);
@@ -900,7 +908,7 @@ void or_gnn_backward(int64_t n, const int32_t *Lrowptr, const int32_t *Lcol, con
                     double dz = d * W2[u] * (1.0 - a1[u] * a1[u]);
                     db1[u] += dz;
                     for (int f = 0; f < 20; ++f) {
-                        double w = bf16 ? or_round_bf16(W1[u * 20 + f]) : W1[u * 20 + f];
+                        double w = (bf16 & 1) ? or_round_bf16(W1[u * 20 + f]) : W1[u * 20 + f];
                         dW1[u * 20 + f] += dz * h[f];
                         dh[f] += w * dz;
                     }

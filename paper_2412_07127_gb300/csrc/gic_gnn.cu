@@ -237,18 +237,6 @@ __global__ void __launch_bounds__(256) k_edge_fwd(int64_t E, const int32_t *__re
 
 // sum / mean aggregation of edge values at node v: its L row, then the
 // off-diagonal entries of its U row (edges (i, v), i > v).
-__device__ __forceinline__ void aggregate(int64_t v, const int32_t *Lrowptr, const int32_t *Urowptr,
-                                          const int32_t *tperm, const float *e, float &S, float &M)
-{
-    float s = 0.f;
-    const int32_t la = Lrowptr[v], lb = Lrowptr[v + 1];
-    for (int32_t p = la; p < lb; ++p) s += e[p];
-    const int32_t ua = Urowptr[v], ub = Urowptr[v + 1];
-    for (int32_t q = ua + 1; q < ub; ++q) s += e[tperm[q]];
-    S = s;
-    M = s / (float)((lb - la) + (ub - ua) - 1);
-}
-
 // Node MLP: xout = W4 tanh(W3 [x, S, M] + b3) + b4. Saves S, M if asked.
 __global__ void __launch_bounds__(256) k_node_fwd(int64_t n, const int32_t *__restrict__ Lrowptr,
                                                   const int32_t *__restrict__ Urowptr, const int32_t *__restrict__ tperm,
@@ -265,7 +253,7 @@ __global__ void __launch_bounds__(256) k_node_fwd(int64_t n, const int32_t *__re
     __syncthreads();
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         float S, M;
-        aggregate(v, Lrowptr, Urowptr, tperm, e, S, M);
+        gnn_aggregate(v, Lrowptr, Urowptr, tperm, e, S, M);
         if (Ssave) {
             Ssave[v] = S;
             Msave[v] = M;
@@ -830,12 +818,16 @@ struct FwdBufs {
 
 int edge_fwd_tc(gic_handle *h, int64_t E, const int32_t *Lrow, const int32_t *Lcol, const float *ein,
                 const float *e0, const float *x, const float *theta, int l, float *eout);
+int node_fwd_tc(gic_handle *h, int64_t n, const int32_t *Lrowptr, const int32_t *Urowptr, const int32_t *tperm,
+                const float *e, const float *x, const float *theta, int l, float *xout);
 
 // bf16: the edge MLP's first layer on the tensor cores (BF16 inputs and W1,
-// FP32 accumulation; gic_gnn_tc.cu), else FP32 on the CUDA cores
+// FP32 accumulation; gic_gnn_tc.cu), else FP32 on the CUDA cores; bf16_node:
+// the node MLP's two layers too (inference only: the training backward of
+// the node MLP is FP32)
 static int gnn_forward_impl(gic_handle *h, const Pattern &p, int ngraphs, const float *theta, const float *x9,
                             const float *e0, const FwdBufs &B, double *mu, double *sig, double *parts,
-                            bool bf16 = false)
+                            bool bf16 = false, bool bf16_node = false)
 {
     GIC_TRY(graphnorm(h, p, ngraphs, theta, x9, B.x[0], mu, sig, parts));
     const int64_t E = p.nnzL;
@@ -848,9 +840,13 @@ static int gnn_forward_impl(gic_handle *h, const Pattern &p, int ngraphs, const 
                                                            B.eout[l]);
         }
         if (l < 2) {
-            ++h->launches;
-            k_node_fwd<<<grid1(h, p.n), 256, 0, h->stream>>>(p.n, p.Lrowptr, p.Urowptr, p.tperm, B.eout[l], B.x[l],
-                                                            theta, l, B.x[l + 1], B.S[l], B.M[l]);
+            if (bf16_node && !B.S[l]) {
+                GIC_TRY(node_fwd_tc(h, p.n, p.Lrowptr, p.Urowptr, p.tperm, B.eout[l], B.x[l], theta, l, B.x[l + 1]));
+            } else {
+                ++h->launches;
+                k_node_fwd<<<grid1(h, p.n), 256, 0, h->stream>>>(p.n, p.Lrowptr, p.Urowptr, p.tperm, B.eout[l],
+                                                                B.x[l], theta, l, B.x[l + 1], B.S[l], B.M[l]);
+            }
         }
         GIC_CUDA_TRY(cudaGetLastError());
     }
@@ -965,7 +961,8 @@ int gic_gnn_forward(gic_handle *h, const gic_pattern *P, int ngraphs, const floa
     B.ein[0] = const_cast<float *>(e0); B.eout[0] = W.ea;
     B.ein[1] = W.ea; B.eout[1] = W.eb;
     B.ein[2] = W.eb; B.eout[2] = g;
-    return gnn_forward_impl(h, p, ngraphs, theta, x9, e0, B, W.mu, W.sig, W.parts, h->tune_gnn_bf16 != 0);
+    return gnn_forward_impl(h, p, ngraphs, theta, x9, e0, B, W.mu, W.sig, W.parts, h->tune_gnn_bf16 != 0,
+                            h->tune_gnn_bf16 != 0);
 }
 
 int gic_gnn_forward_train(gic_handle *h, const gic_pattern *P, int ngraphs, const float *theta, const float *x9,

@@ -43,11 +43,18 @@ __device__ __forceinline__ uint32_t tc_off(int row, int k)
     return (uint32_t)((row >> 3) * 512 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
-__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr)
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint64_t sbo = 512)
 {
-    const uint64_t lbo = 128, sbo = 512;
+    const uint64_t lbo = 128;
     return (uint64_t)((saddr >> 4) & 0x3FFF) | (((lbo >> 4) & 0x3FFF) << 16) | (((sbo >> 4) & 0x3FFF) << 32) |
            (1ull << 46); // descriptor version 1, base offset 0, no swizzle
+}
+
+// the same layout for a tile whose K is 16 (two core matrices along K: rows
+// of core matrices 256 bytes apart)
+__device__ __forceinline__ uint32_t tc_off16(int row, int k)
+{
+    return (uint32_t)((row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
 // kind::f16 instruction descriptor: D FP32, A and B BF16, both K-major,
@@ -211,6 +218,205 @@ int edge_fwd_tc(gic_handle *h, int64_t E, const int32_t *Lrow, const int32_t *Lc
     if (tiles < 1) tiles = 1;
     ++h->launches;
     k_edge_fwd_tc<<<(unsigned)tiles, TC_M, 0, h->stream>>>(E, Lrow, Lcol, ein, e0, x, theta, l, eout, h->dev_err);
+    GIC_CUDA_TRY(cudaGetLastError());
+    return GIC_OK;
+}
+
+
+// ------------------------------------------------------------ node MLP
+// Per block the node MLP maps every node's input u = [x (9), S, M] to
+//     x_new = W4 tanh(W3 u + b3) + b4,   W3: 32 x 11, W4: 9 x 32,
+// two (nodes x K) by (K x N) products: (n x 11)(11 x 32) and (n x 32)(32 x 9).
+// A CTA takes tiles of 128 nodes: each thread aggregates its node's S and M,
+// rounds u to BF16 into shared memory (K padded 11 -> 16), one thread issues
+// the first MMA (M 128, N 32, K 16) into TMEM columns 0-31; every thread reads
+// its 32 accumulators, adds b3, applies tanh (the accurate one: the hardware
+// approximation's error would move the BF16 rounding of the activations that
+// follows), rounds the activations to BF16
+// into a second K-major tile (K = 32), and one thread issues the second
+// product (N 16 with W4 padded from 9 rows, two K-steps) into columns 32-47;
+// the threads read their 9 outputs and add b4.
+constexpr int TN_K1 = 16;            // padded node-MLP input width
+constexpr int TN_N2 = 16;            // padded output width (9)
+constexpr uint32_t TN_COLS = 64;     // TMEM columns: hidden 0-31, outputs 32-47
+constexpr uint32_t TN_IDESC1 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
+                               ((uint32_t)(TC_M >> 4) << 24);
+constexpr uint32_t TN_IDESC2 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN_N2 >> 3) << 17) |
+                               ((uint32_t)(TC_M >> 4) << 24);
+
+__device__ __forceinline__ int tc_off_node(int l) { return tc_off_edge(l) + TC_NP_EDGE; }
+
+__device__ __forceinline__ bool tc_wait(uint32_t mb, uint32_t phase, unsigned *err)
+{
+    int done = 0;
+    for (long long it = 0; it < (SPIN_LIMIT >> 2) && !done; ++it) {
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(mb), "r"(phase)
+                     : "memory");
+    }
+    if (!done) atomicOr(err, ERR_TIMEOUT);
+    return done != 0;
+}
+
+__global__ void __launch_bounds__(TC_M) k_node_fwd_tc(int64_t n, const int32_t *__restrict__ Lrowptr,
+                                                      const int32_t *__restrict__ Urowptr,
+                                                      const int32_t *__restrict__ tperm, const float *__restrict__ e,
+                                                      const float *__restrict__ x, const float *__restrict__ theta,
+                                                      int l, float *__restrict__ xout, unsigned *err)
+{
+    __shared__ __align__(128) unsigned char sA1[TC_M * TN_K1 * 2];
+    __shared__ __align__(128) unsigned char sB1[TC_N * TN_K1 * 2];
+    __shared__ __align__(128) unsigned char sA2[TC_M * TC_K * 2];
+    __shared__ __align__(128) unsigned char sB2[TN_N2 * TC_K * 2];
+    __shared__ float b3[TC_N], b4[TN_N2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ __align__(8) unsigned long long mbar;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const float *P = theta + tc_off_node(l);
+    const float *W3 = P, *W4 = P + TC_N * 11 + TC_N;
+    for (int idx = tid; idx < TC_N * TN_K1; idx += TC_M) {
+        const int r = idx / TN_K1, k = idx % TN_K1;
+        *(uint16_t *)(sB1 + tc_off16(r, k)) = tc_bf16(k < 11 ? W3[r * 11 + k] : 0.0f);
+    }
+    for (int idx = tid; idx < TN_N2 * TC_K; idx += TC_M) {
+        const int f = idx / TC_K, k = idx % TC_K;
+        *(uint16_t *)(sB2 + tc_off(f, k)) = tc_bf16(f < 9 ? W4[f * TC_N + k] : 0.0f);
+    }
+    if (tid < TC_N) b3[tid] = P[TC_N * 11 + tid];
+    if (tid < TN_N2) b4[tid] = (tid < 9) ? P[TC_N * 11 + TC_N + 9 * TC_N + tid] : 0.0f;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(&tmem_slot)),
+                     "r"(TN_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const uint32_t a1 = (uint32_t)__cvta_generic_to_shared(sA1), bb1 = (uint32_t)__cvta_generic_to_shared(sB1);
+    const uint32_t a2 = (uint32_t)__cvta_generic_to_shared(sA2), bb2 = (uint32_t)__cvta_generic_to_shared(sB2);
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar);
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16; // this warp's TMEM lanes
+    uint32_t phase = 0;
+    const int64_t ntiles = (n + TC_M - 1) / TC_M;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t v = tile * TC_M + tid;
+        const bool valid = v < n;
+        float u[TN_K1];
+#pragma unroll
+        for (int f = 0; f < TN_K1; ++f) u[f] = 0.0f;
+        if (valid) {
+            float S, M;
+            gnn_aggregate(v, Lrowptr, Urowptr, tperm, e, S, M);
+#pragma unroll
+            for (int f = 0; f < 9; ++f) u[f] = x[9 * v + f];
+            u[9] = S;
+            u[10] = M;
+        }
+        *(uint4 *)(sA1 + tc_off16(tid, 0)) =
+            make_uint4(tc_pack(u[0], u[1]), tc_pack(u[2], u[3]), tc_pack(u[4], u[5]), tc_pack(u[6], u[7]));
+        *(uint4 *)(sA1 + tc_off16(tid, 8)) =
+            make_uint4(tc_pack(u[8], u[9]), tc_pack(u[10], u[11]), tc_pack(u[12], u[13]), tc_pack(u[14], u[15]));
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            const uint64_t ad = tc_desc(a1, 256), bd = tc_desc(bb1, 256);
+            asm volatile("{\n\t.reg .pred acc;\n\t"
+                         "setp.ne.b32 acc, %4, 0;\n\t"
+                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, acc;\n\t}" ::"r"(tmem),
+                         "l"(ad), "l"(bd), "r"(TN_IDESC1), "r"(0));
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
+                         : "memory");
+        }
+        const bool ok1 = tc_wait(mb, phase, err);
+        phase ^= 1u;
+        if (!__syncthreads_and(ok1)) break; // the accumulator may still be written: stop using it
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        uint32_t r[32];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                     "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+                     "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                       "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                       "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+                       "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+                       "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                     : "r"(tmem + lane_base));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        float a[TC_N];
+#pragma unroll
+        for (int k = 0; k < TC_N; ++k) a[k] = tanhf(__uint_as_float(r[k]) + b3[k]); // rounded to BF16 next
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            *(uint4 *)(sA2 + tc_off(tid, 8 * c)) =
+                make_uint4(tc_pack(a[8 * c], a[8 * c + 1]), tc_pack(a[8 * c + 2], a[8 * c + 3]),
+                           tc_pack(a[8 * c + 4], a[8 * c + 5]), tc_pack(a[8 * c + 6], a[8 * c + 7]));
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+#pragma unroll
+            for (int s2 = 0; s2 < 2; ++s2) {
+                const uint64_t ad = tc_desc(a2 + s2 * 256), bd = tc_desc(bb2 + s2 * 256);
+                asm volatile("{\n\t.reg .pred acc;\n\t"
+                             "setp.ne.b32 acc, %4, 0;\n\t"
+                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, acc;\n\t}" ::"r"(tmem + 32u),
+                             "l"(ad), "l"(bd), "r"(TN_IDESC2), "r"(s2));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
+                         : "memory");
+        }
+        const bool ok2 = tc_wait(mb, phase, err);
+        phase ^= 1u;
+        if (!__syncthreads_and(ok2)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        uint32_t o[16];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                     "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                     : "=r"(o[0]), "=r"(o[1]), "=r"(o[2]), "=r"(o[3]), "=r"(o[4]), "=r"(o[5]), "=r"(o[6]),
+                       "=r"(o[7]), "=r"(o[8]), "=r"(o[9]), "=r"(o[10]), "=r"(o[11]), "=r"(o[12]), "=r"(o[13]),
+                       "=r"(o[14]), "=r"(o[15])
+                     : "r"(tmem + lane_base + 32u));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (valid) {
+#pragma unroll
+            for (int f = 0; f < 9; ++f) xout[9 * v + f] = __uint_as_float(o[f]) + b4[f];
+        }
+        // every thread's TMEM reads (and the tile's shared-memory reads by the
+        // MMAs) finish before the next tile overwrites them
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN_COLS));
+}
+
+int node_fwd_tc(gic_handle *h, int64_t n, const int32_t *Lrowptr, const int32_t *Urowptr, const int32_t *tperm,
+                const float *e, const float *x, const float *theta, int l, float *xout)
+{
+    // up to 8 CTAs per SM (8 x 64 TMEM columns = the SM's 512)
+    int64_t tiles = (n + TC_M - 1) / TC_M, cap = (int64_t)h->num_sms * 8;
+    if (tiles > cap) tiles = cap;
+    if (tiles < 1) tiles = 1;
+    ++h->launches;
+    k_node_fwd_tc<<<(unsigned)tiles, TC_M, 0, h->stream>>>(n, Lrowptr, Urowptr, tperm, e, x, theta, l, xout,
+                                                           h->dev_err);
     GIC_CUDA_TRY(cudaGetLastError());
     return GIC_OK;
 }

@@ -340,6 +340,22 @@ constexpr int MAXDIM = 48; // max lower entries of a row handled by IC(0)
 }  // namespace gic
 
 namespace gic {
+// Node v's aggregation of the edge values e of the lower pattern with its
+// diagonal (Section "Model Architecture"): every edge sends its value to both
+// endpoints, a self-loop once; S = the sum, M = the mean over the incident
+// edges (v's L row, then the strictly upper part of its U row).
+__device__ __forceinline__ void gnn_aggregate(int64_t v, const int32_t *Lrowptr, const int32_t *Urowptr,
+                                              const int32_t *tperm, const float *e, float &S, float &M)
+{
+    float s = 0.f;
+    const int32_t la = Lrowptr[v], lb = Lrowptr[v + 1];
+    for (int32_t p = la; p < lb; ++p) s += e[p];
+    const int32_t ua = Urowptr[v], ub = Urowptr[v + 1];
+    for (int32_t q = ua + 1; q < ub; ++q) s += e[tperm[q]];
+    S = s;
+    M = s / (float)((lb - la) + (ub - ua) - 1);
+}
+
 // level-sliced schedule of a pattern (gic_ssolve.cu)
 int build_ssched(gic_handle *h, Pattern &P);
 void free_ssched(SliceSched &S);

@@ -62,10 +62,9 @@ static SliceView view_of(const SliceSched &S)
 // Wait until no lane of the warp holds a sentinel among its B values: all
 // pending words are reloaded together each round (the values of a wave come
 // from several slices and land at different times, so polling them one at a
-// time would serialise their round trips: measured 1.5x slower), with a
-// back-off between rounds (NEAR: only after the first 32 rounds); bounded
-// (then ERR_TIMEOUT and NaN values).
-template <typename T, int B, bool NEAR>
+// time would serialise their round trips: measured 1.5x slower), with a short
+// back-off after the first rounds; bounded (then ERR_TIMEOUT and NaN values).
+template <typename T, int B>
 __device__ __forceinline__ void s_wait(const T *x, const int32_t (&c)[B], T (&v)[B], unsigned *err,
                                        unsigned sleep_ns, int lane)
 {
@@ -86,10 +85,7 @@ __device__ __forceinline__ void s_wait(const T *x, const int32_t (&c)[B], T (&v)
                 if (c[b] >= 0 && is_sentinel(v[b])) v[b] = qnan_of<T>();
             return;
         }
-        // the near wave polls tight (its hand-off is the sweep's critical
-        // path); the other waits are taken well ahead of their data and back
-        // off from the first round, which keeps their polls out of the L2
-        if (NEAR ? it >= 32 : true) __nanosleep(it >= 65536 ? 256 : (NEAR ? 32 : (sleep_ns ? sleep_ns : 96)));
+        if (it >= 32) __nanosleep(it >= 65536 ? 256 : (sleep_ns ? sleep_ns : 32));
     }
 }
 
@@ -174,7 +170,7 @@ __global__ void __launch_bounds__(SBLOCK, 2) k_ssolve(SliceView S, const T *__re
                 cn[b] = (act && k < We) ? cp[(int64_t)k * ng] : -1;
                 kn[b] = (k < We) ? kp[(int64_t)k * 32] : (T)0;
             }
-            s_wait<T, SBATCH, false>(x, c, v, err, sleep_ns, lane);
+            s_wait<T, SBATCH>(x, c, v, err, sleep_ns, lane);
 #pragma unroll
             for (int b = 0; b < SBATCH; ++b) {
                 if (k0 + b < We) { // uniform over the warp
@@ -212,7 +208,7 @@ __global__ void __launch_bounds__(SBLOCK, 2) k_ssolve(SliceView S, const T *__re
 #pragma unroll
             for (int b = 0; b < SNEAR; ++b) vn[b] = (cn2[b] >= 0) ? ld_relaxed(x + cn2[b]) : (T)0;
             cp_async_wait<0>(); // this lane's late coefficients are in shared memory
-            s_wait<T, SFAR, false>(x, cf, vf, err, sleep_ns, lane);
+            s_wait<T, SFAR>(x, cf, vf, err, sleep_ns, lane);
 #pragma unroll
             for (int b = 0; b < SFAR; ++b) {
                 if (b < Wf) { // uniform over the warp
@@ -223,7 +219,7 @@ __global__ void __launch_bounds__(SBLOCK, 2) k_ssolve(SliceView S, const T *__re
                     else acc3 = fma(kb, vf[b], acc3);
                 }
             }
-            s_wait<T, SNEAR, true>(x, cn2, vn, err, sleep_ns, lane);
+            s_wait<T, SNEAR>(x, cn2, vn, err, sleep_ns, lane);
 #pragma unroll
             for (int b = 0; b < SNEAR; ++b) {
                 if (b < Wn) {

@@ -56,12 +56,13 @@ def _dense_gnn(T, x9, e0, theta, bf16=False):
             S = B @ e_new
             M = S / deg
             u = np.concatenate([x, S[:, None], M[:, None]], axis=1)
-            x = np.tanh(u @ P(f"W3_{l}").T + P(f"b3_{l}")) @ P(f"W4_{l}").T + P(f"b4_{l}")
+            rn = (lambda a: O.round_bf16(a)) if bf16 == 3 else (lambda a: a)
+            x = rn(np.tanh(rn(u) @ rn(P(f"W3_{l}")).T + P(f"b3_{l}"))) @ rn(P(f"W4_{l}")).T + P(f"b4_{l}")
         e = e_new
     return e
 
 
-@pytest.mark.parametrize("bf16", [False, True])
+@pytest.mark.parametrize("bf16", [False, True, 3])
 def test_gnn_forward_matches_dense_restatement(bf16):
     N = 2
     A = O.fem_hex_assemble(N, I.material_field(N, 3))
