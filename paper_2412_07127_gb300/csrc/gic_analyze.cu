@@ -314,39 +314,69 @@ __global__ void k_group_stats(int32_t ngroups, const int32_t *grp, const int32_t
     atomicMax(&stats[2], mG);
 }
 
-// Row levels, one warp per group, sync-free: level[] starts at -1 and every
-// row's level is written once; a warp waits (bounded) for the levels of its
-// group's external lower columns. Groups are taken in round-robin order by a
-// co-resident grid, so the smallest unfinished group always progresses.
-__global__ void k_levels(int32_t ngroups, const int32_t *grp, const int32_t *Lrowptr, const int32_t *Lcol,
-                         int32_t *level, int32_t *maxlev, unsigned *err)
+// Chains for k_levels: group g continues the chain of group g-1 when its
+// first row reads a row of group g-1 (the last external lower column of that
+// row is at or after group g-1's first row; columns are sorted ascending).
+__global__ void k_chain_flags(int32_t ngroups, const int32_t *grp, const int32_t *Lrowptr, const int32_t *Lcol,
+                              int32_t *cflag)
+{
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = grp[g];
+        const int32_t m = Lrowptr[s + 1] - Lrowptr[s] - 1; // external lower columns of the first row
+        cflag[g] = (g == 0) || m == 0 || Lcol[Lrowptr[s + 1] - 2] < grp[g - 1];
+    }
+}
+
+// Row levels, sync-free: level[] starts at -1 and every row's level is written
+// once. A warp takes one chain (a maximal run of consecutive groups each of
+// which reads the one before it) and does its groups in order, waiting
+// (bounded) for the levels of each group's external lower columns; chains
+// are taken in round-robin order by a co-resident grid, so the first
+// unfinished chain always progresses (its inputs lie in earlier chains or
+// earlier in itself). Chains rather than single groups: taking groups one by
+// one in index order keeps at most one grid's worth of consecutive groups in
+// flight, and on a structured mesh that window is a fraction of a plane of
+// nodes whose dependency chains then serialise plane after plane. A chain is
+// itself sequential (each group's level exceeds its predecessor's), so
+// walking it in one warp replaces a cross-warp hand-off per group by a step
+// within the warp; on a lexicographic mesh the chains are the rows of nodes
+// along x.
+__global__ void k_levels(int32_t nchains, const int32_t *chain, const int32_t *grp, const int32_t *Lrowptr,
+                         const int32_t *Lcol, int32_t *level, int32_t *maxlev, unsigned *err)
 {
     int lane = threadIdx.x & 31;
     int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int mx_all = 0;
-    for (int64_t g = w; g < ngroups; g += nw) {
-        int32_t s = grp[g], e = grp[g + 1] - 1;
-        int32_t b0 = Lrowptr[s];
-        int32_t m = Lrowptr[s + 1] - b0 - 1;
-        int mx = -1;
-        for (int32_t k = lane; k < m; k += 32) {
-            int32_t j = Lcol[b0 + k];
-            int v = ld_acquire_i32(level + j);
-            long long it = 0;
-            while (v < 0 && it < SPIN_LIMIT) {
-                if (it > 32) __nanosleep(64);
-                v = ld_acquire_i32(level + j);
-                ++it;
-                if ((it & 1023) == 0 && *((volatile unsigned *)err) != 0u) break;
+    for (int64_t c = w; c < nchains; c += nw) {
+        const int32_t g1 = chain[c + 1];
+        for (int32_t g = chain[c]; g < g1; ++g) {
+            int32_t s = grp[g], e = grp[g + 1] - 1;
+            int32_t b0 = Lrowptr[s];
+            int32_t m = Lrowptr[s + 1] - b0 - 1;
+            int mx = -1;
+            for (int32_t k = lane; k < m; k += 64) {
+                // two columns per lane in flight at once
+                bool two = k + 32 < m;
+                int32_t j0 = Lcol[b0 + k], j1 = two ? Lcol[b0 + k + 32] : j0;
+                int v0 = ld_acquire_i32(level + j0), v1 = ld_acquire_i32(level + j1);
+                long long it = 0;
+                while ((v0 < 0 || v1 < 0) && it < SPIN_LIMIT) {
+                    if (it > 32) __nanosleep(64);
+                    if (v0 < 0) v0 = ld_acquire_i32(level + j0);
+                    if (v1 < 0) v1 = ld_acquire_i32(level + j1);
+                    ++it;
+                    if ((it & 1023) == 0 && *((volatile unsigned *)err) != 0u) break;
+                }
+                if (v0 < 0 || v1 < 0) { atomicOr(err, ERR_TIMEOUT); v0 = max(v0, 0); v1 = max(v1, 0); }
+                mx = max(mx, max(v0, v1));
             }
-            if (v < 0) { atomicOr(err, ERR_TIMEOUT); v = 0; }
-            mx = max(mx, v);
-        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane <= e - s) st_release_i32(level + s + lane, mx + 1 + lane);
-        mx_all = max(mx_all, mx + 1 + (e - s));
+            for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (lane <= e - s) st_release_i32(level + s + lane, mx + 1 + lane);
+            mx_all = max(mx_all, mx + 1 + (e - s));
+            __syncwarp(); // this group's levels are visible to the warp's next group
+        }
     }
     if (lane == 0) atomicMax(maxlev, mx_all);
 }
@@ -895,12 +925,21 @@ static int analyze_impl(gic_handle *h, int64_t n, int64_t nnz, const int32_t *ro
     CUDA_STEP(cudaMalloc(&P.level, sizeof(int32_t) * (size_t)n));
     CUDA_STEP(cudaMemsetAsync(P.level, 0xff, sizeof(int32_t) * (size_t)n, h->stream));
     {
+        // chains of groups (flags in gflag, their index in gid, starts in key)
         int32_t ng = P.ngroups;
-        const int32_t *g_ = P.grp, *lr = P.Lrowptr, *lc = P.Lcol;
+        ++h->launches;
+        k_chain_flags<<<grid_rows(h, ng), T_ROWS, 0, h->stream>>>(ng, P.grp, P.Lrowptr, P.Lcol, gflag);
+        CUDA_STEP(cudaGetLastError());
+        STEP(scan_i32<false>(h, gflag, ng, gid, &tot));
+        int32_t nch = (int32_t)tot;
+        ++h->launches;
+        k_group_starts<<<grid_rows(h, ng), T_ROWS, 0, h->stream>>>(ng, gflag, gid, key, nch);
+        CUDA_STEP(cudaGetLastError());
+        const int32_t *ch = key, *g_ = P.grp, *lr = P.Lrowptr, *lc = P.Lcol;
         int32_t *lv = P.level, *ml = stats + 3;
         unsigned *er = h->dev_err;
-        void *args[] = {&ng, &g_, &lr, &lc, &lv, &ml, &er};
-        STEP(launch_persistent(h, (const void *)k_levels, 256, 0, ng, args));
+        void *args[] = {&nch, &ch, &g_, &lr, &lc, &lv, &ml, &er};
+        STEP(launch_persistent(h, (const void *)k_levels, 256, 0, nch, args));
     }
     {
         int32_t *hs = (int32_t *)h->host_pinned;
