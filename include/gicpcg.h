@@ -125,6 +125,17 @@ int gic_solve_kernels_chosen(gic_handle *h, const gic_pattern *P, int l_dtype, i
  * of whole row groups of one level) and the forward sweep's slice count. */
 int gic_pattern_solve_kernels(const gic_pattern *P, int32_t *warp_specialised, int32_t *level_sliced,
                               int32_t *slices);
+/* Pair-sliced schedule of an analysed pattern (outputs host, any may be
+ * NULL): *mode = 1 paired levels, 2 one level per step, 0 or negative: not
+ * built (-bits: 1 a group substitutes more than 3 groups, 2 a column outside
+ * the earlier pairs, 4/8/16/32 a far / near / right-hand-side / early list
+ * beyond the kernels' register budget, 128 groups of more than 3 rows, 256
+ * not asked for: built when GIC_TUNE_PIPELINE is 5 at analysis time, or
+ * automatic and the system in the band where the automatic choice takes
+ * these kernels);
+ * *slices = forward slices; *glevels = group levels (longest chain of
+ * dependent row groups). */
+int gic_pattern_pair_schedule(const gic_pattern *P, int32_t *mode, int32_t *slices, int32_t *glevels);
 /* Copies of the analysis (device outputs, any may be NULL): Lrowptr (n+1),
  * Lcol (nnzL), level (n), group start rows (ngroups+1). */
 int gic_pattern_export(gic_handle *h, const gic_pattern *P, int32_t *Lrowptr, int32_t *Lcol,
@@ -327,8 +338,13 @@ int gic_adam_step(gic_handle *h, int64_t np, float *theta, const float *grad, fl
  * polling: low 16 bits = nanoseconds slept between polls, bit 16 set = one
  * polling lane per warp (default 1<<16);
  * GIC_TUNE_PIPELINE = triangular-solve kernels: 4 (default) = automatic
- * (level-sliced from 48 chunks per SM, else warp-specialised, where the
- * pattern admits them, else staged one-warp), 3 = level-sliced solves (one
+ * (below 48 chunks per SM warp-specialised, up to 120 pair-sliced, above
+ * level-sliced, each where the pattern admits them, else staged one-warp),
+ * 5 = pair-sliced solves (two
+ * lanes per row; the group levels taken two at a time, the second level's
+ * reads of the first substituted by their own solve, so one cross-SM
+ * hand-off serves two levels) where the analysis built them, else as 3;
+ * 3 = level-sliced solves (one
  * lane per row; slices of whole row groups of one level, premultiplied
  * blocks) where the pattern admits them, else 2 = warp-specialised solves on
  * premultiplied row-group blocks (groups of <= 3 rows, <= 61 external
@@ -345,13 +361,16 @@ int gic_adam_step(gic_handle *h, int64_t np, float *theta, const float *grad, fl
  * BF16 inputs and W1, FP32 accumulation; FP32 master weights), the backward
  * recomputing the hidden layer from the same BF16-rounded inputs and W1 and
  * passing the gradient straight through the rounding (both calls must see
- * the same setting). */
+ * the same setting); GIC_TUNE_PAIR_LEVELS (read by gic_analyze) = 0
+ * (default): the pair-sliced schedule pairs the levels, 1: one level per
+ * step (the same two-lanes-per-row kernels without substitution). */
 #define GIC_TUNE_SOLVE_WARPS_PER_SM 1
 #define GIC_TUNE_POLL 2
 #define GIC_TUNE_PIPELINE 3
 #define GIC_TUNE_QDELTA 4
 #define GIC_TUNE_GNN_BF16 5
 #define GIC_TUNE_TRAIN_BF16 6
+#define GIC_TUNE_PAIR_LEVELS 7
 int gic_set_tuning(gic_handle *h, int key, int value);
 
 /* Failure-path self-test of the bounded device waits: one warp waits on a

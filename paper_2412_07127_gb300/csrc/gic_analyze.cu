@@ -341,8 +341,10 @@ __global__ void k_chain_flags(int32_t ngroups, const int32_t *grp, const int32_t
 // walking it in one warp replaces a cross-warp hand-off per group by a step
 // within the warp; on a lexicographic mesh the chains are the rows of nodes
 // along x.
+// With rowstep = 0 the same walk gives group levels: every row of a group
+// gets 1 + the largest level among the group's external lower columns.
 __global__ void k_levels(int32_t nchains, const int32_t *chain, const int32_t *grp, const int32_t *Lrowptr,
-                         const int32_t *Lcol, int32_t *level, int32_t *maxlev, unsigned *err)
+                         const int32_t *Lcol, int rowstep, int32_t *level, int32_t *maxlev, unsigned *err)
 {
     int lane = threadIdx.x & 31;
     int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -373,8 +375,8 @@ __global__ void k_levels(int32_t nchains, const int32_t *chain, const int32_t *g
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            if (lane <= e - s) st_release_i32(level + s + lane, mx + 1 + lane);
-            mx_all = max(mx_all, mx + 1 + (e - s));
+            if (lane <= e - s) st_release_i32(level + s + lane, mx + 1 + rowstep * lane);
+            mx_all = max(mx_all, mx + 1 + rowstep * (e - s));
             __syncwarp(); // this group's levels are visible to the warp's next group
         }
     }
@@ -665,6 +667,9 @@ static void free_pattern(Pattern &p)
     cudaFree(p.qb_cnt);
     free_ssched(p.sf);
     free_ssched(p.sb);
+    free_psched(p.pf);
+    free_psched(p.pb);
+    cudaFree(p.glev);
     free_bsr(p);
     p = Pattern();
 }
@@ -938,17 +943,26 @@ static int analyze_impl(gic_handle *h, int64_t n, int64_t nnz, const int32_t *ro
         const int32_t *ch = key, *g_ = P.grp, *lr = P.Lrowptr, *lc = P.Lcol;
         int32_t *lv = P.level, *ml = stats + 3;
         unsigned *er = h->dev_err;
-        void *args[] = {&nch, &ch, &g_, &lr, &lc, &lv, &ml, &er};
+        int rowstep = 1;
+        void *args[] = {&nch, &ch, &g_, &lr, &lc, &rowstep, &lv, &ml, &er};
+        STEP(launch_persistent(h, (const void *)k_levels, 256, 0, nch, args));
+        // group levels (same chains), for the pair-sliced schedule
+        CUDA_STEP(cudaMalloc(&P.glev, sizeof(int32_t) * (size_t)n));
+        CUDA_STEP(cudaMemsetAsync(P.glev, 0xff, sizeof(int32_t) * (size_t)n, h->stream));
+        lv = P.glev;
+        ml = stats + 5;
+        rowstep = 0;
         STEP(launch_persistent(h, (const void *)k_levels, 256, 0, nch, args));
     }
     {
         int32_t *hs = (int32_t *)h->host_pinned;
-        CUDA_STEP(cudaMemcpyAsync(hs, stats, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, h->stream));
+        CUDA_STEP(cudaMemcpyAsync(hs, stats, sizeof(int32_t) * 6, cudaMemcpyDeviceToHost, h->stream));
         CUDA_STEP(cudaStreamSynchronize(h->stream));
         P.max_ext_lower = hs[0];
         P.max_ext_upper = hs[1];
         P.max_group = hs[2];
         P.nlevels = n > 0 ? hs[3] + 1 : 0; // levels are 0-based
+        P.nglev = n > 0 ? hs[5] + 1 : 0;
     }
     STEP(read_and_clear_dev_err(h, &flags));
     if (flags & ERR_TIMEOUT) { rc = GIC_ERR_TIMEOUT; goto out; }
@@ -957,6 +971,7 @@ static int analyze_impl(gic_handle *h, int64_t n, int64_t nnz, const int32_t *ro
     if (!P.bsr_ready) STEP(build_sell(h, P)); // the SELL-32 copy serves only patterns without node blocks
     STEP(build_qsched(h, P));
     STEP(build_ssched(h, P));
+    STEP(build_psched(h, P));
 out:
 #undef STEP
 #undef CUDA_STEP
@@ -1011,6 +1026,15 @@ int gic_pattern_solve_kernels(const gic_pattern *P, int32_t *warp_specialised, i
     if (warp_specialised) *warp_specialised = P->p.qready;
     if (level_sliced) *level_sliced = P->p.sready;
     if (slices) *slices = P->p.sf.nsl;
+    return GIC_OK;
+}
+
+int gic_pattern_pair_schedule(const gic_pattern *P, int32_t *mode, int32_t *slices, int32_t *glevels)
+{
+    if (!P) return GIC_ERR_INVALID_ARG;
+    if (mode) *mode = P->p.pready ? P->p.pready : -P->p.pwhy;
+    if (slices) *slices = P->p.pf.nsl;
+    if (glevels) *glevels = P->p.nglev;
     return GIC_OK;
 }
 

@@ -270,6 +270,21 @@ struct SliceSched {
     int32_t *col = nullptr;
 };
 
+// Pair-sliced schedule of one sweep (gic_psolve.cu): slices of whole groups
+// with at most 16 rows, two lanes per row (lane 2i + h: row i of the slice,
+// half h), each half taking every other column of each part of the group's
+// list. Per slice: w steps per lane, of which we early and wf far (the rest
+// near), wr right-hand-side steps, ng groups; kv / kr = first coefficient
+// step (32 values each), kc / krc = first column word (2 per group and step).
+struct PairSched {
+    int32_t nsl = 0;
+    int64_t steps = 0, ncol = 0, rsteps = 0, nrcol = 0;
+    int32_t *w = nullptr, *we = nullptr, *wf = nullptr, *wr = nullptr, *ng = nullptr;
+    int64_t *kv = nullptr, *kc = nullptr, *kr = nullptr, *krc = nullptr;
+    int2 *lane = nullptr;
+    int32_t *col = nullptr, *rcol = nullptr;
+};
+
 struct Pattern {
     int64_t n = 0, nnzA = 0, nnzL = 0;
     int32_t ngroups = 0, nlevels = 0;
@@ -328,6 +343,16 @@ struct Pattern {
     // levels. Needs the warp-specialised schedule (its column orders).
     int sready = 0;
     SliceSched sf, sb;
+    // Pair-sliced schedule (gic_psolve.cu): group levels (glev, per row: the
+    // longest dependency chain of groups ending at the row's group), and per
+    // sweep the groups taken two levels at a time; a group at the second
+    // level of a pair has the rows it reads at the first substituted by
+    // their own solve, so that both levels of a pair only read earlier
+    // pairs. Needs groups of at most 3 rows.
+    int32_t nglev = 0;
+    int32_t *glev = nullptr;
+    int pready = 0, pwhy = 0; // pwhy: why not built (bits, see gic_psolve.cu)
+    PairSched pf, pb;
     int device = 0;
 };
 
@@ -359,6 +384,9 @@ __device__ __forceinline__ void gnn_aggregate(int64_t v, const int32_t *Lrowptr,
 // level-sliced schedule of a pattern (gic_ssolve.cu)
 int build_ssched(gic_handle *h, Pattern &P);
 void free_ssched(SliceSched &S);
+// pair-sliced schedule of a pattern (gic_psolve.cu)
+int build_psched(gic_handle *h, Pattern &P);
+void free_psched(PairSched &S);
 // 3x3 node-block SpMV layout of a pattern (gic_bsr.cu)
 int build_bsr(gic_handle *h, Pattern &P);
 void free_bsr(Pattern &P);
@@ -382,6 +410,7 @@ struct gic_handle {
     int tune_qdelta = 6;                // level window of the "late" columns (pattern analysis)
     int tune_gnn_bf16 = 1;              // GNN inference: edge MLP on the tensor cores in BF16 (0: FP32)
     int tune_train_bf16 = 0;            // GNN training forward/backward: BF16 edge MLP (1) or FP32 (0)
+    int tune_pair_levels = 0;           // pair-sliced schedule: 0 paired levels, 1 one level per step
 };
 
 namespace gic {

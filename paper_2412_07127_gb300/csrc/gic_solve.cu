@@ -970,10 +970,12 @@ __global__ void __launch_bounds__(SPMV_BLOCK) k_spmv_sell(int64_t n, int64_t nsl
 }
 
 // p = z + beta p (p = z on the first step); z back to the sentinel (ZT:
-// float for the FP32 preconditioner vectors). With IDENT the preconditioner
-// is the identity and z is r itself.
+// float for the FP32 preconditioner vectors), and y too when yr is given
+// (the pair-sliced backward sweep reads y without resetting it). With IDENT
+// the preconditioner is the identity and z is r itself.
 template <bool IDENT, typename ZT>
-__global__ void __launch_bounds__(VEC_BLOCK) k_update_p(int64_t n, ZT *z, double *p, const double *r, Scalars *sc)
+__global__ void __launch_bounds__(VEC_BLOCK) k_update_p(int64_t n, ZT *z, double *p, const double *r, ZT *yr,
+                                                        Scalars *sc)
 {
     if (sc->done) return;
     const int first = (sc->iter == 0);
@@ -986,6 +988,7 @@ __global__ void __launch_bounds__(VEC_BLOCK) k_update_p(int64_t n, ZT *z, double
             const double zi = (double)z[i];
             p[i] = first ? zi : fma(beta, p[i], zi);
             z[i] = sentinel_of<ZT>();
+            if (yr) yr[i] = sentinel_of<ZT>();
         }
     }
 }
@@ -1110,11 +1113,14 @@ static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 // and sums in FP32 too.
 // SM-local (gic_bsolve.cu) on the same blocks where the pattern's chunk
 // blocks allow it.
-enum SolveMode { MODE_GEN64, MODE_GEN32, MODE_P64, MODE_P32, MODE_Q64, MODE_Q32, MODE_S64, MODE_S32, MODE_IDENT };
+enum SolveMode {
+    MODE_GEN64, MODE_GEN32, MODE_P64, MODE_P32, MODE_Q64, MODE_Q32, MODE_S64, MODE_S32, MODE_D64, MODE_D32, MODE_IDENT
+};
 
-static bool f32_vectors(SolveMode m) { return m == MODE_P32 || m == MODE_Q32 || m == MODE_S32; }
+static bool f32_vectors(SolveMode m) { return m == MODE_P32 || m == MODE_Q32 || m == MODE_S32 || m == MODE_D32; }
 static bool premultiplied(SolveMode m) { return m == MODE_Q64 || m == MODE_Q32; }
 static bool sliced(SolveMode m) { return m == MODE_S64 || m == MODE_S32; }
+static bool paired(SolveMode m) { return m == MODE_D64 || m == MODE_D32; }
 
 struct SolveWs {
     void *Uval;                   // U values (generic, pipelined), backward blocks (warp-specialised) or
@@ -1139,11 +1145,18 @@ static SolveMode solve_mode(const gic_handle *h, const Pattern &P, int l_dtype)
     if (l_dtype == GIC_IDENTITY) return MODE_IDENT;
     // automatic choice (measured on the hex systems from 40^3 to 148^3): the
     // level-sliced kernels (one lane per row) where many independent groups
-    // are ready at once, i.e. many chunks per SM; else the warp-specialised
-    // kernels (three warps per chunk, most arithmetic off the dependency
-    // chain) where the pattern admits them, else the staged one-warp kernels
+    // are ready at once, i.e. many chunks per SM; the pair-sliced ones (half
+    // the hand-offs, 1.7x the arithmetic) in a middle band; else the
+    // warp-specialised kernels (three warps per chunk, most arithmetic off
+    // the dependency chain) where the pattern admits them, else the staged
+    // one-warp kernels
     int pipeline = h->tune_pipeline;
-    if (pipeline >= 4) pipeline = (P.nchunks >= (int64_t)SLICED_CHUNKS_PER_SM * h->num_sms) ? 3 : 2;
+    if (pipeline == 4 || pipeline > 5) {
+        const int64_t c = P.nchunks, sms = h->num_sms;
+        pipeline = (c < (int64_t)SLICED_CHUNKS_PER_SM * sms) ? 2
+                   : (P.pready == 1 && c < (int64_t)PAIRED_CHUNKS_PER_SM * sms) ? 5 : 3;
+    }
+    if (pipeline == 5 && P.pready) return (l_dtype == GIC_F32) ? MODE_D32 : MODE_D64;
     if (pipeline >= 3 && P.sready) return (l_dtype == GIC_F32) ? MODE_S32 : MODE_S64;
     if (pipeline >= 2 && P.qready) return (l_dtype == GIC_F32) ? MODE_Q32 : MODE_Q64;
     const bool pipe = pipeline && pipelined_fits(P);
@@ -1165,8 +1178,10 @@ static SolveWs carve(const Pattern &PA, const Pattern &PL, int l_dtype, SolveMod
     char *c = (char *)ws;
     size_t off = 0;
     size_t es = (l_dtype == GIC_F32) ? 4 : 8;
-    const size_t fb = sliced(mode) ? s_values_bytes(PL.sf, es) : es * (size_t)P.nnzL;
-    const size_t bb = sliced(mode) ? s_values_bytes(PL.sb, es) : es * (size_t)P.nnzL;
+    const size_t fb = sliced(mode) ? s_values_bytes(PL.sf, es)
+                      : paired(mode) ? p_values_bytes(PL.pf, es) : es * (size_t)P.nnzL;
+    const size_t bb = sliced(mode) ? s_values_bytes(PL.sb, es)
+                      : paired(mode) ? p_values_bytes(PL.pb, es) : es * (size_t)P.nnzL;
     o.sc = (Scalars *)(c + off); off += align_up(sizeof(Scalars));
     o.partials = (double *)(c + off); off += align_up(sizeof(double) * 2 * MAX_PARTIALS);
     o.Uval = c + off; off += (l_dtype == GIC_IDENTITY) ? 0 : align_up(bb);
@@ -1345,6 +1360,7 @@ static int setup_factor(gic_handle *h, const Pattern &P, SolveMode mode, const v
 {
     if (premultiplied(mode)) return q_setup(h, P, f32_vectors(mode), Lval, W.Qf, W.Uval);
     if (sliced(mode)) return s_setup(h, P, f32_vectors(mode), Lval, W.Qf, W.Uval);
+    if (paired(mode)) return p_setup(h, P, f32_vectors(mode), Lval, W.Qf, W.Uval);
     int64_t cnt = P.nnzL > P.n ? P.nnzL : P.n;
     unsigned gr = vec_grid(h, cnt, 256);
     ++h->launches;
@@ -1423,6 +1439,8 @@ static int precondition(gic_handle *h, const Pattern &P, SolveMode mode, const v
     case MODE_Q32: GIC_TRY(q_lsolve(h, P, true, W.Qf, W.r32, W.y32, W.sc)); break;
     case MODE_S64: GIC_TRY(s_lsolve(h, P, false, W.Qf, W.r, W.y, W.sc)); break;
     case MODE_S32: GIC_TRY(s_lsolve(h, P, true, W.Qf, W.r32, W.y32, W.sc)); break;
+    case MODE_D64: GIC_TRY(p_lsolve(h, P, false, W.Qf, W.r, W.y, W.sc)); break;
+    case MODE_D32: GIC_TRY(p_lsolve(h, P, true, W.Qf, W.r32, W.y32, W.sc)); break;
     default: break;
     }
     PROF_END(GIC_PROF_LSOLVE);
@@ -1445,6 +1463,8 @@ static int precondition(gic_handle *h, const Pattern &P, SolveMode mode, const v
     case MODE_Q32: GIC_TRY(q_ltsolve(h, P, true, true, W.Uval, W.y32, W.z32, W.r, W.partials, W.sc)); break;
     case MODE_S64: GIC_TRY(s_ltsolve(h, P, false, true, W.Uval, W.y, W.z, W.r, W.partials, W.sc)); break;
     case MODE_S32: GIC_TRY(s_ltsolve(h, P, true, true, W.Uval, W.y32, W.z32, W.r, W.partials, W.sc)); break;
+    case MODE_D64: GIC_TRY(p_ltsolve(h, P, false, true, W.Uval, W.y, W.z, W.r, W.partials, W.sc)); break;
+    case MODE_D32: GIC_TRY(p_ltsolve(h, P, true, true, W.Uval, W.y32, W.z32, W.r, W.partials, W.sc)); break;
     default: break;
     }
     PROF_END(GIC_PROF_LTSOLVE);
@@ -1463,7 +1483,7 @@ static int pcg_iteration(gic_handle *h, const Pattern &P, const Pattern &PL, Sol
         ++h->launches;
         k_ident_rz<<<vg, VEC_BLOCK, 0, h->stream>>>(n, W.r, W.partials, W.sc);
         ++h->launches;
-        k_update_p<true, double><<<vg, VEC_BLOCK, 0, h->stream>>>(n, W.z, W.p, W.r, W.sc);
+        k_update_p<true, double><<<vg, VEC_BLOCK, 0, h->stream>>>(n, W.z, W.p, W.r, nullptr, W.sc);
         GIC_CUDA_TRY(cudaGetLastError());
         PROF_END(GIC_PROF_VECTOR);
     } else {
@@ -1471,9 +1491,11 @@ static int pcg_iteration(gic_handle *h, const Pattern &P, const Pattern &PL, Sol
         PROF_BEGIN(GIC_PROF_VECTOR);
         ++h->launches;
         if (f32_vectors(mode))
-            k_update_p<false, float><<<vg, VEC_BLOCK, 0, h->stream>>>(n, W.z32, W.p, W.r, W.sc);
+            k_update_p<false, float><<<vg, VEC_BLOCK, 0, h->stream>>>(n, W.z32, W.p, W.r,
+                                                                      paired(mode) ? W.y32 : nullptr, W.sc);
         else
-            k_update_p<false, double><<<vg, VEC_BLOCK, 0, h->stream>>>(n, W.z, W.p, W.r, W.sc);
+            k_update_p<false, double><<<vg, VEC_BLOCK, 0, h->stream>>>(n, W.z, W.p, W.r,
+                                                                       paired(mode) ? W.y : nullptr, W.sc);
         GIC_CUDA_TRY(cudaGetLastError());
         PROF_END(GIC_PROF_VECTOR);
     }
@@ -1607,6 +1629,8 @@ static int standalone_solve(gic_handle *h, const Pattern &p, const void *valL, i
         case MODE_Q32: GIC_TRY(q_lsolve(h, p, true, W.Qf, W.r32, W.y32, nullptr)); break;
         case MODE_S64: GIC_TRY(s_lsolve(h, p, false, W.Qf, in, out, nullptr)); break;
         case MODE_S32: GIC_TRY(s_lsolve(h, p, true, W.Qf, W.r32, W.y32, nullptr)); break;
+        case MODE_D64: GIC_TRY(p_lsolve(h, p, false, W.Qf, in, out, nullptr)); break;
+        case MODE_D32: GIC_TRY(p_lsolve(h, p, true, W.Qf, W.r32, W.y32, nullptr)); break;
         default: break;
         }
         PROF_END(GIC_PROF_LSOLVE);
@@ -1631,6 +1655,8 @@ static int standalone_solve(gic_handle *h, const Pattern &p, const void *valL, i
         case MODE_Q32: GIC_TRY(q_ltsolve(h, p, true, false, W.Uval, W.r32, W.y32, nullptr, nullptr, nullptr)); break;
         case MODE_S64: GIC_TRY(s_ltsolve(h, p, false, false, W.Uval, yy, out, nullptr, nullptr, nullptr)); break;
         case MODE_S32: GIC_TRY(s_ltsolve(h, p, true, false, W.Uval, W.r32, W.y32, nullptr, nullptr, nullptr)); break;
+        case MODE_D64: GIC_TRY(p_ltsolve(h, p, false, false, W.Uval, yy, out, nullptr, nullptr, nullptr)); break;
+        case MODE_D32: GIC_TRY(p_ltsolve(h, p, true, false, W.Uval, W.r32, W.y32, nullptr, nullptr, nullptr)); break;
         default: break;
         }
         PROF_END(GIC_PROF_LTSOLVE);
@@ -1745,7 +1771,7 @@ int gic_pcg_split(gic_handle *h, const gic_pattern *PA, const double *valA, cons
     if (p.n != pl.n) return GIC_ERR_INVALID_ARG;
     SolveMode mode = solve_mode(h, pl, l_dtype);
     SolveWs W = carve(p, pl, l_dtype, mode, ws);
-    if (ws_bytes < W.bytes && sliced(mode)) { // a workspace sized before the analysis
+    if (ws_bytes < W.bytes && (sliced(mode) || paired(mode))) { // a workspace sized before the analysis
         mode = (l_dtype == GIC_F32) ? MODE_Q32 : MODE_Q64;
         W = carve(p, pl, l_dtype, mode, ws);
     }
@@ -1792,6 +1818,7 @@ int gic_set_tuning(gic_handle *h, int key, int value)
     case GIC_TUNE_QDELTA: h->tune_qdelta = value; return GIC_OK;
     case GIC_TUNE_GNN_BF16: h->tune_gnn_bf16 = value; return GIC_OK;
     case GIC_TUNE_TRAIN_BF16: h->tune_train_bf16 = value; return GIC_OK;
+    case GIC_TUNE_PAIR_LEVELS: h->tune_pair_levels = value; return GIC_OK;
     default: return GIC_ERR_INVALID_ARG;
     }
 }
@@ -1801,6 +1828,7 @@ int gic_solve_kernels_chosen(gic_handle *h, const gic_pattern *P, int l_dtype, i
     GIC_TRY(check_pattern(h, P));
     if (!pipeline || (l_dtype != GIC_F64 && l_dtype != GIC_F32)) return GIC_ERR_INVALID_ARG;
     switch (solve_mode(h, P->p, l_dtype)) {
+    case MODE_D64: case MODE_D32: *pipeline = 5; break;
     case MODE_S64: case MODE_S32: *pipeline = 3; break;
     case MODE_Q64: case MODE_Q32: *pipeline = 2; break;
     case MODE_P64: case MODE_P32: *pipeline = 1; break;

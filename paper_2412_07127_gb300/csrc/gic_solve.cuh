@@ -104,6 +104,11 @@ int q_ltsolve(gic_handle *h, const Pattern &P, bool f32, bool pcg, const void *K
 // Level-sliced solves (gic_ssolve.cu): s_setup writes a factor's
 // coefficients in the slice layout into Sf (forward) and Sb (backward),
 // s_values_bytes(sched, element size) bytes each.
+size_t p_values_bytes(const PairSched &S, size_t es);
+int p_setup(gic_handle *h, const Pattern &P, bool f32, const void *Lval, void *Vf, void *Vb);
+int p_lsolve(gic_handle *h, const Pattern &P, bool f32, const void *Vf, const void *r, void *y, const Scalars *sc);
+int p_ltsolve(gic_handle *h, const Pattern &P, bool f32, bool pcg, const void *Vb, const void *y, void *z,
+              const double *rd, double *partials, Scalars *sc);
 size_t s_values_bytes(const SliceSched &S, size_t es);
 int s_setup(gic_handle *h, const Pattern &P, bool f32, const void *Lval, void *Sf, void *Sb);
 int s_lsolve(gic_handle *h, const Pattern &P, bool f32, const void *Sf, const void *r, void *y, const Scalars *sc);
@@ -119,5 +124,12 @@ int bsr_spmv(gic_handle *h, const Pattern &P, int mode, const double *bval, cons
 
 // automatic solve choice: level-sliced kernels from this many chunks per SM
 constexpr int SLICED_CHUNKS_PER_SM = 48;
+// Automatic choice of the solve kernels by chunks (for hex elasticity the
+// x-pencils) per SM, measured on the hex systems from 40^3 to 148^3: below
+// SLICED_CHUNKS_PER_SM the warp-specialised kernels, up to
+// PAIRED_CHUNKS_PER_SM the pair-sliced ones (whose pair schedule the
+// analysis builds only then, or when the pipeline setting asks for them),
+// above it the level-sliced ones.
+constexpr int PAIRED_CHUNKS_PER_SM = 120;
 
 }  // namespace gic

@@ -52,6 +52,7 @@ _SIGS = {
     "gic_pattern_schedule": (_int, [_vp, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i64)]),
     "gic_pattern_solve_kernels": (_int, [_vp, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i32)]),
     "gic_pattern_spmv_layout": (_int, [_vp, C.POINTER(_i32), C.POINTER(_i64)]),
+    "gic_pattern_pair_schedule": (_int, [_vp, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i32)]),
     "gic_solve_kernels_chosen": (_int, [_vp, _vp, _int, C.POINTER(_i32)]),
     "gic_ic0": (_int, [_vp, _vp, _vp, _vp, _dbl, C.POINTER(_i64)]),
     "gic_ic0_auto": (_int, [_vp, _vp, _vp, _vp, _int, C.POINTER(_dbl), C.POINTER(_i64)]),
@@ -197,6 +198,9 @@ class Pattern:
         nbk, ent = _i32(), _i64()
         _call("gic_pattern_spmv_layout", p, C.byref(nbk), C.byref(ent))
         self.node_blocks, self.spmv_entries = nbk.value, ent.value
+        pm, ps, gl = _i32(), _i32(), _i32()
+        _call("gic_pattern_pair_schedule", p, C.byref(pm), C.byref(ps), C.byref(gl))
+        self.pair_mode, self.pair_slices, self.group_levels = pm.value, ps.value, gl.value
 
     def export(self, h: Handle):
         dev = self.rowptr.device
@@ -374,6 +378,7 @@ def error_flags(h: Handle):
 
 GIC_TUNE_SOLVE_WARPS_PER_SM, GIC_TUNE_POLL, GIC_TUNE_PIPELINE, GIC_TUNE_QDELTA, GIC_TUNE_GNN_BF16 = 1, 2, 3, 4, 5
 GIC_TUNE_TRAIN_BF16 = 6
+GIC_TUNE_PAIR_LEVELS = 7
 POLL_ONE_LANE = 1 << 16
 
 
@@ -393,7 +398,7 @@ def selftest_wait_timeout(h: Handle, polls=4096):
     return lib().gic_selftest_wait_timeout(h.h, polls)
 
 
-SOLVE_KERNELS = {3: "level-sliced", 2: "warp-specialised", 1: "staged one-warp", 0: "generic"}
+SOLVE_KERNELS = {5: "pair-sliced", 3: "level-sliced", 2: "warp-specialised", 1: "staged one-warp", 0: "generic"}
 
 
 def solve_kernels_chosen(h: Handle, P: Pattern, l_dtype=GIC_F64):

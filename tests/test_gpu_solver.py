@@ -142,19 +142,23 @@ def _node_block_spd(nodes, density, seed):
     return S + np.diag(np.abs(S).sum(1) + 1.0)
 
 
+@pytest.mark.parametrize("pipeline", [4, 5])
 @pytest.mark.parametrize("nodes,density", [(7, 0.3), (100, 0.05), (333, 0.012)])
-def test_pcg_node_block_pattern_matches_oracle(G, h, nodes, density):
+def test_pcg_node_block_pattern_matches_oracle(G, h, nodes, density, pipeline):
     """The block SpMV path of the PCG on a non-mesh node-block matrix
     (slices of 32 nodes with ragged widths and a partial last slice; rows
-    within the IC(0) kernel's 48 lower entries)."""
+    within the IC(0) kernel's 48 lower entries), with the automatic and the
+    pair-sliced solves (where the analysis built them)."""
     A = O.csr_from_dense(_node_block_spd(nodes, density, nodes))
     rp, c, v = _upload(A)
+    G.set_tuning(h, G.GIC_TUNE_PIPELINE, pipeline) # before the analysis: it builds the pair schedule
     P = G.Pattern(h, rp, c)
     assert P.node_blocks == 1
     b = np.random.default_rng(nodes).uniform(-1, 1, A.n)
     Lg, bad = G.ic0(h, P, v)
     assert bad == -1
     res = G.pcg(h, P, v, Lg, _dev(b), rtol=1e-10)
+    G.set_tuning(h, G.GIC_TUNE_PIPELINE, 4)
     Lo, _ = O.ic0(A)
     ro = O.pcg(A, b, Lo, tol=1e-10)
     assert res["status"] == 0 and _iters_ok(res["iters"], ro["iters"]), (res["iters"], ro["iters"])
@@ -267,12 +271,13 @@ def test_spmv_matches_oracle(G, h):
     assert abs(_np(d)[0] - x @ yo) <= 1e-12 * abs(x @ yo)
 
 
-@pytest.mark.parametrize("pipeline", [4, 3, 2, 1, 0])
+@pytest.mark.parametrize("pipeline", [5, 4, 3, 2, 1, 0])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("case", ["fem8", "fem5", "random", "tridiag"])
 def test_triangular_solves_match_oracle(G, h, dtype, case, pipeline):
-    """Every solve path (level-sliced, warp-specialised and pipelined where the
-    pattern allows, generic) against the oracle on the same factor."""
+    """Every solve path (pair-sliced, level-sliced, warp-specialised and
+    pipelined where the pattern allows, generic) against the oracle on the
+    same factor."""
     G.set_tuning(h, G.GIC_TUNE_PIPELINE, pipeline)
     if case == "fem8":
         A = O.fem_hex_assemble(8, I.material_field(8, 5))
@@ -289,6 +294,8 @@ def test_triangular_solves_match_oracle(G, h, dtype, case, pipeline):
     rp, c, v = _upload(A)
     P = G.Pattern(h, rp, c)
     Ld = _dev(Lval).to(dtype)
+    if pipeline == 5 and case.startswith("fem"):
+        assert P.pair_mode == 1 and G.solve_kernels_chosen(h, P) == "pair-sliced"
     r = np.random.default_rng(2).uniform(-1, 1, A.n)
     y = G.lsolve(h, P, Ld, _dev(r))
     z = G.ltsolve(h, P, Ld, y)
@@ -326,8 +333,53 @@ def test_solve_late_window_variants(G, h, qdelta, pipeline):
     G.set_tuning(h, G.GIC_TUNE_PIPELINE, 4)
 
 
+@pytest.mark.parametrize("pair_levels", [0, 1])
+def test_pair_sliced_schedule_variants(G, h, pair_levels):
+    """Pair-sliced solves with the levels paired (second level substituted)
+    and one level per step: hex 6^3 against the oracle, and the schedule's
+    group levels are the node levels x + 2y + 4z (7N - 3 of them)."""
+    N = 6
+    A = O.fem_hex_assemble(N, I.material_field(N, 12))
+    Lo, _ = O.ic0(A)
+    rp, c, v = _upload(A)
+    G.set_tuning(h, G.GIC_TUNE_PAIR_LEVELS, pair_levels)
+    G.set_tuning(h, G.GIC_TUNE_PIPELINE, 5)
+    P = G.Pattern(h, rp, c)
+    G.set_tuning(h, G.GIC_TUNE_PAIR_LEVELS, 0)
+    assert P.group_levels == 7 * N - 3 and P.nlevels == 3 * P.group_levels
+    assert P.pair_mode == (1 if pair_levels == 0 else 2), P.pair_mode
+    r = np.random.default_rng(4).uniform(-1, 1, A.n)
+    y = G.lsolve(h, P, _dev(Lo.val), _dev(r))
+    z = G.ltsolve(h, P, _dev(Lo.val), y)
+    b = I.rhs(A.n, 12)
+    Lg, _ = G.ic0(h, P, v)
+    res = G.pcg(h, P, v, Lg, _dev(b), rtol=1e-8)
+    G.set_tuning(h, G.GIC_TUNE_PIPELINE, 4)
+    yo = O.lsolve(Lo, r)
+    assert _rel(_np(y), yo) <= 1e-11
+    assert _rel(_np(z), O.ltsolve(Lo, yo)) <= 1e-11
+    ro = O.pcg(A, b, Lo, tol=1e-8)
+    assert res["status"] == 0 and _iters_ok(res["iters"], ro["iters"]), (res["iters"], ro["iters"])
+    assert np.linalg.norm(_np(res["x"]) - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
+    assert G.error_flags(h) == 0
+
+
+def test_pair_schedule_built_only_when_used(G, h):
+    """With the automatic choice a small system (below the pair-sliced band)
+    gets no pair schedule (reason 256: not asked for); asked for, it gets one."""
+    A = O.fem_hex_assemble(4, I.material_field(4, 3))
+    rp, c, v = _upload(A)
+    G.set_tuning(h, G.GIC_TUNE_PIPELINE, 4)
+    P = G.Pattern(h, rp, c)
+    assert P.pair_mode == -256 and G.solve_kernels_chosen(h, P) == "warp-specialised"
+    G.set_tuning(h, G.GIC_TUNE_PIPELINE, 5)
+    P5 = G.Pattern(h, rp, c)
+    assert P5.pair_mode == 1 and G.solve_kernels_chosen(h, P5) == "pair-sliced"
+    G.set_tuning(h, G.GIC_TUNE_PIPELINE, 4)
+
+
 # ---------------------------------------------------------------- A7 PCG
-@pytest.mark.parametrize("pipeline", [4, 3])
+@pytest.mark.parametrize("pipeline", [5, 4, 3])
 @pytest.mark.parametrize("N", [2, 4, 8, 12])
 def test_pcg_matches_oracle(G, h, N, pipeline):
     G.set_tuning(h, G.GIC_TUNE_PIPELINE, pipeline)
@@ -363,7 +415,7 @@ def test_plain_cg_matches_oracle(G, h):
     assert np.linalg.norm(x - ro["x"]) <= 1e-6 * np.linalg.norm(ro["x"])
 
 
-@pytest.mark.parametrize("pipeline", [3, 2, 1, 0])
+@pytest.mark.parametrize("pipeline", [5, 3, 2, 1, 0])
 def test_pcg_f32_factor(G, h, pipeline):
     G.set_tuning(h, G.GIC_TUNE_PIPELINE, pipeline)
     N = 8
