@@ -11,7 +11,7 @@ Bounds: the FP64 factor takes the oracle's iterations within 2% and gives
 x within 1e-6 (relative, on the sampled entries and in norm). The FP32 apply
 also sums in FP32, so against the oracle it is a different preconditioner
 stopped at the same residual: its x agrees to 1e-5, and its iteration count
-is compared with the oracle's FP64 count within 2% (the benchmark spec's bound)."""
+is compared with the oracle's FP64 count within 2%."""
 import json
 import os
 
