@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-f32", action="store_true", help="skip the FP32-apply comparison")
+    ap.add_argument("--mixed-N", type=int, default=69,
+                    help="size of the mixed-precision side measurement (FP32 factor apply with the GNN "
+                         "correction and IC(0) fallback against all-FP64 plain IC(0)-PCG); 0 skips it")
     ap.add_argument("--side-steps", type=int, default=2,
                     help="steps of each comparison run after the timed region")
     ap.add_argument("--pipeline", type=int, default=4,
@@ -364,6 +367,63 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------- GPU arm
+def mixed_precision(G, I, h, dev, stream, N, seed, theta, steps, pol):
+    """The mixed-precision comparison at N^3 (about 1M dofs at 69^3), after
+    the headline's timed steps: FP64 CG vectors and scalars with the factor
+    applied in FP32, the GNN correction with the IC(0) fallback, against
+    all-FP64 plain IC(0)-PCG on the same system. Each path is timed with CUDA
+    events over `steps` runs after one untimed run."""
+    import numpy as np
+    import torch
+    E = torch.from_numpy(I.material_field(N, seed)).to(dev)
+    b = torch.from_numpy(I.rhs(3 * N * (N + 1) ** 2, seed)).to(dev)
+    rp, c, v = G.fem_hex_assemble(h, N, E)
+    P = G.Pattern(h, rp, c)
+    ws = {d: G.workspace(h, P, G.GIC_WS_PCG, d) for d in (G.GIC_F64, G.GIC_F32)}
+    wsg = G.gnn_workspace(h, P, 1, training=False)
+    L = torch.empty(P.nnzL, dtype=torch.float64, device=dev)
+    Lg = torch.empty_like(L)
+    g = torch.empty(P.nnzL, dtype=torch.float32, device=dev)
+    x = torch.empty_like(b)
+
+    def run(path):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        G.ic0_auto(h, P, v, out=L)
+        Lr, ldt, ok = L, G.GIC_F64, True
+        if path == "gnn_ic_f32L":
+            x9, e0_, scale, _ = G.features(h, P, v)
+            G.gnn_forward(h, P, theta, x9, e0_, ws=wsg, g=g)
+            _, ok = G.gnn_correct(h, P, L, g, scale, out=Lg)
+            Lr = Lg if ok else L
+        if path != "ic0_f64":
+            Lr, ldt = G.to_f32(h, Lr), G.GIC_F32
+        x.zero_()
+        r = G.pcg(h, P, v, Lr, b, x=x, ws=ws[ldt])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3, r, ok
+
+    res = {}
+    for path in ("gnn_ic_f32L", "ic0_f32L", "ic0_f64"):
+        run(path)
+        runs = [run(path) for _ in range(steps)]
+        res[path] = {"value_s": float(np.mean([t for t, _, _ in runs])), "iters": runs[-1][1]["iters"],
+                     "relres": runs[-1][1]["relres"]}
+        if path == "gnn_ic_f32L":
+            res[path]["gnn_kept"] = bool(runs[-1][2])
+    chosen = "gnn_ic_f32L" if (pol and pol["use_gnn"]) else "ic0_f32L"
+    out = {"workload": f"hex elasticity {N}^3 elements ({P.n} dofs, {P.nnzA} nnz), same generator and seed",
+           "paths": res, "chosen": chosen,
+           "speedup_vs_f64_ic0": res["ic0_f64"]["value_s"] / res[chosen]["value_s"],
+           "iters_vs_f64_ic0": res[chosen]["iters"] / res["ic0_f64"]["iters"] - 1.0,
+           "solve_kernels": {"f64": G.solve_kernels_chosen(h, P, G.GIC_F64),
+                             "f32": G.solve_kernels_chosen(h, P, G.GIC_F32)},
+           "steps": steps}
+    del ws, wsg, P
+    return out
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
@@ -524,6 +584,10 @@ def run_ours(args, rank, world, local):
                         "spmv": "3x3 node blocks" if P.node_blocks else "SELL-32",
                         "spmv_padding": P.spmv_entries / P.nnzA - 1.0},
            "f32_apply": other}
+
+    if args.mixed_N > 0 and args.mixed_N != N:
+        out["mixed_precision"] = mixed_precision(G, I, h, dev, stream, args.mixed_N, seed, theta,
+                                                 max(1, args.side_steps), gnn_policy())
 
     if not args.no_e2e:
         # end to end through the C-ABI with host buffers (pinned)
