@@ -28,11 +28,17 @@
 
 namespace gic {
 
-constexpr int IC_WARPS = 4;
+constexpr int IC_WARPS = 3; // warps per block: 5 blocks of 3 per SM fit the shared memory
+
+// Packed column-major lower triangle of a MAXDIM x MAXDIM block: column v
+// holds rows v..MAXDIM-1 (the sweep reads a column across lanes,
+// consecutive words, conflict-free); half the shared memory of the full
+// square, so more warps fit per SM.
+constexpr int MPACK = MAXDIM * (MAXDIM + 1) / 2;
+__device__ __forceinline__ int pm(int v, int u) { return v * MAXDIM - (v * (v - 1)) / 2 + (u - v); }
 
 struct IcWarpSmem {
-    double M[MAXDIM * MAXDIM];   // column-major (M[v * MAXDIM + u]), lower triangle of the external block:
-                                 // the sweep reads a column across lanes, conflict-free
+    double M[MPACK];             // lower triangle of the external block, M[pm(v, u)] = M[u][v], u >= v
     double invd[MAXDIM];         // 1 / M[v][v]
     double lg[GMAX][MAXDIM];     // external part of each group row
     double lin[GMAX][GMAX + 1];  // in-group part (and diagonal) of each group row
@@ -135,7 +141,7 @@ __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t nchunks, const in
             S.boff[0] = 0;
             for (int b = 0; b < nb; ++b) S.boff[b + 1] += S.boff[b];
         }
-        for (int idx = lane; idx < m * m; idx += 32) S.M[(idx / m) * MAXDIM + (idx % m)] = 0.0;
+        for (int idx = lane; idx < pm(m, m); idx += 32) S.M[idx] = 0.0; // columns 0..m-1
         __syncwarp();
 
         // gather M[u][v] = L_{J[u],J[v]} (v <= u) block by block: a block's
@@ -177,8 +183,8 @@ __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t nchunks, const in
                 if (v < 0) continue;
 #pragma unroll
                 for (int r = 0; r < 3; ++r)
-                    if (r < gb) S.M[v * MAXDIM + u0 + r] = vv[k][r];
-                for (int r = 3; r < gb; ++r) S.M[v * MAXDIM + u0 + r] = Lval[S.rs[u0 + r] + pp[k]];
+                    if (r < gb) S.M[pm(v, u0 + r)] = vv[k][r];
+                for (int r = 3; r < gb; ++r) S.M[pm(v, u0 + r)] = Lval[S.rs[u0 + r] + pp[k]];
             }
         }
         // the blocks' own lower triangles (in-group entries and diagonals)
@@ -187,7 +193,7 @@ __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t nchunks, const in
             for (int r = 0; r < gb; ++r)
                 for (int q2 = 0; q2 <= r; ++q2) {
                     const double val = Lval[S.rs[u0 + r] + me + q2];
-                    S.M[(u0 + q2) * MAXDIM + u0 + r] = val;
+                    S.M[pm(u0 + q2, u0 + r)] = val;
                     if (q2 == r) S.invd[u0 + r] = 1.0 / val;
                 }
         }
@@ -214,8 +220,8 @@ __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t nchunks, const in
         for (int v = 0; v < m; ++v) {
             const int owner = v & 31;
             const double iv = S.invd[v];
-            const double mu0 = (lane > v && lane < m) ? S.M[v * MAXDIM + lane] * iv : 0.0;
-            const double mu1 = (lane + 32 > v && lane + 32 < m) ? S.M[v * MAXDIM + lane + 32] * iv : 0.0;
+            const double mu0 = (lane > v && lane < m) ? S.M[pm(v, lane)] * iv : 0.0;
+            const double mu1 = (lane + 32 > v && lane + 32 < m) ? S.M[pm(v, lane + 32)] * iv : 0.0;
 #pragma unroll
             for (int t = 0; t < GMAX; ++t) {
                 if (t < G) {
@@ -341,11 +347,8 @@ static int ic0_once(gic_handle *h, const Pattern &P, const double *valA, double 
     k_ic0_prepare<<<(unsigned)blocks, 256, 0, h->stream>>>(P.n, P.Lrowptr, valL, bad_dev);
     GIC_CUDA_TRY(cudaGetLastError());
     size_t smem = sizeof(IcWarpSmem) * IC_WARPS;
-    static int attr_set[64] = {0};
-    if (!attr_set[h->device & 63]) {
-        GIC_CUDA_TRY(cudaFuncSetAttribute(k_ic0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set[h->device & 63] = 1;
-    }
+    // set on every call (a host-side attribute of the current context; cheap)
+    GIC_CUDA_TRY(cudaFuncSetAttribute(k_ic0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int32_t nc = P.nchunks;
     const int32_t *ord = P.ord_f, *cg = P.chunk_grp, *g = P.grp, *rg = P.rowgrp, *ar = P.rowptr, *lr = P.Lrowptr,
                   *lc = P.Lcol;
