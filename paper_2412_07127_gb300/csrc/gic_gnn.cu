@@ -63,20 +63,21 @@ __device__ __forceinline__ double block_sum_d(double v, double *sh)
 
 // ------------------------------------------------------------ A4 features
 // pass 0: sum of tril values per graph; pass 1: sum of squared deviations.
+// Sums over graph g's lower-triangle entries of A (pass 0: values; pass 1:
+// squared deviations from the mean), one thread per entry (coalesced): L
+// entry e of row i = Lrow[e] is A entry rowptr[i] + (e - Lrowptr[i]).
 __global__ void k_tril_moments(int pass, int64_t ng, const int32_t *rowptr, const int32_t *Lrowptr,
-                               const double *valA, const double *mean, double *partials)
+                               const int32_t *Lrow, const double *valA, const double *mean, double *partials)
 {
     __shared__ double sh[RB / 32];
     const int g = blockIdx.y;
-    const int64_t r0 = (int64_t)g * ng;
+    const int64_t e0 = Lrowptr[(int64_t)g * ng], e1 = Lrowptr[(int64_t)(g + 1) * ng];
     const double mu = pass ? mean[g] : 0.0;
     double acc = 0.0;
-    for (int64_t i = r0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < r0 + ng; i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t a = rowptr[i], cnt = Lrowptr[i + 1] - Lrowptr[i];
-        for (int32_t k = 0; k < cnt; ++k) {
-            double v = valA[a + k];
-            acc += pass ? (v - mu) * (v - mu) : v;
-        }
+    for (int64_t e = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < e1; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = Lrow[e];
+        const double v = valA[rowptr[i] + (e - Lrowptr[i])];
+        acc += pass ? (v - mu) * (v - mu) : v;
     }
     double s = block_sum_d(acc, sh);
     if (threadIdx.x == 0) partials[g * gridDim.x + blockIdx.x] = s;
@@ -94,50 +95,126 @@ __global__ void k_tril_finish(int pass, int64_t ng, const int32_t *Lrowptr, cons
     else scale[g] = sqrt(s / cnt);
 }
 
-// x9 per node, e0 = tril values / s, optional Ahat = A / s.
+// x9 per node: a warp takes 32 consecutive rows, four at a time with eight
+// lanes per row (a row's entries across its lanes: full sectors, loads of
+// several entries in flight per lane), the statistics reduced over the
+// eight lanes and handed to the lane numbered like the row; then every
+// lane finishes its own row (the divisions and the FP64 sin / cos run
+// lane-parallel). Features: degree (off-diagonal count), max / min / mean /
+// variance of the neighbours' degrees, diagonal dominance |a_ii| / sum
+// |a_ij| and |a_ii| / max |a_ij| (j != i), and the position encoding sin /
+// cos of the row's index within its graph. The degree statistics are exact
+// integer sums (the variance as (cnt sum d^2 - (sum d)^2) / cnt^2, the
+// exact value of the mean squared deviation), so only the |a_ij| sum costs
+// an FP64 operation per entry (FP64 is this GPU's scarce pipe); positive
+// doubles compare like their bit patterns, so their maximum is an integer
+// maximum.
 __global__ void k_features(int64_t n, int64_t ng, const int32_t *rowptr, const int32_t *col, const double *valA,
-                           const int32_t *Lrowptr, const double *scale, float *x9, float *e0, float *Ahat)
+                           float *x9)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int g = (int)(i / ng);
-        const double s = scale[g];
-        const int32_t a = rowptr[i], b = rowptr[i + 1];
-        double dmax = 0, dmin = 0, dsum = 0, diag = 0, offsum = 0, offmax = 0;
-        int cnt = 0;
-        for (int32_t p = a; p < b; ++p) {
-            const int32_t j = col[p];
-            const double v = valA[p];
-            if (Ahat) Ahat[p] = (float)(v / s);
-            if (j == i) { diag = fabs(v); continue; }
-            const double dj = (double)(rowptr[j + 1] - rowptr[j] - 1);
-            if (cnt == 0 || dj > dmax) dmax = dj;
-            if (cnt == 0 || dj < dmin) dmin = dj;
-            dsum += dj;
-            cnt++;
-            offsum += fabs(v);
-            if (fabs(v) > offmax) offmax = fabs(v);
+    const int lane = threadIdx.x & 31, sub = lane >> 3, sl = lane & 7;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = w0 * 32; base < n; base += nw * 32) {
+        int m_dmax = 0, m_dmin = 0, m_cnt = 0, m_len = 0;
+        long long m_dsum = 0, m_dsq = 0, m_diag = 0, m_offmax = 0;
+        double m_offsum = 0.0;
+        const int rows = (int)((n - base < 32) ? (n - base) : 32);
+        for (int r0 = 0; r0 < rows; r0 += 4) {
+            const int r = r0 + sub;
+            const int64_t i = base + r;
+            const bool on = r < rows;
+            const int32_t a = on ? rowptr[i] : 0, b = on ? rowptr[i + 1] : 0;
+            int dmax = -1, dmin = 0x7fffffff, cnt = 0;
+            long long dsum = 0, dsq = 0, diag = 0, offmax = 0; // |a| as its bit pattern
+            double offsum = 0.0;
+#pragma unroll 4
+            for (int32_t p = a + sl; p < b; p += 8) {
+                const int32_t j = col[p];
+                const double v = fabs(valA[p]);
+                const long long vb = __double_as_longlong(v);
+                if (j == i) {
+                    diag = vb;
+                } else {
+                    const int dj = rowptr[j + 1] - rowptr[j] - 1;
+                    dmax = max(dmax, dj);
+                    dmin = min(dmin, dj);
+                    dsum += dj;
+                    dsq += (long long)dj * dj;
+                    ++cnt;
+                    offsum += v;
+                    offmax = max(offmax, vb);
+                }
+            }
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) {
+                dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+                dmin = min(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+                cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+                dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+                dsq += __shfl_xor_sync(0xffffffffu, dsq, o);
+                diag = max(diag, __shfl_xor_sync(0xffffffffu, diag, o));
+                offmax = max(offmax, __shfl_xor_sync(0xffffffffu, offmax, o));
+                offsum += __shfl_xor_sync(0xffffffffu, offsum, o);
+            }
+            const int len = b - a;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) { // row r0 + q's statistics (held by lanes 8q..8q+7) to lane r0 + q
+                const int t0 = __shfl_sync(0xffffffffu, dmax, 8 * q), t1 = __shfl_sync(0xffffffffu, dmin, 8 * q);
+                const int t2 = __shfl_sync(0xffffffffu, cnt, 8 * q), t3 = __shfl_sync(0xffffffffu, len, 8 * q);
+                const long long t4 = __shfl_sync(0xffffffffu, dsum, 8 * q), t5 = __shfl_sync(0xffffffffu, dsq, 8 * q);
+                const long long t6 = __shfl_sync(0xffffffffu, diag, 8 * q);
+                const long long t7 = __shfl_sync(0xffffffffu, offmax, 8 * q);
+                const double t8 = __shfl_sync(0xffffffffu, offsum, 8 * q);
+                if (lane == r0 + q) {
+                    m_dmax = t0; m_dmin = t1; m_cnt = t2; m_len = t3;
+                    m_dsum = t4; m_dsq = t5; m_diag = t6; m_offmax = t7; m_offsum = t8;
+                }
+            }
         }
-        const double dmean = cnt ? dsum / cnt : 0.0;
-        double dsq = 0.0;
-        for (int32_t p = a; p < b; ++p) {
-            const int32_t j = col[p];
-            if (j == i) continue;
-            const double t = (double)(rowptr[j + 1] - rowptr[j] - 1) - dmean;
-            dsq += t * t;
+        if (lane < rows) {
+            const int64_t i = base + lane;
+            double sn, cs;
+            sincos((double)(i % ng), &sn, &cs);
+            float *xv = x9 + 9 * i;
+            const double c = (double)m_cnt, diag = __longlong_as_double(m_diag);
+            const double offmax = __longlong_as_double(m_offmax);
+            xv[0] = (float)(m_len - 1);
+            xv[1] = (float)(m_cnt ? m_dmax : 0);
+            xv[2] = (float)(m_cnt ? m_dmin : 0);
+            xv[3] = (float)(m_cnt ? (double)m_dsum / c : 0.0);
+            xv[4] = (float)(m_cnt ? (double)(m_cnt * m_dsq - m_dsum * m_dsum) / (c * c) : 0.0);
+            xv[5] = (float)(m_offsum > 0 ? diag / m_offsum : 0.0);
+            xv[6] = (float)(offmax > 0 ? diag / offmax : 0.0);
+            xv[7] = (float)sn;
+            xv[8] = (float)cs;
         }
-        const double pos = (double)(i - (int64_t)g * ng);
-        float *xv = x9 + 9 * i;
-        xv[0] = (float)(b - a - 1);
-        xv[1] = (float)dmax;
-        xv[2] = (float)dmin;
-        xv[3] = (float)dmean;
-        xv[4] = (float)(cnt ? dsq / cnt : 0.0);
-        xv[5] = (float)(offsum > 0 ? diag / offsum : 0.0);
-        xv[6] = (float)(offmax > 0 ? diag / offmax : 0.0);
-        xv[7] = (float)sin(pos);
-        xv[8] = (float)cos(pos);
-        const int32_t lb = Lrowptr[i], lc = Lrowptr[i + 1] - lb;
-        for (int32_t k = 0; k < lc; ++k) e0[lb + k] = (float)(valA[a + k] / s);
+    }
+}
+
+// e0 = tril(A) / s per lower entry (one thread per entry), and, if asked,
+// Ahat = A / s per entry of A; s of the entry's graph (rows g ng ..).
+__global__ void k_scaled_values(int64_t nnzL, int64_t nnzA, int64_t ng, int ngraphs, const int32_t *rowptr,
+                                const int32_t *Lrowptr, const int32_t *Lrow, const double *valA, const double *scale,
+                                float *e0, float *Ahat)
+{
+    __shared__ double inv[64];
+    for (int k = threadIdx.x; k < ngraphs && k < 64; k += blockDim.x) inv[k] = 1.0 / scale[k];
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnzL; e += stride) {
+        const int32_t i = Lrow[e];
+        const int gi = (ngraphs == 1) ? 0 : (int)(i / ng);
+        const double r = (gi < 64) ? inv[gi] : 1.0 / scale[gi];
+        e0[e] = (float)(valA[rowptr[i] + (e - Lrowptr[i])] * r);
+    }
+    if (!Ahat) return;
+    // graph boundaries in A's entries: graph k owns rowptr[k ng] ..
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnzA; p += stride) {
+        int gi = 0;
+        while (gi + 1 < ngraphs && rowptr[(int64_t)(gi + 1) * ng] <= p) ++gi;
+        const double r = (gi < 64) ? inv[gi] : 1.0 / scale[gi];
+        Ahat[p] = (float)(valA[p] * r);
     }
 }
 
@@ -282,20 +359,34 @@ __global__ void __launch_bounds__(256) k_node_fwd(int64_t n, const int32_t *__re
 // ------------------------------------------------------------ A6 correction
 // Original units, FP64 factor: off-diagonal LIC + sqrt(s) g, diagonal
 // LIC exp(g/2). bad |= 1 if a diagonal is not positive and finite.
-__global__ void k_correct(int64_t E, int64_t ng, const int32_t *Lrow, const int32_t *Lcol, const double *LIC,
-                          const float *g, const double *scale, double *Lout, unsigned *bad)
+__global__ void k_correct(int64_t E, int64_t ng, int ngraphs, const int32_t *Lrow, const int32_t *Lcol,
+                          const double *LIC, const float *g, const double *scale, double *Lout, unsigned *bad)
 {
+    __shared__ double sq[64]; // sqrt(s) per graph, once per block
+    for (int k = threadIdx.x; k < ngraphs && k < 64; k += blockDim.x) sq[k] = sqrt(scale[k]);
+    __syncthreads();
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
         const int32_t i = Lrow[p];
         const double gp = (double)g[p];
-        if (Lcol[p] == i) {
-            const double d = LIC[p] * exp(gp / 2.0);
-            Lout[p] = d;
-            if (!(d > 0.0) || !isfinite(d)) atomicOr(bad, 1u);
-        } else {
-            Lout[p] = LIC[p] + sqrt(scale[i / ng]) * gp;
+        if (Lcol[p] != i) { // the diagonals follow in k_correct_diag (their exp would diverge every warp)
+            const int gi = (ngraphs == 1) ? 0 : (int)(i / ng);
+            const double r = (gi < 64) ? sq[gi] : sqrt(scale[gi]);
+            Lout[p] = LIC[p] + r * gp;
             if (!isfinite(Lout[p])) atomicOr(bad, 1u);
         }
+    }
+}
+
+// The correction's diagonal entries, one thread per row (the diagonal is
+// the last entry of each L row): L_ii = L_IC,ii exp(g_ii / 2).
+__global__ void k_correct_diag(int64_t n, const int32_t *Lrowptr, const double *LIC, const float *g, double *Lout,
+                               unsigned *bad)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t p = Lrowptr[i + 1] - 1;
+        const double d = LIC[p] * exp((double)g[p] / 2.0);
+        Lout[p] = d;
+        if (!(d > 0.0) || !isfinite(d)) atomicOr(bad, 1u);
     }
 }
 
@@ -915,17 +1006,24 @@ int gic_features(gic_handle *h, const gic_pattern *P, int ngraphs, const double 
     double *mean = (double *)h->dev_small;            // ngraphs <= 4096
     double *parts = (double *)h->dev_small + 4096;    // GX * ngraphs, checked below
     if ((size_t)(4096 + GX * ngraphs) * 8 > 60000) return GIC_ERR_UNSUPPORTED;
-    dim3 gr(GX, ngraphs);
+    // the moments run one thread per lower entry: as many blocks per graph
+    // as the partials area holds, up to 8 per SM in all
+    const int gx = (int)std::max<int64_t>(GX, std::min<int64_t>((int64_t)h->num_sms * 8 / ngraphs,
+                                                               (60000 / 8 - 4096) / ngraphs));
+    dim3 gr(gx, ngraphs);
     ++h->launches;
-    k_tril_moments<<<gr, RB, 0, h->stream>>>(0, ng, p.rowptr, p.Lrowptr, valA, mean, parts);
+    k_tril_moments<<<gr, RB, 0, h->stream>>>(0, ng, p.rowptr, p.Lrowptr, p.Lrow, valA, mean, parts);
     ++h->launches;
-    k_tril_finish<<<ngraphs, 32, 0, h->stream>>>(0, ng, p.Lrowptr, parts, GX, mean, scale_dev);
+    k_tril_finish<<<ngraphs, 32, 0, h->stream>>>(0, ng, p.Lrowptr, parts, gx, mean, scale_dev);
     ++h->launches;
-    k_tril_moments<<<gr, RB, 0, h->stream>>>(1, ng, p.rowptr, p.Lrowptr, valA, mean, parts);
+    k_tril_moments<<<gr, RB, 0, h->stream>>>(1, ng, p.rowptr, p.Lrowptr, p.Lrow, valA, mean, parts);
     ++h->launches;
-    k_tril_finish<<<ngraphs, 32, 0, h->stream>>>(1, ng, p.Lrowptr, parts, GX, mean, scale_dev);
+    k_tril_finish<<<ngraphs, 32, 0, h->stream>>>(1, ng, p.Lrowptr, parts, gx, mean, scale_dev);
     ++h->launches;
-    k_features<<<grid1(h, p.n), 256, 0, h->stream>>>(p.n, ng, p.rowptr, p.col, valA, p.Lrowptr, scale_dev, x9, e0, Ahat);
+    k_features<<<grid1(h, p.n), 256, 0, h->stream>>>(p.n, ng, p.rowptr, p.col, valA, x9);
+    ++h->launches;
+    k_scaled_values<<<grid1(h, p.nnzL), 256, 0, h->stream>>>(p.nnzL, p.nnzA, ng, ngraphs, p.rowptr, p.Lrowptr, p.Lrow,
+                                                            valA, scale_dev, e0, Ahat);
     GIC_CUDA_TRY(cudaGetLastError());
     if (scale_host) {
         GIC_CUDA_TRY(cudaMemcpyAsync(scale_host, scale_dev, 8 * (size_t)ngraphs, cudaMemcpyDeviceToHost, h->stream));
@@ -1041,7 +1139,10 @@ int gic_gnn_correct(gic_handle *h, const gic_pattern *P, int ngraphs, const doub
     unsigned *bad = (unsigned *)((char *)h->dev_small + 61000);
     GIC_CUDA_TRY(cudaMemsetAsync(bad, 0, 4, h->stream));
     ++h->launches;
-    k_correct<<<grid1(h, p.nnzL), 256, 0, h->stream>>>(p.nnzL, p.n / ngraphs, p.Lrow, p.Lcol, LIC, g, scale_dev, Lout, bad);
+    k_correct<<<grid1(h, p.nnzL), 256, 0, h->stream>>>(p.nnzL, p.n / ngraphs, ngraphs, p.Lrow, p.Lcol, LIC, g,
+                                                       scale_dev, Lout, bad);
+    ++h->launches;
+    k_correct_diag<<<grid1(h, p.n), 256, 0, h->stream>>>(p.n, p.Lrowptr, LIC, g, Lout, bad);
     GIC_CUDA_TRY(cudaGetLastError());
     if (diag_ok) {
         unsigned *hb = (unsigned *)((char *)h->host_pinned + 3000);
