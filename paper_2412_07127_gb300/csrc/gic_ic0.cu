@@ -30,26 +30,29 @@ namespace gic {
 
 constexpr int IC_WARPS = 3; // warps per block: 5 blocks of 3 per SM fit the shared memory
 
-// Packed column-major lower triangle of a MAXDIM x MAXDIM block: column v
-// holds rows v..MAXDIM-1 (the sweep reads a column across lanes,
-// consecutive words, conflict-free); half the shared memory of the full
-// square, so more warps fit per SM.
-constexpr int MPACK = MAXDIM * (MAXDIM + 1) / 2;
-__device__ __forceinline__ int pm(int v, int u) { return v * MAXDIM - (v * (v - 1)) / 2 + (u - v); }
+// Packed column-major lower triangle of an MD x MD block: column v holds
+// rows v..MD-1 (the sweep reads a column across lanes, consecutive words,
+// conflict-free); half the shared memory of the full square, so more warps
+// fit per SM. The kernel is built for two sizes: external widths up to 40
+// and groups up to 3 rows (hex elasticity: 39 and 3; ~9 KB per warp, 24
+// warps per SM) and the general MAXDIM / GMAX.
+template <int MD>
+__device__ __forceinline__ int pm(int v, int u) { return v * MD - (v * (v - 1)) / 2 + (u - v); }
 
+template <int MD, int GM>
 struct IcWarpSmem {
-    double M[MPACK];             // lower triangle of the external block, M[pm(v, u)] = M[u][v], u >= v
-    double invd[MAXDIM];         // 1 / M[v][v]
-    double lg[GMAX][MAXDIM];     // external part of each group row
-    double lin[GMAX][GMAX + 1];  // in-group part (and diagonal) of each group row
-    int32_t J[MAXDIM];
-    int32_t rs[MAXDIM];          // start of row J[u] in L
-    int32_t len[MAXDIM];         // length of row J[u] in L (its diagonal included)
+    double M[MD * (MD + 1) / 2]; // lower triangle of the external block, M[pm(v, u)] = M[u][v], u >= v
+    double invd[MD];         // 1 / M[v][v]
+    double lg[GM][MD];     // external part of each group row
+    double lin[GM][GM + 1];  // in-group part (and diagonal) of each group row
+    int32_t J[MD];
+    int32_t rs[MD];          // start of row J[u] in L
+    int32_t len[MD];         // length of row J[u] in L (its diagonal included)
     // J holds whole row groups (rows of a group are identical in A, which is
     // symmetric), and a group's rows share their external columns: blocks
-    int32_t bu0[MAXDIM];         // first u of block b
-    int32_t bG[MAXDIM];          // rows of block b
-    int32_t boff[MAXDIM + 1];    // prefix of the blocks' external lengths
+    int32_t bu0[MD];         // first u of block b
+    int32_t bG[MD];          // rows of block b
+    int32_t boff[MD + 1];    // prefix of the blocks' external lengths
     int nb;
     double dd[6];                // the group's dot products l_t . l_q, q <= t (G <= 3)
     double ain[6];               // the group's in-group entries of A, (t, q <= t) at t(t+1)/2 + q (G <= 3)
@@ -67,6 +70,7 @@ __device__ __forceinline__ int find_in(const int32_t *J, int lo, int hi, int32_t
     return -1;
 }
 
+template <int MD, int GM>
 __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t nchunks, const int32_t *__restrict__ ord,
                                                        const int32_t *__restrict__ chunk_grp,
                                                        const int32_t *__restrict__ grp,
@@ -81,7 +85,7 @@ __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t nchunks, const in
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    IcWarpSmem &S = reinterpret_cast<IcWarpSmem *>(smem_raw)[wib];
+    IcWarpSmem<MD, GM> &S = reinterpret_cast<IcWarpSmem<MD, GM> *>(smem_raw)[wib];
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const double qnan = __longlong_as_double(0x7ff8000000000000ll);
@@ -92,7 +96,7 @@ __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t nchunks, const in
         const int32_t s = grp[g];
         const int G = grp[g + 1] - s;
         const int32_t b0 = Lrowptr[s];
-        const int m = Lrowptr[s + 1] - b0 - 1; // external columns (host checked m <= MAXDIM)
+        const int m = Lrowptr[s + 1] - b0 - 1; // external columns (host checked m <= MD)
 
         // 1. external columns, their readiness (relaxed polling, one fence
         // after the last wait), their row starts and lengths, and the blocks
@@ -141,7 +145,7 @@ __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t nchunks, const in
             S.boff[0] = 0;
             for (int b = 0; b < nb; ++b) S.boff[b + 1] += S.boff[b];
         }
-        for (int idx = lane; idx < pm(m, m); idx += 32) S.M[idx] = 0.0; // columns 0..m-1
+        for (int idx = lane; idx < pm<MD>(m, m); idx += 32) S.M[idx] = 0.0; // columns 0..m-1
         __syncwarp();
 
         // gather M[u][v] = L_{J[u],J[v]} (v <= u) block by block: a block's
@@ -183,8 +187,8 @@ __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t nchunks, const in
                 if (v < 0) continue;
 #pragma unroll
                 for (int r = 0; r < 3; ++r)
-                    if (r < gb) S.M[pm(v, u0 + r)] = vv[k][r];
-                for (int r = 3; r < gb; ++r) S.M[pm(v, u0 + r)] = Lval[S.rs[u0 + r] + pp[k]];
+                    if (r < gb) S.M[pm<MD>(v, u0 + r)] = vv[k][r];
+                for (int r = 3; r < gb; ++r) S.M[pm<MD>(v, u0 + r)] = Lval[S.rs[u0 + r] + pp[k]];
             }
         }
         // the blocks' own lower triangles (in-group entries and diagonals)
@@ -193,7 +197,7 @@ __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t nchunks, const in
             for (int r = 0; r < gb; ++r)
                 for (int q2 = 0; q2 <= r; ++q2) {
                     const double val = Lval[S.rs[u0 + r] + me + q2];
-                    S.M[pm(u0 + q2, u0 + r)] = val;
+                    S.M[pm<MD>(u0 + q2, u0 + r)] = val;
                     if (q2 == r) S.invd[u0 + r] = 1.0 / val;
                 }
         }
@@ -201,9 +205,9 @@ __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t nchunks, const in
 
         // 2. external parts of all group rows: forward sweep over v ascending.
         // Lane owns columns u = lane and lane + 32 of every row.
-        double acc0[GMAX], acc1[GMAX];
+        double acc0[GM], acc1[GM];
 #pragma unroll
-        for (int t = 0; t < GMAX; ++t) {
+        for (int t = 0; t < GM; ++t) {
             acc0[t] = 0.0;
             acc1[t] = 0.0;
             if (t < G) {
@@ -220,10 +224,10 @@ __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t nchunks, const in
         for (int v = 0; v < m; ++v) {
             const int owner = v & 31;
             const double iv = S.invd[v];
-            const double mu0 = (lane > v && lane < m) ? S.M[pm(v, lane)] * iv : 0.0;
-            const double mu1 = (lane + 32 > v && lane + 32 < m) ? S.M[pm(v, lane + 32)] * iv : 0.0;
+            const double mu0 = (lane > v && lane < m) ? S.M[pm<MD>(v, lane)] * iv : 0.0;
+            const double mu1 = (lane + 32 > v && lane + 32 < m) ? S.M[pm<MD>(v, lane + 32)] * iv : 0.0;
 #pragma unroll
-            for (int t = 0; t < GMAX; ++t) {
+            for (int t = 0; t < GM; ++t) {
                 if (t < G) {
                     const double a = __shfl_sync(0xffffffffu, (v < 32) ? acc0[t] : acc1[t], owner);
                     acc0[t] = fma(-mu0, a, acc0[t]);
@@ -232,7 +236,7 @@ __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t nchunks, const in
             }
         }
 #pragma unroll
-        for (int t = 0; t < GMAX; ++t) {
+        for (int t = 0; t < GM; ++t) {
             if (t < G) {
                 if (lane < m) S.lg[t][lane] = acc0[t] * S.invd[lane];
                 if (lane + 32 < m) S.lg[t][lane + 32] = acc1[t] * S.invd[lane + 32];
@@ -346,16 +350,18 @@ static int ic0_once(gic_handle *h, const Pattern &P, const double *valA, double 
     ++h->launches;
     k_ic0_prepare<<<(unsigned)blocks, 256, 0, h->stream>>>(P.n, P.Lrowptr, valL, bad_dev);
     GIC_CUDA_TRY(cudaGetLastError());
-    size_t smem = sizeof(IcWarpSmem) * IC_WARPS;
+    const bool small = P.max_ext_lower <= 40 && P.max_group <= 3;
+    const void *fn = small ? (const void *)k_ic0<40, 3> : (const void *)k_ic0<MAXDIM, GMAX>;
+    size_t smem = (small ? sizeof(IcWarpSmem<40, 3>) : sizeof(IcWarpSmem<MAXDIM, GMAX>)) * IC_WARPS;
     // set on every call (a host-side attribute of the current context; cheap)
-    GIC_CUDA_TRY(cudaFuncSetAttribute(k_ic0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GIC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int32_t nc = P.nchunks;
     const int32_t *ord = P.ord_f, *cg = P.chunk_grp, *g = P.grp, *rg = P.rowgrp, *ar = P.rowptr, *lr = P.Lrowptr,
                   *lc = P.Lcol;
     unsigned *er = h->dev_err;
     int poll = h->tune_poll;
     void *args[] = {&nc, &ord, &cg, &g, &rg, &ar, &valA, &lr, &lc, &valL, &alpha, &bad_dev, &er, &poll};
-    GIC_TRY(launch_persistent(h, (const void *)k_ic0, IC_WARPS * 32, smem, nc, args));
+    GIC_TRY(launch_persistent(h, fn, IC_WARPS * 32, smem, nc, args));
     unsigned long long *hb = (unsigned long long *)((char *)h->host_pinned + 2048);
     GIC_CUDA_TRY(cudaMemcpyAsync(hb, bad_dev, sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
     unsigned flags = 0;
