@@ -28,7 +28,7 @@
 
 namespace gic {
 
-constexpr int IC_WARPS = 3; // warps per block: 5 blocks of 3 per SM fit the shared memory
+constexpr int IC_WARPS = 3; // warps per block (the general variant fits 5 such blocks per SM, the hex-sized one 8)
 
 // Packed column-major lower triangle of an MD x MD block: column v holds
 // rows v..MD-1 (the sweep reads a column across lanes, consecutive words,
