@@ -1199,9 +1199,11 @@ static SolveWs carve(const Pattern &PA, const Pattern &PL, int l_dtype, SolveMod
 }
 
 // Workspace bound for a PCG on a pattern not analysed yet (the end-to-end
-// call): the warp-specialised layout plus room for the level-sliced one on
-// patterns like the hex systems' (one slice per 10 groups of 3 rows, a few
-// padded steps); a pattern that needs more runs the warp-specialised solves.
+// call): the warp-specialised layout plus room for the level-sliced and
+// pair-sliced ones on patterns like the hex systems' (level-sliced: one
+// slice per 10 groups of 3 rows, a few padded steps; pair-sliced: ≈ 2x the
+// factor's entries per sweep for the substituted groups' longer lists); a
+// pattern that needs more runs the warp-specialised solves.
 size_t pcg_ws_bytes(int64_t n, int64_t nnzL, int64_t sell_nnz, int l_dtype)
 {
     Pattern P;
@@ -1210,7 +1212,7 @@ size_t pcg_ws_bytes(int64_t n, int64_t nnzL, int64_t sell_nnz, int l_dtype)
     P.sell_nnz = sell_nnz;
     const size_t es = (l_dtype == GIC_F32) ? 4 : 8;
     const SolveMode m = (l_dtype == GIC_F32) ? MODE_Q32 : MODE_Q64;
-    return carve(P, P, l_dtype, m, nullptr).bytes + 2 * es * (size_t)(nnzL / 8 + 8 * n) + 4096;
+    return carve(P, P, l_dtype, m, nullptr).bytes + es * (size_t)(nnzL / 4 * 9 + 16 * n) + 4096;
 }
 
 static unsigned vec_grid(gic_handle *h, int64_t n, int block)
