@@ -648,34 +648,6 @@ __global__ void k_psetup(PairView S, const int32_t *__restrict__ Lrowptr, const 
 }
 
 // ------------------------------------------------------------ solve
-// Wait until no lane of the warp holds a sentinel among its B values (all
-// pending words reloaded together each round; bounded, then ERR_TIMEOUT and
-// NaN values), as in the level-sliced solves.
-template <typename T, int B>
-__device__ __forceinline__ void p_wait(const T *x, const int32_t (&c)[B], T (&v)[B], unsigned *err,
-                                       unsigned sleep_ns, int lane)
-{
-    for (long long it = 0;; ++it) {
-        bool pend = false;
-#pragma unroll
-        for (int b = 0; b < B; ++b) {
-            if (c[b] >= 0 && is_sentinel(v[b])) {
-                v[b] = ld_relaxed(x + c[b]);
-                pend |= is_sentinel(v[b]);
-            }
-        }
-        if (!__any_sync(0xffffffffu, pend)) return;
-        if (it >= SPIN_LIMIT || ((it & 255) == 255 && *((volatile unsigned *)err) != 0u)) {
-            if (it >= SPIN_LIMIT && lane == 0) atomicOr(err, ERR_TIMEOUT);
-#pragma unroll
-            for (int b = 0; b < B; ++b)
-                if (c[b] >= 0 && is_sentinel(v[b])) v[b] = qnan_of<T>();
-            return;
-        }
-        if (it >= 32) __nanosleep(it >= 65536 ? 256 : (sleep_ns ? sleep_ns : 32));
-    }
-}
-
 // FWD: L y = r (x = y, rhs = r). Backward: L^T z = y (x = z, rhs = y); with
 // PCG it also forms r^T z in FP64 and beta = r_k^T z_k / r_{k-1}^T z_{k-1}
 // (Algorithm 1) in the last warp to finish. x must hold the sentinel; the
@@ -778,7 +750,7 @@ __global__ void __launch_bounds__(PBLOCK, 4) k_psolve(PairView S, const T *__res
                 cn[b] = (act && k < We) ? cp[(int64_t)k * cs] : -1;
                 kn[b] = (k < We) ? kp[(int64_t)k * 32] : (T)0;
             }
-            p_wait<T, PBATCH>(x, c, v, err, sleep_ns, lane);
+            slice_wait<T, PBATCH>(x, c, v, err, sleep_ns, lane);
             if (k0 == 0) {
 #pragma unroll
                 for (int b = 0; b < PRHS; ++b)
@@ -816,7 +788,7 @@ __global__ void __launch_bounds__(PBLOCK, 4) k_psolve(PairView S, const T *__res
             for (int b = 0; b < PFAR; ++b) vf[b] = (cf[b] >= 0) ? ld_relaxed(x + cf[b]) : (T)0;
 #pragma unroll
             for (int b = 0; b < PNEAR; ++b) vq[b] = (cq[b] >= 0) ? ld_relaxed(x + cq[b]) : (T)0;
-            p_wait<T, PFAR>(x, cf, vf, err, sleep_ns, lane);
+            slice_wait<T, PFAR>(x, cf, vf, err, sleep_ns, lane);
 #pragma unroll
             for (int b = 0; b < PFAR; ++b) {
                 if (b < Wf) { // uniform over the warp
@@ -827,7 +799,7 @@ __global__ void __launch_bounds__(PBLOCK, 4) k_psolve(PairView S, const T *__res
                     else acc3 = fma(kb, vf[b], acc3);
                 }
             }
-            p_wait<T, PNEAR>(x, cq, vq, err, sleep_ns, lane);
+            slice_wait<T, PNEAR>(x, cq, vq, err, sleep_ns, lane);
 #pragma unroll
             for (int b = 0; b < PNEAR; ++b) {
                 if (b < Wn) {

@@ -123,6 +123,37 @@ int bsr_spmv(gic_handle *h, const Pattern &P, int mode, const double *bval, cons
              const double *b, double *partials, Scalars *sc);
 
 // automatic solve choice: level-sliced kernels from this many chunks per SM
+// Level- and pair-sliced solves: wait until no lane of the warp holds a
+// sentinel among its B values. All pending words are reloaded together each
+// round (the values of a wave come from several slices and land at
+// different times, so polling them one at a time would serialise their
+// round trips: measured 1.5x slower), with a short back-off after the first
+// rounds; bounded (then ERR_TIMEOUT and NaN values).
+template <typename T, int B>
+__device__ __forceinline__ void slice_wait(const T *x, const int32_t (&c)[B], T (&v)[B], unsigned *err,
+                                       unsigned sleep_ns, int lane)
+{
+    for (long long it = 0;; ++it) {
+        bool pend = false;
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            if (c[b] >= 0 && is_sentinel(v[b])) {
+                v[b] = ld_relaxed(x + c[b]);
+                pend |= is_sentinel(v[b]);
+            }
+        }
+        if (!__any_sync(0xffffffffu, pend)) return;
+        if (it >= SPIN_LIMIT || ((it & 255) == 255 && *((volatile unsigned *)err) != 0u)) {
+            if (it >= SPIN_LIMIT && lane == 0) atomicOr(err, ERR_TIMEOUT);
+#pragma unroll
+            for (int b = 0; b < B; ++b)
+                if (c[b] >= 0 && is_sentinel(v[b])) v[b] = qnan_of<T>();
+            return;
+        }
+        if (it >= 32) __nanosleep(it >= 65536 ? 256 : (sleep_ns ? sleep_ns : 32));
+    }
+}
+
 constexpr int SLICED_CHUNKS_PER_SM = 48;
 // Automatic choice of the solve kernels by chunks (for hex elasticity the
 // x-pencils) per SM, measured on the hex systems from 40^3 to 148^3: below

@@ -59,36 +59,6 @@ static SliceView view_of(const SliceSched &S)
     return SliceView{S.nsl, S.w, S.we, S.ng, S.kv, S.kc, S.lane, S.col};
 }
 
-// Wait until no lane of the warp holds a sentinel among its B values: all
-// pending words are reloaded together each round (the values of a wave come
-// from several slices and land at different times, so polling them one at a
-// time would serialise their round trips: measured 1.5x slower), with a short
-// back-off after the first rounds; bounded (then ERR_TIMEOUT and NaN values).
-template <typename T, int B>
-__device__ __forceinline__ void s_wait(const T *x, const int32_t (&c)[B], T (&v)[B], unsigned *err,
-                                       unsigned sleep_ns, int lane)
-{
-    for (long long it = 0;; ++it) {
-        bool pend = false;
-#pragma unroll
-        for (int b = 0; b < B; ++b) {
-            if (c[b] >= 0 && is_sentinel(v[b])) {
-                v[b] = ld_relaxed(x + c[b]);
-                pend |= is_sentinel(v[b]);
-            }
-        }
-        if (!__any_sync(0xffffffffu, pend)) return;
-        if (it >= SPIN_LIMIT || ((it & 255) == 255 && *((volatile unsigned *)err) != 0u)) {
-            if (it >= SPIN_LIMIT && lane == 0) atomicOr(err, ERR_TIMEOUT);
-#pragma unroll
-            for (int b = 0; b < B; ++b)
-                if (c[b] >= 0 && is_sentinel(v[b])) v[b] = qnan_of<T>();
-            return;
-        }
-        if (it >= 32) __nanosleep(it >= 65536 ? 256 : (sleep_ns ? sleep_ns : 32));
-    }
-}
-
 // FWD: L y = r (x = y, rhs = r). Backward: L^T z = y (x = z, rhs = y); with
 // PCG it also resets y to the sentinel for the next forward sweep and forms
 // r^T z in FP64, then beta = r_k^T z_k / r_{k-1}^T z_{k-1} (Algorithm 1) in
@@ -170,7 +140,7 @@ __global__ void __launch_bounds__(SBLOCK, 2) k_ssolve(SliceView S, const T *__re
                 cn[b] = (act && k < We) ? cp[(int64_t)k * ng] : -1;
                 kn[b] = (k < We) ? kp[(int64_t)k * 32] : (T)0;
             }
-            s_wait<T, SBATCH>(x, c, v, err, sleep_ns, lane);
+            slice_wait<T, SBATCH>(x, c, v, err, sleep_ns, lane);
 #pragma unroll
             for (int b = 0; b < SBATCH; ++b) {
                 if (k0 + b < We) { // uniform over the warp
@@ -208,7 +178,7 @@ __global__ void __launch_bounds__(SBLOCK, 2) k_ssolve(SliceView S, const T *__re
 #pragma unroll
             for (int b = 0; b < SNEAR; ++b) vn[b] = (cn2[b] >= 0) ? ld_relaxed(x + cn2[b]) : (T)0;
             cp_async_wait<0>(); // this lane's late coefficients are in shared memory
-            s_wait<T, SFAR>(x, cf, vf, err, sleep_ns, lane);
+            slice_wait<T, SFAR>(x, cf, vf, err, sleep_ns, lane);
 #pragma unroll
             for (int b = 0; b < SFAR; ++b) {
                 if (b < Wf) { // uniform over the warp
@@ -219,7 +189,7 @@ __global__ void __launch_bounds__(SBLOCK, 2) k_ssolve(SliceView S, const T *__re
                     else acc3 = fma(kb, vf[b], acc3);
                 }
             }
-            s_wait<T, SNEAR>(x, cn2, vn, err, sleep_ns, lane);
+            slice_wait<T, SNEAR>(x, cn2, vn, err, sleep_ns, lane);
 #pragma unroll
             for (int b = 0; b < SNEAR; ++b) {
                 if (b < Wn) {
