@@ -980,7 +980,28 @@ __global__ void __launch_bounds__(VEC_BLOCK) k_update_p(int64_t n, ZT *z, double
     if (sc->done) return;
     const int first = (sc->iter == 0);
     const double beta = sc->beta;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    // two independent elements per iteration (twice the loads in flight)
+    const int64_t st = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + st < n; i += 2 * st) {
+        const int64_t j = i + st;
+        if (IDENT) {
+            const double zi = r[i], zj = r[j], pi = first ? 0.0 : p[i], pj = first ? 0.0 : p[j];
+            p[i] = first ? zi : fma(beta, pi, zi);
+            p[j] = first ? zj : fma(beta, pj, zj);
+        } else {
+            const double zi = (double)z[i], zj = (double)z[j], pi = first ? 0.0 : p[i], pj = first ? 0.0 : p[j];
+            p[i] = first ? zi : fma(beta, pi, zi);
+            p[j] = first ? zj : fma(beta, pj, zj);
+            z[i] = sentinel_of<ZT>();
+            z[j] = sentinel_of<ZT>();
+            if (yr) {
+                yr[i] = sentinel_of<ZT>();
+                yr[j] = sentinel_of<ZT>();
+            }
+        }
+    }
+    if (i < n) {
         if (IDENT) {
             const double zi = r[i];
             p[i] = first ? zi : fma(beta, p[i], zi);
@@ -1029,7 +1050,25 @@ __global__ void __launch_bounds__(VEC_BLOCK) k_update_xr(int64_t n, double *x, d
     __shared__ double sh[VEC_BLOCK / 32];
     const double alpha = sc->alpha;
     double d = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    // two independent elements per iteration (twice the loads in flight)
+    const int64_t st = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + st < n; i += 2 * st) {
+        const int64_t j = i + st;
+        const double pi = p[i], pj = p[j], wi = w[i], wj = w[j], xi = x[i], xj = x[j], r0 = r[i], r1 = r[j];
+        x[i] = fma(alpha, pi, xi);
+        x[j] = fma(alpha, pj, xj);
+        const double ri = fma(-alpha, wi, r0), rj = fma(-alpha, wj, r1);
+        r[i] = ri;
+        r[j] = rj;
+        if (r32) {
+            r32[i] = (float)ri;
+            r32[j] = (float)rj;
+        }
+        d = fma(ri, ri, d);
+        d = fma(rj, rj, d);
+    }
+    if (i < n) {
         x[i] = fma(alpha, p[i], x[i]);
         const double ri = fma(-alpha, w[i], r[i]);
         r[i] = ri;
@@ -1218,7 +1257,7 @@ size_t pcg_ws_bytes(int64_t n, int64_t nnzL, int64_t sell_nnz, int l_dtype)
 static unsigned vec_grid(gic_handle *h, int64_t n, int block)
 {
     int64_t b = (n + block - 1) / block;
-    int64_t cap = (int64_t)h->num_sms * 4;
+    int64_t cap = (int64_t)h->num_sms * 8; // 64 warps per SM: enough loads in flight for HBM
     if (b > cap) b = cap;
     if (b < 1) b = 1;
     return (unsigned)b;
