@@ -262,15 +262,28 @@ __global__ void k_gn_finish(int pass, int64_t ng, const double *partials, int np
     else sig[9 * g + f] = sqrt(s / (double)ng + 1e-5);
 }
 
-__global__ void k_gn_apply(int64_t n, int64_t ng, const float *x9, const float *theta, const double *mu,
-                           const double *sig, float *x0)
+__global__ void k_gn_apply(int64_t n, int64_t ng, int ngraphs, const float *x9, const float *theta,
+                           const double *mu, const double *sig, float *x0)
 {
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * 9; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t v = t / 9;
-        const int f = (int)(t % 9);
-        const int g = (int)(v / ng);
-        double c = (double)x9[t] - (double)theta[18 + f] * mu[9 * g + f];
-        x0[t] = (float)((double)theta[f] * c / sig[9 * g + f] + (double)theta[9 + f]);
+    // per graph and feature: alpha mu and gamma / sigma (one division each)
+    __shared__ double am[16 * 9], gs[16 * 9];
+    for (int k = threadIdx.x; k < 9 * ngraphs && k < 16 * 9; k += blockDim.x) {
+        const int f = k % 9;
+        am[k] = (double)theta[18 + f] * mu[k];
+        gs[k] = (double)theta[f] / sig[k];
+    }
+    __syncthreads();
+    // one node per thread, its nine features contiguous
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int g = (ngraphs == 1) ? 0 : (int)(v / ng);
+#pragma unroll
+        for (int f = 0; f < 9; ++f) {
+            const int k = 9 * g + f;
+            const double a = (g < 16) ? am[k] : (double)theta[18 + f] * mu[k];
+            const double q = (g < 16) ? gs[k] : (double)theta[f] / sig[k];
+            const double c = (double)x9[9 * v + f] - a;
+            x0[9 * v + f] = (float)(q * c + (double)theta[9 + f]);
+        }
     }
 }
 
@@ -893,7 +906,7 @@ static int graphnorm(gic_handle *h, const Pattern &p, int ngraphs, const float *
     ++h->launches;
     k_gn_finish<<<ngraphs, 32, 0, h->stream>>>(1, ng, parts, GX, mu, sig);
     ++h->launches;
-    k_gn_apply<<<grid1(h, p.n * 9), 256, 0, h->stream>>>(p.n, ng, x9, theta, mu, sig, x0);
+    k_gn_apply<<<grid1(h, p.n), 256, 0, h->stream>>>(p.n, ng, ngraphs, x9, theta, mu, sig, x0);
     GIC_CUDA_TRY(cudaGetLastError());
     return GIC_OK;
 }
