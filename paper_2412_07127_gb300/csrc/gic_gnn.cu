@@ -64,20 +64,27 @@ __device__ __forceinline__ double block_sum_d(double v, double *sh)
 // ------------------------------------------------------------ A4 features
 // pass 0: sum of tril values per graph; pass 1: sum of squared deviations.
 // Sums over graph g's lower-triangle entries of A (pass 0: values; pass 1:
-// squared deviations from the mean), one thread per entry (coalesced): L
-// entry e of row i = Lrow[e] is A entry rowptr[i] + (e - Lrowptr[i]).
+// squared deviations from the mean): eight lanes per row (a row's lower
+// entries are the first Lrowptr[i+1] - Lrowptr[i] of its A entries; full
+// sectors, several loads in flight per lane), rows strided over the grid.
 __global__ void k_tril_moments(int pass, int64_t ng, const int32_t *rowptr, const int32_t *Lrowptr,
-                               const int32_t *Lrow, const double *valA, const double *mean, double *partials)
+                               const double *valA, const double *mean, double *partials)
 {
     __shared__ double sh[RB / 32];
     const int g = blockIdx.y;
-    const int64_t e0 = Lrowptr[(int64_t)g * ng], e1 = Lrowptr[(int64_t)(g + 1) * ng];
+    const int64_t r0 = (int64_t)g * ng;
     const double mu = pass ? mean[g] : 0.0;
+    const int sl = threadIdx.x & 7;
+    const int64_t q0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const int64_t nq = ((int64_t)gridDim.x * blockDim.x) >> 3;
     double acc = 0.0;
-    for (int64_t e = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < e1; e += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t i = Lrow[e];
-        const double v = valA[rowptr[i] + (e - Lrowptr[i])];
-        acc += pass ? (v - mu) * (v - mu) : v;
+    for (int64_t i = r0 + q0; i < r0 + ng; i += nq) {
+        const int32_t a = rowptr[i], cnt = Lrowptr[i + 1] - Lrowptr[i];
+#pragma unroll 4
+        for (int32_t k = sl; k < cnt; k += 8) {
+            const double v = valA[a + k];
+            acc += pass ? (v - mu) * (v - mu) : v;
+        }
     }
     double s = block_sum_d(acc, sh);
     if (threadIdx.x == 0) partials[g * gridDim.x + blockIdx.x] = s;
@@ -420,11 +427,16 @@ __global__ void k_correct_bwd(int64_t E, const int32_t *Lrow, const int32_t *Lco
 }
 
 // LhatIC = LIC / sqrt(s) per graph, FP32.
-__global__ void k_scale_factor(int64_t E, int64_t ng, const int32_t *Lrow, const double *LIC, const double *scale,
-                               float *out)
+__global__ void k_scale_factor(int64_t E, int64_t ng, int ngraphs, const int32_t *Lrow, const double *LIC,
+                               const double *scale, float *out)
 {
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x)
-        out[p] = (float)(LIC[p] / sqrt(scale[Lrow[p] / ng]));
+    __shared__ double sq[64]; // sqrt(s) per graph, once per block
+    for (int k = threadIdx.x; k < ngraphs && k < 64; k += blockDim.x) sq[k] = sqrt(scale[k]);
+    __syncthreads();
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < E; p += (int64_t)gridDim.x * blockDim.x) {
+        const int g = (ngraphs == 1) ? 0 : (int)((uint32_t)Lrow[p] / (uint32_t)ng); // rows and ng fit 32 bits
+        out[p] = (float)(LIC[p] / ((g < 64) ? sq[g] : sqrt(scale[g])));
+    }
 }
 
 // ------------------------------------------------------------ A8 probe loss
@@ -1019,17 +1031,17 @@ int gic_features(gic_handle *h, const gic_pattern *P, int ngraphs, const double 
     double *mean = (double *)h->dev_small;            // ngraphs <= 4096
     double *parts = (double *)h->dev_small + 4096;    // GX * ngraphs, checked below
     if ((size_t)(4096 + GX * ngraphs) * 8 > 60000) return GIC_ERR_UNSUPPORTED;
-    // the moments run one thread per lower entry: as many blocks per graph
-    // as the partials area holds, up to 8 per SM in all
+    // the moments: as many blocks per graph as the partials area holds, up
+    // to 8 per SM in all
     const int gx = (int)std::max<int64_t>(GX, std::min<int64_t>((int64_t)h->num_sms * 8 / ngraphs,
                                                                (60000 / 8 - 4096) / ngraphs));
     dim3 gr(gx, ngraphs);
     ++h->launches;
-    k_tril_moments<<<gr, RB, 0, h->stream>>>(0, ng, p.rowptr, p.Lrowptr, p.Lrow, valA, mean, parts);
+    k_tril_moments<<<gr, RB, 0, h->stream>>>(0, ng, p.rowptr, p.Lrowptr, valA, mean, parts);
     ++h->launches;
     k_tril_finish<<<ngraphs, 32, 0, h->stream>>>(0, ng, p.Lrowptr, parts, gx, mean, scale_dev);
     ++h->launches;
-    k_tril_moments<<<gr, RB, 0, h->stream>>>(1, ng, p.rowptr, p.Lrowptr, p.Lrow, valA, mean, parts);
+    k_tril_moments<<<gr, RB, 0, h->stream>>>(1, ng, p.rowptr, p.Lrowptr, valA, mean, parts);
     ++h->launches;
     k_tril_finish<<<ngraphs, 32, 0, h->stream>>>(1, ng, p.Lrowptr, parts, gx, mean, scale_dev);
     ++h->launches;
@@ -1173,7 +1185,8 @@ int gic_scale_factor(gic_handle *h, const gic_pattern *P, int ngraphs, const dou
     if (!LIC || !scale_dev || !LIChat) return GIC_ERR_INVALID_ARG;
     const Pattern &p = P->p;
     ++h->launches;
-    k_scale_factor<<<grid1(h, p.nnzL), 256, 0, h->stream>>>(p.nnzL, p.n / ngraphs, p.Lrow, LIC, scale_dev, LIChat);
+    k_scale_factor<<<grid1(h, p.nnzL), 256, 0, h->stream>>>(p.nnzL, p.n / ngraphs, ngraphs, p.Lrow, LIC, scale_dev,
+                                                            LIChat);
     GIC_CUDA_TRY(cudaGetLastError());
     return GIC_OK;
 }
