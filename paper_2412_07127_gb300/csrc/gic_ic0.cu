@@ -148,9 +148,14 @@ __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t nchunks, const in
         for (int idx = lane; idx < pm<MD>(m, m); idx += 32) S.M[idx] = 0.0; // columns 0..m-1
         __syncwarp();
 
-        // gather M[u][v] = L_{J[u],J[v]} (v <= u) block by block: a block's
-        // external column is looked up in J once for all its rows; four
-        // (column, values) reads in flight per lane
+        // 1 / L_{J[v],J[v]} (the last entry of row J[v]) first: the gather
+        // stores each column already scaled by it, so the sweep's dependent
+        // step is one shuffle and one FMA with no multiply per column
+        for (int u = lane; u < m; u += 32) S.invd[u] = 1.0 / Lval[S.rs[u] + S.len[u] - 1];
+        __syncwarp();
+        // gather M[u][v] / M[v][v] = L_{J[u],J[v]} / L_{J[v],J[v]} (v < u)
+        // block by block: a block's external column is looked up in J once
+        // for all its rows; four (column, values) reads in flight per lane
         const int nb = S.nb, PT = S.boff[nb];
         int bcur = 0;
         for (int base = lane; base < PT; base += 128) {
@@ -185,21 +190,20 @@ __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t nchunks, const in
                 const int u0 = S.bu0[bb[k]], gb = S.bG[bb[k]];
                 const int v = find_in(S.J, 0, u0, cc[k]);
                 if (v < 0) continue;
+                const double iv = S.invd[v];
 #pragma unroll
                 for (int r = 0; r < 3; ++r)
-                    if (r < gb) S.M[pm<MD>(v, u0 + r)] = vv[k][r];
-                for (int r = 3; r < gb; ++r) S.M[pm<MD>(v, u0 + r)] = Lval[S.rs[u0 + r] + pp[k]];
+                    if (r < gb) S.M[pm<MD>(v, u0 + r)] = vv[k][r] * iv;
+                for (int r = 3; r < gb; ++r) S.M[pm<MD>(v, u0 + r)] = Lval[S.rs[u0 + r] + pp[k]] * iv;
             }
         }
-        // the blocks' own lower triangles (in-group entries and diagonals)
+        // the blocks' own strictly lower triangles (in-group entries), scaled
+        // the same way
         for (int b = lane; b < nb; b += 32) {
             const int u0 = S.bu0[b], gb = S.bG[b], me = S.boff[b + 1] - S.boff[b];
-            for (int r = 0; r < gb; ++r)
-                for (int q2 = 0; q2 <= r; ++q2) {
-                    const double val = Lval[S.rs[u0 + r] + me + q2];
-                    S.M[pm<MD>(u0 + q2, u0 + r)] = val;
-                    if (q2 == r) S.invd[u0 + r] = 1.0 / val;
-                }
+            for (int r = 1; r < gb; ++r)
+                for (int q2 = 0; q2 < r; ++q2)
+                    S.M[pm<MD>(u0 + q2, u0 + r)] = Lval[S.rs[u0 + r] + me + q2] * S.invd[u0 + q2];
         }
         __syncwarp();
 
@@ -217,15 +221,14 @@ __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t nchunks, const in
             }
         }
         // Column v's accumulator is final once the sweep reaches it, so each
-        // step broadcasts it unscaled and the lanes fold 1 / M[v][v] into
-        // their coefficient (independent of the chain, issued ahead): the
-        // dependent chain per step is one shuffle and one FMA; the values
-        // l = acc / M[v][v] are formed once at the end.
+        // step broadcasts it unscaled and the lanes apply their coefficient,
+        // stored already divided by M[v][v]: the dependent chain per step is
+        // one shuffle and one FMA; the values l = acc / M[v][v] are formed
+        // once at the end.
         for (int v = 0; v < m; ++v) {
             const int owner = v & 31;
-            const double iv = S.invd[v];
-            const double mu0 = (lane > v && lane < m) ? S.M[pm<MD>(v, lane)] * iv : 0.0;
-            const double mu1 = (lane + 32 > v && lane + 32 < m) ? S.M[pm<MD>(v, lane + 32)] * iv : 0.0;
+            const double mu0 = (lane > v && lane < m) ? S.M[pm<MD>(v, lane)] : 0.0;
+            const double mu1 = (lane + 32 > v && lane + 32 < m) ? S.M[pm<MD>(v, lane + 32)] : 0.0;
 #pragma unroll
             for (int t = 0; t < GM; ++t) {
                 if (t < G) {
