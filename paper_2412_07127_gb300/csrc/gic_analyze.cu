@@ -670,6 +670,7 @@ static void free_pattern(Pattern &p)
     free_psched(p.pf);
     free_psched(p.pb);
     cudaFree(p.glev);
+    cudaFree(p.ic_ord);
     free_bsr(p);
     p = Pattern();
 }
@@ -848,6 +849,39 @@ static int build_qsched(gic_handle *h, Pattern &P)
 }
 
 
+__global__ void k_group_glev(int32_t ngroups, const int32_t *grp, const int32_t *glev, int32_t *out)
+{
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += (int64_t)gridDim.x * blockDim.x)
+        out[g] = glev[grp[g]];
+}
+
+// IC(0)'s schedule: the groups in group-level order (stable counting sort
+// on the host; index order within a level). Every dependency of a group is
+// at a lower level, so a co-resident grid taking them round-robin always
+// has the first unfinished one runnable.
+static int build_ic_order(gic_handle *h, Pattern &P, int32_t *tmp)
+{
+    const int32_t ng = P.ngroups;
+    if (ng == 0 || P.nglev <= 0) return GIC_OK;
+    ++h->launches;
+    k_group_glev<<<grid_rows(h, ng), T_ROWS, 0, h->stream>>>(ng, P.grp, P.glev, tmp);
+    GIC_CUDA_TRY(cudaGetLastError());
+    std::vector<int32_t> gl(ng), ord(ng);
+    std::vector<int64_t> cnt((size_t)P.nglev + 1, 0);
+    GIC_CUDA_TRY(cudaMemcpyAsync(gl.data(), tmp, 4 * (size_t)ng, cudaMemcpyDeviceToHost, h->stream));
+    GIC_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    for (int32_t g = 0; g < ng; ++g) {
+        if (gl[g] < 0 || gl[g] >= P.nglev) return GIC_ERR_INVALID_ARG;
+        ++cnt[gl[g] + 1];
+    }
+    for (int32_t k = 0; k < P.nglev; ++k) cnt[k + 1] += cnt[k];
+    for (int32_t g = 0; g < ng; ++g) ord[cnt[gl[g]]++] = g;
+    GIC_CUDA_TRY(cudaMalloc(&P.ic_ord, 4 * (size_t)ng));
+    GIC_CUDA_TRY(cudaMemcpyAsync(P.ic_ord, ord.data(), 4 * (size_t)ng, cudaMemcpyHostToDevice, h->stream));
+    GIC_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return GIC_OK;
+}
+
 static int analyze_impl(gic_handle *h, int64_t n, int64_t nnz, const int32_t *rowptr, const int32_t *col, Pattern &P)
 {
     P.n = n;
@@ -966,6 +1000,7 @@ static int analyze_impl(gic_handle *h, int64_t n, int64_t nnz, const int32_t *ro
     }
     STEP(read_and_clear_dev_err(h, &flags));
     if (flags & ERR_TIMEOUT) { rc = GIC_ERR_TIMEOUT; goto out; }
+    STEP(build_ic_order(h, P, gflag));
     STEP(build_schedule(h, P, gflag, gid, tmp2_a, tmp2_b));
     STEP(build_bsr(h, P));
     if (!P.bsr_ready) STEP(build_sell(h, P)); // the SELL-32 copy serves only patterns without node blocks

@@ -91,8 +91,10 @@ __global__ void __launch_bounds__(IC_WARPS * 32) k_ic0(int32_t nchunks, const in
     const double qnan = __longlong_as_double(0x7ff8000000000000ll);
 
     for (int64_t pos = w; pos < nchunks; pos += nw) {
+      // chunks of consecutive groups, or (chunk_grp null) single groups
       const int32_t ch = ord[pos];
-      for (int32_t g = chunk_grp[ch]; g < chunk_grp[ch + 1]; ++g) {
+      const int32_t g0 = chunk_grp ? chunk_grp[ch] : ch, g1 = chunk_grp ? chunk_grp[ch + 1] : ch + 1;
+      for (int32_t g = g0; g < g1; ++g) {
         const int32_t s = grp[g];
         const int G = grp[g + 1] - s;
         const int32_t b0 = Lrowptr[s];
@@ -358,9 +360,11 @@ static int ic0_once(gic_handle *h, const Pattern &P, const double *valA, double 
     size_t smem = (small ? sizeof(IcWarpSmem<40, 3>) : sizeof(IcWarpSmem<MAXDIM, GMAX>)) * IC_WARPS;
     // set on every call (a host-side attribute of the current context; cheap)
     GIC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int32_t nc = P.nchunks;
-    const int32_t *ord = P.ord_f, *cg = P.chunk_grp, *g = P.grp, *rg = P.rowgrp, *ar = P.rowptr, *lr = P.Lrowptr,
-                  *lc = P.Lcol;
+    // single groups in group-level order where the analysis made that order
+    // (warps take the next ready group instead of walking a whole chunk)
+    int32_t nc = P.ic_ord ? P.ngroups : P.nchunks;
+    const int32_t *ord = P.ic_ord ? P.ic_ord : P.ord_f, *cg = P.ic_ord ? nullptr : P.chunk_grp, *g = P.grp,
+                  *rg = P.rowgrp, *ar = P.rowptr, *lr = P.Lrowptr, *lc = P.Lcol;
     unsigned *er = h->dev_err;
     int poll = h->tune_poll;
     void *args[] = {&nc, &ord, &cg, &g, &rg, &ar, &valA, &lr, &lc, &valL, &alpha, &bad_dev, &er, &poll};

@@ -351,6 +351,7 @@ struct Pattern {
     // pairs. Needs groups of at most 3 rows.
     int32_t nglev = 0;
     int32_t *glev = nullptr;
+    int32_t *ic_ord = nullptr; // the groups in group-level order (IC(0)'s schedule)
     int pready = 0, pwhy = 0; // pwhy: why not built (bits, see gic_psolve.cu)
     PairSched pf, pb;
     int device = 0;
