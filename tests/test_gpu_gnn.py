@@ -1,7 +1,8 @@
 """GPU parity of the GNN correction and its training path (A4-A6, A8-A10)
 against the FP64 oracle, through the C-ABI. The GPU computes in FP32: graph
 inputs to FP32 rounding, the GNN output g and the probe loss within 1e-5
-relative (norm-wise), gradients within 1e-3 (sums over many edges in FP32)."""
+relative (norm-wise), gradients within 1e-3 (FP32 activations whose rounding
+sums over many edges of both signs amplify)."""
 import numpy as np
 import pytest
 import torch

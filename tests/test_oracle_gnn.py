@@ -308,3 +308,41 @@ def test_gnn_forward_hand_worked_two_nodes():
     assert np.allclose(M0, gold["M0"], rtol=1e-14, atol=1e-15)
     assert np.allclose(x1[:, :2], gold["x1_f0_f1"], rtol=1e-14, atol=1e-15)
     assert np.allclose(g, gold["g"], rtol=1e-14, atol=1e-15)
+
+
+def _two_copies(A):
+    """A (+) A: the block-diagonal matrix of two disjoint copies of A."""
+    n, nnz = A.n, A.nnz
+    rowptr = np.concatenate([A.rowptr, A.rowptr[1:] + nnz])
+    return O.CSR(rowptr, np.concatenate([A.col, A.col + n]), np.concatenate([A.val, A.val]))
+
+
+def test_two_disjoint_copies_give_each_copy_its_own_output():
+    """One graph made of two disjoint copies of a graph: the features are the
+    copy's own except the row position (sin i, cos i), the scale s (a
+    population deviation) is unchanged, and with the copy's inputs stacked
+    twice the network's output is the copy's output twice -- aggregation
+    stays within a component, and GraphNorm's per-feature mean and mean
+    square over all nodes are unchanged by duplication. A dropped
+    self-loop, a neighbour index off by one or a norm over edges instead of
+    nodes would break it."""
+    A, T = _graph(36, 11)
+    A2 = _two_copies(A)
+    T2 = O.lower(A2)
+    assert np.array_equal(T2.rowptr, np.concatenate([T.rowptr, T.rowptr[1:] + T.nnz]))
+    x9, e0, s = O.features(A)
+    x92, e02, s2 = O.features(A2)
+    assert abs(s2 - s) <= 1e-14 * s
+    assert np.allclose(x92[:A.n, :7], x9[:, :7], rtol=1e-13, atol=1e-13)
+    assert np.allclose(x92[A.n:, :7], x9[:, :7], rtol=1e-13, atol=1e-13)
+    assert np.allclose(x92[:, 7], np.sin(np.arange(2 * A.n)), atol=1e-13)
+    assert np.allclose(e02, np.concatenate([e0, e0]), rtol=1e-13, atol=1e-15)
+    th = I.gnn_init(3, out_scale=1.0)
+    rng = np.random.default_rng(12)
+    for name in ("gn_gamma", "gn_beta", "gn_alpha"):
+        off, shape = I.param_slices()[name]
+        th[off:off + int(np.prod(shape))] = rng.uniform(0.3, 1.5, int(np.prod(shape)))
+    g = O.gnn_forward(T, x9, e0, th)
+    g2 = O.gnn_forward(T2, np.vstack([x9, x9]), np.concatenate([e0, e0]), th)
+    assert np.abs(g).max() > 0
+    assert np.allclose(g2, np.concatenate([g, g]), rtol=1e-11, atol=1e-13 * np.abs(g).max())
