@@ -321,11 +321,11 @@ def test_two_disjoint_copies_give_each_copy_its_own_output():
     """One graph made of two disjoint copies of a graph: the features are the
     copy's own except the row position (sin i, cos i), the scale s (a
     population deviation) is unchanged, and with the copy's inputs stacked
-    twice the network's output is the copy's output twice -- aggregation
-    stays within a component, and GraphNorm's per-feature mean and mean
-    square over all nodes are unchanged by duplication. A dropped
-    self-loop, a neighbour index off by one or a norm over edges instead of
-    nodes would break it."""
+    twice the network's output is the copy's output twice: messages and
+    neighbour reads stay within a component (an index shifted by one
+    leaks across the border between the copies) and GraphNorm's statistics
+    are means, unchanged by duplication (a sum, or a count of the graph's
+    size, would change them)."""
     A, T = _graph(36, 11)
     A2 = _two_copies(A)
     T2 = O.lower(A2)
