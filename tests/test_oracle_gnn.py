@@ -321,11 +321,12 @@ def test_two_disjoint_copies_give_each_copy_its_own_output():
     """One graph made of two disjoint copies of a graph: the features are the
     copy's own except the row position (sin i, cos i), the scale s (a
     population deviation) is unchanged, and with the copy's inputs stacked
-    twice the network's output is the copy's output twice: messages and
-    neighbour reads stay within a component (an index shifted by one
-    leaks across the border between the copies) and GraphNorm's statistics
-    are means, unchanged by duplication (a sum, or a count of the graph's
-    size, would change them)."""
+    twice the network's output is the copy's output twice: messages stay
+    within a component (one added to the next row instead of its own leaks
+    across the border between the copies) and GraphNorm's statistics are
+    means over all nodes, unchanged by duplication (a divisor other than
+    the node count would change them). Both mistakes, planted in the
+    oracle, fail this test."""
     A, T = _graph(36, 11)
     A2 = _two_copies(A)
     T2 = O.lower(A2)
