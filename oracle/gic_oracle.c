@@ -33,7 +33,9 @@
  *                             full-row counts / row sums of A (each edge to
  *                             both endpoints, a self-loop once), means = sums
  *                             / incident-edge count; a hand-worked 2-node
- *                             graph; an independent dense restatement. The
+ *                             graph; two disjoint copies in one graph give
+ *                             the copy's output twice; an independent dense
+ *                             restatement. The
  *                             layout itself is a reading (Figure 1 is missing
  *                             from the text): parity unpinned against the
  *                             paper for the architecture, not its arithmetic.
