@@ -405,8 +405,8 @@ static int build_pdir(gic_handle *h, Pattern &P, int paired, const std::vector<i
     const unsigned gr = pgrid(h, ng);
     int64_t *doff = nullptr, *droff = nullptr;
     int32_t *list = nullptr, *rlist = nullptr;
-    int rc = GIC_OK;
-    do {
+    // the body returns early on any error; the temporaries are freed after it
+    const int rc = [&]() -> int {
         GIC_CUDA_TRY(cudaMemsetAsync(dflag, 0, sizeof(unsigned), h->stream));
         ++h->launches;
         k_pcomp<FWD, 0><<<gr, 256, 0, h->stream>>>(P.n, ng, paired, P.grp, P.rowgrp, P.glev, P.Lrowptr, P.Lcol,
@@ -421,8 +421,7 @@ static int build_pdir(gic_handle *h, Pattern &P, int paired, const std::vector<i
         GIC_CUDA_TRY(cudaStreamSynchronize(h->stream));
         if (flag) {
             P.pwhy |= (int)flag;
-            rc = GIC_ERR_UNSUPPORTED;
-            break;
+            return GIC_ERR_UNSUPPORTED;
         }
         std::vector<int64_t> off(ng), roff(ng);
         int64_t tot = 0, rtot = 0;
@@ -433,8 +432,8 @@ static int build_pdir(gic_handle *h, Pattern &P, int paired, const std::vector<i
             tot += (k & 255) + ((k >> 8) & 255) + ((k >> 16) & 255) + ((k >> 24) & 255);
             rtot += rcnt[g];
         }
-        if ((rc = to_device(h, &doff, off)) != GIC_OK) break;
-        if ((rc = to_device(h, &droff, roff)) != GIC_OK) break;
+        GIC_TRY(to_device(h, &doff, off));
+        GIC_TRY(to_device(h, &droff, roff));
         GIC_CUDA_TRY(cudaMalloc(&list, 4 * (size_t)(tot > 0 ? tot : 1)));
         GIC_CUDA_TRY(cudaMalloc(&rlist, 4 * (size_t)(rtot > 0 ? rtot : 1)));
         ++h->launches;
@@ -442,13 +441,14 @@ static int build_pdir(gic_handle *h, Pattern &P, int paired, const std::vector<i
                                                    P.Urowptr, P.Ucol, dcnt, drcnt, doff, droff, list, rlist,
                                                    dflag);
         GIC_CUDA_TRY(cudaGetLastError());
-        if ((rc = plan_pslices(h, ng, FWD, paired, hgrp, hgl, cnt, rcnt, S)) != GIC_OK) break;
+        GIC_TRY(plan_pslices(h, ng, FWD, paired, hgrp, hgl, cnt, rcnt, S));
         ++h->launches;
         k_pcols<<<pgrid(h, (int64_t)S.nsl * 32), 256, 0, h->stream>>>(pview_of(S), gid, dcnt, drcnt, doff, droff, list,
                                                                       rlist, S.col, S.rcol);
         GIC_CUDA_TRY(cudaGetLastError());
         GIC_CUDA_TRY(cudaStreamSynchronize(h->stream));
-    } while (0);
+        return GIC_OK;
+    }();
     cudaFree(doff);
     cudaFree(droff);
     cudaFree(list);
