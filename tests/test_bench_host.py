@@ -50,3 +50,43 @@ def test_ncu_traffic_needs_matching_size_precision_and_source(tmp_path, monkeypa
     assert bench.ncu_traffic("ltsolve", 148, "f32") is None
     (src / "k.cu").write_text("changed")
     assert bench.ncu_traffic("ltsolve", 148, "f64") is None
+
+
+def test_clock_sampler_summary_from_nvidia_smi_rows():
+    """The clock record the timing rules read: median SM clock under load,
+    the maximum, and every throttle reason seen Active in any sample."""
+    class _Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    cs = bench.ClockSampler(0)
+    cs.proc = _Done()
+    na, act = "Not Active", "Active"
+    cs.rows = [["2070", "2070", "650.1", "0x0", na, na, na, na],
+               ["2055", "2070", "731.9", "0x4", na, na, na, act],
+               ["2070", "2070", "700.0", "0x0", na, na, na, na],
+               ["[N/A]", "2070", "699.0", "0x0", na, na, na, na],
+               ["short row"]]
+    rec = cs.stop()
+    assert rec["sm_mhz"] == 2070.0 and rec["sm_max_mhz"] == 2070.0
+    assert rec["reasons"] == ["sw_power_cap"]
+    assert rec["samples"] == 4 and rec["power_w_max"] == 731.9
+    cs.rows = [["1200", "2070", "400", "0x0", act, na, na, na]]
+    assert cs.stop()["reasons"] == ["hw_slowdown"]
+
+
+def test_kernel_bytes_hand_count_at_one_element():
+    """Algorithmic bytes for the 1-element system (n = 12 free dofs: the
+    clamped face removed), counted by hand from its sizes: CSR of A or L once
+    plus the vectors once."""
+    n, nnz, nnzL, _ = bench.workload_sizes(1)
+    assert (n, nnz) == (12, 144) and nnzL == (nnz + n) // 2
+    kb = bench.kernel_bytes(1, "f64")
+    assert kb["spmv"] == 12 * 144 + 4 * 13 + 16 * 12
+    assert kb["lsolve"] == 12 * 78 + 4 * 13 + 16 * 12
+    assert kb["ltsolve"] == kb["lsolve"] + 8 * 12
+    k32 = bench.kernel_bytes(1, "f32")
+    assert k32["lsolve"] == 8 * 78 + 4 * 13 + 8 * 12
