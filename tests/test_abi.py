@@ -39,3 +39,21 @@ def test_status_strings_without_gpu():
         assert lib.gic_status_string(s)
     n, nnz = gicpcg.fem_hex_sizes(40)
     assert (n, nnz) == (201720, 15548742)
+
+
+def test_binding_argument_counts_match_header():
+    """Every ctypes signature in the binding has as many arguments as the
+    header's prototype (a missing or extra argument would shift every later
+    one in the call)."""
+    from paper_2412_07127_gb300 import gicpcg
+    src = open(os.path.join(ROOT, "include", "gicpcg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    protos = re.findall(r"\b(gic_\w+)\s*\(([^;{()]*)\)\s*;", src)
+    assert len(protos) >= 15
+    bad = []
+    for name, args in protos:
+        a = args.strip()
+        count = 0 if a in ("", "void") else a.count(",") + 1
+        if name in gicpcg._SIGS and len(gicpcg._SIGS[name][1]) != count:
+            bad.append((name, count, len(gicpcg._SIGS[name][1])))
+    assert not bad, bad
