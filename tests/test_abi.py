@@ -57,3 +57,47 @@ def test_binding_argument_counts_match_header():
         if name in gicpcg._SIGS and len(gicpcg._SIGS[name][1]) != count:
             bad.append((name, count, len(gicpcg._SIGS[name][1])))
     assert not bad, bad
+
+
+def _kind_of_c(param):
+    """'p' pointer, 'f8'/'f4' floating, 'i8'/'i4' integer, from a C parameter."""
+    p = " ".join(param.replace("const", " ").split())
+    if "*" in p:
+        return "p"
+    t = p.rsplit(" ", 1)[0] if " " in p else p
+    if t == "double":
+        return "f8"
+    if t == "float":
+        return "f4"
+    if t in ("int64_t", "size_t", "uint64_t", "long long"):
+        return "i8"
+    if t in ("int", "int32_t", "unsigned", "uint32_t"):
+        return "i4"
+    return "?" + t
+
+
+def _kind_of_ctypes(t):
+    if t is ctypes.c_void_p or t is ctypes.c_char_p or hasattr(t, "_type_") and isinstance(t._type_, type):
+        return "p"
+    if t in (ctypes.c_double, ctypes.c_float):
+        return "f%d" % ctypes.sizeof(t)
+    return "i%d" % ctypes.sizeof(t)
+
+
+def test_binding_argument_kinds_match_header():
+    """Each argument's kind and width (pointer, 8- or 4-byte integer, double
+    or float) in the binding is the header's, so no value is truncated or
+    passed in the wrong register class."""
+    from paper_2412_07127_gb300 import gicpcg
+    src = open(os.path.join(ROOT, "include", "gicpcg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    bad = []
+    for name, args in re.findall(r"\b(gic_\w+)\s*\(([^;{()]*)\)\s*;", src):
+        a = args.strip()
+        if a in ("", "void") or name not in gicpcg._SIGS:
+            continue
+        want = [_kind_of_c(x) for x in a.split(",")]
+        have = [_kind_of_ctypes(t) for t in gicpcg._SIGS[name][1]]
+        if want != have:
+            bad.append((name, want, have))
+    assert not bad, bad
